@@ -290,7 +290,7 @@ int cg_grow_chains(int32_t n_chains, int32_t sites, double L, double bond, doubl
                 /* after many restarts accept the least-bad candidate, but
                  * never one closer than a hard floor (the discrete angles put
                  * a chain on a diamond lattice, so exact self-overlaps exist) */
-                double hard2 = restarts < 200 ? 0.04 : (restarts < 1000 ? 0.0225 : 0.0);
+                double hard2 = restarts < 200 ? 0.0625 : (restarts < 400 ? 0.0484 : (restarts < 1000 ? 0.04 : 0.0));
                 if (restarts >= 40 && bestd > hard2) {
                     memcpy(gr.x + 3 * a, best, sizeof best);
                     grid_add(&gr, a);

@@ -1,0 +1,186 @@
+/*
+ * md.h -- C ABI of the GB300 engine for united-atom polyethylene molecular
+ * dynamics (Xu, Ren, Ge, Yu, Yang, Li: "Molecular Dynamics Simulation of
+ * Macromolecules Using Graphics Processing Unit").
+ *
+ * What a system is (Sec. 2, Table I, Table II): molecules of one type, linear
+ * chains of `sites_per_chain` united atoms (CH3 ends = type C_33, CH2 interior
+ * = type C_32), in a periodic cube.  Energy E = E_nb + E_b + E_a + E_d
+ * (Eqs. 1, 3): truncated Lennard-Jones between all pairs except 1-2 and 1-3
+ * bonded neighbours (Eq. 2, Sec. 3.1), harmonic bonds (Eq. 4), harmonic angles
+ * in theta (Eq. 5) and cosine dihedrals (Eq. 6).  Each call below runs the
+ * per-timestep path of Secs. 3.1-3.4 entirely on one GPU: binning into cells,
+ * neighbour list every `rebin_every` steps, LJ and bonded forces, integration.
+ *
+ * Units: nm, ps, amu, kJ/mol, kelvin.  Forces kJ/mol/nm.
+ * Atom order: "original order" = replicas concatenated, chain-major inside a
+ * replica (atom = chain * sites_per_chain + MAIDX - 1, 0-based: GAIDX - 1).
+ *
+ * Ownership: every pointer argument is a HOST pointer unless stated.  Input
+ * arrays are copied during the call; output arrays are written by the call.
+ * No pointer is retained after a call returns, except `workspace` (below).
+ *
+ * Errors: every int-returning function returns MD_OK (0) or a negative
+ * MD_E* code; md_last_error() then holds a one-line message.  Device-side
+ * conditions (neighbour-list overflow, fixed-point overflow, non-finite
+ * state, displacement beyond skin/2) are raised on the GPU as flags and
+ * reported by the next synchronising call (md_step, md_sync).  The library
+ * never traps or spins on the GPU.
+ *
+ * Threads: a system must not be used from two host threads at once.
+ */
+#ifndef MD_GB300_H
+#define MD_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  MD_OK = 0,
+  MD_EINVAL = -1,      /* malformed descriptor or argument */
+  MD_ENOMEM = -2,      /* device allocation failed or workspace too small */
+  MD_ECUDA = -3,       /* a CUDA call failed */
+  MD_EOVERFLOW = -4,   /* neighbour-list capacity or fixed-point range exceeded */
+  MD_EUNSTABLE = -5,   /* non-finite state, or an atom moved more than skin/2 between rebins */
+  MD_ETIMEOUT = -6     /* a bounded device wait gave up */
+};
+
+enum { MD_PLAIN_FP32 = 0, MD_MIXED = 1 };   /* precision forms */
+enum { MD_NVE = 0, MD_VRESCALE = 1 };       /* thermostat */
+
+typedef struct md_system md_system;         /* opaque, owned by the library */
+
+/* Force-field parameters (Table I; index 0 = C_32, 1 = C_33).  Unlike pairs
+ * use geometric means of eps and sigma. */
+typedef struct {
+  double eps[2];      /* LJ well depth, kJ/mol (Eq. 2) */
+  double sigma[2];    /* LJ sigma, nm (Eq. 2) */
+  double mass[2];     /* amu */
+  double kb, b0;      /* Eq. 4: kJ/mol/nm^2, nm */
+  double ka, theta0;  /* Eq. 5: kJ/mol/rad^2, rad */
+  double kphi, phis;  /* Eq. 6: kJ/mol, rad */
+  int32_t n_mult;     /* Eq. 6 periodicity n */
+  int32_t pad;
+} md_params;
+
+typedef struct {
+  int32_t n_replicas;          /* independent systems stepped together (>= 1) */
+  int32_t sites_per_chain;     /* NAOM (Table II), 4 .. 511 */
+  const int32_t *n_chains;     /* [n_replicas] */
+  const double *box;           /* [n_replicas] cube side L, nm; L >= 3 (rc + skin) */
+  const double *pos;           /* [3 * N] x,y,z per atom, original order (any image) */
+  const double *vel;           /* [3 * N] nm/ps, original order */
+  const double *T_target;      /* [n_replicas] thermostat targets (K); may be NULL for MD_NVE */
+  md_params params;
+  double dt;                   /* time step, ps */
+  double rc;                   /* LJ cutoff, nm (pairs with r >= rc are left out, Sec. 3.2) */
+  double skin;                 /* neighbour-list skin, nm; list radius rc + skin */
+  double tau_t;                /* thermostat coupling time, ps */
+  int32_t rebin_every;         /* steps between rebin + list builds (paper: 10) */
+  int32_t precision;           /* MD_PLAIN_FP32 or MD_MIXED */
+  int32_t thermostat;          /* MD_NVE or MD_VRESCALE */
+  int32_t nbr_capacity;        /* neighbour slots per atom; 0 = chosen from density */
+  void *cuda_stream;           /* cudaStream_t to run on; NULL = a stream the library creates */
+  void *workspace;             /* optional DEVICE memory for all buffers (see md_workspace_size);
+                                  NULL = the library allocates.  Must outlive the system. */
+  size_t workspace_bytes;
+} md_desc;
+
+/* Per-replica energies of the current state (Eqs. 1-6). */
+typedef struct {
+  double lj;            /* truncated LJ, Eq. 2 */
+  double lj_shifted;    /* same with each pair shifted by -E(rc) (continuous) */
+  double bond, angle, dihedral;   /* Eqs. 4, 5, 6 */
+  double kinetic;       /* 1/2 sum m v^2 */
+  double temperature;   /* 2 KE / ((3N - 3) k_B) */
+  double total;         /* lj_shifted + bond + angle + dihedral + kinetic */
+  double virial[6];     /* sum r (x) f: xx, yy, zz, xy, xz, yz (kJ/mol) */
+  double pressure;      /* (2 KE + tr virial) / (3 V), kJ/mol/nm^3 */
+} md_energy_t;
+
+/* Bytes of device memory md_create needs for this descriptor. */
+int md_workspace_size(const md_desc *desc, size_t *bytes);
+
+/* Validate, copy the initial state to the GPU, bin, build the neighbour list,
+ * evaluate F(t0) and capture the per-cycle CUDA graph.  Sets *out. */
+int md_create(const md_desc *desc, md_system **out);
+
+/* Advance n_steps time steps (velocity Verlet; Leap-Frog positions, Sec. 3.4).
+ * The neighbour list is rebuilt at the start of every block of rebin_every
+ * steps and of every call.  Synchronises and reports device flags. */
+int md_step(md_system *sys, int64_t n_steps);
+
+/* Same, without synchronising; flags are reported by the next md_sync. */
+int md_step_async(md_system *sys, int64_t n_steps);
+
+/* Wait for queued work and report device flags (then clear them). */
+int md_sync(md_system *sys);
+
+/* Total force on every atom at the current positions, [3 * N] host doubles,
+ * original order, kJ/mol/nm. */
+int md_forces(md_system *sys, double *f_out);
+
+/* Energies of every replica at the current state, out[n_replicas]. */
+int md_energy(md_system *sys, md_energy_t *out);
+
+/* Re-bin the current positions and rebuild the neighbour list (Sec. 3.1). */
+int md_rebin(md_system *sys);
+
+/* Current state: positions wrapped into [0, L) ([3 * N]), velocities
+ * ([3 * N]) and periodic image counters ([3 * N], may be NULL); any output
+ * may be NULL.  Unwrapped position = pos + images * L. */
+int md_get_state(md_system *sys, double *pos, double *vel, int32_t *images);
+
+/* Replace positions and velocities ([3 * N] each, original order), reset the
+ * image counters, re-bin and recompute the forces. */
+int md_set_state(md_system *sys, const double *pos, const double *vel);
+
+/* Replace the force-field parameters and recompute the forces. */
+int md_set_params(md_system *sys, const md_params *params);
+
+/* Thermostat targets per replica ([n_replicas] kelvin). */
+int md_set_temperature(md_system *sys, const double *T_target);
+
+/* The cudaStream_t the system runs on (for events and ordering). */
+void *md_stream(md_system *sys);
+
+/* Sizes: n_atoms, n_cells, neighbour capacity, cells per side of replica 0. */
+int md_info(md_system *sys, int64_t *n_atoms, int64_t *n_cells, int32_t *nbr_capacity, int32_t *cells_per_side);
+
+/* Binning result of the last rebin (Sec. 3.1): cell_of[N] (original order),
+ * cell_start[n_cells + 1] and perm[N] (sorted slot -> original atom), where
+ * the cells of replica r follow those of replicas 0..r-1 and a replica's
+ * cell index is (cz * M + cy) * M + cx.  Any output may be NULL. */
+int md_get_bins(md_system *sys, int32_t *cell_of, int32_t *cell_start, int32_t *perm);
+
+/* Neighbour list of the last rebin: count[N] and entries[cap * N], both by
+ * ORIGINAL atom index; entries hold original neighbour indices (only the
+ * first count[i] of row i are meaningful).  cap = md_info's nbr_capacity. */
+int md_get_neighbors(md_system *sys, int32_t *count, int32_t *entries);
+
+/* Per-kernel GPU time recording.  When enabled, CUDA events bracket every
+ * kernel group of each step (rebin, neighbour build, integrate, LJ, bonded)
+ * and md_step / md_sync accumulate their durations.  ms_total[5] and
+ * launches[5] are in that order; md_profile_reset clears them. */
+int md_profile_enable(md_system *sys, int32_t on);
+int md_profile_read(md_system *sys, double *ms_total, int64_t *launches);
+int md_profile_reset(md_system *sys);
+
+/* Kernel launches per call of md_step(n_steps) (all library kernels). */
+int64_t md_launches_per_call(md_system *sys, int64_t n_steps);
+
+void md_destroy(md_system *sys);
+
+/* Message of the last failure on this system (or of the last failed
+ * md_create when sys is NULL).  Valid until the next call. */
+const char *md_last_error(const md_system *sys);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MD_GB300_H */

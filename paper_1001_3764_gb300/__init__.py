@@ -1,0 +1,357 @@
+"""Python binding of the GB300 united-atom polyethylene MD engine.
+
+Argument marshalling only: every step of the method runs in the CUDA library
+libmdgb300.so behind the C ABI of include/md.h (same function names).  PyTorch
+supplies device memory (the workspace) and the CUDA stream.  There is no CPU
+fallback: if the library is missing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+
+from . import build as _build
+
+LIB_PATH = _build.LIB
+
+MD_OK, MD_EINVAL, MD_ENOMEM, MD_ECUDA, MD_EOVERFLOW, MD_EUNSTABLE, MD_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
+MD_PLAIN_FP32, MD_MIXED = 0, 1
+MD_NVE, MD_VRESCALE = 0, 1
+KB = 0.0083144626  # kJ/mol/K
+
+_ERRNAMES = {MD_EINVAL: "MD_EINVAL", MD_ENOMEM: "MD_ENOMEM", MD_ECUDA: "MD_ECUDA",
+             MD_EOVERFLOW: "MD_EOVERFLOW", MD_EUNSTABLE: "MD_EUNSTABLE", MD_ETIMEOUT: "MD_ETIMEOUT"}
+
+
+class MDError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_ERRNAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class md_params(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_double * 2), ("sigma", ctypes.c_double * 2), ("mass", ctypes.c_double * 2),
+                ("kb", ctypes.c_double), ("b0", ctypes.c_double), ("ka", ctypes.c_double),
+                ("theta0", ctypes.c_double), ("kphi", ctypes.c_double), ("phis", ctypes.c_double),
+                ("n_mult", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+class md_desc(ctypes.Structure):
+    _fields_ = [("n_replicas", ctypes.c_int32), ("sites_per_chain", ctypes.c_int32),
+                ("n_chains", ctypes.c_void_p), ("box", ctypes.c_void_p), ("pos", ctypes.c_void_p),
+                ("vel", ctypes.c_void_p), ("T_target", ctypes.c_void_p), ("params", md_params),
+                ("dt", ctypes.c_double), ("rc", ctypes.c_double), ("skin", ctypes.c_double),
+                ("tau_t", ctypes.c_double), ("rebin_every", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("thermostat", ctypes.c_int32), ("nbr_capacity", ctypes.c_int32),
+                ("cuda_stream", ctypes.c_void_p), ("workspace", ctypes.c_void_p),
+                ("workspace_bytes", ctypes.c_size_t)]
+
+
+class md_energy_t(ctypes.Structure):
+    _fields_ = [("lj", ctypes.c_double), ("lj_shifted", ctypes.c_double), ("bond", ctypes.c_double),
+                ("angle", ctypes.c_double), ("dihedral", ctypes.c_double), ("kinetic", ctypes.c_double),
+                ("temperature", ctypes.c_double), ("total", ctypes.c_double),
+                ("virial", ctypes.c_double * 6), ("pressure", ctypes.c_double)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "virial"}
+        d["virial"] = list(self.virial)
+        return d
+
+
+EXPORTS = ["md_workspace_size", "md_create", "md_step", "md_step_async", "md_sync", "md_forces", "md_energy",
+           "md_rebin", "md_get_state", "md_set_state", "md_set_params", "md_set_temperature", "md_stream",
+           "md_info", "md_get_bins", "md_get_neighbors", "md_profile_enable", "md_profile_read",
+           "md_profile_reset", "md_launches_per_call", "md_destroy", "md_last_error"]
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libmdgb300.so (built by build.build()); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"CUDA library {path} is missing: run paper_1001_3764_gb300.build.build() "
+                          "(or __graft_entry__.build()) on a machine with nvcc")
+    L = ctypes.CDLL(path)
+    P, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    sig = {
+        "md_workspace_size": ([P, P], ctypes.c_int),
+        "md_create": ([P, P], ctypes.c_int),
+        "md_step": ([P, i64], ctypes.c_int),
+        "md_step_async": ([P, i64], ctypes.c_int),
+        "md_sync": ([P], ctypes.c_int),
+        "md_forces": ([P, P], ctypes.c_int),
+        "md_energy": ([P, P], ctypes.c_int),
+        "md_rebin": ([P], ctypes.c_int),
+        "md_get_state": ([P, P, P, P], ctypes.c_int),
+        "md_set_state": ([P, P, P], ctypes.c_int),
+        "md_set_params": ([P, P], ctypes.c_int),
+        "md_set_temperature": ([P, P], ctypes.c_int),
+        "md_stream": ([P], P),
+        "md_info": ([P, P, P, P, P], ctypes.c_int),
+        "md_get_bins": ([P, P, P, P], ctypes.c_int),
+        "md_get_neighbors": ([P, P, P], ctypes.c_int),
+        "md_profile_enable": ([P, i32], ctypes.c_int),
+        "md_profile_read": ([P, P, P], ctypes.c_int),
+        "md_profile_reset": ([P], ctypes.c_int),
+        "md_launches_per_call": ([P, i64], i64),
+        "md_destroy": ([P], None),
+        "md_last_error": ([P], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = L
+    return L
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _check(rc, handle=None):
+    if rc != MD_OK:
+        raise MDError(rc, load().md_last_error(handle).decode())
+
+
+def default_params() -> dict:
+    """Table I of the paper with these readings: 14.027/15.035 amu masses and
+    0.3624/0.3699 nm sigmas for C_32/C_33; epsilon (not printed) 46 K and 98 K
+    times k_B; k_b = 292880 kJ/mol/nm^2, b0 = 0.153 nm; k_a = 418.4
+    kJ/mol/rad^2, theta0 = 109.471 deg; k_phi = 4.184 kJ/mol, n = 3, phi_s = 0."""
+    return dict(eps=(46.0 * KB, 98.0 * KB), sigma=(0.3624, 0.3699), mass=(14.027, 15.035),
+                kb=292880.0, b0=0.153, ka=418.4, theta0=math.radians(109.471),
+                kphi=4.184, phis=0.0, n_mult=3)
+
+
+def make_params(p: dict) -> md_params:
+    q = md_params()
+    q.eps[:] = p["eps"]; q.sigma[:] = p["sigma"]; q.mass[:] = p["mass"]
+    q.kb, q.b0, q.ka, q.theta0 = p["kb"], p["b0"], p["ka"], p["theta0"]
+    q.kphi, q.phis, q.n_mult = p["kphi"], p["phis"], int(p["n_mult"])
+    return q
+
+
+# ---------------------------------------------------------------- thin wrappers (C ABI names)
+
+def md_workspace_size(desc: md_desc) -> int:
+    b = ctypes.c_size_t()
+    _check(load().md_workspace_size(ctypes.byref(desc), ctypes.byref(b)))
+    return b.value
+
+
+def md_create(desc: md_desc):
+    h = ctypes.c_void_p()
+    _check(load().md_create(ctypes.byref(desc), ctypes.byref(h)))
+    return h
+
+
+def md_step(h, n: int):
+    _check(load().md_step(h, n), h)
+
+
+def md_step_async(h, n: int):
+    _check(load().md_step_async(h, n), h)
+
+
+def md_sync(h):
+    _check(load().md_sync(h), h)
+
+
+def md_forces(h, n_atoms: int) -> np.ndarray:
+    f = np.empty((n_atoms, 3))
+    _check(load().md_forces(h, _p(f)), h)
+    return f
+
+
+def md_energy(h, n_replicas: int) -> list:
+    out = (md_energy_t * n_replicas)()
+    _check(load().md_energy(h, out), h)
+    return [out[r].as_dict() for r in range(n_replicas)]
+
+
+def md_rebin(h):
+    _check(load().md_rebin(h), h)
+
+
+def md_get_state(h, n_atoms: int):
+    x = np.empty((n_atoms, 3)); v = np.empty((n_atoms, 3)); img = np.empty((n_atoms, 3), np.int32)
+    _check(load().md_get_state(h, _p(x), _p(v), _p(img)), h)
+    return x, v, img
+
+
+def md_set_state(h, pos, vel):
+    pos = np.ascontiguousarray(pos, np.float64); vel = np.ascontiguousarray(vel, np.float64)
+    _check(load().md_set_state(h, _p(pos), _p(vel)), h)
+
+
+def md_set_params(h, p: dict):
+    q = make_params(p)
+    _check(load().md_set_params(h, ctypes.byref(q)), h)
+
+
+def md_set_temperature(h, T):
+    T = np.ascontiguousarray(T, np.float64)
+    _check(load().md_set_temperature(h, _p(T)), h)
+
+
+def md_stream(h) -> int:
+    return load().md_stream(h) or 0
+
+
+def md_info(h):
+    n, c = ctypes.c_int64(), ctypes.c_int64()
+    cap, M = ctypes.c_int32(), ctypes.c_int32()
+    _check(load().md_info(h, ctypes.byref(n), ctypes.byref(c), ctypes.byref(cap), ctypes.byref(M)), h)
+    return dict(n_atoms=n.value, n_cells=c.value, nbr_capacity=cap.value, cells_per_side=M.value)
+
+
+def md_get_bins(h, n_atoms: int, n_cells: int):
+    co = np.empty(n_atoms, np.int32); cs = np.empty(n_cells + 1, np.int32); pm = np.empty(n_atoms, np.int32)
+    _check(load().md_get_bins(h, _p(co), _p(cs), _p(pm)), h)
+    return co, cs, pm
+
+
+def md_get_neighbors(h, n_atoms: int, cap: int):
+    cnt = np.empty(n_atoms, np.int32); ent = np.zeros((n_atoms, cap), np.int32)
+    _check(load().md_get_neighbors(h, _p(cnt), _p(ent)), h)
+    return cnt, ent
+
+
+def md_profile_enable(h, on: bool):
+    _check(load().md_profile_enable(h, int(on)), h)
+
+
+def md_profile_read(h):
+    ms = np.zeros(5); n = np.zeros(5, np.int64)
+    _check(load().md_profile_read(h, _p(ms), _p(n)), h)
+    return ms, n
+
+
+def md_profile_reset(h):
+    _check(load().md_profile_reset(h), h)
+
+
+def md_launches_per_call(h, n: int) -> int:
+    return int(load().md_launches_per_call(h, n))
+
+
+def md_destroy(h):
+    if h:
+        load().md_destroy(h)
+
+
+def md_last_error(h=None) -> str:
+    return load().md_last_error(h).decode()
+
+
+# ---------------------------------------------------------------- convenience object
+
+PROFILE_GROUPS = ("rebin", "nbr_build", "integrate", "lj", "bonded")
+
+
+class System:
+    """One or more periodic melts (replicas) stepped together on the GPU.
+
+    `melts` is a dict or a list of dicts with keys pos (N,3), vel (N,3), L,
+    n_chains, sites (the chaingen format).  Device memory is a torch uint8
+    tensor handed to the library as its workspace; the library runs on a
+    torch stream (`self.stream`).
+    """
+
+    def __init__(self, melts, precision: int = MD_MIXED, dt: float = 0.001, rc: float = 1.0,
+                 skin: float = 0.1, rebin_every: int = 10, thermostat: int = MD_NVE, T_target=None,
+                 tau_t: float = 0.1, params: dict | None = None, nbr_capacity: int = 0, device: int = 0,
+                 use_torch_memory: bool = True):
+        import torch
+        load()
+        if isinstance(melts, dict):
+            melts = [melts]
+        self.melts = melts
+        self.n_replicas = len(melts)
+        self.sites = int(melts[0]["sites"])
+        self.params = dict(default_params() if params is None else params)
+        self._n_chains = np.array([m["n_chains"] for m in melts], np.int32)
+        self._box = np.array([m["L"] for m in melts], np.float64)
+        self._pos = np.ascontiguousarray(np.concatenate([m["pos"] for m in melts]), np.float64)
+        self._vel = np.ascontiguousarray(np.concatenate([m["vel"] for m in melts]), np.float64)
+        self.n_atoms = len(self._pos)
+        self._T = None if T_target is None else np.ascontiguousarray(np.broadcast_to(
+            np.asarray(T_target, np.float64), (self.n_replicas,)))
+        self.device = torch.device("cuda", device)
+        self.stream = torch.cuda.Stream(device=self.device)
+        d = md_desc()
+        d.n_replicas = self.n_replicas
+        d.sites_per_chain = self.sites
+        d.n_chains = _p(self._n_chains); d.box = _p(self._box)
+        d.pos = _p(self._pos); d.vel = _p(self._vel)
+        d.T_target = _p(self._T)
+        d.params = make_params(self.params)
+        d.dt, d.rc, d.skin, d.tau_t = dt, rc, skin, tau_t
+        d.rebin_every, d.precision, d.thermostat = rebin_every, precision, thermostat
+        d.nbr_capacity = nbr_capacity
+        d.cuda_stream = self.stream.cuda_stream
+        self.workspace = None
+        if use_torch_memory:
+            nbytes = md_workspace_size(d)
+            self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+            addr = self.workspace.data_ptr()
+            d.workspace = (addr + 255) // 256 * 256
+            d.workspace_bytes = nbytes
+        self.desc = d
+        torch.cuda.synchronize(self.device)
+        self.h = md_create(d)
+        self.info = md_info(self.h)
+        self.dt, self.rebin_every = dt, rebin_every
+
+    def step(self, n: int, sync: bool = True):
+        (md_step if sync else md_step_async)(self.h, n)
+
+    def sync(self):
+        md_sync(self.h)
+
+    def forces(self):
+        return md_forces(self.h, self.n_atoms)
+
+    def energy(self):
+        return md_energy(self.h, self.n_replicas)
+
+    def rebin(self):
+        md_rebin(self.h)
+
+    def state(self):
+        return md_get_state(self.h, self.n_atoms)
+
+    def set_state(self, pos, vel):
+        md_set_state(self.h, pos, vel)
+
+    def set_params(self, p: dict):
+        self.params = dict(p)
+        md_set_params(self.h, p)
+
+    def set_temperature(self, T):
+        md_set_temperature(self.h, np.broadcast_to(np.asarray(T, np.float64), (self.n_replicas,)))
+
+    def bins(self):
+        return md_get_bins(self.h, self.n_atoms, self.info["n_cells"])
+
+    def neighbors(self):
+        return md_get_neighbors(self.h, self.n_atoms, self.info["nbr_capacity"])
+
+    def close(self):
+        if getattr(self, "h", None):
+            md_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,230 @@
+// k_bin.cu -- on-GPU cell binning and neighbour-list build (Sec. 3.1).
+//
+// The paper's GBIN_NEW claims a slot per atom with atomicAdd into a
+// fixed-capacity bin (Sec. 3.1, GBIN_NEW listing).  Here the same histogram
+// feeds a counting sort: histogram -> exclusive scan -> scatter -> per-cell
+// rank by atom index.  The result is a stable order (cell, atom index) that
+// does not depend on the order in which atomics were served, and no bin has
+// a capacity limit.  Cell indices are computed in FP64 from the master
+// positions with explicitly rounded operations, so they equal the oracle's.
+//
+// Sorted positions are stored in units of the cell side relative to the
+// centre of the atom's cell (|u| <= 1/2 at the rebin), so neighbour cells are
+// offset by exact integers and an FP32 coordinate carries about 2^-25 h.
+//
+// The neighbour list (Sec. 3.1, last paragraphs) is rebuilt from the cells
+// every `rebin_every` steps with radius r_c + skin.  One thread block per
+// home cell stages each of the 27 neighbour cells in shared memory; each
+// thread scans them for its home atom.  Exclusions (1-2, 1-3 neighbours only,
+// Sec. 3.1) are applied here, so the force kernel needs no exclusion test.
+#include "md_kernels.cuh"
+
+namespace mdg {
+
+// --------------------------------------------------------------- helpers
+__device__ __forceinline__ int find_rep_by_cell(const RepDev* reps, int n_reps, int c) {
+  int lo = 0, hi = n_reps - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (reps[mid].cell_base <= c) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// cell coordinate along one axis: s = x - L floor(x/L); k = floor(s * M/L)
+__device__ __forceinline__ int cell_coord(double x, double L, double inv_h, int M) {
+  double s = __dsub_rn(x, __dmul_rn(L, floor(__ddiv_rn(x, L))));
+  int k = (int)floor(__dmul_rn(s, inv_h));
+  return k < 0 ? 0 : (k > M - 1 ? M - 1 : k);
+}
+
+// --------------------------------------------------------------- histogram
+template <typename T>
+__global__ void __launch_bounds__(256) k_bin_count(const T* __restrict__ x, int N, const Tile* __restrict__ tiles,
+                                                   const RepDev* __restrict__ reps, int* __restrict__ cell_of,
+                                                   int* __restrict__ cellc, int* __restrict__ count,
+                                                   int* __restrict__ slot) {
+  const Tile t = tiles[blockIdx.x];
+  if ((int)threadIdx.x >= t.len) return;
+  const int i = t.start + threadIdx.x;
+  const RepDev& R = reps[t.rep];
+  const double L = R.L, ih = R.inv_h;
+  const int M = R.M;
+  int cx = cell_coord((double)x[i], L, ih, M);
+  int cy = cell_coord((double)x[N + i], L, ih, M);
+  int cz = cell_coord((double)x[2 * N + i], L, ih, M);
+  int c = R.cell_base + (cz * M + cy) * M + cx;
+  cell_of[i] = c;
+  cellc[i] = cx | (cy << 10) | (cz << 20);
+  slot[i] = atomicAdd(count + c, 1);
+}
+
+void launch_bin_count(bool mixed, const void* x, int N, const Tile* tiles, int n_tiles, const RepDev* reps,
+                      int* cell_of, int* cellc, int* count, int* slot, cudaStream_t st) {
+  if (mixed)
+    k_bin_count<double><<<n_tiles, 256, 0, st>>>((const double*)x, N, tiles, reps, cell_of, cellc, count, slot);
+  else
+    k_bin_count<float><<<n_tiles, 256, 0, st>>>((const float*)x, N, tiles, reps, cell_of, cellc, count, slot);
+}
+
+// --------------------------------------------------------------- exclusive scan (one block)
+__global__ void __launch_bounds__(1024) k_scan(const int* __restrict__ count, int* __restrict__ start, int C) {
+  __shared__ int part[1024];
+  const int tid = threadIdx.x;
+  const int per = (C + 1023) / 1024;
+  const int b = tid * per, e = min(b + per, C);
+  int s = 0;
+  for (int k = b; k < e; ++k) s += count[k];
+  part[tid] = s;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {     // Hillis-Steele inclusive scan
+    int v = tid >= off ? part[tid - off] : 0;
+    __syncthreads();
+    part[tid] += v;
+    __syncthreads();
+  }
+  int run = part[tid] - s;
+  for (int k = b; k < e; ++k) { start[k] = run; run += count[k]; }
+  if (tid == 1023) start[C] = part[1023];
+}
+
+void launch_scan(const int* count, int* cell_start, int C, cudaStream_t st) {
+  k_scan<<<1, 1024, 0, st>>>(count, cell_start, C);
+}
+
+// --------------------------------------------------------------- scatter
+__global__ void __launch_bounds__(256) k_bin_scatter(const int* __restrict__ cell_of, const int* __restrict__ slot,
+                                                     const int* __restrict__ cell_start, int* __restrict__ tmp, int N) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) tmp[cell_start[cell_of[i]] + slot[i]] = i;
+}
+
+void launch_bin_scatter(const int* cell_of, const int* slot, const int* cell_start, int* tmp, int N,
+                        cudaStream_t st) {
+  if (N > 0) k_bin_scatter<<<(N + 255) / 256, 256, 0, st>>>(cell_of, slot, cell_start, tmp, N);
+}
+
+// --------------------------------------------------------------- per-cell stable order + sorted arrays
+constexpr int kSortCap = 2048;
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_cell_sort(const T* __restrict__ x, int N, const int* __restrict__ cell_start,
+                                                   const int* __restrict__ tmp, const int* __restrict__ cellc,
+                                                   const uint16_t* __restrict__ site, const RepDev* __restrict__ reps,
+                                                   int n_reps, int sites, int* __restrict__ perm,
+                                                   int* __restrict__ inv_perm, float4* __restrict__ pos,
+                                                   int* __restrict__ tag, float4* __restrict__ ref) {
+  __shared__ int ids[kSortCap];
+  const int c = blockIdx.x;
+  const int b = cell_start[c], n = cell_start[c + 1] - b;
+  if (n == 0) return;
+  const RepDev& R = reps[find_rep_by_cell(reps, n_reps, c)];
+  const bool in_smem = n <= kSortCap;
+  if (in_smem)
+    for (int k = threadIdx.x; k < n; k += blockDim.x) ids[k] = tmp[b + k];
+  __syncthreads();
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const int id = in_smem ? ids[k] : tmp[b + k];
+    int rank = 0;
+    if (in_smem) {
+      for (int q = 0; q < n; ++q) rank += ids[q] < id;
+    } else {
+      for (int q = 0; q < n; ++q) rank += tmp[b + q] < id;
+    }
+    const int s = b + rank;
+    perm[s] = id;
+    inv_perm[id] = s;
+    const int cc = cellc[id];
+    float4 p;
+    p.x = cell_unit(x[id], cc & 1023, 0, R);
+    p.y = cell_unit(x[N + id], (cc >> 10) & 1023, 0, R);
+    p.z = cell_unit(x[2 * N + id], (cc >> 20) & 1023, 0, R);
+    p.w = 0.0f;
+    pos[s] = p;
+    ref[id] = p;
+    const int st = site[id];
+    const int chain = R.chain_off + (id - R.atom_off) / sites;
+    const int type = (st == 0 || st == sites - 1) ? 1 : 0;
+    tag[s] = (chain << 9) | st | (type << kTagTypeBit);
+  }
+}
+
+void launch_cell_sort(bool mixed, const void* x, int N, const int* cell_start, const int* tmp, const int* cellc,
+                      const uint16_t* site, const RepDev* reps, int n_reps, int C, int sites, int* perm,
+                      int* inv_perm, float4* pos, int* tag, float4* ref, cudaStream_t st) {
+  if (mixed)
+    k_cell_sort<double><<<C, 128, 0, st>>>((const double*)x, N, cell_start, tmp, cellc, site, reps, n_reps, sites,
+                                           perm, inv_perm, pos, tag, ref);
+  else
+    k_cell_sort<float><<<C, 128, 0, st>>>((const float*)x, N, cell_start, tmp, cellc, site, reps, n_reps, sites,
+                                          perm, inv_perm, pos, tag, ref);
+}
+
+// --------------------------------------------------------------- neighbour list
+constexpr int kNbrBlock = 64;
+
+__global__ void __launch_bounds__(kNbrBlock) k_nbr_build(const float4* __restrict__ pos, const int* __restrict__ tag,
+                                                         const int* __restrict__ cell_start,
+                                                         const RepDev* __restrict__ reps, int n_reps,
+                                                         int* __restrict__ nbr, int* __restrict__ ncount, int cap,
+                                                         int Npad, unsigned* __restrict__ flags) {
+  __shared__ float4 sp[kNbrBlock];
+  __shared__ int st[kNbrBlock];
+  const int c = blockIdx.x;
+  const RepDev& R = reps[find_rep_by_cell(reps, n_reps, c)];
+  const int M = R.M, lc = c - R.cell_base;
+  const int cx = lc % M, cy = (lc / M) % M, cz = lc / (M * M);
+  const float rlist2 = R.rlist2u;
+  const int b = cell_start[c], n = cell_start[c + 1] - b;
+  for (int i0 = 0; i0 < n; i0 += kNbrBlock) {
+    const int i = i0 + threadIdx.x;
+    const bool active = i < n;
+    const int s = b + i;
+    float4 pi = active ? pos[s] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const int ti = active ? (tag[s] & (int)kTagMask) : 0;
+    int cnt = 0;
+    for (int k = 0; k < 27; ++k) {
+      const int ox = k % 3 - 1, oy = (k / 3) % 3 - 1, oz = k / 9 - 1;
+      const int nc = R.cell_base + (((cz + oz + M) % M) * M + ((cy + oy + M) % M)) * M + ((cx + ox + M) % M);
+      const int jb = cell_start[nc], jn = cell_start[nc + 1] - jb;
+      // in cell units the neighbour cell's centre sits at integer offset o
+      const float sx = pi.x - (float)ox, sy = pi.y - (float)oy, sz = pi.z - (float)oz;
+      for (int j0 = 0; j0 < jn; j0 += kNbrBlock) {
+        __syncthreads();
+        if (j0 + (int)threadIdx.x < jn) {
+          sp[threadIdx.x] = pos[jb + j0 + threadIdx.x];
+          st[threadIdx.x] = tag[jb + j0 + threadIdx.x];
+        }
+        __syncthreads();
+        const int m = min(kNbrBlock, jn - j0);
+        if (active) {
+          for (int q = 0; q < m; ++q) {
+            const float dx = sx - sp[q].x, dy = sy - sp[q].y, dz = sz - sp[q].z;
+            const float r2 = dx * dx + dy * dy + dz * dz;
+            const int tj = st[q];
+            const int dtag = ti - (tj & (int)kTagMask);
+            if (r2 < rlist2 && (dtag > 2 || dtag < -2)) {
+              if (cnt < cap)
+                nbr[(size_t)cnt * Npad + s] =
+                    (jb + j0 + q) | (k << kNbrIndexBits) | (int)(((unsigned)tj >> kTagTypeBit) << 31);
+              ++cnt;
+            }
+          }
+        }
+      }
+    }
+    if (active) {
+      ncount[s] = min(cnt, cap);
+      if (cnt > cap) atomicOr(flags, kFlagNbrOverflow);
+    }
+  }
+}
+
+void launch_nbr_build(const float4* pos, const int* tag, const int* cell_start, const RepDev* reps, int n_reps,
+                      int C, float rlist2, int* nbr, int* ncount, int cap, int Npad, unsigned* flags,
+                      cudaStream_t st) {
+  (void)rlist2;
+  k_nbr_build<<<C, kNbrBlock, 0, st>>>(pos, tag, cell_start, reps, n_reps, nbr, ncount, cap, Npad, flags);
+}
+
+}  // namespace mdg

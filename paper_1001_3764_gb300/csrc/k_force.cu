@@ -1,0 +1,336 @@
+// k_force.cu -- Lennard-Jones (Eq. 2) and Dreiding II bonded forces
+// (Eqs. 4-6) on sm_103a.
+//
+// LJ: one thread per home atom in cell-sorted order walks its neighbour list
+// (Sec. 3.2).  Positions are FP32 coordinates in units of the cell side,
+// relative to each atom's cell centre; a pair's separation is
+// (u_i - u_j) - o_k, where o_k is the integer neighbour-cell offset stored in
+// the list entry, so there is no minimum-image arithmetic and no
+// large-magnitude FP32 subtraction in the pair loop.  The LJ constants are
+// pre-scaled to cell units per replica and the sum is scaled back by 1/h.  Truncation follows the Sec. 3.2
+// listing: r2inv = 0 when r^2 >= r_c^2.  The per-atom sum is formed in FP32
+// in list order and stored once (FP32, or int64 fixed point 2^-32 kJ/mol/nm
+// in the mixed form).  Energy and virial are reduced with warp shuffles in FP64.
+//
+// Bonded: each thread block owns a contiguous range of atoms (whole or partial
+// chains) plus a 3-atom halo.  Bond vectors are formed once per bond (FP64
+// differences of the master positions in the mixed form, exact FP32
+// differences in the plain form), every bond/angle/dihedral term is evaluated
+// once by the thread of its first atom, and each home atom then sums the
+// contributions of the (at most 2+3+4) terms that contain it in a fixed
+// order.  This removes the paper's 2x/3x/4x redundant per-home-atom flops
+// (Sec. 3.3) without atomics.  The kernel also adds the LJ force (gathered
+// from sorted order) so the integrator reads one force per atom.
+#include <type_traits>
+
+#include "md_kernels.cuh"
+
+namespace mdg {
+
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block reduction of NV doubles into out[NV] (thread 0 holds the result).
+// Fixed shape, so the summation order is the same on every run.
+template <int NV, int NT>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double* out) {
+  __shared__ double red[NV][NT / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    double s = warp_sum(v[k]);
+    if (lane == 0) red[k][w] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double s = 0.0;
+      for (int q = 0; q < NT / 32; ++q) s += red[k][q];
+      out[k] = s;
+    }
+  }
+}
+
+__device__ __forceinline__ long long to_fix(float f, unsigned* flags) {
+  if (!(fabsf(f) < 2.0e9f)) { atomicOr(flags, kFlagFixOverflow); return 0; }
+  return __float2ll_rn(f * 4294967296.0f);
+}
+
+// ======================================================================= LJ
+constexpr int kEnergyVals = 8;   // lj, lj_shifted, vxx, vyy, vzz, vxy, vxz, vyz
+
+template <bool MIXED, bool ENERGY, int NT>
+__global__ void __launch_bounds__(NT) k_lj(const float4* __restrict__ pos, const int* __restrict__ tag,
+                                           const int* __restrict__ nbr, const int* __restrict__ ncount, int Npad,
+                                           const Tile* __restrict__ tiles, const RepDev* __restrict__ reps,
+                                           const ForceParams fp, void* __restrict__ flj, double* __restrict__ epart,
+                                           unsigned* __restrict__ flags) {
+  // neighbour-cell offsets o_k in cell units (k = (oz+1)*9 + (oy+1)*3 + ox+1)
+  __shared__ float ofx[27], ofy[27], ofz[27];
+  const Tile t = tiles[blockIdx.x];
+  if (threadIdx.x < 27) {
+    const int k = threadIdx.x;
+    ofx[k] = (float)(k % 3 - 1);
+    ofy[k] = (float)((k / 3) % 3 - 1);
+    ofz[k] = (float)(k / 9 - 1);
+  }
+  __syncthreads();
+  const RepDev& R = reps[t.rep];
+  const int s = t.start + threadIdx.x;
+  const bool active = (int)threadIdx.x < t.len;
+  float fx = 0.f, fy = 0.f, fz = 0.f;
+  float e = 0.f, es = 0.f, vxx = 0.f, vyy = 0.f, vzz = 0.f, vxy = 0.f, vxz = 0.f, vyz = 0.f;
+  if (active) {
+    const float4 pi = pos[s];
+    const int ti = (tag[s] >> kTagTypeBit) & 1;
+    // pair constants in cell units for j of type 0 and 1
+    const float a0 = 12.f * R.C12u[ti], b0 = 6.f * R.C6u[ti];
+    const float a1 = 12.f * R.C12u[ti + 1], b1 = 6.f * R.C6u[ti + 1];
+    const float rc2 = R.rc2u;
+    const int n = ncount[s];
+    const int* np = nbr + s;
+#pragma unroll 4
+    for (int q = 0; q < n; ++q) {
+      const int en = __ldg(np + (size_t)q * Npad);
+      const int j = en & (int)kNbrIndexMask;
+      const int k = (en >> kNbrIndexBits) & 31;
+      const float4 pj = __ldg(pos + j);
+      const float dx = (pi.x - pj.x) - ofx[k];
+      const float dy = (pi.y - pj.y) - ofy[k];
+      const float dz = (pi.z - pj.z) - ofz[k];
+      const float r2 = dx * dx + dy * dy + dz * dz;
+      const bool tj = en < 0;
+      const float A = tj ? a1 : a0, B = tj ? b1 : b0;
+      const float ir2 = r2 < rc2 ? rcp_approx(r2) : 0.f;
+      const float ir6 = ir2 * ir2 * ir2;
+      const float ff = ir2 * ir6 * (A * ir6 - B);
+      fx += ff * dx;
+      fy += ff * dy;
+      fz += ff * dz;
+      if (ENERGY) {
+        const float eij = ir6 * (R.C12u[ti + tj] * ir6 - R.C6u[ti + tj]);
+        if (r2 < rc2) {
+          e += eij;
+          es += eij - fp.erc[ti][tj];
+        }
+        vxx += dx * dx * ff; vyy += dy * dy * ff; vzz += dz * dz * ff;
+        vxy += dx * dy * ff; vxz += dx * dz * ff; vyz += dy * dz * ff;
+      }
+    }
+    // back from cell units: F = (sum ff_u du) / h
+    const float ih = R.ih_hi;
+    fx *= ih; fy *= ih; fz *= ih;
+    if (MIXED) {
+      F4i o;
+      o.x = to_fix(fx, flags); o.y = to_fix(fy, flags); o.z = to_fix(fz, flags); o.w = 0;
+      reinterpret_cast<F4i*>(flj)[s] = o;
+    } else {
+      reinterpret_cast<float4*>(flj)[s] = make_float4(fx, fy, fz, 0.f);
+    }
+  }
+  if (ENERGY) {
+    // full list: every pair is seen twice, hence the halves
+    double v[kEnergyVals] = {0.5 * e, 0.5 * es, 0.5 * vxx, 0.5 * vyy, 0.5 * vzz, 0.5 * vxy, 0.5 * vxz, 0.5 * vyz};
+    block_sum<kEnergyVals, NT>(v, epart + (size_t)blockIdx.x * kEnergyVals);
+  }
+}
+
+void launch_lj(bool mixed, bool energy, const float4* pos, const int* tag, const int* nbr, const int* ncount,
+               int Npad, const Tile* tiles, int n_tiles, const RepDev* reps, const ForceParams& fp, void* flj,
+               double* epart, unsigned* flags, int block, cudaStream_t st) {
+  (void)block;
+  constexpr int NT = 128;
+  if (mixed) {
+    if (energy) k_lj<true, true, NT><<<n_tiles, NT, 0, st>>>(pos, tag, nbr, ncount, Npad, tiles, reps, fp, flj, epart, flags);
+    else k_lj<true, false, NT><<<n_tiles, NT, 0, st>>>(pos, tag, nbr, ncount, Npad, tiles, reps, fp, flj, epart, flags);
+  } else {
+    if (energy) k_lj<false, true, NT><<<n_tiles, NT, 0, st>>>(pos, tag, nbr, ncount, Npad, tiles, reps, fp, flj, epart, flags);
+    else k_lj<false, false, NT><<<n_tiles, NT, 0, st>>>(pos, tag, nbr, ncount, Npad, tiles, reps, fp, flj, epart, flags);
+  }
+}
+
+// ======================================================================= bonded
+constexpr int kBondedBlock = 256;
+constexpr int kHalo = 3;
+constexpr int kBondedVals = 9;   // bond, angle, dihedral, vxx, vyy, vzz, vxy, vxz, vyz
+
+struct f3 { float x, y, z; };
+__device__ __forceinline__ f3 mk(float x, float y, float z) { return {x, y, z}; }
+__device__ __forceinline__ f3 operator+(f3 a, f3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+__device__ __forceinline__ f3 operator-(f3 a, f3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ f3 operator-(f3 a) { return {-a.x, -a.y, -a.z}; }
+__device__ __forceinline__ f3 operator*(float s, f3 a) { return {s * a.x, s * a.y, s * a.z}; }
+__device__ __forceinline__ float dot(f3 a, f3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ f3 cross(f3 a, f3 b) {
+  return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+
+// bond vector x_{m+1} - x_m under the minimum image
+__device__ __forceinline__ float bond_comp(double a, double b, double L, double hL) {
+  double d = b - a;
+  if (d > hL) d -= L; else if (d < -hL) d += L;
+  return __double2float_rn(d);
+}
+// FP32 master: the difference of two nearby floats is exact; across a face the
+// partner is first moved by L (exact when it lies near the face, L being an
+// FP32 number), so the result is again the exact difference.
+__device__ __forceinline__ float bond_comp(float a, float b, float L, float hL) {
+  float d = b - a;
+  if (d > hL) d = (b - L) - a; else if (d < -hL) d = b - (a - L);
+  return d;
+}
+
+__device__ __forceinline__ void add_vir(float (&W)[6], f3 r, f3 f) {
+  W[0] += r.x * f.x; W[1] += r.y * f.y; W[2] += r.z * f.z;
+  W[3] += r.x * f.y; W[4] += r.x * f.z; W[5] += r.y * f.z;
+}
+
+template <bool MIXED, bool ENERGY>
+__global__ void __launch_bounds__(kBondedBlock) k_bonded(const void* __restrict__ xv, const uint16_t* __restrict__ site,
+                                                         const int* __restrict__ inv_perm, const void* __restrict__ flj,
+                                                         int N, const Tile* __restrict__ tiles,
+                                                         const RepDev* __restrict__ reps, const ForceParams fp,
+                                                         void* __restrict__ Fout, double* __restrict__ epart,
+                                                         unsigned* __restrict__ flags) {
+  using T = typename std::conditional<MIXED, double, float>::type;
+  const T* x = reinterpret_cast<const T*>(xv);
+  __shared__ f3 bv[kBondedBlock + 2 * kHalo];
+  __shared__ f3 fbd[kBondedBlock], fan_a[kBondedBlock], fan_c[kBondedBlock];
+  __shared__ f3 fdi1[kBondedBlock], fdi2[kBondedBlock], fdi3[kBondedBlock];
+  const Tile t = tiles[blockIdx.x];
+  const RepDev& R = reps[t.rep];
+  const int lo = R.atom_off, hi = R.atom_off + R.n_atoms;
+  const int S = fp.sites;
+  const int base = t.start - kHalo;
+  // 1. bond vectors b_m = x_{m+1} - x_m for m in [start-3, start+len+3)
+  for (int q = threadIdx.x; q < t.len + 2 * kHalo; q += blockDim.x) {
+    const int m = base + q;
+    f3 b = mk(0.f, 0.f, 0.f);
+    if (m >= lo && m + 1 < hi && site[m] < S - 1) {
+      if (MIXED) {
+        b.x = bond_comp((double)x[m], (double)x[m + 1], R.L, R.half_L);
+        b.y = bond_comp((double)x[N + m], (double)x[N + m + 1], R.L, R.half_L);
+        b.z = bond_comp((double)x[2 * N + m], (double)x[2 * N + m + 1], R.L, R.half_L);
+      } else {
+        b.x = bond_comp((float)x[m], (float)x[m + 1], R.Lf, R.half_Lf);
+        b.y = bond_comp((float)x[N + m], (float)x[N + m + 1], R.Lf, R.half_Lf);
+        b.z = bond_comp((float)x[2 * N + m], (float)x[2 * N + m + 1], R.Lf, R.half_Lf);
+      }
+    }
+    bv[q] = b;
+  }
+  __syncthreads();
+  // 2. terms starting at atom m = base + q
+  float Eb = 0.f, Ea = 0.f, Ed = 0.f;
+  float W[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  {
+    const int q = threadIdx.x;
+    const int m = base + q;
+    f3 z = mk(0.f, 0.f, 0.f);
+    f3 fb = z, fa = z, fc = z, f1 = z, f2 = z, f3v = z;
+    if (q < t.len + kHalo && m >= lo && m < hi) {
+      const int sm = site[m];
+      const bool own = m >= t.start;   // energy/virial counted once, by the owning tile
+      if (sm <= S - 2) {               // bond (m, m+1), Eq. (4)
+        const f3 b = bv[q];
+        const float r = sqrtf(dot(b, b));
+        const float dr = r - fp.b0;
+        const float g = fp.kb * dr / r;
+        fb = g * b;                    // force on atom m
+        if (ENERGY && own) { Eb += 0.5f * fp.kb * dr * dr; add_vir(W, b, -fb); }
+      }
+      if (sm <= S - 3) {               // angle (m, m+1, m+2), vertex m+1, Eq. (5)
+        const f3 u = -bv[q], w = bv[q + 1];
+        const float lu = sqrtf(dot(u, u)), lw = sqrtf(dot(w, w));
+        const f3 cr = cross(u, w);
+        const float sn = sqrtf(dot(cr, cr)), cs = dot(u, w);
+        const float th = atan2f(sn, cs);
+        const float dth = th - fp.theta0;
+        const float inv = 1.0f / (lu * lw);
+        const float sin_t = sn * inv, cos_t = cs * inv;
+        if (sin_t > 1e-6f) {
+          const float g = fp.ka * dth / sin_t;
+          const f3 uh = (1.0f / lu) * u, wh = (1.0f / lw) * w;
+          fa = (g / lu) * (wh - cos_t * uh);
+          fc = (g / lw) * (uh - cos_t * wh);
+        }
+        if (ENERGY && own) { Ea += 0.5f * fp.ka * dth * dth; add_vir(W, u, fa); add_vir(W, w, fc); }
+      }
+      if (sm <= S - 4) {               // dihedral (m .. m+3), Eq. (6), IUPAC phi
+        const f3 b1 = bv[q], b2 = bv[q + 1], b3 = bv[q + 2];
+        const f3 mm = cross(b1, b2), nn = cross(b2, b3);
+        const float lb2 = sqrtf(dot(b2, b2)), m2 = dot(mm, mm), n2 = dot(nn, nn);
+        const float phi = atan2f(lb2 * dot(b1, nn), dot(mm, nn));
+        const float arg = (float)fp.n_mult * phi - fp.phis;
+        float sa, ca;
+        sincosf(arg, &sa, &ca);
+        if (m2 > 1e-24f && n2 > 1e-24f) {
+          const float dEdphi = -fp.kphi * (float)fp.n_mult * sa;
+          const float cam = -lb2 / m2, cdn = lb2 / n2;
+          const float cbm = lb2 / m2 + dot(b1, b2) / (lb2 * m2), cbn = dot(b2, b3) / (lb2 * n2);
+          const f3 ga = cam * mm, gd = cdn * nn, gb = cbm * mm + cbn * nn;
+          const f3 gc = -(ga + gb + gd);
+          f1 = -dEdphi * ga; f2 = -dEdphi * gb; f3v = -dEdphi * gc;
+          if (ENERGY && own) {
+            const f3 f4 = -(f1 + f2 + f3v);
+            add_vir(W, b1, f2); add_vir(W, b1 + b2, f3v); add_vir(W, b1 + b2 + b3, f4);
+          }
+        }
+        if (ENERGY && own) Ed += fp.kphi * (1.0f + ca);
+      }
+    }
+    if (q < kBondedBlock) {
+      fbd[q] = fb; fan_a[q] = fa; fan_c[q] = fc; fdi1[q] = f1; fdi2[q] = f2; fdi3[q] = f3v;
+    }
+  }
+  __syncthreads();
+  // 3. sum the contributions on each home atom in a fixed order
+  if ((int)threadIdx.x < t.len) {
+    const int q = threadIdx.x + kHalo;
+    const int i = t.start + threadIdx.x;
+    f3 F = fbd[q] - fbd[q - 1];
+    F = F + fan_a[q] - (fan_a[q - 1] + fan_c[q - 1]) + fan_c[q - 2];
+    F = F + fdi1[q] + fdi2[q - 1] + fdi3[q - 2] - (fdi1[q - 3] + fdi2[q - 3] + fdi3[q - 3]);
+    const int s = inv_perm[i];
+    if (MIXED) {
+      const F4i l = reinterpret_cast<const F4i*>(flj)[s];
+      F4i o;
+      o.x = l.x + to_fix(F.x, flags);
+      o.y = l.y + to_fix(F.y, flags);
+      o.z = l.z + to_fix(F.z, flags);
+      o.w = 0;
+      reinterpret_cast<F4i*>(Fout)[i] = o;
+    } else {
+      const float4 l = reinterpret_cast<const float4*>(flj)[s];
+      reinterpret_cast<float4*>(Fout)[i] = make_float4(l.x + F.x, l.y + F.y, l.z + F.z, 0.f);
+    }
+  }
+  if (ENERGY) {
+    double v[kBondedVals] = {Eb, Ea, Ed, W[0], W[1], W[2], W[3], W[4], W[5]};
+    block_sum<kBondedVals, kBondedBlock>(v, epart + (size_t)blockIdx.x * kBondedVals);
+  }
+}
+
+void launch_bonded(bool mixed, bool energy, const void* x, const uint16_t* site, const int* inv_perm,
+                   const void* flj, int N, const Tile* tiles, int n_tiles, const RepDev* reps,
+                   const ForceParams& fp, void* F, double* epart, unsigned* flags, cudaStream_t st) {
+  if (mixed) {
+    if (energy) k_bonded<true, true><<<n_tiles, kBondedBlock, 0, st>>>(x, site, inv_perm, flj, N, tiles, reps, fp, F, epart, flags);
+    else k_bonded<true, false><<<n_tiles, kBondedBlock, 0, st>>>(x, site, inv_perm, flj, N, tiles, reps, fp, F, epart, flags);
+  } else {
+    if (energy) k_bonded<false, true><<<n_tiles, kBondedBlock, 0, st>>>(x, site, inv_perm, flj, N, tiles, reps, fp, F, epart, flags);
+    else k_bonded<false, false><<<n_tiles, kBondedBlock, 0, st>>>(x, site, inv_perm, flj, N, tiles, reps, fp, F, epart, flags);
+  }
+}
+
+}  // namespace mdg

@@ -1,0 +1,218 @@
+// k_integrate.cu -- velocity-Verlet update (Sec. 3.4), kinetic energy and
+// weak-coupling thermostat, energy reductions.
+//
+// Velocity Verlet gives the positions of the paper's Leap-Frog scheme.  A
+// step is split as: [complete the previous step's second half-kick, kinetic
+// energy, thermostat scale] + [first half-kick, drift] in one kernel (mode
+// KKD); a call's first step skips the completion (KD) and its last step is
+// closed by a kick-only pass (K), so the state at every API boundary is
+// (x(t), v(t), F(t)).
+//
+// The paper's Nose-Hoover coupling needs the whole-system kinetic energy,
+// which it sums through a per-atom array and a tree reduction (Sec. 3.4).
+// Here each block writes one FP64 partial; the last block to finish (ticket
+// counter, no waiting) sums the partials of each replica in tile order, so
+// the sum has a fixed order, and computes that replica's rescaling factor.
+// The factor computed at step k is applied at step k+1 (one-step lag).
+//
+// The drift also refreshes the FP32 cell-unit positions in sorted order for
+// the force kernels, wraps positions into [0, L) with image counters, and
+// flags atoms that moved more than skin/2 since the last rebin.
+#include <type_traits>
+
+#include "md_kernels.cuh"
+
+namespace mdg {
+
+__device__ __forceinline__ double warp_sum_i(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+constexpr int kIntBlock = 256;
+
+template <bool MIXED, int MODE, bool KE, bool THERMO>
+__global__ void __launch_bounds__(kIntBlock) k_integrate(void* __restrict__ xv, void* __restrict__ vv,
+                                                         int* __restrict__ img, const void* __restrict__ Fv,
+                                                         const uint16_t* __restrict__ site,
+                                                         const int* __restrict__ cellc,
+                                                         const int* __restrict__ inv_perm,
+                                                         const float4* __restrict__ ref, float4* __restrict__ pos,
+                                                         int N, const Tile* __restrict__ tiles,
+                                                         const RepDev* __restrict__ reps, int n_reps,
+                                                         const ForceParams fp, double* __restrict__ kepart,
+                                                         unsigned* __restrict__ done, double* __restrict__ ke_out,
+                                                         double* __restrict__ lam, double tau,
+                                                         unsigned* __restrict__ flags) {
+  using T = typename std::conditional<MIXED, double, float>::type;
+  T* x = reinterpret_cast<T*>(xv);
+  T* v = reinterpret_cast<T*>(vv);
+  const Tile t = tiles[blockIdx.x];
+  const RepDev& R = reps[t.rep];
+  const int i = t.start + threadIdx.x;
+  double ke = 0.0;
+  if ((int)threadIdx.x < t.len) {
+    const int sm = site[i];
+    const int type = (sm == 0 || sm == fp.sites - 1) ? 1 : 0;
+    const T hdt_m = (T)(0.5 * fp.dt * fp.inv_mass[type]);
+    T F[3] = {(T)0, (T)0, (T)0};
+    if (MODE == kKineticOnly) {
+    } else if (MIXED) {
+      const F4i f = reinterpret_cast<const F4i*>(Fv)[i];
+      F[0] = (T)((double)f.x * kFixInv); F[1] = (T)((double)f.y * kFixInv); F[2] = (T)((double)f.z * kFixInv);
+    } else {
+      const float4 f = reinterpret_cast<const float4*>(Fv)[i];
+      F[0] = f.x; F[1] = f.y; F[2] = f.z;
+    }
+    T vi[3] = {v[i], v[N + i], v[2 * N + i]};
+    if (MODE == kKickKickDrift || MODE == kKickOnly) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) vi[a] += hdt_m * F[a];   // v(t): close the previous step
+    }
+    if (KE) {
+      const double m = fp.mass[type];
+      ke = 0.5 * m * ((double)vi[0] * vi[0] + (double)vi[1] * vi[1] + (double)vi[2] * vi[2]);
+    }
+    if (MODE == kKickOnly) {
+      v[i] = vi[0]; v[N + i] = vi[1]; v[2 * N + i] = vi[2];
+    } else if (MODE == kKickDrift || MODE == kKickKickDrift) {
+      if (THERMO) {
+        const T l = (T)lam[t.rep];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) vi[a] *= l;
+      }
+      const T dt = (T)fp.dt;
+      const T L = (T)R.L;
+      const int cc = cellc[i];
+      const float4 r0 = ref[i];
+      const float r0a[3] = {r0.x, r0.y, r0.z};
+      const float halfM = 0.5f * R.Mf;
+      float loc[3], d2 = 0.f;
+      bool bad = false;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        vi[a] += hdt_m * F[a];
+        T xa = x[a * N + i] + dt * vi[a];
+        if (xa >= L) { xa -= L; img[a * N + i] += 1; }
+        else if (xa < (T)0) { xa += L; img[a * N + i] -= 1; if (xa >= L) xa = (T)0; }
+        x[a * N + i] = xa;
+        v[a * N + i] = vi[a];
+        // cell units in the frame of the rebin cell; an atom that crossed a
+        // face since the rebin is moved back by one box (M cell units)
+        const int c = (cc >> (10 * a)) & 1023;
+        float ua = cell_unit(xa, c, 0, R);
+        const float du = ua - r0a[a];
+        if (du > halfM || du < -halfM) ua = cell_unit(xa, c, du > halfM ? -1 : 1, R);
+        loc[a] = ua;
+        const float d = ua - r0a[a];
+        d2 += d * d;
+        bad |= !isfinite(xa) || !isfinite(vi[a]);
+      }
+      if (d2 > R.hs2u) atomicOr(flags, kFlagDisplacement);
+      if (bad) atomicOr(flags, kFlagNaN);
+      pos[inv_perm[i]] = make_float4(loc[0], loc[1], loc[2], 0.f);
+    }
+  }
+  if (KE) {
+    __shared__ double red[kIntBlock / 32];
+    __shared__ bool last;
+    double s = warp_sum_i(ke);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double b = 0.0;
+      for (int q = 0; q < kIntBlock / 32; ++q) b += red[q];
+      kepart[blockIdx.x] = b;
+      __threadfence();
+      last = atomicAdd(done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last) {
+      __threadfence();
+      for (int r = threadIdx.x; r < n_reps; r += blockDim.x) {
+        const RepDev& Q = reps[r];
+        double sum = 0.0;
+        for (int q = 0; q < Q.n_tiles; ++q) sum += __ldcg(kepart + Q.tile_off + q);
+        ke_out[r] = sum;
+        if (THERMO) {
+          const double T_inst = 2.0 * sum / (Q.dof * 0.0083144626);
+          lam[r] = sqrt(1.0 + fp.dt / tau * (Q.T0 / T_inst - 1.0));
+        }
+      }
+      if (threadIdx.x == 0) *done = 0u;
+    }
+  }
+}
+
+template <bool MIXED>
+static void launch_int_t(IntegMode mode, bool ke, bool th, void* x, void* v, int* img, const void* F,
+                         const uint16_t* site, const int* cellc, const int* inv_perm, const float4* ref, float4* pos,
+                         int N, const Tile* tiles, int n_tiles, const RepDev* reps, int n_reps,
+                         const ForceParams& fp, double* kepart, unsigned* done, double* ke_out, double* lam,
+                         double tau, unsigned* flags, cudaStream_t st) {
+#define MDG_INT(MODE, KE, TH)                                                                                   \
+  k_integrate<MIXED, MODE, KE, TH><<<n_tiles, kIntBlock, 0, st>>>(x, v, img, F, site, cellc, inv_perm, ref,     \
+                                                                  pos, N, tiles, reps, n_reps, fp, kepart, done, \
+                                                                  ke_out, lam, tau, flags)
+  // With the thermostat on, every step that starts (KD, KKD) takes the
+  // temperature of the unscaled v(t_k), scales v(t_k) by the factor of the
+  // previous step and leaves the factor of step k for the next one.  The
+  // closing kick (K) only completes v; the next call's KD picks up from there.
+  if (mode == kKickDrift) {
+    if (th) MDG_INT(kKickDrift, true, true); else MDG_INT(kKickDrift, false, false);
+  } else if (mode == kKickKickDrift) {
+    if (th) MDG_INT(kKickKickDrift, true, true);
+    else if (ke) MDG_INT(kKickKickDrift, true, false);
+    else MDG_INT(kKickKickDrift, false, false);
+  } else if (mode == kKickOnly) {
+    if (ke) MDG_INT(kKickOnly, true, false);
+    else MDG_INT(kKickOnly, false, false);
+  } else {
+    MDG_INT(kKineticOnly, true, false);
+  }
+#undef MDG_INT
+}
+
+void launch_integrate(bool mixed, IntegMode mode, bool ke, bool thermostat, void* x, void* v, int* img,
+                      const void* F, const uint16_t* site, const int* cellc, const int* inv_perm, const float4* ref,
+                      float4* pos, int N, const Tile* tiles, int n_tiles, const RepDev* reps, int n_reps,
+                      const ForceParams& fp, double* kepart, unsigned* done, double* ke_out, double* lam,
+                      double tau, unsigned* flags, cudaStream_t st) {
+  if (mixed)
+    launch_int_t<true>(mode, ke, thermostat, x, v, img, F, site, cellc, inv_perm, ref, pos, N, tiles, n_tiles, reps,
+                       n_reps, fp, kepart, done, ke_out, lam, tau, flags, st);
+  else
+    launch_int_t<false>(mode, ke, thermostat, x, v, img, F, site, cellc, inv_perm, ref, pos, N, tiles, n_tiles, reps,
+                        n_reps, fp, kepart, done, ke_out, lam, tau, flags, st);
+}
+
+// ---------------------------------------------------------------- energy reduction
+// out[r*16 + k]: k = 0 lj, 1 lj_shifted, 2 bond, 3 angle, 4 dihedral, 5..10 virial
+__global__ void k_energy_reduce(const double* __restrict__ lj_part, const double* __restrict__ b_part,
+                                const Tile* __restrict__ lj_tiles, int n_lj_tiles,
+                                const Tile* __restrict__ b_tiles, int n_b_tiles, int n_reps, double* __restrict__ out) {
+  for (int r = threadIdx.x; r < n_reps; r += blockDim.x) {
+    double acc[11] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int q = 0; q < n_lj_tiles; ++q) {
+      if (lj_tiles[q].rep != r) continue;
+      const double* p = lj_part + (size_t)q * 8;
+      acc[0] += p[0]; acc[1] += p[1];
+      for (int k = 0; k < 6; ++k) acc[5 + k] += p[2 + k];
+    }
+    for (int q = 0; q < n_b_tiles; ++q) {
+      if (b_tiles[q].rep != r) continue;
+      const double* p = b_part + (size_t)q * 9;
+      acc[2] += p[0]; acc[3] += p[1]; acc[4] += p[2];
+      for (int k = 0; k < 6; ++k) acc[5 + k] += p[3 + k];
+    }
+    for (int k = 0; k < 11; ++k) out[r * 16 + k] = acc[k];
+  }
+}
+
+void launch_energy_reduce(const double* lj_part, const double* b_part, const Tile* lj_tiles, int n_lj_tiles,
+                          const Tile* b_tiles, int n_b_tiles, int n_reps, double* out, cudaStream_t st) {
+  k_energy_reduce<<<1, 256, 0, st>>>(lj_part, b_part, lj_tiles, n_lj_tiles, b_tiles, n_b_tiles, n_reps, out);
+}
+
+}  // namespace mdg

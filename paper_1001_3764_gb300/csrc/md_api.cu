@@ -1,0 +1,683 @@
+// md_api.cu -- host runtime and C ABI of the GB300 MD engine (include/md.h).
+//
+// One md_system owns: a replica table, tile tables, every device buffer (one
+// allocation, or a caller workspace), a stream, and a CUDA graph holding one
+// rebin cycle (rebin + neighbour list + rebin_every steps).  Kernels are in
+// k_bin.cu, k_force.cu and k_integrate.cu.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/md.h"
+#include "md_kernels.cuh"
+
+using namespace mdg;
+
+namespace {
+
+constexpr int kLjTile = 128;     // atoms per LJ block (sorted order)
+constexpr int kIntTile = 224;    // atoms per integrator / bonded block (original order)
+constexpr int kNumProf = 5;      // rebin, neighbour build, integrate, lj, bonded
+constexpr double kKB = 0.0083144626;
+
+thread_local std::string g_create_error;
+
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+}  // namespace
+
+struct md_system {
+  // configuration
+  int n_reps = 0, S = 0, R = 10;
+  int64_t N = 0;
+  int C = 0, Npad = 0, cap = 0;
+  bool mixed = false, thermo = false;
+  double dt = 0, rc = 0, skin = 0, tau = 0.1;
+  md_params params{};
+  ForceParams fp{};
+  std::vector<RepDev> reps_h;
+  std::vector<Tile> t_lj, t_int;
+  std::vector<double> T0;
+  // memory
+  char* base = nullptr;
+  size_t bytes = 0;
+  bool own_mem = false;
+  RepDev* reps = nullptr;
+  Tile *tiles_lj = nullptr, *tiles_int = nullptr;
+  void *x = nullptr, *v = nullptr, *F = nullptr, *flj = nullptr;
+  int* img = nullptr;
+  uint16_t* site = nullptr;
+  int *cellc = nullptr, *inv_perm = nullptr, *tag = nullptr, *perm = nullptr;
+  float4 *ref = nullptr, *pos = nullptr;
+  int *nbr = nullptr, *ncount = nullptr, *count = nullptr, *cell_start = nullptr, *cell_of = nullptr;
+  int *slot = nullptr, *tmp = nullptr;
+  double *lj_part = nullptr, *b_part = nullptr, *kepart = nullptr, *ke_out = nullptr, *lam = nullptr;
+  double* e_out = nullptr;
+  unsigned *done = nullptr, *flags = nullptr;
+  // execution
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  cudaGraphExec_t cycle = nullptr;
+  bool profile = false;
+  std::vector<cudaEvent_t> ev;
+  int ev_used = 0;
+  double prof_ms[kNumProf] = {0, 0, 0, 0, 0};
+  int64_t prof_n[kNumProf] = {0, 0, 0, 0, 0};
+  std::string err;
+};
+
+// ------------------------------------------------------------------ helpers
+static int fail(md_system* s, int code, const std::string& msg) {
+  if (s) s->err = msg; else g_create_error = msg;
+  return code;
+}
+#define CU(call)                                                                                      \
+  do {                                                                                                \
+    cudaError_t e_ = (call);                                                                          \
+    if (e_ != cudaSuccess) return fail(s, MD_ECUDA, std::string(#call ": ") + cudaGetErrorString(e_)); \
+  } while (0)
+
+static void fill_force_params(md_system* s) {
+  const md_params& p = s->params;
+  ForceParams& f = s->fp;
+  for (RepDev& q : s->reps_h)
+    for (int t = 0; t < 3; ++t) {
+      const int a = t >= 1 ? 1 : 0, b = t >= 2 ? 1 : 0;
+      const int ta = (t == 1) ? 0 : a;   // pair (0,1) for t = 1
+      const int tb = (t == 1) ? 1 : b;
+      double eps = std::sqrt(p.eps[ta] * p.eps[tb]);
+      double sig = std::sqrt(p.sigma[ta] * p.sigma[tb]) * q.inv_h;   // sigma in cell units
+      double s6 = sig * sig * sig * sig * sig * sig;
+      q.C6u[t] = (float)(4.0 * eps * s6);
+      q.C12u[t] = (float)(4.0 * eps * s6 * s6);
+    }
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b) {
+      double eps = std::sqrt(p.eps[a] * p.eps[b]);
+      double sig = std::sqrt(p.sigma[a] * p.sigma[b]);
+      double s6 = sig * sig * sig * sig * sig * sig;
+      double c6 = 4.0 * eps * s6, c12 = 4.0 * eps * s6 * s6;
+      double ir6 = 1.0 / (s->rc * s->rc * s->rc * s->rc * s->rc * s->rc);
+      f.c6[a][b] = (float)c6;
+      f.c12[a][b] = (float)c12;
+      f.erc[a][b] = (float)(c12 * ir6 * ir6 - c6 * ir6);
+    }
+  f.rc2 = (float)(s->rc * s->rc);
+  f.rlist2 = (float)((s->rc + s->skin) * (s->rc + s->skin));
+  f.kb = (float)p.kb; f.b0 = (float)p.b0; f.ka = (float)p.ka; f.theta0 = (float)p.theta0;
+  f.kphi = (float)p.kphi; f.phis = (float)p.phis; f.n_mult = p.n_mult;
+  f.sites = s->S;
+  f.half_skin2 = (float)(0.25 * s->skin * s->skin);
+  for (int a = 0; a < 2; ++a) { f.mass[a] = p.mass[a]; f.inv_mass[a] = 1.0 / p.mass[a]; }
+  f.dt = s->dt;
+}
+
+// Validate the descriptor and fill geometry, tiles and sizes (no device work).
+static int configure(md_system* s, const md_desc* d) {
+  if (!d) return fail(s, MD_EINVAL, "null descriptor");
+  if (d->n_replicas < 1 || d->n_replicas > kMaxReplicas) return fail(s, MD_EINVAL, "n_replicas out of range");
+  if (d->sites_per_chain < 4 || d->sites_per_chain > 511) return fail(s, MD_EINVAL, "sites_per_chain must be 4..511");
+  if (!d->n_chains || !d->box) return fail(s, MD_EINVAL, "n_chains and box are required");
+  if (!(d->dt > 0) || !(d->rc > 0) || !(d->skin >= 0) || d->rebin_every < 1)
+    return fail(s, MD_EINVAL, "dt, rc must be > 0, skin >= 0, rebin_every >= 1");
+  if (d->precision != MD_PLAIN_FP32 && d->precision != MD_MIXED) return fail(s, MD_EINVAL, "unknown precision");
+  if (d->thermostat != MD_NVE && d->thermostat != MD_VRESCALE) return fail(s, MD_EINVAL, "unknown thermostat");
+  if (d->thermostat == MD_VRESCALE && (!d->T_target || !(d->tau_t > 0)))
+    return fail(s, MD_EINVAL, "thermostat needs T_target and tau_t > 0");
+  for (int a = 0; a < 2; ++a)
+    if (!(d->params.mass[a] > 0) || !(d->params.sigma[a] > 0) || !(d->params.eps[a] >= 0))
+      return fail(s, MD_EINVAL, "masses and sigmas must be > 0, eps >= 0");
+  if (d->params.n_mult < 0 || d->params.n_mult > 12) return fail(s, MD_EINVAL, "n_mult out of range");
+  s->n_reps = d->n_replicas;
+  s->S = d->sites_per_chain;
+  s->R = d->rebin_every;
+  s->mixed = d->precision == MD_MIXED;
+  s->thermo = d->thermostat == MD_VRESCALE;
+  s->dt = d->dt; s->rc = d->rc; s->skin = d->skin; s->tau = d->thermostat ? d->tau_t : 0.1;
+  s->params = d->params;
+  const double rl = d->rc + d->skin;
+  s->reps_h.assign(s->n_reps, RepDev{});
+  s->T0.assign(s->n_reps, 0.0);
+  int64_t atoms = 0, cells = 0, chains = 0;
+  double max_expected = 0.0;
+  s->t_lj.clear(); s->t_int.clear();
+  for (int r = 0; r < s->n_reps; ++r) {
+    const int nc = d->n_chains[r];
+    const double L = d->box[r];
+    if (nc < 1) return fail(s, MD_EINVAL, "every replica needs at least one chain");
+    if (!(L > 0) || !std::isfinite(L)) return fail(s, MD_EINVAL, "box sides must be positive");
+    const int M = (int)std::floor(L / rl);
+    if (M < 3) return fail(s, MD_EINVAL, "box side must be at least 3 (rc + skin)");
+    if (M > 1023) return fail(s, MD_EINVAL, "more than 1023 cells per side");
+    RepDev& q = s->reps_h[r];
+    q.L = L; q.M = M; q.h = L / M; q.inv_h = (double)M / L; q.half_L = 0.5 * L;
+    q.Lf = (float)L; q.hf = (float)q.h; q.half_Lf = (float)(0.5 * L); q.Mf = (float)M;
+    q.ih_hi = (float)q.inv_h; q.ih_lo = (float)(q.inv_h - (double)q.ih_hi);
+    q.rc2u = (float)(d->rc * d->rc * q.inv_h * q.inv_h);
+    q.rlist2u = (float)(rl * rl * q.inv_h * q.inv_h);
+    q.hs2u = (float)(0.25 * d->skin * d->skin * q.inv_h * q.inv_h);
+    q.cell_base = (int)cells; q.atom_off = (int)atoms;
+    q.n_atoms = nc * s->S; q.n_chains = nc; q.chain_off = (int)chains;
+    q.T0 = d->T_target ? d->T_target[r] : 0.0;
+    q.dof = 3.0 * q.n_atoms - 3.0;
+    s->T0[r] = q.T0;
+    q.tile_off = (int)s->t_int.size();
+    for (int o = 0; o < q.n_atoms; o += kIntTile) s->t_int.push_back(Tile{q.atom_off + o, std::min(kIntTile, q.n_atoms - o), r, 0});
+    q.n_tiles = (int)s->t_int.size() - q.tile_off;
+    for (int o = 0; o < q.n_atoms; o += kLjTile) s->t_lj.push_back(Tile{q.atom_off + o, std::min(kLjTile, q.n_atoms - o), r, 0});
+    // chains are locally as dense as a melt even in a sparse box, so the
+    // density used for the capacity is at least that of a dense melt
+    const double rho = std::max(q.n_atoms / (L * L * L), 40.0);
+    max_expected = std::max(max_expected, 4.0 / 3.0 * M_PI * rl * rl * rl * rho);
+    atoms += q.n_atoms; cells += (int64_t)M * M * M; chains += nc;
+    if (atoms >= (int64_t)kNbrIndexMask) return fail(s, MD_EINVAL, "too many atoms (limit 2^26)");
+    if (chains >= (1 << 21)) return fail(s, MD_EINVAL, "too many chains (limit 2^21)");
+    if (cells >= (1 << 26)) return fail(s, MD_EINVAL, "too many cells");
+  }
+  s->N = atoms; s->C = (int)cells;
+  s->Npad = (int)((atoms + 31) / 32 * 32);
+  s->cap = d->nbr_capacity > 0 ? d->nbr_capacity : ((int)std::ceil(1.5 * max_expected + 24.0) + 3) / 4 * 4;
+  if (s->cap > 4096) return fail(s, MD_EINVAL, "neighbour capacity above 4096");
+  fill_force_params(s);
+  return MD_OK;
+}
+
+// Lay out every buffer; with base == nullptr only the size is computed.
+static size_t plan(md_system* s, char* base) {
+  size_t off = 0;
+  auto take = [&](size_t b) -> char* { char* p = base ? base + off : nullptr; off += align256(b); return p; };
+  const size_t N = (size_t)s->N, C = (size_t)s->C;
+  const size_t fsz = s->mixed ? sizeof(double) : sizeof(float);
+  s->reps = (RepDev*)take(sizeof(RepDev) * s->n_reps);
+  s->tiles_lj = (Tile*)take(sizeof(Tile) * s->t_lj.size());
+  s->tiles_int = (Tile*)take(sizeof(Tile) * s->t_int.size());
+  s->x = take(3 * N * fsz);
+  s->v = take(3 * N * fsz);
+  s->img = (int*)take(3 * N * sizeof(int));
+  s->F = take(N * (s->mixed ? sizeof(F4i) : sizeof(float4)));
+  s->flj = take(N * (s->mixed ? sizeof(F4i) : sizeof(float4)));
+  s->site = (uint16_t*)take(N * sizeof(uint16_t));
+  s->cellc = (int*)take(N * sizeof(int));
+  s->ref = (float4*)take(N * sizeof(float4));
+  s->inv_perm = (int*)take(N * sizeof(int));
+  s->pos = (float4*)take(N * sizeof(float4));
+  s->tag = (int*)take(N * sizeof(int));
+  s->perm = (int*)take(N * sizeof(int));
+  s->nbr = (int*)take((size_t)s->cap * s->Npad * sizeof(int));
+  s->ncount = (int*)take(N * sizeof(int));
+  s->count = (int*)take(C * sizeof(int));
+  s->cell_start = (int*)take((C + 1) * sizeof(int));
+  s->cell_of = (int*)take(N * sizeof(int));
+  s->slot = (int*)take(N * sizeof(int));
+  s->tmp = (int*)take(N * sizeof(int));
+  s->lj_part = (double*)take(s->t_lj.size() * 8 * sizeof(double));
+  s->b_part = (double*)take(s->t_int.size() * 9 * sizeof(double));
+  s->kepart = (double*)take(s->t_int.size() * sizeof(double));
+  s->ke_out = (double*)take(s->n_reps * sizeof(double));
+  s->lam = (double*)take(s->n_reps * sizeof(double));
+  s->e_out = (double*)take((size_t)s->n_reps * 16 * sizeof(double));
+  s->done = (unsigned*)take(sizeof(unsigned));
+  s->flags = (unsigned*)take(sizeof(unsigned));
+  return off;
+}
+
+// ------------------------------------------------------------------ enqueue helpers
+static void prof_mark(md_system* s) {
+  // external records: inside a stream capture they become event-record nodes
+  if (s->profile && s->ev_used < (int)s->ev.size())
+    cudaEventRecordWithFlags(s->ev[s->ev_used++], s->st, cudaEventRecordExternal);
+}
+
+static void enqueue_rebin(md_system* s) {
+  cudaMemsetAsync(s->count, 0, sizeof(int) * s->C, s->st);
+  launch_bin_count(s->mixed, s->x, (int)s->N, s->tiles_int, (int)s->t_int.size(), s->reps, s->cell_of, s->cellc,
+                   s->count, s->slot, s->st);
+  launch_scan(s->count, s->cell_start, s->C, s->st);
+  launch_bin_scatter(s->cell_of, s->slot, s->cell_start, s->tmp, (int)s->N, s->st);
+  launch_cell_sort(s->mixed, s->x, (int)s->N, s->cell_start, s->tmp, s->cellc, s->site, s->reps, s->n_reps, s->C,
+                   s->S, s->perm, s->inv_perm, s->pos, s->tag, s->ref, s->st);
+  prof_mark(s);
+  launch_nbr_build(s->pos, s->tag, s->cell_start, s->reps, s->n_reps, s->C, s->fp.rlist2, s->nbr, s->ncount, s->cap,
+                   s->Npad, s->flags, s->st);
+  prof_mark(s);
+}
+static const int kRebinLaunches = 6;   // memset counted as a launch
+
+static void enqueue_forces(md_system* s, bool energy) {
+  launch_lj(s->mixed, energy, s->pos, s->tag, s->nbr, s->ncount, s->Npad, s->tiles_lj, (int)s->t_lj.size(), s->reps,
+            s->fp, s->flj, s->lj_part, s->flags, kLjTile, s->st);
+  prof_mark(s);
+  launch_bonded(s->mixed, energy, s->x, s->site, s->inv_perm, s->flj, (int)s->N, s->tiles_int, (int)s->t_int.size(),
+                s->reps, s->fp, s->F, s->b_part, s->flags, s->st);
+  prof_mark(s);
+}
+
+static void enqueue_integrate(md_system* s, IntegMode mode, bool ke) {
+  launch_integrate(s->mixed, mode, ke, s->thermo, s->x, s->v, s->img, s->F, s->site, s->cellc,
+                   s->inv_perm, s->ref, s->pos, (int)s->N, s->tiles_int, (int)s->t_int.size(), s->reps, s->n_reps,
+                   s->fp, s->kepart, s->done, s->ke_out, s->lam, s->tau, s->flags, s->st);
+  prof_mark(s);
+}
+
+// one block of k steps: rebin + list, k velocity-Verlet steps
+static void enqueue_block(md_system* s, int k) {
+  s->ev_used = 0;
+  prof_mark(s);
+  enqueue_rebin(s);
+  enqueue_integrate(s, kKickDrift, false);
+  enqueue_forces(s, false);
+  for (int j = 1; j < k; ++j) {
+    enqueue_integrate(s, kKickKickDrift, false);
+    enqueue_forces(s, false);
+  }
+  enqueue_integrate(s, kKickOnly, false);
+}
+static int64_t block_launches(int k) { return kRebinLaunches + 3LL * k + 1; }
+
+// accumulate the event timings of the last block (requires a finished stream)
+static void prof_collect(md_system* s, int k) {
+  if (!s->profile || s->ev_used < 3 + 3 * k + 1) return;
+  float ms;
+  cudaEventElapsedTime(&ms, s->ev[0], s->ev[1]); s->prof_ms[0] += ms; s->prof_n[0] += 5;
+  cudaEventElapsedTime(&ms, s->ev[1], s->ev[2]); s->prof_ms[1] += ms; s->prof_n[1] += 1;
+  int e = 2;
+  for (int j = 0; j < k; ++j) {
+    cudaEventElapsedTime(&ms, s->ev[e], s->ev[e + 1]); s->prof_ms[2] += ms; s->prof_n[2] += 1;
+    cudaEventElapsedTime(&ms, s->ev[e + 1], s->ev[e + 2]); s->prof_ms[3] += ms; s->prof_n[3] += 1;
+    cudaEventElapsedTime(&ms, s->ev[e + 2], s->ev[e + 3]); s->prof_ms[4] += ms; s->prof_n[4] += 1;
+    e += 3;
+  }
+  cudaEventElapsedTime(&ms, s->ev[e], s->ev[e + 1]); s->prof_ms[2] += ms; s->prof_n[2] += 1;
+}
+
+static int capture_cycle(md_system* s) {
+  if (s->cycle) { cudaGraphExecDestroy(s->cycle); s->cycle = nullptr; }
+  cudaGraph_t g;
+  CU(cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal));
+  enqueue_block(s, s->R);
+  cudaError_t e = cudaStreamEndCapture(s->st, &g);
+  if (e != cudaSuccess) return fail(s, MD_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&s->cycle, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(s, MD_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  return MD_OK;
+}
+
+static int check_flags(md_system* s) {
+  unsigned f = 0;
+  CU(cudaStreamSynchronize(s->st));
+  CU(cudaMemcpy(&f, s->flags, sizeof f, cudaMemcpyDeviceToHost));
+  if (!f) return MD_OK;
+  CU(cudaMemset(s->flags, 0, sizeof(unsigned)));
+  if (f & kFlagNbrOverflow) return fail(s, MD_EOVERFLOW, "neighbour list capacity exceeded (raise nbr_capacity)");
+  if (f & kFlagFixOverflow) return fail(s, MD_EOVERFLOW, "force beyond the fixed-point range (|F| >= 2^31 kJ/mol/nm)");
+  if (f & kFlagNaN) return fail(s, MD_EUNSTABLE, "non-finite position or velocity");
+  if (f & kFlagDisplacement) return fail(s, MD_EUNSTABLE, "an atom moved more than skin/2 between rebins (raise skin or lower rebin_every)");
+  if (f & kFlagTimeout) return fail(s, MD_ETIMEOUT, "a bounded device wait gave up");
+  return fail(s, MD_ECUDA, "unknown device flag");
+}
+
+// upload positions (wrapped) and velocities, reset images
+static int upload_state(md_system* s, const double* pos, const double* vel) {
+  const size_t N = (size_t)s->N;
+  std::vector<double> xd(3 * N), vd(3 * N);
+  for (int r = 0; r < s->n_reps; ++r) {
+    const RepDev& q = s->reps_h[r];
+    for (int i = q.atom_off; i < q.atom_off + q.n_atoms; ++i)
+      for (int a = 0; a < 3; ++a) {
+        double xa = pos[3 * (size_t)i + a];
+        if (!std::isfinite(xa) || !std::isfinite(vel[3 * (size_t)i + a]))
+          return fail(s, MD_EINVAL, "non-finite input position or velocity");
+        xa -= q.L * std::floor(xa / q.L);
+        if (xa >= q.L || xa < 0) xa = 0.0;
+        if (!s->mixed && (float)xa >= (float)q.L) xa = 0.0;
+        xd[a * N + i] = xa;
+        vd[a * N + i] = vel[3 * (size_t)i + a];
+      }
+  }
+  if (s->mixed) {
+    CU(cudaMemcpyAsync(s->x, xd.data(), 3 * N * sizeof(double), cudaMemcpyHostToDevice, s->st));
+    CU(cudaMemcpyAsync(s->v, vd.data(), 3 * N * sizeof(double), cudaMemcpyHostToDevice, s->st));
+    CU(cudaStreamSynchronize(s->st));
+  } else {
+    std::vector<float> xf(3 * N), vf(3 * N);
+    for (size_t k = 0; k < 3 * N; ++k) { xf[k] = (float)xd[k]; vf[k] = (float)vd[k]; }
+    CU(cudaMemcpyAsync(s->x, xf.data(), 3 * N * sizeof(float), cudaMemcpyHostToDevice, s->st));
+    CU(cudaMemcpyAsync(s->v, vf.data(), 3 * N * sizeof(float), cudaMemcpyHostToDevice, s->st));
+    CU(cudaStreamSynchronize(s->st));
+  }
+  CU(cudaMemsetAsync(s->img, 0, 3 * N * sizeof(int), s->st));
+  return MD_OK;
+}
+
+static int refresh(md_system* s) {
+  const bool p = s->profile;
+  s->profile = false;
+  enqueue_rebin(s);
+  enqueue_forces(s, false);
+  s->profile = p;
+  return check_flags(s);
+}
+
+// ------------------------------------------------------------------ C ABI
+extern "C" {
+
+int md_workspace_size(const md_desc* desc, size_t* bytes) {
+  md_system tmp;
+  md_system* s = &tmp;
+  int rc = configure(s, desc);
+  if (rc) { g_create_error = s->err; return rc; }
+  if (!bytes) return fail(nullptr, MD_EINVAL, "null output");
+  *bytes = plan(s, nullptr);
+  return MD_OK;
+}
+
+int md_create(const md_desc* d, md_system** out) {
+  if (!out) return fail(nullptr, MD_EINVAL, "null output pointer");
+  *out = nullptr;
+  md_system* s = new md_system();
+  int rc = configure(s, d);
+  if (rc) { g_create_error = s->err; delete s; return rc; }
+  if (!d->pos || !d->vel) { delete s; return fail(nullptr, MD_EINVAL, "pos and vel are required"); }
+  auto bail = [&](int code) { g_create_error = s->err; md_destroy(s); return code; };
+  s->bytes = plan(s, nullptr);
+  if (d->workspace) {
+    if (d->workspace_bytes < s->bytes) {
+      fail(s, MD_ENOMEM, "workspace too small: need " + std::to_string(s->bytes) + " bytes");
+      return bail(MD_ENOMEM);
+    }
+    if (((uintptr_t)d->workspace & 255) != 0) { fail(s, MD_EINVAL, "workspace must be 256-byte aligned"); return bail(MD_EINVAL); }
+    s->base = (char*)d->workspace;
+  } else {
+    if (cudaMalloc(&s->base, s->bytes) != cudaSuccess) {
+      cudaGetLastError();
+      s->base = nullptr;
+      fail(s, MD_ENOMEM, "cudaMalloc of " + std::to_string(s->bytes) + " bytes failed");
+      return bail(MD_ENOMEM);
+    }
+    s->own_mem = true;
+  }
+  plan(s, s->base);
+  if (d->cuda_stream) {
+    s->st = (cudaStream_t)d->cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking) != cudaSuccess) {
+      fail(s, MD_ECUDA, "stream creation failed");
+      return bail(MD_ECUDA);
+    }
+    s->own_stream = true;
+  }
+  // static tables
+  std::vector<uint16_t> site(s->N);
+  for (int64_t i = 0; i < s->N; ++i) site[i] = 0;
+  for (int r = 0; r < s->n_reps; ++r) {
+    const RepDev& q = s->reps_h[r];
+    for (int i = 0; i < q.n_atoms; ++i) site[q.atom_off + i] = (uint16_t)(i % s->S);
+  }
+  std::vector<double> ones(s->n_reps, 1.0);
+  auto up = [&](void* dst, const void* src, size_t b) {
+    return cudaMemcpyAsync(dst, src, b, cudaMemcpyHostToDevice, s->st) == cudaSuccess;
+  };
+  bool ok = up(s->reps, s->reps_h.data(), sizeof(RepDev) * s->n_reps) &&
+            up(s->tiles_lj, s->t_lj.data(), sizeof(Tile) * s->t_lj.size()) &&
+            up(s->tiles_int, s->t_int.data(), sizeof(Tile) * s->t_int.size()) &&
+            up(s->site, site.data(), sizeof(uint16_t) * s->N) &&
+            up(s->lam, ones.data(), sizeof(double) * s->n_reps) &&
+            cudaMemsetAsync(s->done, 0, sizeof(unsigned), s->st) == cudaSuccess &&
+            cudaMemsetAsync(s->flags, 0, sizeof(unsigned), s->st) == cudaSuccess &&
+            cudaStreamSynchronize(s->st) == cudaSuccess;
+  if (!ok) { fail(s, MD_ECUDA, "initial upload failed"); return bail(MD_ECUDA); }
+  rc = upload_state(s, d->pos, d->vel);
+  if (rc) return bail(rc);
+  rc = refresh(s);
+  if (rc) return bail(rc);
+  rc = capture_cycle(s);
+  if (rc) return bail(rc);
+  *out = s;
+  return MD_OK;
+}
+
+int md_step_async(md_system* s, int64_t n) {
+  if (!s || n < 0) return fail(s, MD_EINVAL, "bad arguments");
+  const int64_t full = n / s->R, rem = n % s->R;
+  for (int64_t c = 0; c < full; ++c) {
+    CU(cudaGraphLaunch(s->cycle, s->st));
+    if (s->profile) {
+      s->ev_used = (int)std::min<int64_t>(s->ev.size(), 3 + 3 * s->R + 1);
+      CU(cudaStreamSynchronize(s->st));
+      prof_collect(s, s->R);
+    }
+  }
+  if (rem) {
+    enqueue_block(s, (int)rem);
+    CU(cudaGetLastError());
+    if (s->profile) { CU(cudaStreamSynchronize(s->st)); prof_collect(s, (int)rem); }
+  }
+  return MD_OK;
+}
+
+int md_step(md_system* s, int64_t n) {
+  int rc = md_step_async(s, n);
+  if (rc) return rc;
+  return check_flags(s);
+}
+
+int md_sync(md_system* s) {
+  if (!s) return fail(s, MD_EINVAL, "null system");
+  return check_flags(s);
+}
+
+int md_forces(md_system* s, double* f_out) {
+  if (!s || !f_out) return fail(s, MD_EINVAL, "bad arguments");
+  CU(cudaStreamSynchronize(s->st));
+  const size_t N = (size_t)s->N;
+  if (s->mixed) {
+    std::vector<F4i> h(N);
+    CU(cudaMemcpy(h.data(), s->F, N * sizeof(F4i), cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < N; ++i) {
+      f_out[3 * i] = (double)h[i].x * kFixInv;
+      f_out[3 * i + 1] = (double)h[i].y * kFixInv;
+      f_out[3 * i + 2] = (double)h[i].z * kFixInv;
+    }
+  } else {
+    std::vector<float4> h(N);
+    CU(cudaMemcpy(h.data(), s->F, N * sizeof(float4), cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < N; ++i) { f_out[3 * i] = h[i].x; f_out[3 * i + 1] = h[i].y; f_out[3 * i + 2] = h[i].z; }
+  }
+  return MD_OK;
+}
+
+int md_energy(md_system* s, md_energy_t* out) {
+  if (!s || !out) return fail(s, MD_EINVAL, "bad arguments");
+  const bool p = s->profile;
+  s->profile = false;
+  enqueue_forces(s, true);
+  launch_energy_reduce(s->lj_part, s->b_part, s->tiles_lj, (int)s->t_lj.size(), s->tiles_int, (int)s->t_int.size(),
+                       s->n_reps, s->e_out, s->st);
+  // kinetic energy of the current velocities (a pass that only reads v)
+  launch_integrate(s->mixed, kKineticOnly, true, false, s->x, s->v, s->img, s->F, s->site, s->cellc, s->inv_perm,
+                   s->ref, s->pos, (int)s->N, s->tiles_int, (int)s->t_int.size(), s->reps, s->n_reps, s->fp,
+                   s->kepart, s->done, s->ke_out, s->lam, s->tau, s->flags, s->st);
+  s->profile = p;
+  CU(cudaGetLastError());
+  std::vector<double> e((size_t)s->n_reps * 16), ke(s->n_reps);
+  CU(cudaMemcpyAsync(e.data(), s->e_out, e.size() * sizeof(double), cudaMemcpyDeviceToHost, s->st));
+  CU(cudaMemcpyAsync(ke.data(), s->ke_out, ke.size() * sizeof(double), cudaMemcpyDeviceToHost, s->st));
+  int rc = check_flags(s);
+  if (rc) return rc;
+  for (int r = 0; r < s->n_reps; ++r) {
+    md_energy_t& o = out[r];
+    const double* q = e.data() + 16 * r;
+    o.lj = q[0]; o.lj_shifted = q[1]; o.bond = q[2]; o.angle = q[3]; o.dihedral = q[4];
+    for (int k = 0; k < 6; ++k) o.virial[k] = q[5 + k];
+    o.kinetic = ke[r];
+    o.temperature = 2.0 * ke[r] / (s->reps_h[r].dof * kKB);
+    o.total = o.lj_shifted + o.bond + o.angle + o.dihedral + o.kinetic;
+    const double V = s->reps_h[r].L * s->reps_h[r].L * s->reps_h[r].L;
+    o.pressure = (2.0 * o.kinetic + o.virial[0] + o.virial[1] + o.virial[2]) / (3.0 * V);
+  }
+  return MD_OK;
+}
+
+int md_rebin(md_system* s) {
+  if (!s) return fail(s, MD_EINVAL, "null system");
+  const bool p = s->profile;
+  s->profile = false;
+  enqueue_rebin(s);
+  s->profile = p;
+  return check_flags(s);
+}
+
+int md_get_state(md_system* s, double* pos, double* vel, int32_t* images) {
+  if (!s) return fail(s, MD_EINVAL, "null system");
+  CU(cudaStreamSynchronize(s->st));
+  const size_t N = (size_t)s->N;
+  auto fetch = [&](const void* src, double* dst) -> int {
+    if (!dst) return MD_OK;
+    if (s->mixed) {
+      std::vector<double> h(3 * N);
+      CU(cudaMemcpy(h.data(), src, 3 * N * sizeof(double), cudaMemcpyDeviceToHost));
+      for (size_t i = 0; i < N; ++i)
+        for (int a = 0; a < 3; ++a) dst[3 * i + a] = h[a * N + i];
+    } else {
+      std::vector<float> h(3 * N);
+      CU(cudaMemcpy(h.data(), src, 3 * N * sizeof(float), cudaMemcpyDeviceToHost));
+      for (size_t i = 0; i < N; ++i)
+        for (int a = 0; a < 3; ++a) dst[3 * i + a] = h[a * N + i];
+    }
+    return MD_OK;
+  };
+  int rc = fetch(s->x, pos);
+  if (rc) return rc;
+  rc = fetch(s->v, vel);
+  if (rc) return rc;
+  if (images) {
+    std::vector<int> h(3 * N);
+    CU(cudaMemcpy(h.data(), s->img, 3 * N * sizeof(int), cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < N; ++i)
+      for (int a = 0; a < 3; ++a) images[3 * i + a] = h[a * N + i];
+  }
+  return MD_OK;
+}
+
+int md_set_state(md_system* s, const double* pos, const double* vel) {
+  if (!s || !pos || !vel) return fail(s, MD_EINVAL, "bad arguments");
+  CU(cudaStreamSynchronize(s->st));
+  int rc = upload_state(s, pos, vel);
+  if (rc) return rc;
+  return refresh(s);
+}
+
+int md_set_params(md_system* s, const md_params* p) {
+  if (!s || !p) return fail(s, MD_EINVAL, "bad arguments");
+  for (int a = 0; a < 2; ++a)
+    if (!(p->mass[a] > 0) || !(p->sigma[a] > 0) || !(p->eps[a] >= 0))
+      return fail(s, MD_EINVAL, "masses and sigmas must be > 0, eps >= 0");
+  CU(cudaStreamSynchronize(s->st));
+  s->params = *p;
+  fill_force_params(s);
+  CU(cudaMemcpy(s->reps, s->reps_h.data(), sizeof(RepDev) * s->n_reps, cudaMemcpyHostToDevice));
+  int rc = capture_cycle(s);
+  if (rc) return rc;
+  const bool pf = s->profile;
+  s->profile = false;
+  enqueue_forces(s, false);
+  s->profile = pf;
+  return check_flags(s);
+}
+
+int md_set_temperature(md_system* s, const double* T) {
+  if (!s || !T) return fail(s, MD_EINVAL, "bad arguments");
+  CU(cudaStreamSynchronize(s->st));
+  for (int r = 0; r < s->n_reps; ++r) { s->reps_h[r].T0 = T[r]; s->T0[r] = T[r]; }
+  CU(cudaMemcpy(s->reps, s->reps_h.data(), sizeof(RepDev) * s->n_reps, cudaMemcpyHostToDevice));
+  return MD_OK;
+}
+
+void* md_stream(md_system* s) { return s ? (void*)s->st : nullptr; }
+
+int md_info(md_system* s, int64_t* n_atoms, int64_t* n_cells, int32_t* cap, int32_t* M) {
+  if (!s) return fail(s, MD_EINVAL, "null system");
+  if (n_atoms) *n_atoms = s->N;
+  if (n_cells) *n_cells = s->C;
+  if (cap) *cap = s->cap;
+  if (M) *M = s->reps_h[0].M;
+  return MD_OK;
+}
+
+int md_get_bins(md_system* s, int32_t* cell_of, int32_t* cell_start, int32_t* perm) {
+  if (!s) return fail(s, MD_EINVAL, "null system");
+  CU(cudaStreamSynchronize(s->st));
+  if (cell_of) CU(cudaMemcpy(cell_of, s->cell_of, s->N * sizeof(int), cudaMemcpyDeviceToHost));
+  if (cell_start) CU(cudaMemcpy(cell_start, s->cell_start, (s->C + 1) * sizeof(int), cudaMemcpyDeviceToHost));
+  if (perm) CU(cudaMemcpy(perm, s->perm, s->N * sizeof(int), cudaMemcpyDeviceToHost));
+  return MD_OK;
+}
+
+int md_get_neighbors(md_system* s, int32_t* count, int32_t* entries) {
+  if (!s) return fail(s, MD_EINVAL, "null system");
+  CU(cudaStreamSynchronize(s->st));
+  const size_t N = (size_t)s->N;
+  std::vector<int> cnt(N), pm(N), lst((size_t)s->cap * s->Npad);
+  CU(cudaMemcpy(cnt.data(), s->ncount, N * sizeof(int), cudaMemcpyDeviceToHost));
+  CU(cudaMemcpy(pm.data(), s->perm, N * sizeof(int), cudaMemcpyDeviceToHost));
+  if (entries) CU(cudaMemcpy(lst.data(), s->nbr, lst.size() * sizeof(int), cudaMemcpyDeviceToHost));
+  for (size_t sl = 0; sl < N; ++sl) {
+    const int i = pm[sl];
+    if (count) count[i] = cnt[sl];
+    if (entries)
+      for (int q = 0; q < cnt[sl]; ++q)
+        entries[(size_t)i * s->cap + q] = pm[(unsigned)lst[(size_t)q * s->Npad + sl] & kNbrIndexMask];
+  }
+  return MD_OK;
+}
+
+int md_profile_enable(md_system* s, int32_t on) {
+  if (!s) return fail(s, MD_EINVAL, "null system");
+  CU(cudaStreamSynchronize(s->st));
+  const int need = 3 + 3 * s->R + 1;
+  while ((int)s->ev.size() < need) {
+    cudaEvent_t e;
+    CU(cudaEventCreate(&e));
+    s->ev.push_back(e);
+  }
+  s->profile = on != 0;
+  return capture_cycle(s);   // the graph carries the event records when on
+}
+
+int md_profile_read(md_system* s, double* ms, int64_t* n) {
+  if (!s) return fail(s, MD_EINVAL, "null system");
+  for (int k = 0; k < kNumProf; ++k) {
+    if (ms) ms[k] = s->prof_ms[k];
+    if (n) n[k] = s->prof_n[k];
+  }
+  return MD_OK;
+}
+
+int md_profile_reset(md_system* s) {
+  if (!s) return fail(s, MD_EINVAL, "null system");
+  for (int k = 0; k < kNumProf; ++k) { s->prof_ms[k] = 0; s->prof_n[k] = 0; }
+  return MD_OK;
+}
+
+int64_t md_launches_per_call(md_system* s, int64_t n) {
+  if (!s || n <= 0) return 0;
+  const int64_t full = n / s->R, rem = n % s->R;
+  return full * block_launches(s->R) + (rem ? block_launches((int)rem) : 0);
+}
+
+void md_destroy(md_system* s) {
+  if (!s) return;
+  if (s->st) cudaStreamSynchronize(s->st);
+  if (s->cycle) cudaGraphExecDestroy(s->cycle);
+  for (cudaEvent_t e : s->ev) cudaEventDestroy(e);
+  if (s->own_mem && s->base) cudaFree(s->base);
+  if (s->own_stream && s->st) cudaStreamDestroy(s->st);
+  delete s;
+}
+
+const char* md_last_error(const md_system* s) { return s ? s->err.c_str() : g_create_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,131 @@
+// md_kernels.cuh -- device-side data layout and kernel launchers of the GB300
+// MD engine (united-atom polyethylene, Xu et al., Secs. 2-3).
+//
+// Layout in HBM (N atoms over all replicas, C cells over all replicas):
+//   original (chain-major) order, index i:
+//     mixed form : x, v  double SoA [3][N];   plain form : float SoA [3][N]
+//     img        int32 SoA [3][N]  periodic image counters
+//     F          force, AoS 32 B/atom: int64x3 fixed point (mixed) or float x3
+//     site       uint16 [N] position of the atom in its chain (MAIDX - 1)
+//     cellc      int32 [N] packed cell coordinates at the last rebin
+//     ref        float4 [N] cell-unit position at the last rebin
+//     inv_perm   int32 [N] sorted slot of atom i
+//   sorted (cell-major) order, index s:
+//     pos        float4 [N] position in cell units relative to the centre of the
+//                atom's cell at the last rebin, u = (x - (c + 1/2) h) / h; w unused
+//     tag        int32 [N]  chain*512 + site | type << 30
+//     perm       int32 [N]  original index of slot s
+//     Flj        AoS 32 B   LJ force on slot s
+//     nbr        int32 [cap][Npad] neighbour entries (column-major, coalesced)
+//     ncount     int32 [N]
+//   cells: count int32 [C], cell_start int32 [C+1]
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mdg {
+
+constexpr int kMaxReplicas = 4096;
+constexpr int kTagTypeBit = 30;
+constexpr uint32_t kTagMask = (1u << 30) - 1;
+constexpr int kNbrIndexBits = 26;                     // j in entry bits 0..25
+constexpr uint32_t kNbrIndexMask = (1u << kNbrIndexBits) - 1;
+constexpr double kFixScale = 4294967296.0;            // 2^32 per kJ/mol/nm
+constexpr double kFixInv = 1.0 / 4294967296.0;
+
+// Error flags (bitmask in device memory)
+enum : uint32_t {
+  kFlagNbrOverflow = 1u,      // neighbour list capacity exceeded
+  kFlagFixOverflow = 2u,      // |F| too large for the fixed-point range
+  kFlagNaN = 4u,              // non-finite position or velocity
+  kFlagDisplacement = 8u,     // an atom moved more than skin/2 since the rebin
+  kFlagTimeout = 16u,         // a bounded device wait gave up
+};
+
+struct RepDev {
+  double L, h, inv_h, half_L;   // box, cell side, M/L, L/2
+  float Lf, hf, half_Lf, Mf;    // FP32 copies; Mf = M (the box side in cell units)
+  float ih_hi, ih_lo;           // 1/h split into two floats (ih_hi + ih_lo = 1/h to ~2^-48)
+  float rc2u, rlist2u;          // (r_c / h)^2, ((r_c + skin) / h)^2
+  float hs2u, pad1;             // (skin / 2 / h)^2
+  // LJ constants in cell units, by type pair t_i + t_j (0: C_32-C_32,
+  // 1: C_32-C_33, 2: C_33-C_33): C6u = c6 / h^6, C12u = c12 / h^12
+  float C6u[3], C12u[3];
+  float pad2[2];
+  int M, cell_base, atom_off, n_atoms;
+  int n_chains, chain_off, tile_off, n_tiles;
+  double T0, dof;
+};
+
+struct Tile { int start, len, rep, pad; };
+
+// Position of atom x (one axis) in cell units relative to the centre of cell
+// c, shifted by w box lengths (w = +1/-1 for an atom that crossed a face
+// since the rebin): u = x/h - (c + 1/2) + w M.
+// FP64 master: one FMA in FP64, then one rounding to FP32.
+__device__ __forceinline__ float cell_unit(double x, int c, int w, const RepDev& R) {
+  const double k = (double)c + 0.5 - (double)w * (double)R.M;
+  return __double2float_rn(fma(x, R.inv_h, -k));
+}
+// FP32 master: x/h as p + e (exact product error by FMA, plus the low part of
+// 1/h), minus the exact integer-plus-half k; one final rounding.
+__device__ __forceinline__ float cell_unit(float x, int c, int w, const RepDev& R) {
+  const float k = (float)c + 0.5f - (float)w * R.Mf;
+  const float p = x * R.ih_hi;
+  const float e = fmaf(x, R.ih_hi, -p);
+  return __fadd_rn(__fsub_rn(p, k), fmaf(x, R.ih_lo, e));
+}
+
+// Per-system constants passed by value to kernels.
+struct ForceParams {
+  float c6[2][2], c12[2][2];      // 4 eps sigma^6, 4 eps sigma^12 (geometric mixing)
+  float erc[2][2];                // pair energy at r_c (for the shifted energy)
+  float rc2, rlist2;              // cutoff^2, list radius^2 (float)
+  float kb, b0, ka, theta0;       // Eqs. (4), (5)
+  float kphi, phis;               // Eq. (6)
+  int n_mult;
+  int sites;                      // atoms per chain (NAOM)
+  float half_skin2;               // (skin/2)^2
+  float pad;
+  double mass[2], inv_mass[2];
+  double dt;
+};
+
+struct F4i { long long x, y, z, w; };   // fixed-point force, 32 B
+
+// ---------------------------------------------------------------- binning
+void launch_bin_count(bool mixed, const void* x, int N, const Tile* tiles, int n_tiles,
+                      const RepDev* reps, int* cell_of, int* cellc, int* count, int* slot,
+                      cudaStream_t st);
+void launch_scan(const int* count, int* cell_start, int C, cudaStream_t st);
+void launch_bin_scatter(const int* cell_of, const int* slot, const int* cell_start, int* tmp, int N,
+                        cudaStream_t st);
+void launch_cell_sort(bool mixed, const void* x, int N, const int* cell_start, const int* tmp,
+                      const int* cellc, const uint16_t* site, const RepDev* reps, int n_reps, int C,
+                      int sites, int* perm, int* inv_perm, float4* pos, int* tag, float4* ref,
+                      cudaStream_t st);
+void launch_nbr_build(const float4* pos, const int* tag, const int* cell_start, const RepDev* reps,
+                      int n_reps, int C, float rlist2, int* nbr, int* ncount, int cap, int Npad,
+                      unsigned* flags, cudaStream_t st);
+
+// ---------------------------------------------------------------- forces
+void launch_lj(bool mixed, bool energy, const float4* pos, const int* tag, const int* nbr, const int* ncount, int Npad,
+               const Tile* tiles, int n_tiles, const RepDev* reps, const ForceParams& fp,
+               void* flj, double* epart, unsigned* flags, int block, cudaStream_t st);
+void launch_bonded(bool mixed, bool energy, const void* x, const uint16_t* site, const int* inv_perm,
+                   const void* flj, int N, const Tile* tiles, int n_tiles, const RepDev* reps,
+                   const ForceParams& fp, void* F, double* epart, unsigned* flags, cudaStream_t st);
+
+// ---------------------------------------------------------------- integration
+enum IntegMode { kKickDrift = 0, kKickKickDrift = 1, kKickOnly = 2, kKineticOnly = 3 };
+void launch_integrate(bool mixed, IntegMode mode, bool ke, bool thermostat, void* x, void* v, int* img,
+                      const void* F, const uint16_t* site, const int* cellc, const int* inv_perm,
+                      const float4* ref, float4* pos, int N, const Tile* tiles, int n_tiles,
+                      const RepDev* reps, int n_reps, const ForceParams& fp, double* kepart,
+                      unsigned* done, double* ke_out, double* lam, double tau, unsigned* flags,
+                      cudaStream_t st);
+void launch_energy_reduce(const double* lj_part, const double* b_part, const Tile* lj_tiles,
+                          int n_lj_tiles, const Tile* b_tiles, int n_b_tiles, int n_reps,
+                          double* out, cudaStream_t st);
+
+}  // namespace mdg

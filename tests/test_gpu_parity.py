@@ -1,0 +1,288 @@
+"""CUDA path vs the FP64 oracle, through the C ABI, on seeded melts.
+
+Tolerances (stated here, derived from the arithmetic):
+  * binning: bit-exact (cell ids are FP64 on both sides)
+  * neighbour pairs: every pair the oracle finds inside r_c is listed; every
+    listed pair lies inside r_c + skin (+1e-5 nm of FP32 rounding)
+  * forces: the relative force error ||F_gpu - F_oracle||_2 / ||F_oracle||_2
+    over all atoms is <= 1e-5, and every atom obeys
+    |F_gpu - F_oracle|_max <= 5e-5 * RMS_i |F_oracle| (FP32 coordinates carry
+    ~7e-8 nm and FP32 bond lengths ~1e-8 nm of rounding, which at hot-start
+    contacts and stiff bonds gives up to ~1e-5 on single atoms), except atoms
+    with a pair within 2e-6 nm of r_c (the FP32 and FP64 cutoff tests may
+    disagree there), which get |F(r_c)| per such pair on top
+  * energies: 1e-5 relative (FP32 terms summed in FP64)
+  * short trajectories: 1e-5 nm after 50 steps
+"""
+import numpy as np
+import pytest
+from scipy.spatial import cKDTree
+
+import chaingen
+import oracle
+import paper_1001_3764_gb300 as md
+
+pytestmark = pytest.mark.gpu
+
+FORCE_TOL = 1e-5       # relative RMS force error
+ATOM_TOL = 5e-5        # per-atom max error / RMS force
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    md.load()
+
+
+def _oracle(melt, params=None):
+    n = melt["n_chains"]
+    return oracle.System(oracle.chain_topology(melt["sites"]), n, melt["L"], params=params,
+                         use_cells=n * melt["sites"] > 3000)
+
+
+def _ambiguous_pairs(x, L, rc, tol=2e-6):
+    tr = cKDTree(np.mod(x, L), boxsize=L)
+    pairs = tr.query_pairs(rc + tol, output_type="ndarray")
+    if len(pairs) == 0:
+        return np.zeros(len(x), int)
+    d = x[pairs[:, 0]] - x[pairs[:, 1]]
+    d -= L * np.round(d / L)
+    r = np.linalg.norm(d, axis=1)
+    amb = pairs[np.abs(r - rc) < tol]
+    cnt = np.zeros(len(x), int)
+    np.add.at(cnt, amb[:, 0], 1)
+    np.add.at(cnt, amb[:, 1], 1)
+    return cnt
+
+
+def check_forces(f_gpu, f_orc, x, L, params=None):
+    p = params or oracle.default_params()
+    scale = np.sqrt(np.mean(np.sum(f_orc ** 2, axis=1)))
+    err = np.abs(f_gpu - f_orc).max(axis=1)
+    amb = _ambiguous_pairs(x, L, 1.0)
+    sig, eps = max(p["sigma"]), max(p["eps"])
+    f_rc = abs(24 * eps * (2 * sig ** 12 - sig ** 6))   # |F(r_c)| bound at r_c = 1 nm
+    allowed = ATOM_TOL * scale + amb * 1.01 * f_rc
+    bad = np.where(err > allowed)[0]
+    assert len(bad) == 0, f"{len(bad)} atoms off; worst rel {err.max() / scale:.3e}"
+    clean = amb == 0
+    rel = np.sqrt(np.sum((f_gpu - f_orc)[clean] ** 2) / np.sum(f_orc[clean] ** 2))
+    assert rel <= FORCE_TOL, f"relative force error {rel:.3e}"
+    return rel, err.max() / scale
+
+
+@pytest.mark.parametrize("precision", [md.MD_MIXED, md.MD_PLAIN_FP32])
+@pytest.mark.parametrize("n_chains,L", [(10, None), (1, 3.4), (30, 5.2)])
+def test_binning_is_bit_exact(precision, n_chains, L):
+    m = chaingen.melt(n_chains, seed=21, L=L)
+    s = md.System(m, precision=precision)
+    x, _, _ = s.state()
+    M = s.info["cells_per_side"]
+    assert M == int(m["L"] // 1.1)
+    co, cs, pm = s.bins()
+    oc, ocs, opm = oracle.bin_atoms(x, m["L"], M)
+    assert np.array_equal(co, oc)
+    assert np.array_equal(cs, ocs)
+    assert np.array_equal(pm, opm)
+    s.close()
+
+
+@pytest.mark.parametrize("precision", [md.MD_MIXED, md.MD_PLAIN_FP32])
+def test_neighbour_pairs(precision):
+    m = chaingen.melt(20, seed=5, L=4.6)
+    s = md.System(m, precision=precision)
+    x, _, _ = s.state()
+    L = m["L"]
+    cnt, ent = s.neighbors()
+    listed = set()
+    for i in range(len(x)):
+        for j in ent[i, :cnt[i]]:
+            listed.add((i, int(j)))
+    # symmetric full list
+    assert all((j, i) in listed for (i, j) in listed)
+    tr = cKDTree(np.mod(x, L), boxsize=L)
+    pairs = tr.query_pairs(1.1 + 1e-5, output_type="ndarray")
+    d = x[pairs[:, 0]] - x[pairs[:, 1]]
+    d -= L * np.round(d / L)
+    r = np.linalg.norm(d, axis=1)
+    same = pairs[:, 0] // 150 == pairs[:, 1] // 150
+    excl = same & (np.abs(pairs[:, 0] - pairs[:, 1]) <= 2)
+    must = {(int(a), int(b)) for (a, b), rr, e in zip(pairs, r, excl) if rr < 1.1 - 1e-5 and not e}
+    may = {(int(a), int(b)) for (a, b), e in zip(pairs, excl) if not e}
+    half = {(min(i, j), max(i, j)) for (i, j) in listed}
+    assert must <= half
+    assert half <= may
+    s.close()
+
+
+@pytest.mark.parametrize("precision", [md.MD_MIXED, md.MD_PLAIN_FP32])
+@pytest.mark.parametrize("n_chains,seed,L", [(10, 1, None), (2, 3, 3.4), (40, 9, None)])
+def test_forces_match_oracle(precision, n_chains, seed, L):
+    m = chaingen.melt(n_chains, seed=seed, L=L)
+    s = md.System(m, precision=precision)
+    x, _, _ = s.state()
+    f = s.forces()
+    f_orc, _, _ = _oracle(m).forces(x)
+    check_forces(f, f_orc, x, m["L"])
+    s.close()
+
+
+@pytest.mark.parametrize("precision", [md.MD_MIXED, md.MD_PLAIN_FP32])
+def test_energies_match_oracle(precision):
+    m = chaingen.melt(10, seed=4)
+    s = md.System(m, precision=precision)
+    x, v, _ = s.state()
+    e = s.energy()[0]
+    ref = _oracle(m)
+    _, en, vir = ref.forces(x)
+    ke = ref.kinetic(v)
+    for got, want in [(e["lj"], en[0]), (e["lj_shifted"], en[1]), (e["bond"], en[2]), (e["angle"], en[3]),
+                      (e["dihedral"], en[4]), (e["kinetic"], ke)]:
+        assert got == pytest.approx(want, rel=1e-5, abs=1e-3)
+    assert np.allclose(e["virial"], vir, rtol=1e-4, atol=1e-2 * np.abs(vir).max())
+    s.close()
+
+
+@pytest.mark.parametrize("precision,tol", [(md.MD_MIXED, 1e-5), (md.MD_PLAIN_FP32, 2e-4)])
+def test_short_trajectory_matches_oracle(precision, tol):
+    m = chaingen.melt(4, seed=12, L=3.6, T=300.0)
+    s = md.System(m, precision=precision, rebin_every=5)
+    x0, v0, _ = s.state()
+    s.step(50)
+    x, v, img = s.state()
+    xo, vo, _, _, _ = _oracle(m).run(x0, v0, 0.001, 50, sample_every=0)
+    d = x + img * m["L"] - xo
+    assert np.abs(d).max() < tol
+    s.close()
+
+
+def test_mixed_form_is_deterministic():
+    m = chaingen.melt(12, seed=2)
+    runs = []
+    for _ in range(2):
+        s = md.System(m, precision=md.MD_MIXED, rebin_every=2)
+        s.step(100)
+        runs.append((s.state(), s.forces()))
+        s.close()
+    (xa, va, ia), fa = runs[0]
+    (xb, vb, ib), fb = runs[1]
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb) and np.array_equal(ia, ib)
+    assert np.array_equal(fa, fb)
+
+
+def test_net_force_vanishes():
+    m = chaingen.melt(10, seed=6)
+    s = md.System(m, precision=md.MD_MIXED)
+    f = s.forces()
+    scale = np.sqrt(np.mean(np.sum(f ** 2, axis=1)))
+    assert np.abs(f.sum(0)).max() < 1e-6 * scale * np.sqrt(len(f))
+    s.close()
+
+
+def test_thermostat_temperature_series_matches_oracle():
+    m = chaingen.melt(4, seed=8, L=3.6, T=450.0)
+    s = md.System(m, precision=md.MD_MIXED, thermostat=md.MD_VRESCALE, T_target=300.0, tau_t=0.02)
+    x0, v0, _ = s.state()
+    temps = [s.energy()[0]["temperature"]]
+    for _ in range(30):
+        s.step(1)
+        temps.append(s.energy()[0]["temperature"])
+    _, _, _, smp, _ = _oracle(m).run(x0, v0, 0.001, 30, thermostat=True, T0=300.0, tau=0.02)
+    assert np.allclose(temps, smp[:, 7], rtol=2e-5)
+    assert temps[-1] < temps[0]
+    s.close()
+
+
+def test_replicas_equal_separate_runs_and_oracle():
+    melts = [chaingen.melt(c, seed=40 + c) for c in (10, 25, 12)]
+    both = md.System(melts, precision=md.MD_MIXED, rebin_every=4)
+    fb = both.forces()
+    off = 0
+    for m in melts:
+        alone = md.System(m, precision=md.MD_MIXED)
+        fa = alone.forces()
+        n = len(m["pos"])
+        assert np.array_equal(fb[off:off + n], fa)
+        x, _, _ = alone.state()
+        check_forces(fa, _oracle(m).forces(x)[0], x, m["L"])
+        alone.close()
+        off += n
+    both.step(20)
+    xb, _, _ = both.state()
+    off = 0
+    for m in melts:
+        alone = md.System(m, precision=md.MD_MIXED, rebin_every=4)
+        alone.step(20)
+        xa, _, _ = alone.state()
+        assert np.array_equal(xb[off:off + len(xa)], xa)
+        off += len(xa)
+        alone.close()
+    both.close()
+
+
+@pytest.mark.parametrize("sites", [4, 7, 150])
+def test_short_chains_and_rebin_every_step(sites):
+    n_chains = max(1, 1500 // sites)
+    m = chaingen.melt(n_chains, sites=sites, seed=3, L=3.6)
+    params = oracle.default_params()
+    s = md.System(m, precision=md.MD_MIXED, rebin_every=1)
+    x, _, _ = s.state()
+    ref = oracle.System(oracle.chain_topology(sites), n_chains, m["L"], use_cells=False)
+    check_forces(s.forces(), ref.forces(x)[0], x, m["L"], params)
+    s.step(7)
+    x, _, _ = s.state()
+    check_forces(s.forces(), ref.forces(x)[0], x, m["L"], params)
+    s.close()
+
+
+def test_displacement_beyond_half_skin_is_reported():
+    m = chaingen.melt(10, seed=1)
+    s = md.System(m, precision=md.MD_MIXED, skin=0.002, rebin_every=10)
+    with pytest.raises(md.MDError) as e:
+        s.step(10)
+    assert e.value.code == md.MD_EUNSTABLE
+    s.close()
+
+
+def test_workspace_and_library_allocation_agree():
+    m = chaingen.melt(10, seed=13)
+    a = md.System(m, use_torch_memory=True, rebin_every=3)
+    b = md.System(m, use_torch_memory=False, rebin_every=3)
+    a.step(15); b.step(15)
+    assert np.array_equal(a.state()[0], b.state()[0])
+    a.close(); b.close()
+
+
+@pytest.mark.parametrize("precision", [md.MD_MIXED, md.MD_PLAIN_FP32])
+def test_full_size_sampled_forces(precision):
+    """1.5M sites (10,000 chains, L = 35.68 nm), as benchmarked: forces of
+    sampled atoms against the oracle's all-atom sums."""
+    m = chaingen.melt(10000, seed=3)
+    s = md.System(m, precision=precision)
+    x, _, _ = s.state()
+    f = s.forces()
+    rng = np.random.default_rng(0)
+    sel = np.sort(rng.choice(len(x), 48, replace=False))
+    ref = _oracle(m)
+    f_lj = ref.lj_atoms(x, sel)
+    f_b, _, _ = ref.bonded(x)
+    f_orc = f_lj + f_b[sel]
+    scale = np.sqrt(np.mean(np.sum(f ** 2, axis=1)))
+    L = m["L"]
+    tr = cKDTree(np.mod(x, L), boxsize=L)
+    amb = np.zeros(len(sel), int)
+    for k, i in enumerate(sel):
+        for j in tr.query_ball_point(np.mod(x[i], L), 1.0 + 2e-6):
+            d = x[i] - x[j]
+            d -= L * np.round(d / L)
+            amb[k] += abs(np.linalg.norm(d) - 1.0) < 2e-6
+    p = oracle.default_params()
+    f_rc = abs(24 * max(p["eps"]) * (2 * max(p["sigma"]) ** 12 - max(p["sigma"]) ** 6))
+    err = np.abs(f[sel] - f_orc).max(axis=1)
+    assert np.all(err <= ATOM_TOL * scale + amb * 1.01 * f_rc), (err / scale).max()
+    clean = amb == 0
+    rel = np.sqrt(np.sum((f[sel] - f_orc)[clean] ** 2) / np.sum(f_orc[clean] ** 2))
+    assert rel <= FORCE_TOL, rel
+    s.close()
