@@ -1,0 +1,334 @@
+"""Throughput of the united-atom polyethylene MD hot path on one GB300.
+
+Workload (N = 1): a 0.77 g/cm^3 polyethylene melt of 10,000 chains x 150
+united atoms (1.5M sites, L = 35.68 nm), r_c = 1.0 nm, skin 0.1 nm, neighbour
+list rebuilt every 10 steps, dt = 1 fs, NVE velocity Verlet, mixed precision
+(FP32 pair and bonded math, int64 fixed-point force sums, FP64 state).
+One benchmark "step" is one pass of the whole hot path: rebin + neighbour list
++ 10 MD steps (one CUDA-graph launch).  Metric: atom-steps/s of MD steps.
+
+Under torchrun (--gpus N > 1) every rank runs its own independent replica melt
+(replicas only: the method has no exchange between independent systems), and
+the value is the sum over ranks ("scaling": "weak").
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload (the slow reference arm of this build).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+MD_STEPS_PER_BENCH_STEP = 10
+N_CHAINS = 10000
+SITES = 150
+DT_PS = 0.001
+FLOP_PER_ATOM_LJ = 69.2 * 20.0       # unique pairs within r_c per atom x flops per pair (Newton-3 count)
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x 2 x max SM clock
+WORKLOAD = ("PE melt 10,000 chains x 150 united atoms (1.5M sites), 0.77 g/cm3, L=35.68 nm, "
+            "rc=1.0 nm, skin=0.1 nm, rebin every 10 steps, dt=1 fs, NVE velocity Verlet")
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, index: int):
+        self.index, self.proc, self.path = index, None, None
+
+    def start(self):
+        self.path = os.path.join("/tmp", f"bench_clocks_{os.getpid()}.csv")
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [c.strip() for c in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1])); mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _traffic(kernel_src: str):
+    """DRAM bytes per LJ launch from the committed ncu summary, if the kernel
+    source is unchanged since the capture (else None)."""
+    path = os.path.join(ROOT, "profiles", "lj_dram_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    kv = {}
+    for line in open(path):
+        if "=" in line and not line.startswith("#"):
+            k, v = line.split("=", 1)
+            kv[k.strip()] = v.strip()
+    h = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+    if kv.get("source_sha256_16") != h:
+        return None
+    try:
+        return float(kv["bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def make_workload(rank: int, chains: int = N_CHAINS):
+    import chaingen
+    return chaingen.melt(chains, SITES, seed=3 + 1000 * rank, T=500.0)
+
+
+def equilibrate(md, melt):
+    """Relax the generator's hot contacts: weak-coupling thermostat at 500 K,
+    neighbour list every 2 steps (untimed set-up)."""
+    eq = md.System(melt, precision=md.MD_MIXED, thermostat=md.MD_VRESCALE, T_target=500.0,
+                   tau_t=0.05, rebin_every=2)
+    eq.step(1500)
+    x, v, _ = eq.state()
+    eq.close()
+    return dict(melt, pos=x, vel=v)
+
+
+def drift(md, melt, precision, n_steps=2000, every=100):
+    """NVE energy drift (least-squares slope of the total energy with shifted
+    LJ) in kT per atom per ns."""
+    s = md.System(melt, precision=precision)
+    t, e, T = [], [], []
+    for k in range(n_steps // every + 1):
+        en = s.energy()[0]
+        t.append(k * every * DT_PS); e.append(en["total"]); T.append(en["temperature"])
+        if k < n_steps // every:
+            s.step(every)
+    s.close()
+    slope = np.polyfit(np.array(t) * 1e-3, np.array(e), 1)[0]     # kJ/mol per ns
+    kT = 0.0083144626 * float(np.mean(T))
+    return {"kT_per_atom_per_ns": float(slope / (kT * len(melt["pos"]))), "steps": n_steps,
+            "T_mean": float(np.mean(T)), "window_ns": n_steps * DT_PS * 1e-3}
+
+
+def cpu_baseline(melt, steps=4):
+    """FP64 oracle (cell list, OpenMP on every host core): `steps`
+    velocity-Verlet steps of the same melt (steps + 1 force evaluations)."""
+    import oracle
+    cores = os.cpu_count() or 1
+    ref = oracle.System(oracle.chain_topology(SITES), melt["n_chains"], melt["L"], use_cells=True, nthreads=cores)
+    t0 = time.perf_counter()
+    ref.run(melt["pos"], melt["vel"], DT_PS, steps, sample_every=0)
+    el = time.perf_counter() - t0
+    n = len(melt["pos"])
+    return {"value": n * steps / el, "unit": "atom-steps/s", "cores": cores, "kind": "oracle",
+            "sample": f"{steps} velocity-Verlet steps ({steps + 1} force evaluations) of the {n}-site melt, "
+                      f"FP64 cell-list oracle, OpenMP {cores} threads, {el:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    melt = make_workload(0)
+    import oracle
+    cores = os.cpu_count() or 1
+    ref = oracle.System(oracle.chain_topology(SITES), melt["n_chains"], melt["L"], use_cells=True, nthreads=cores)
+    x, v = melt["pos"], melt["vel"]
+    ref.run(x, v, DT_PS, 0, sample_every=0)            # warm-up: one force evaluation
+    t0 = time.perf_counter()
+    ref.run(x, v, DT_PS, args.steps, sample_every=0)   # one MD step per bench step
+    el = time.perf_counter() - t0
+    n = len(x)
+    value = n * args.steps / el
+    cb = {"value": value, "unit": "atom-steps/s", "cores": cores, "kind": "oracle",
+          "sample": f"{args.steps} velocity-Verlet steps ({args.steps + 1} force evaluations) of the "
+                    f"{n}-site melt, FP64 cell-list oracle, OpenMP {cores} threads"}
+    print(json.dumps({"impl": "reference", "metric": "atom-steps/s", "value": value, "unit": "atom-steps/s",
+                      "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                      "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+                      "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                      "config": {"workload": WORKLOAD, "sites": n, "md_steps_per_bench_step": 1},
+                      "cpu_baseline": cb,
+                      "e2e": {"value": value, "unit": "atom-steps/s", "h2d_bytes_per_step": 0,
+                              "d2h_bytes_per_step": 0}}), flush=True)
+
+
+def run_gpu(args):
+    import torch
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    import paper_1001_3764_gb300 as md
+
+    melt = equilibrate(md, make_workload(rank, args.chains))
+    n_atoms = len(melt["pos"])
+
+    results = {}
+    forms = (("mixed", md.MD_MIXED),) if args.ncu_region else (("mixed", md.MD_MIXED), ("plain", md.MD_PLAIN_FP32))
+    for name, prec in forms:
+        s = md.System(melt, precision=prec)
+        st = torch.cuda.ExternalStream(md.md_stream(s.h))
+        for _ in range(args.warmup):
+            s.step(MD_STEPS_PER_BENCH_STEP)
+        md.md_profile_enable(s.h, True)
+        md.md_profile_reset(s.h)
+        clocks = ClockSampler(local)
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        clocks.start()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if args.ncu_region:
+            torch.cuda.profiler.start()
+        a.record(st)
+        for _ in range(args.steps):
+            s.step(MD_STEPS_PER_BENCH_STEP, sync=False)
+        b.record(st)
+        s.sync()
+        if args.ncu_region:
+            torch.cuda.profiler.stop()
+        torch.cuda.synchronize()
+        ck = clocks.stop()
+        ms = a.elapsed_time(b)
+        if ws > 1:
+            t = torch.tensor([ms], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        prof_ms, prof_n = md.md_profile_read(s.h)
+        md.md_profile_enable(s.h, False)
+        launches = md.md_launches_per_call(s.h, MD_STEPS_PER_BENCH_STEP) * args.steps
+        results[name] = dict(ms=ms, clocks=ck, prof_ms=prof_ms, prof_n=prof_n, launches=launches)
+        if name == "mixed" and not args.ncu_region:
+            # end to end through the public API with host buffers: upload the
+            # state from pinned host memory, run one cycle, read the energies
+            pos_h = torch.from_numpy(np.ascontiguousarray(melt["pos"])).pin_memory().numpy()
+            vel_h = torch.from_numpy(np.ascontiguousarray(melt["vel"])).pin_memory().numpy()
+            s.set_state(pos_h, vel_h)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                s.set_state(pos_h, vel_h)
+                s.step(MD_STEPS_PER_BENCH_STEP)
+                s.energy()
+            e2e_s = time.perf_counter() - t0
+            results[name]["e2e_s"] = e2e_s
+            results[name]["e2e_h2d"] = pos_h.nbytes + vel_h.nbytes
+            results[name]["e2e_d2h"] = ctypes_size_energy(md)
+        s.close()
+
+    if args.ncu_region:
+        if rank == 0:
+            m = results["mixed"]
+            print(json.dumps({"ncu_region": True, "ms_per_step": m["ms"] / args.steps, "sites": n_atoms,
+                              "launches": int(m["launches"])}), flush=True)
+        return
+    # energy drift of both forms (outside the timed region)
+    dr = {name: drift(md, melt, prec) for name, prec in (("mixed", md.MD_MIXED), ("plain", md.MD_PLAIN_FP32))}
+
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
+    m = results["mixed"]
+    md_steps = MD_STEPS_PER_BENCH_STEP * args.steps
+    value = ws * n_atoms * md_steps / (m["ms"] * 1e-3)
+    plain_value = ws * n_atoms * md_steps / (results["plain"]["ms"] * 1e-3)
+    ns_day = md_steps / (m["ms"] * 1e-3) * DT_PS * 1e-3 * 86400
+    lj_ms = m["prof_ms"][3] / max(m["prof_n"][3], 1)
+    achieved = FLOP_PER_ATOM_LJ * n_atoms / (lj_ms * 1e-3) / 1e12
+    src = os.path.join(ROOT, "paper_1001_3764_gb300", "csrc", "k_force.cu")
+    traffic = _traffic(src)
+    e2e_val = ws * n_atoms * md_steps / m["e2e_s"]
+    out = {
+        "metric": "atom-steps/s", "value": value, "unit": "atom-steps/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": m["ms"] / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+i64+f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sites": n_atoms, "md_steps_per_bench_step": MD_STEPS_PER_BENCH_STEP,
+                   "precision": "mixed (FP32 pair/bonded math, int64 fixed-point forces, FP64 state)",
+                   "l2": "inputs larger than L2 (neighbour list ~1 GB, state ~100 MB)",
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
+        "ns_per_day": ns_day,
+        "plain_fp32": {"value": plain_value,
+                       "ns_per_day": md_steps / (results["plain"]["ms"] * 1e-3) * DT_PS * 1e-3 * 86400,
+                       "ms_per_step": results["plain"]["ms"] / args.steps},
+        "drift_kT_per_atom_per_ns": {k: v["kT_per_atom_per_ns"] for k, v in dr.items()},
+        "drift_detail": dr,
+        "kernel_ms_per_launch": {g: float(t / max(n, 1)) for g, t, n in
+                                 zip(md.PROFILE_GROUPS, m["prof_ms"], m["prof_n"])},
+        "roofline": {"kernel": "k_lj (LJ force, Eq. 2)", "bound": "alu", "achieved": achieved,
+                     "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                     "flop_per_atom": FLOP_PER_ATOM_LJ, "traffic": traffic},
+        "e2e": {"value": e2e_val, "unit": "atom-steps/s", "h2d_bytes_per_step": m["e2e_h2d"],
+                "d2h_bytes_per_step": m["e2e_d2h"]},
+        "gpu_launches": int(m["launches"]),
+        "clocks": m["clocks"],
+    }
+    if ws == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(melt)
+    print(json.dumps(out), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def ctypes_size_energy(md):
+    import ctypes
+    return ctypes.sizeof(md.md_energy_t)
+
+
+def main():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--chains", type=int, default=N_CHAINS, help="chains of 150 sites (default 10,000 = 1.5M sites)")
+    p.add_argument("--ncu-region", action="store_true",
+                   help="profile only the timed loop of the mixed form (cudaProfilerStart/Stop); "
+                        "skips the plain form, e2e, drift and CPU baseline")
+    args = p.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

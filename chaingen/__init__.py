@@ -96,10 +96,12 @@ def melt(n_chains: int, sites: int = 150, seed: int = 1, T: float = 500.0,
          density_g_cm3: float = 0.77, L: float | None = None, r_min: float = 0.27,
          p_trans: float = 0.6) -> dict:
     """One periodic melt: pos (N,3) wrapped in [0,L), vel (N,3), types (N,),
-    masses (N,), chain-major atom order (atom = chain*sites + index)."""
+    masses (N,), chain-major atom order (atom = chain*sites + index).  L is
+    rounded to a multiple of 2^-20 nm so that it is exact in FP32."""
     lib = _load()
     if L is None:
         L = box_length(n_chains, sites, density_g_cm3)
+    L = round(float(L) * 2**20) / 2**20     # every box side is exactly representable in FP32
     N = n_chains * sites
     pos = np.empty((N, 3), dtype=np.float64)
     relaxed = lib.cg_grow_chains(n_chains, sites, L, BOND, r_min, p_trans,

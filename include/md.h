@@ -162,6 +162,12 @@ int md_get_bins(md_system *sys, int32_t *cell_of, int32_t *cell_start, int32_t *
  * first count[i] of row i are meaningful).  cap = md_info's nbr_capacity. */
 int md_get_neighbors(md_system *sys, int32_t *count, int32_t *entries);
 
+/* FP32 cell-unit coordinates the force kernels read, [3 * N] in original
+ * order: u = x / h - (c + 1/2) for the atom's cell c at the last rebin
+ * (Sec. 3.1 cells of side h = L / M), moved by whole boxes for atoms that
+ * crossed a face since then.  For checking the position pipeline. */
+int md_get_cell_units(md_system *sys, float *u);
+
 /* Per-kernel GPU time recording.  When enabled, CUDA events bracket every
  * kernel group of each step (rebin, neighbour build, integrate, LJ, bonded)
  * and md_step / md_sync accumulate their durations.  ms_total[5] and

@@ -64,7 +64,7 @@ class md_energy_t(ctypes.Structure):
 
 EXPORTS = ["md_workspace_size", "md_create", "md_step", "md_step_async", "md_sync", "md_forces", "md_energy",
            "md_rebin", "md_get_state", "md_set_state", "md_set_params", "md_set_temperature", "md_stream",
-           "md_info", "md_get_bins", "md_get_neighbors", "md_profile_enable", "md_profile_read",
+           "md_info", "md_get_bins", "md_get_neighbors", "md_get_cell_units", "md_profile_enable", "md_profile_read",
            "md_profile_reset", "md_launches_per_call", "md_destroy", "md_last_error"]
 
 _lib = None
@@ -97,6 +97,7 @@ def load(path: str = LIB_PATH):
         "md_info": ([P, P, P, P, P], ctypes.c_int),
         "md_get_bins": ([P, P, P, P], ctypes.c_int),
         "md_get_neighbors": ([P, P, P], ctypes.c_int),
+        "md_get_cell_units": ([P, P], ctypes.c_int),
         "md_profile_enable": ([P, i32], ctypes.c_int),
         "md_profile_read": ([P, P, P], ctypes.c_int),
         "md_profile_reset": ([P], ctypes.c_int),
@@ -223,6 +224,12 @@ def md_get_neighbors(h, n_atoms: int, cap: int):
     cnt = np.empty(n_atoms, np.int32); ent = np.zeros((n_atoms, cap), np.int32)
     _check(load().md_get_neighbors(h, _p(cnt), _p(ent)), h)
     return cnt, ent
+
+
+def md_get_cell_units(h, n_atoms: int):
+    u = np.empty((n_atoms, 3), np.float32)
+    _check(load().md_get_cell_units(h, _p(u)), h)
+    return u
 
 
 def md_profile_enable(h, on: bool):

@@ -11,12 +11,7 @@
 // Sorted positions are stored in units of the cell side relative to the
 // centre of the atom's cell (|u| <= 1/2 at the rebin), so neighbour cells are
 // offset by exact integers and an FP32 coordinate carries about 2^-25 h.
-//
-// The neighbour list (Sec. 3.1, last paragraphs) is rebuilt from the cells
-// every `rebin_every` steps with radius r_c + skin.  One thread block per
-// home cell stages each of the 27 neighbour cells in shared memory; each
-// thread scans them for its home atom.  Exclusions (1-2, 1-3 neighbours only,
-// Sec. 3.1) are applied here, so the force kernel needs no exclusion test.
+// The neighbour list itself is built in k_lj.cu.
 #include "md_kernels.cuh"
 
 namespace mdg {
@@ -31,10 +26,14 @@ __device__ __forceinline__ int find_rep_by_cell(const RepDev* reps, int n_reps, 
   return lo;
 }
 
-// cell coordinate along one axis: s = x - L floor(x/L); k = floor(s * M/L)
+// cell coordinate along one axis: s = x - L floor(x/L); k = floor(s * M/L).
+// The integrator keeps x in [0, L), where the wrap leaves x unchanged, so the
+// FP64 division is only taken for positions outside the box.
 __device__ __forceinline__ int cell_coord(double x, double L, double inv_h, int M) {
-  double s = __dsub_rn(x, __dmul_rn(L, floor(__ddiv_rn(x, L))));
-  int k = (int)floor(__dmul_rn(s, inv_h));
+  double s = x;
+  if (__double_as_longlong(x) < 0 || __double_as_longlong(x) >= __double_as_longlong(L))
+    s = __dsub_rn(x, __dmul_rn(L, floor(__ddiv_rn(x, L))));
+  int k = __double2int_rd(__dmul_rn(s, inv_h));
   return k < 0 ? 0 : (k > M - 1 ? M - 1 : k);
 }
 
@@ -158,73 +157,6 @@ void launch_cell_sort(bool mixed, const void* x, int N, const int* cell_start, c
   else
     k_cell_sort<float><<<C, 128, 0, st>>>((const float*)x, N, cell_start, tmp, cellc, site, reps, n_reps, sites,
                                           perm, inv_perm, pos, tag, ref);
-}
-
-// --------------------------------------------------------------- neighbour list
-constexpr int kNbrBlock = 64;
-
-__global__ void __launch_bounds__(kNbrBlock) k_nbr_build(const float4* __restrict__ pos, const int* __restrict__ tag,
-                                                         const int* __restrict__ cell_start,
-                                                         const RepDev* __restrict__ reps, int n_reps,
-                                                         int* __restrict__ nbr, int* __restrict__ ncount, int cap,
-                                                         int Npad, unsigned* __restrict__ flags) {
-  __shared__ float4 sp[kNbrBlock];
-  __shared__ int st[kNbrBlock];
-  const int c = blockIdx.x;
-  const RepDev& R = reps[find_rep_by_cell(reps, n_reps, c)];
-  const int M = R.M, lc = c - R.cell_base;
-  const int cx = lc % M, cy = (lc / M) % M, cz = lc / (M * M);
-  const float rlist2 = R.rlist2u;
-  const int b = cell_start[c], n = cell_start[c + 1] - b;
-  for (int i0 = 0; i0 < n; i0 += kNbrBlock) {
-    const int i = i0 + threadIdx.x;
-    const bool active = i < n;
-    const int s = b + i;
-    float4 pi = active ? pos[s] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const int ti = active ? (tag[s] & (int)kTagMask) : 0;
-    int cnt = 0;
-    for (int k = 0; k < 27; ++k) {
-      const int ox = k % 3 - 1, oy = (k / 3) % 3 - 1, oz = k / 9 - 1;
-      const int nc = R.cell_base + (((cz + oz + M) % M) * M + ((cy + oy + M) % M)) * M + ((cx + ox + M) % M);
-      const int jb = cell_start[nc], jn = cell_start[nc + 1] - jb;
-      // in cell units the neighbour cell's centre sits at integer offset o
-      const float sx = pi.x - (float)ox, sy = pi.y - (float)oy, sz = pi.z - (float)oz;
-      for (int j0 = 0; j0 < jn; j0 += kNbrBlock) {
-        __syncthreads();
-        if (j0 + (int)threadIdx.x < jn) {
-          sp[threadIdx.x] = pos[jb + j0 + threadIdx.x];
-          st[threadIdx.x] = tag[jb + j0 + threadIdx.x];
-        }
-        __syncthreads();
-        const int m = min(kNbrBlock, jn - j0);
-        if (active) {
-          for (int q = 0; q < m; ++q) {
-            const float dx = sx - sp[q].x, dy = sy - sp[q].y, dz = sz - sp[q].z;
-            const float r2 = dx * dx + dy * dy + dz * dz;
-            const int tj = st[q];
-            const int dtag = ti - (tj & (int)kTagMask);
-            if (r2 < rlist2 && (dtag > 2 || dtag < -2)) {
-              if (cnt < cap)
-                nbr[(size_t)cnt * Npad + s] =
-                    (jb + j0 + q) | (k << kNbrIndexBits) | (int)(((unsigned)tj >> kTagTypeBit) << 31);
-              ++cnt;
-            }
-          }
-        }
-      }
-    }
-    if (active) {
-      ncount[s] = min(cnt, cap);
-      if (cnt > cap) atomicOr(flags, kFlagNbrOverflow);
-    }
-  }
-}
-
-void launch_nbr_build(const float4* pos, const int* tag, const int* cell_start, const RepDev* reps, int n_reps,
-                      int C, float rlist2, int* nbr, int* ncount, int cap, int Npad, unsigned* flags,
-                      cudaStream_t st) {
-  (void)rlist2;
-  k_nbr_build<<<C, kNbrBlock, 0, st>>>(pos, tag, cell_start, reps, n_reps, nbr, ncount, cap, Npad, flags);
 }
 
 }  // namespace mdg

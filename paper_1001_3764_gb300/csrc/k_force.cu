@@ -66,99 +66,6 @@ __device__ __forceinline__ long long to_fix(float f, unsigned* flags) {
   return __float2ll_rn(f * 4294967296.0f);
 }
 
-// ======================================================================= LJ
-constexpr int kEnergyVals = 8;   // lj, lj_shifted, vxx, vyy, vzz, vxy, vxz, vyz
-
-template <bool MIXED, bool ENERGY, int NT>
-__global__ void __launch_bounds__(NT) k_lj(const float4* __restrict__ pos, const int* __restrict__ tag,
-                                           const int* __restrict__ nbr, const int* __restrict__ ncount, int Npad,
-                                           const Tile* __restrict__ tiles, const RepDev* __restrict__ reps,
-                                           const ForceParams fp, void* __restrict__ flj, double* __restrict__ epart,
-                                           unsigned* __restrict__ flags) {
-  // neighbour-cell offsets o_k in cell units (k = (oz+1)*9 + (oy+1)*3 + ox+1)
-  __shared__ float ofx[27], ofy[27], ofz[27];
-  const Tile t = tiles[blockIdx.x];
-  if (threadIdx.x < 27) {
-    const int k = threadIdx.x;
-    ofx[k] = (float)(k % 3 - 1);
-    ofy[k] = (float)((k / 3) % 3 - 1);
-    ofz[k] = (float)(k / 9 - 1);
-  }
-  __syncthreads();
-  const RepDev& R = reps[t.rep];
-  const int s = t.start + threadIdx.x;
-  const bool active = (int)threadIdx.x < t.len;
-  float fx = 0.f, fy = 0.f, fz = 0.f;
-  float e = 0.f, es = 0.f, vxx = 0.f, vyy = 0.f, vzz = 0.f, vxy = 0.f, vxz = 0.f, vyz = 0.f;
-  if (active) {
-    const float4 pi = pos[s];
-    const int ti = (tag[s] >> kTagTypeBit) & 1;
-    // pair constants in cell units for j of type 0 and 1
-    const float a0 = 12.f * R.C12u[ti], b0 = 6.f * R.C6u[ti];
-    const float a1 = 12.f * R.C12u[ti + 1], b1 = 6.f * R.C6u[ti + 1];
-    const float rc2 = R.rc2u;
-    const int n = ncount[s];
-    const int* np = nbr + s;
-#pragma unroll 4
-    for (int q = 0; q < n; ++q) {
-      const int en = __ldg(np + (size_t)q * Npad);
-      const int j = en & (int)kNbrIndexMask;
-      const int k = (en >> kNbrIndexBits) & 31;
-      const float4 pj = __ldg(pos + j);
-      const float dx = (pi.x - pj.x) - ofx[k];
-      const float dy = (pi.y - pj.y) - ofy[k];
-      const float dz = (pi.z - pj.z) - ofz[k];
-      const float r2 = dx * dx + dy * dy + dz * dz;
-      const bool tj = en < 0;
-      const float A = tj ? a1 : a0, B = tj ? b1 : b0;
-      const float ir2 = r2 < rc2 ? rcp_approx(r2) : 0.f;
-      const float ir6 = ir2 * ir2 * ir2;
-      const float ff = ir2 * ir6 * (A * ir6 - B);
-      fx += ff * dx;
-      fy += ff * dy;
-      fz += ff * dz;
-      if (ENERGY) {
-        const float eij = ir6 * (R.C12u[ti + tj] * ir6 - R.C6u[ti + tj]);
-        if (r2 < rc2) {
-          e += eij;
-          es += eij - fp.erc[ti][tj];
-        }
-        vxx += dx * dx * ff; vyy += dy * dy * ff; vzz += dz * dz * ff;
-        vxy += dx * dy * ff; vxz += dx * dz * ff; vyz += dy * dz * ff;
-      }
-    }
-    // back from cell units: F = (sum ff_u du) / h
-    const float ih = R.ih_hi;
-    fx *= ih; fy *= ih; fz *= ih;
-    if (MIXED) {
-      F4i o;
-      o.x = to_fix(fx, flags); o.y = to_fix(fy, flags); o.z = to_fix(fz, flags); o.w = 0;
-      reinterpret_cast<F4i*>(flj)[s] = o;
-    } else {
-      reinterpret_cast<float4*>(flj)[s] = make_float4(fx, fy, fz, 0.f);
-    }
-  }
-  if (ENERGY) {
-    // full list: every pair is seen twice, hence the halves
-    double v[kEnergyVals] = {0.5 * e, 0.5 * es, 0.5 * vxx, 0.5 * vyy, 0.5 * vzz, 0.5 * vxy, 0.5 * vxz, 0.5 * vyz};
-    block_sum<kEnergyVals, NT>(v, epart + (size_t)blockIdx.x * kEnergyVals);
-  }
-}
-
-void launch_lj(bool mixed, bool energy, const float4* pos, const int* tag, const int* nbr, const int* ncount,
-               int Npad, const Tile* tiles, int n_tiles, const RepDev* reps, const ForceParams& fp, void* flj,
-               double* epart, unsigned* flags, int block, cudaStream_t st) {
-  (void)block;
-  constexpr int NT = 128;
-  if (mixed) {
-    if (energy) k_lj<true, true, NT><<<n_tiles, NT, 0, st>>>(pos, tag, nbr, ncount, Npad, tiles, reps, fp, flj, epart, flags);
-    else k_lj<true, false, NT><<<n_tiles, NT, 0, st>>>(pos, tag, nbr, ncount, Npad, tiles, reps, fp, flj, epart, flags);
-  } else {
-    if (energy) k_lj<false, true, NT><<<n_tiles, NT, 0, st>>>(pos, tag, nbr, ncount, Npad, tiles, reps, fp, flj, epart, flags);
-    else k_lj<false, false, NT><<<n_tiles, NT, 0, st>>>(pos, tag, nbr, ncount, Npad, tiles, reps, fp, flj, epart, flags);
-  }
-}
-
 // ======================================================================= bonded
 constexpr int kBondedBlock = 256;
 constexpr int kHalo = 3;
@@ -175,11 +82,31 @@ __device__ __forceinline__ f3 cross(f3 a, f3 b) {
   return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
 }
 
-// bond vector x_{m+1} - x_m under the minimum image
-__device__ __forceinline__ float bond_comp(double a, double b, double L, double hL) {
+// bond vector x_{m+1} - x_m under the minimum image (FP64 master); |d| > L/2
+// is tested on the bit patterns (integer pipe), which order like the values
+__device__ __forceinline__ double bond_diff(double a, double b, double L, double hL) {
   double d = b - a;
-  if (d > hL) d -= L; else if (d < -hL) d += L;
-  return __double2float_rn(d);
+  const long long bd = __double_as_longlong(d);
+  if ((bd & 0x7fffffffffffffffll) > __double_as_longlong(hL)) d = bd < 0 ? d + L : d - L;
+  return d;
+}
+
+// |b|^2 - b0^2 for an exact FP32 vector b: each square is split into its
+// rounded value and exact error (FMA), the rounded parts are summed with
+// error-free two-sums, and b0^2 = c_hi + c_lo is subtracted from the
+// leading part, where the two nearly cancel without rounding.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ float sq_minus(f3 b, float c_hi, float c_lo) {
+  const float px = b.x * b.x, py = b.y * b.y, pz = b.z * b.z;
+  const float ex = fmaf(b.x, b.x, -px), ey = fmaf(b.y, b.y, -py), ez = fmaf(b.z, b.z, -pz);
+  float s1, e1, s2, e2;
+  two_sum(px, py, s1, e1);
+  two_sum(s1, pz, s2, e2);
+  return (s2 - c_hi) + ((e1 + e2) + (ex + ey + ez) - c_lo);
 }
 // FP32 master: the difference of two nearby floats is exact; across a face the
 // partner is first moved by L (exact when it lies near the face, L being an
@@ -205,6 +132,7 @@ __global__ void __launch_bounds__(kBondedBlock) k_bonded(const void* __restrict_
   using T = typename std::conditional<MIXED, double, float>::type;
   const T* x = reinterpret_cast<const T*>(xv);
   __shared__ f3 bv[kBondedBlock + 2 * kHalo];
+  __shared__ float bD[kBondedBlock + 2 * kHalo];   // r^2 - b0^2 of each bond, free of cancellation
   __shared__ f3 fbd[kBondedBlock], fan_a[kBondedBlock], fan_c[kBondedBlock];
   __shared__ f3 fdi1[kBondedBlock], fdi2[kBondedBlock], fdi3[kBondedBlock];
   const Tile t = tiles[blockIdx.x];
@@ -216,18 +144,23 @@ __global__ void __launch_bounds__(kBondedBlock) k_bonded(const void* __restrict_
   for (int q = threadIdx.x; q < t.len + 2 * kHalo; q += blockDim.x) {
     const int m = base + q;
     f3 b = mk(0.f, 0.f, 0.f);
+    float D = 0.f;
     if (m >= lo && m + 1 < hi && site[m] < S - 1) {
       if (MIXED) {
-        b.x = bond_comp((double)x[m], (double)x[m + 1], R.L, R.half_L);
-        b.y = bond_comp((double)x[N + m], (double)x[N + m + 1], R.L, R.half_L);
-        b.z = bond_comp((double)x[2 * N + m], (double)x[2 * N + m + 1], R.L, R.half_L);
+        const double dx = bond_diff((double)x[m], (double)x[m + 1], R.L, R.half_L);
+        const double dy = bond_diff((double)x[N + m], (double)x[N + m + 1], R.L, R.half_L);
+        const double dz = bond_diff((double)x[2 * N + m], (double)x[2 * N + m + 1], R.L, R.half_L);
+        b = mk(__double2float_rn(dx), __double2float_rn(dy), __double2float_rn(dz));
+        D = __double2float_rn(fma(dx, dx, fma(dy, dy, fma(dz, dz, -fp.b0sq))));
       } else {
         b.x = bond_comp((float)x[m], (float)x[m + 1], R.Lf, R.half_Lf);
         b.y = bond_comp((float)x[N + m], (float)x[N + m + 1], R.Lf, R.half_Lf);
         b.z = bond_comp((float)x[2 * N + m], (float)x[2 * N + m + 1], R.Lf, R.half_Lf);
+        D = sq_minus(b, fp.b0sq_hi, fp.b0sq_lo);
       }
     }
     bv[q] = b;
+    bD[q] = D;
   }
   __syncthreads();
   // 2. terms starting at atom m = base + q
@@ -244,7 +177,7 @@ __global__ void __launch_bounds__(kBondedBlock) k_bonded(const void* __restrict_
       if (sm <= S - 2) {               // bond (m, m+1), Eq. (4)
         const f3 b = bv[q];
         const float r = sqrtf(dot(b, b));
-        const float dr = r - fp.b0;
+        const float dr = bD[q] / (r + fp.b0);   // r - b0 without cancellation
         const float g = fp.kb * dr / r;
         fb = g * b;                    // force on atom m
         if (ENERGY && own) { Eb += 0.5f * fp.kb * dr * dr; add_vir(W, b, -fb); }

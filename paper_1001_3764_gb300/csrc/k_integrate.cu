@@ -32,6 +32,11 @@ __device__ __forceinline__ double warp_sum_i(double v) {
 
 constexpr int kIntBlock = 256;
 
+__device__ __forceinline__ bool past_box(double x, double L) { return __double_as_longlong(x) >= __double_as_longlong(L); }
+__device__ __forceinline__ bool past_box(float x, float L) { return __float_as_int(x) >= __float_as_int(L); }
+__device__ __forceinline__ bool negative(double x) { return __double_as_longlong(x) < 0; }
+__device__ __forceinline__ bool negative(float x) { return __float_as_int(x) < 0; }
+
 template <bool MIXED, int MODE, bool KE, bool THERMO>
 __global__ void __launch_bounds__(kIntBlock) k_integrate(void* __restrict__ xv, void* __restrict__ vv,
                                                          int* __restrict__ img, const void* __restrict__ Fv,
@@ -44,7 +49,7 @@ __global__ void __launch_bounds__(kIntBlock) k_integrate(void* __restrict__ xv, 
                                                          const ForceParams fp, double* __restrict__ kepart,
                                                          unsigned* __restrict__ done, double* __restrict__ ke_out,
                                                          double* __restrict__ lam, double tau,
-                                                         unsigned* __restrict__ flags) {
+                                                         unsigned* __restrict__ flags, const double* __restrict__ kt) {
   using T = typename std::conditional<MIXED, double, float>::type;
   T* x = reinterpret_cast<T*>(xv);
   T* v = reinterpret_cast<T*>(vv);
@@ -55,18 +60,24 @@ __global__ void __launch_bounds__(kIntBlock) k_integrate(void* __restrict__ xv, 
   if ((int)threadIdx.x < t.len) {
     const int sm = site[i];
     const int type = (sm == 0 || sm == fp.sites - 1) ? 1 : 0;
-    const T hdt_m = (T)(0.5 * fp.dt * fp.inv_mass[type]);
+    // mixed form: F stays in fixed-point units (int64 -> FP64 is a fast
+    // conversion) and 2^-32 is folded into dt / 2m
+    T hdt_m;
+    if constexpr (MIXED) hdt_m = fp.hdt_m_fix[type]; else hdt_m = fp.hdt_m_f[type];
     T F[3] = {(T)0, (T)0, (T)0};
     if (MODE == kKineticOnly) {
     } else if (MIXED) {
       const F4i f = reinterpret_cast<const F4i*>(Fv)[i];
-      F[0] = (T)((double)f.x * kFixInv); F[1] = (T)((double)f.y * kFixInv); F[2] = (T)((double)f.z * kFixInv);
+      F[0] = (T)(double)f.x; F[1] = (T)(double)f.y; F[2] = (T)(double)f.z;
     } else {
       const float4 f = reinterpret_cast<const float4*>(Fv)[i];
       F[0] = f.x; F[1] = f.y; F[2] = f.z;
     }
     T vi[3] = {v[i], v[N + i], v[2 * N + i]};
-    if (MODE == kKickKickDrift || MODE == kKickOnly) {
+    // Without a kinetic-energy read-out the two half kicks of KKD are one
+    // kick of dt F/m (the full-step velocity is never needed in between).
+    constexpr bool kMerged = MODE == kKickKickDrift && !KE;
+    if ((MODE == kKickKickDrift && KE) || MODE == kKickOnly) {
 #pragma unroll
       for (int a = 0; a < 3; ++a) vi[a] += hdt_m * F[a];   // v(t): close the previous step
     }
@@ -82,8 +93,8 @@ __global__ void __launch_bounds__(kIntBlock) k_integrate(void* __restrict__ xv, 
 #pragma unroll
         for (int a = 0; a < 3; ++a) vi[a] *= l;
       }
-      const T dt = (T)fp.dt;
-      const T L = (T)R.L;
+      T dt, L;
+      if constexpr (MIXED) { dt = fp.dt; L = R.L; } else { dt = fp.dt_f; L = R.Lf; }
       const int cc = cellc[i];
       const float4 r0 = ref[i];
       const float r0a[3] = {r0.x, r0.y, r0.z};
@@ -92,22 +103,25 @@ __global__ void __launch_bounds__(kIntBlock) k_integrate(void* __restrict__ xv, 
       bool bad = false;
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        vi[a] += hdt_m * F[a];
+        vi[a] = kMerged ? vi[a] + (hdt_m + hdt_m) * F[a] : vi[a] + hdt_m * F[a];
         T xa = x[a * N + i] + dt * vi[a];
-        if (xa >= L) { xa -= L; img[a * N + i] += 1; }
-        else if (xa < (T)0) { xa += L; img[a * N + i] -= 1; if (xa >= L) xa = (T)0; }
+        // wrap into [0, L): for non-negative IEEE numbers the bit patterns
+        // order like the values, so the tests run on the integer pipe
+        if (past_box(xa, L)) { xa -= L; img[a * N + i] += 1; }
+        else if (negative(xa)) { xa += L; img[a * N + i] -= 1; if (past_box(xa, L)) xa = (T)0; }
         x[a * N + i] = xa;
         v[a * N + i] = vi[a];
         // cell units in the frame of the rebin cell; an atom that crossed a
         // face since the rebin is moved back by one box (M cell units)
         const int c = (cc >> (10 * a)) & 1023;
-        float ua = cell_unit(xa, c, 0, R);
+        float ua;
+        if constexpr (MIXED) ua = cell_unit_t(xa, c, R, kt); else ua = cell_unit(xa, c, 0, R);
         const float du = ua - r0a[a];
         if (du > halfM || du < -halfM) ua = cell_unit(xa, c, du > halfM ? -1 : 1, R);
         loc[a] = ua;
         const float d = ua - r0a[a];
         d2 += d * d;
-        bad |= !isfinite(xa) || !isfinite(vi[a]);
+        bad |= !isfinite(ua);          // a non-finite x or v reaches u
       }
       if (d2 > R.hs2u) atomicOr(flags, kFlagDisplacement);
       if (bad) atomicOr(flags, kFlagNaN);
@@ -145,16 +159,35 @@ __global__ void __launch_bounds__(kIntBlock) k_integrate(void* __restrict__ xv, 
   }
 }
 
+// kt[c] = c + 1/2 for the FP64 cell-unit conversion; one copy per device
+__device__ double g_centre[1024];
+__global__ void k_fill_centre() {
+  for (int c = threadIdx.x; c < 1024; c += blockDim.x) g_centre[c] = (double)c + 0.5;
+}
+const double* centre_table() {
+  static int filled_on = -1;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (filled_on != dev) {      // once per device (a process normally uses one)
+    k_fill_centre<<<1, 256>>>();
+    cudaDeviceSynchronize();
+    filled_on = dev;
+  }
+  void* p = nullptr;
+  cudaGetSymbolAddress(&p, g_centre);
+  return (const double*)p;
+}
+
 template <bool MIXED>
 static void launch_int_t(IntegMode mode, bool ke, bool th, void* x, void* v, int* img, const void* F,
                          const uint16_t* site, const int* cellc, const int* inv_perm, const float4* ref, float4* pos,
                          int N, const Tile* tiles, int n_tiles, const RepDev* reps, int n_reps,
                          const ForceParams& fp, double* kepart, unsigned* done, double* ke_out, double* lam,
-                         double tau, unsigned* flags, cudaStream_t st) {
+                         double tau, unsigned* flags, const double* kt, cudaStream_t st) {
 #define MDG_INT(MODE, KE, TH)                                                                                   \
   k_integrate<MIXED, MODE, KE, TH><<<n_tiles, kIntBlock, 0, st>>>(x, v, img, F, site, cellc, inv_perm, ref,     \
                                                                   pos, N, tiles, reps, n_reps, fp, kepart, done, \
-                                                                  ke_out, lam, tau, flags)
+                                                                  ke_out, lam, tau, flags, kt)
   // With the thermostat on, every step that starts (KD, KKD) takes the
   // temperature of the unscaled v(t_k), scales v(t_k) by the factor of the
   // previous step and leaves the factor of step k for the next one.  The
@@ -178,41 +211,44 @@ void launch_integrate(bool mixed, IntegMode mode, bool ke, bool thermostat, void
                       const void* F, const uint16_t* site, const int* cellc, const int* inv_perm, const float4* ref,
                       float4* pos, int N, const Tile* tiles, int n_tiles, const RepDev* reps, int n_reps,
                       const ForceParams& fp, double* kepart, unsigned* done, double* ke_out, double* lam,
-                      double tau, unsigned* flags, cudaStream_t st) {
+                      double tau, unsigned* flags, const double* kt, cudaStream_t st) {
   if (mixed)
     launch_int_t<true>(mode, ke, thermostat, x, v, img, F, site, cellc, inv_perm, ref, pos, N, tiles, n_tiles, reps,
-                       n_reps, fp, kepart, done, ke_out, lam, tau, flags, st);
+                       n_reps, fp, kepart, done, ke_out, lam, tau, flags, kt, st);
   else
     launch_int_t<false>(mode, ke, thermostat, x, v, img, F, site, cellc, inv_perm, ref, pos, N, tiles, n_tiles, reps,
-                        n_reps, fp, kepart, done, ke_out, lam, tau, flags, st);
+                        n_reps, fp, kepart, done, ke_out, lam, tau, flags, kt, st);
 }
 
 // ---------------------------------------------------------------- energy reduction
+// LJ partials are per cell (replica r owns cells [cell_base, cell_base + M^3)),
+// bonded partials per integrator tile.  Fixed summation order.
 // out[r*16 + k]: k = 0 lj, 1 lj_shifted, 2 bond, 3 angle, 4 dihedral, 5..10 virial
 __global__ void k_energy_reduce(const double* __restrict__ lj_part, const double* __restrict__ b_part,
-                                const Tile* __restrict__ lj_tiles, int n_lj_tiles,
-                                const Tile* __restrict__ b_tiles, int n_b_tiles, int n_reps, double* __restrict__ out) {
+                                const RepDev* __restrict__ reps, const Tile* __restrict__ b_tiles, int n_b_tiles,
+                                int n_reps, double* __restrict__ out) {
   for (int r = threadIdx.x; r < n_reps; r += blockDim.x) {
     double acc[11] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-    for (int q = 0; q < n_lj_tiles; ++q) {
-      if (lj_tiles[q].rep != r) continue;
-      const double* p = lj_part + (size_t)q * 8;
+    const RepDev& R = reps[r];
+    const int c0 = R.cell_base, c1 = R.cell_base + R.M * R.M * R.M;
+    for (int c = c0; c < c1; ++c) {
+      const double* p = lj_part + (size_t)c * 8;
       acc[0] += p[0]; acc[1] += p[1];
       for (int k = 0; k < 6; ++k) acc[5 + k] += p[2 + k];
     }
-    for (int q = 0; q < n_b_tiles; ++q) {
-      if (b_tiles[q].rep != r) continue;
+    for (int q = R.tile_off; q < R.tile_off + R.n_tiles; ++q) {
       const double* p = b_part + (size_t)q * 9;
       acc[2] += p[0]; acc[3] += p[1]; acc[4] += p[2];
       for (int k = 0; k < 6; ++k) acc[5 + k] += p[3 + k];
     }
     for (int k = 0; k < 11; ++k) out[r * 16 + k] = acc[k];
   }
+  (void)b_tiles; (void)n_b_tiles;
 }
 
-void launch_energy_reduce(const double* lj_part, const double* b_part, const Tile* lj_tiles, int n_lj_tiles,
-                          const Tile* b_tiles, int n_b_tiles, int n_reps, double* out, cudaStream_t st) {
-  k_energy_reduce<<<1, 256, 0, st>>>(lj_part, b_part, lj_tiles, n_lj_tiles, b_tiles, n_b_tiles, n_reps, out);
+void launch_energy_reduce(const double* lj_part, const double* b_part, const RepDev* reps, const Tile* b_tiles,
+                          int n_b_tiles, int n_reps, double* out, cudaStream_t st) {
+  k_energy_reduce<<<1, 256, 0, st>>>(lj_part, b_part, reps, b_tiles, n_b_tiles, n_reps, out);
 }
 
 }  // namespace mdg

@@ -1,0 +1,378 @@
+// k_lj.cu -- neighbour list (Sec. 3.1) and Lennard-Jones force (Eq. 2,
+// Sec. 3.2) over shared-memory tiles of the 27 cells around a home cell.
+//
+// One thread block per home cell.  The block stages the atoms of the 27
+// neighbour cells (k = (oz+1)*9 + (oy+1)*3 + ox+1, each cell in sorted order)
+// in shared memory, moved into the home cell's frame: w_j = u_j + o_k in cell
+// units (|w| < 1.6, so FP32 keeps ~6e-8 of a cell side).  A pair separation is
+// then u_i - w_j.  The paper's neighbour-search kernel also assigns a block to
+// a grid cell and stages the 27 cells (Sec. 3.1, last paragraph); here the
+// same staging serves the force kernel, and the list stores 16-bit indices
+// into the staged tile (bit 15 = type of j) instead of global atom ids.
+//
+// List build: every thread scans the whole tile for its home atom (cutoff
+// r_c + skin, 1-2 and 1-3 neighbours excluded, Sec. 3.1), keeps its entries
+// in shared memory and the block writes them out row by row (coalesced).
+//
+// Force: up to four threads share one home atom (entries q = p, p+T, ...),
+// and their partial sums are added in a fixed order, so the result does not
+// depend on scheduling.  Each pair follows the Sec. 3.2 listing: r2inv = 0
+// when r^2 >= r_c^2.
+#include "md_kernels.cuh"
+
+namespace mdg {
+
+constexpr int kStageCapMax = 6144;  // largest 27-cell tile (96 KB of float4); the staged index has 15 bits
+constexpr int kLjBlock = 128;
+
+__device__ __forceinline__ int find_rep_cell(const RepDev* reps, int n_reps, int c) {
+  int lo = 0, hi = n_reps - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (reps[mid].cell_base <= c) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Neighbour-cell table of home cell c: start[k] of each cell's atoms in sorted
+// order and off[k] = position of cell k's first atom in the tile; off[27] =
+// tile size.  Threads 0..31 fill it (one warp scan).
+struct CellTile {
+  int start[27];
+  int off[28];
+  float ox[27], oy[27], oz[27];
+};
+
+__device__ __forceinline__ void tile_setup(CellTile& T, int c, const RepDev& R, const int* __restrict__ cell_start) {
+  if (threadIdx.x < 32) {
+    const int k = threadIdx.x;
+    int n = 0;
+    if (k < 27) {
+      const int M = R.M, lc = c - R.cell_base;
+      const int cx = lc % M, cy = (lc / M) % M, cz = lc / (M * M);
+      const int ox = k % 3 - 1, oy = (k / 3) % 3 - 1, oz = k / 9 - 1;
+      const int nc = R.cell_base + (((cz + oz + M) % M) * M + ((cy + oy + M) % M)) * M + ((cx + ox + M) % M);
+      T.start[k] = cell_start[nc];
+      n = cell_start[nc + 1] - T.start[k];
+      T.ox[k] = (float)ox; T.oy[k] = (float)oy; T.oz[k] = (float)oz;
+    }
+    int incl = n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (k >= o) incl += v;
+    }
+    if (k < 27) T.off[k] = incl - n;
+    if (k == 26) T.off[27] = incl;
+  }
+  __syncthreads();
+}
+
+// Copy the tile into shared memory, shifted into the home cell's frame: warp
+// w copies cells k = w, w + nwarps, ... (each cell is one contiguous run of
+// sorted atoms).
+template <bool WITH_TAG>
+__device__ __forceinline__ void tile_load(const CellTile& T, const float4* __restrict__ pos, const int* __restrict__ tag,
+                                          float4* __restrict__ sp) {
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int k = threadIdx.x >> 5; k < 27; k += nw) {
+    const int n = T.off[k + 1] - T.off[k], j0 = T.start[k], t0 = T.off[k];
+    const float ox = T.ox[k], oy = T.oy[k], oz = T.oz[k];
+    for (int q = lane; q < n; q += 32) {
+      float4 p = __ldg(pos + j0 + q);
+      p.x += ox; p.y += oy; p.z += oz;
+      p.w = WITH_TAG ? __int_as_float(__ldg(tag + j0 + q)) : 0.f;
+      sp[t0 + q] = p;
+    }
+  }
+}
+
+// ===================================================================== build
+// List layout: blocks of 8 entries, block q of sorted atom s is nbr[q * Npad
+// + s], so one 16-byte load gives a thread 8 entries and a warp reads 512
+// contiguous bytes.  ncount[s] is the number of blocks.  Unused slots hold the
+// tile's sentinel index (= tile size): a staged atom placed far outside the
+// cutoff, so a padded slot adds exactly zero force and energy.
+//
+// TP adjacent threads share a home atom; thread p scans 32-atom words
+// p, p + TP, ... of the tile, forms the word's in-range bit mask in a register,
+// drops 1-2/1-3 neighbours and itself (tag test, Sec. 3.1) while turning the
+// set bits into entries, and writes its blocks at p, p + TP, ...; the TP
+// threads then pad to a common number of blocks.
+constexpr int kBuildThreads = 128;
+
+__device__ __forceinline__ uint4 pack_block(unsigned long long lo, unsigned long long hi) {
+  return make_uint4((unsigned)lo, (unsigned)(lo >> 32), (unsigned)hi, (unsigned)(hi >> 32));
+}
+
+__global__ void __launch_bounds__(kBuildThreads) k_nbr_tile(const float4* __restrict__ pos, const int* __restrict__ tag,
+                                                            const int* __restrict__ cell_start,
+                                                            const RepDev* __restrict__ reps, int n_reps,
+                                                            uint4* __restrict__ nbr, int* __restrict__ ncount, int cap,
+                                                            int Npad, int tile_cap, unsigned* __restrict__ flags) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  float4* sp = reinterpret_cast<float4*>(smem);
+  __shared__ CellTile T;
+  const int c = blockIdx.x;
+  const int b = cell_start[c], n = cell_start[c + 1] - b;
+  if (n == 0) return;
+  const RepDev& R = reps[find_rep_cell(reps, n_reps, c)];
+  tile_setup(T, c, R, cell_start);
+  const int total = T.off[27];
+  const int nwords = (total + 32) >> 5;            // room for the sentinel at index total
+  if (nwords * 32 > tile_cap) {
+    if (threadIdx.x == 0) atomicOr(flags, kFlagNbrOverflow);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) ncount[b + i] = 0;
+    return;
+  }
+  tile_load<true>(T, pos, tag, sp);
+  for (int t = total + threadIdx.x; t < nwords * 32; t += blockDim.x) sp[t] = make_float4(1e9f, 1e9f, 1e9f, 0.f);
+  __syncthreads();
+  const float rl2 = R.rlist2u;
+  const unsigned long long sent = (unsigned long long)total;
+  const unsigned long long sent4 = sent | (sent << 16) | (sent << 32) | (sent << 48);
+  const int TP = n >= 64 ? 1 : (n >= 32 ? 2 : 4);
+  const int per_pass = kBuildThreads / TP;
+  const int capb = cap >> 3;
+  for (int a0 = 0; a0 < n; a0 += per_pass) {
+    const int a = a0 + (int)threadIdx.x / TP, p = (int)threadIdx.x % TP;
+    const bool active = a < n;
+    const int s = b + a;
+    int nb = 0, cnt = 0;
+    if (active) {
+      const float4 pi = pos[s];
+      const int ti = tag[s] & (int)kTagMask;
+      unsigned long long lo = 0ull, hi = 0ull;
+      for (int wd = p; wd < nwords; wd += TP) {
+        const float4* w32 = sp + wd * 32;
+        unsigned m = 0u;
+#pragma unroll
+        for (int u = 0; u < 32; ++u) {
+          const float4 w = w32[u];
+          const float dx = pi.x - w.x, dy = pi.y - w.y, dz = pi.z - w.z;
+          const float r2 = dx * dx + dy * dy + dz * dz;
+          m |= (r2 < rl2 ? 1u : 0u) << u;
+        }
+        while (m) {
+          const int u = __ffs(m) - 1;
+          m &= m - 1u;
+          const int t = wd * 32 + u;
+          const int tj = __float_as_int(w32[u].w);
+          const int dtag = ti - (tj & (int)kTagMask);
+          if (dtag <= 2 && dtag >= -2) continue;          // itself, 1-2 and 1-3 neighbours
+          const unsigned long long e = (unsigned long long)(t | (((unsigned)tj >> kTagTypeBit) << 15));
+          const int slot = cnt & 7;
+          if (slot < 4) lo |= e << (16 * slot); else hi |= e << (16 * (slot - 4));
+          if (slot == 7) {
+            const int q = p + TP * nb;
+            if (q < capb) nbr[(size_t)q * Npad + s] = pack_block(lo, hi);
+            ++nb;
+            lo = 0ull; hi = 0ull;
+          }
+          ++cnt;
+        }
+      }
+      const int rem = cnt & 7;
+      if (rem) {                                          // pad the open block with the sentinel
+        const unsigned long long fill = ~0ull << (16 * (rem < 4 ? rem : rem - 4));
+        if (rem < 4) { lo |= sent4 & fill; hi = sent4; } else { hi |= sent4 & fill; }
+        const int q = p + TP * nb;
+        if (q < capb) nbr[(size_t)q * Npad + s] = pack_block(lo, hi);
+        ++nb;
+      }
+    }
+    // common block count of the TP threads of an atom (adjacent lanes)
+    int mb = nb;
+    if (TP >= 2) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, 1));
+    if (TP >= 4) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, 2));
+    if (active) {
+      for (int k = nb; k < mb; ++k) {
+        const int q = p + TP * k;
+        if (q < capb) nbr[(size_t)q * Npad + s] = pack_block(sent4, sent4);
+      }
+      const int nblk = TP * mb;
+      if (p == 0) {
+        ncount[s] = min(nblk, capb);
+        if (nblk > capb) atomicOr(flags, kFlagNbrOverflow);
+      }
+    }
+  }
+}
+
+size_t nbr_tile_smem(int tile_cap) { return (size_t)tile_cap * sizeof(float4); }
+
+void launch_nbr_tile(const float4* pos, const int* tag, const int* cell_start, const RepDev* reps, int n_reps, int C,
+                     uint4* nbr, int* ncount, int cap, int Npad, int tile_cap, unsigned* flags, cudaStream_t st) {
+  k_nbr_tile<<<C, kBuildThreads, nbr_tile_smem(tile_cap), st>>>(pos, tag, cell_start, reps, n_reps, nbr, ncount, cap,
+                                                                Npad, tile_cap, flags);
+}
+
+// ===================================================================== force
+constexpr int kEnergyVals = 8;   // lj, lj_shifted, vxx, vyy, vzz, vxy, vxz, vyz
+
+__device__ __forceinline__ long long fix_of(float f, unsigned* flags) {
+  if (!(fabsf(f) < 2.0e9f)) { atomicOr(flags, kFlagFixOverflow); return 0; }
+  return __float2ll_rn(f * 4294967296.0f);
+}
+
+// one pair of Eq. (2) in cell units (Sec. 3.2 listing: r2inv = 0 beyond r_c)
+template <bool ENERGY>
+__device__ __forceinline__ void lj_pair(unsigned en, const float4* __restrict__ sp, const float4& pi, float rc2, float a0c,
+                                        float b0c, float a1c, float b1c, int ti, const RepDev& R, const ForceParams& fp,
+                                        float& fx, float& fy, float& fz, float (&ev)[8]) {
+  const float4 w = sp[en & 0x7fffu];
+  const bool tj = (en >> 15) != 0;
+  const float dx = pi.x - w.x, dy = pi.y - w.y, dz = pi.z - w.z;
+  const float r2 = dx * dx + dy * dy + dz * dz;
+  const float A = tj ? a1c : a0c, B = tj ? b1c : b0c;
+  const float ir2 = r2 < rc2 ? rcp_approx(r2) : 0.f;
+  const float ir6 = ir2 * ir2 * ir2;
+  const float ff = ir2 * ir6 * (A * ir6 - B);
+  fx += ff * dx;
+  fy += ff * dy;
+  fz += ff * dz;
+  if (ENERGY) {
+    const int tt = ti + (int)tj;
+    const float eij = ir6 * (R.C12u[tt] * ir6 - R.C6u[tt]);
+    if (r2 < rc2) {
+      ev[0] += eij;
+      ev[1] += eij - fp.erc[ti][tj];
+    }
+    ev[2] += dx * dx * ff; ev[3] += dy * dy * ff; ev[4] += dz * dz * ff;
+    ev[5] += dx * dy * ff; ev[6] += dx * dz * ff; ev[7] += dy * dz * ff;
+  }
+}
+
+template <bool MIXED, bool ENERGY>
+__global__ void __launch_bounds__(kLjBlock) k_lj_tile(const float4* __restrict__ pos, const int* __restrict__ tag,
+                                                      const int* __restrict__ cell_start,
+                                                      const uint4* __restrict__ nbr, const int* __restrict__ ncount,
+                                                      int Npad, int tile_cap, const RepDev* __restrict__ reps, int n_reps,
+                                                      const ForceParams fp, void* __restrict__ flj,
+                                                      double* __restrict__ epart, unsigned* __restrict__ flags) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  float4* sp = reinterpret_cast<float4*>(smem);      // the tile, tile_cap entries
+  __shared__ CellTile T;
+  __shared__ double red[kEnergyVals][kLjBlock / 32];
+  const int c = blockIdx.x;
+  const int b = cell_start[c], n = cell_start[c + 1] - b;
+  float ev[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  const RepDev& R = reps[find_rep_cell(reps, n_reps, c)];
+  int total = 0;
+  if (n > 0) {
+    tile_setup(T, c, R, cell_start);
+    total = T.off[27];
+  }
+  if (n > 0 && ((total + 32) & ~31) <= tile_cap) {
+    tile_load<false>(T, pos, tag, sp);
+    if (threadIdx.x == 0) sp[total] = make_float4(1e9f, 1e9f, 1e9f, 0.f);   // sentinel slot
+    __syncthreads();
+    // TP adjacent lanes share one home atom: entry blocks p, p + TP, ...
+    const int TP = n >= kLjBlock / 2 ? 1 : (n >= kLjBlock / 4 ? 2 : 4);
+    const float rc2 = R.rc2u;
+    const float ih = R.ih_hi;
+    for (int a0 = 0; a0 < n; a0 += kLjBlock / TP) {
+      const int na = min(kLjBlock / TP, n - a0);
+      const int a = a0 + (int)threadIdx.x / TP, p = (int)threadIdx.x % TP;
+      const bool active = a < a0 + na;
+      float fx = 0.f, fy = 0.f, fz = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+      if (active) {
+        const int s = b + a;
+        const float4 pi = pos[s];
+        const int ti = (tag[s] >> kTagTypeBit) & 1;
+        const float a0c = 12.f * R.C12u[ti], b0c = 6.f * R.C6u[ti];
+        const float a1c = 12.f * R.C12u[ti + 1], b1c = 6.f * R.C6u[ti + 1];
+        const int nblk = ncount[s];
+        const uint4* np = nbr + s;
+        int blk = p;
+        uint4 E = blk < nblk ? __ldg(np + (size_t)blk * Npad) : make_uint4(0u, 0u, 0u, 0u);
+        while (blk < nblk) {
+          const int nb = blk + TP;
+          const uint4 En = nb < nblk ? __ldg(np + (size_t)nb * Npad) : make_uint4(0u, 0u, 0u, 0u);   // prefetch
+          const unsigned ew[4] = {E.x, E.y, E.z, E.w};
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            lj_pair<ENERGY>(ew[u] & 0xffffu, sp, pi, rc2, a0c, b0c, a1c, b1c, ti, R, fp, fx, fy, fz, ev);
+            lj_pair<ENERGY>(ew[u] >> 16, sp, pi, rc2, a0c, b0c, a1c, b1c, ti, R, fp, gx, gy, gz, ev);
+          }
+          E = En;
+          blk = nb;
+        }
+      }
+      fx += gx; fy += gy; fz += gz;
+      // sum the TP partial forces of an atom (adjacent lanes, fixed order)
+      if (TP >= 2) {
+        fx += __shfl_down_sync(0xffffffffu, fx, 1); fy += __shfl_down_sync(0xffffffffu, fy, 1); fz += __shfl_down_sync(0xffffffffu, fz, 1);
+      }
+      if (TP >= 4) {
+        fx += __shfl_down_sync(0xffffffffu, fx, 2); fy += __shfl_down_sync(0xffffffffu, fy, 2); fz += __shfl_down_sync(0xffffffffu, fz, 2);
+      }
+      if (active && p == 0) {
+        fx *= ih; fy *= ih; fz *= ih;             // back from cell units
+        const int s = b + a;
+        if (MIXED) {
+          F4i o;
+          o.x = fix_of(fx, flags); o.y = fix_of(fy, flags); o.z = fix_of(fz, flags); o.w = 0;
+          reinterpret_cast<F4i*>(flj)[s] = o;
+        } else {
+          reinterpret_cast<float4*>(flj)[s] = make_float4(fx, fy, fz, 0.f);
+        }
+      }
+    }
+  } else if (n > 0 && threadIdx.x == 0) {
+    atomicOr(flags, kFlagNbrOverflow);
+  }
+  if (ENERGY) {
+    double v[kEnergyVals];
+#pragma unroll
+    for (int k = 0; k < kEnergyVals; ++k) v[k] = 0.5 * (double)ev[k];   // full list: every pair twice
+    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < kEnergyVals; ++k) {
+      double sv = v[k];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sv += __shfl_down_sync(0xffffffffu, sv, o);
+      if (lane == 0) red[k][wi] = sv;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int k = 0; k < kEnergyVals; ++k) {
+        double sv = 0.0;
+        for (int q = 0; q < kLjBlock / 32; ++q) sv += red[k][q];
+        epart[(size_t)c * kEnergyVals + k] = sv;
+      }
+    }
+  }
+}
+
+void launch_lj_tile(bool mixed, bool energy, const float4* pos, const int* tag, const int* cell_start,
+                    const uint4* nbr, const int* ncount, int Npad, int tile_cap, const RepDev* reps, int n_reps, int C,
+                    const ForceParams& fp, void* flj, double* epart, unsigned* flags, cudaStream_t st) {
+  const size_t sm = (size_t)tile_cap * sizeof(float4);
+#define MDG_LJ(M, E) k_lj_tile<M, E><<<C, kLjBlock, sm, st>>>(pos, tag, cell_start, nbr, ncount, Npad, tile_cap, reps, n_reps, fp, flj, epart, flags)
+  if (mixed) { if (energy) MDG_LJ(true, true); else MDG_LJ(true, false); }
+  else { if (energy) MDG_LJ(false, true); else MDG_LJ(false, false); }
+#undef MDG_LJ
+}
+
+// Opt in to more than 48 KB of dynamic shared memory (once per device); the
+// attribute is an upper bound, set for the largest tile accepted.
+cudaError_t tile_kernels_init() {
+  const int mx = kStageCapMax * sizeof(float4);
+  cudaError_t e = cudaFuncSetAttribute(k_nbr_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_lj_tile<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_lj_tile<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_lj_tile<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_lj_tile<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  return e;
+}
+
+int tile_capacity_max() { return kStageCapMax; }
+
+}  // namespace mdg

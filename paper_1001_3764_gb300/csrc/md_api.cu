@@ -17,7 +17,6 @@ using namespace mdg;
 
 namespace {
 
-constexpr int kLjTile = 128;     // atoms per LJ block (sorted order)
 constexpr int kIntTile = 224;    // atoms per integrator / bonded block (original order)
 constexpr int kNumProf = 5;      // rebin, neighbour build, integrate, lj, bonded
 constexpr double kKB = 0.0083144626;
@@ -38,24 +37,27 @@ struct md_system {
   md_params params{};
   ForceParams fp{};
   std::vector<RepDev> reps_h;
-  std::vector<Tile> t_lj, t_int;
+  std::vector<Tile> t_int;
   std::vector<double> T0;
   // memory
   char* base = nullptr;
   size_t bytes = 0;
   bool own_mem = false;
   RepDev* reps = nullptr;
-  Tile *tiles_lj = nullptr, *tiles_int = nullptr;
+  Tile* tiles_int = nullptr;
   void *x = nullptr, *v = nullptr, *F = nullptr, *flj = nullptr;
   int* img = nullptr;
   uint16_t* site = nullptr;
   int *cellc = nullptr, *inv_perm = nullptr, *tag = nullptr, *perm = nullptr;
   float4 *ref = nullptr, *pos = nullptr;
-  int *nbr = nullptr, *ncount = nullptr, *count = nullptr, *cell_start = nullptr, *cell_of = nullptr;
+  uint4* nbr = nullptr;
+  int tile_cap = 0;
+  int *ncount = nullptr, *count = nullptr, *cell_start = nullptr, *cell_of = nullptr;
   int *slot = nullptr, *tmp = nullptr;
   double *lj_part = nullptr, *b_part = nullptr, *kepart = nullptr, *ke_out = nullptr, *lam = nullptr;
   double* e_out = nullptr;
   unsigned *done = nullptr, *flags = nullptr;
+  const double* kt = nullptr;
   // execution
   cudaStream_t st = nullptr;
   bool own_stream = false;
@@ -110,7 +112,17 @@ static void fill_force_params(md_system* s) {
   f.kphi = (float)p.kphi; f.phis = (float)p.phis; f.n_mult = p.n_mult;
   f.sites = s->S;
   f.half_skin2 = (float)(0.25 * s->skin * s->skin);
-  for (int a = 0; a < 2; ++a) { f.mass[a] = p.mass[a]; f.inv_mass[a] = 1.0 / p.mass[a]; }
+  f.b0sq = p.b0 * p.b0;
+  f.b0sq_hi = (float)f.b0sq;
+  f.b0sq_lo = (float)(f.b0sq - (double)f.b0sq_hi);
+  for (int a = 0; a < 2; ++a) {
+    f.mass[a] = p.mass[a];
+    f.inv_mass[a] = 1.0 / p.mass[a];
+    f.hdt_m[a] = 0.5 * s->dt / p.mass[a];
+    f.hdt_m_fix[a] = f.hdt_m[a] * kFixInv;
+    f.hdt_m_f[a] = (float)f.hdt_m[a];
+  }
+  f.dt_f = (float)s->dt;
   f.dt = s->dt;
 }
 
@@ -141,8 +153,8 @@ static int configure(md_system* s, const md_desc* d) {
   s->reps_h.assign(s->n_reps, RepDev{});
   s->T0.assign(s->n_reps, 0.0);
   int64_t atoms = 0, cells = 0, chains = 0;
-  double max_expected = 0.0;
-  s->t_lj.clear(); s->t_int.clear();
+  double max_expected = 0.0, max_tile = 0.0;
+  s->t_int.clear();
   for (int r = 0; r < s->n_reps; ++r) {
     const int nc = d->n_chains[r];
     const double L = d->box[r];
@@ -166,11 +178,11 @@ static int configure(md_system* s, const md_desc* d) {
     q.tile_off = (int)s->t_int.size();
     for (int o = 0; o < q.n_atoms; o += kIntTile) s->t_int.push_back(Tile{q.atom_off + o, std::min(kIntTile, q.n_atoms - o), r, 0});
     q.n_tiles = (int)s->t_int.size() - q.tile_off;
-    for (int o = 0; o < q.n_atoms; o += kLjTile) s->t_lj.push_back(Tile{q.atom_off + o, std::min(kLjTile, q.n_atoms - o), r, 0});
     // chains are locally as dense as a melt even in a sparse box, so the
     // density used for the capacity is at least that of a dense melt
     const double rho = std::max(q.n_atoms / (L * L * L), 40.0);
     max_expected = std::max(max_expected, 4.0 / 3.0 * M_PI * rl * rl * rl * rho);
+    max_tile = std::max(max_tile, 27.0 * std::max(q.n_atoms / (L * L * L), 33.0) * q.h * q.h * q.h);
     atoms += q.n_atoms; cells += (int64_t)M * M * M; chains += nc;
     if (atoms >= (int64_t)kNbrIndexMask) return fail(s, MD_EINVAL, "too many atoms (limit 2^26)");
     if (chains >= (1 << 21)) return fail(s, MD_EINVAL, "too many chains (limit 2^21)");
@@ -178,8 +190,15 @@ static int configure(md_system* s, const md_desc* d) {
   }
   s->N = atoms; s->C = (int)cells;
   s->Npad = (int)((atoms + 31) / 32 * 32);
-  s->cap = d->nbr_capacity > 0 ? d->nbr_capacity : ((int)std::ceil(1.5 * max_expected + 24.0) + 3) / 4 * 4;
-  if (s->cap > 4096) return fail(s, MD_EINVAL, "neighbour capacity above 4096");
+  // default list capacity: twice the mean neighbour count at (at least) melt
+  // density plus 64 slots for sentinel padding of the per-thread sub-lists
+  s->cap = d->nbr_capacity > 0 ? d->nbr_capacity : (int)std::ceil(2.0 * max_expected + 64.0);
+  s->cap = (s->cap + 7) / 8 * 8;
+  if (s->cap > 1024) return fail(s, MD_EINVAL, "neighbour capacity above 1024");
+  // 27-cell tile capacity (shared memory per block): 1.4x the mean tile of
+  // the densest replica (at least melt density, 33 sites/nm^3) plus 64, in
+  // multiples of 128 atoms; a larger tile is reported as MD_EOVERFLOW
+  s->tile_cap = std::min(tile_capacity_max(), ((int)std::ceil(1.4 * max_tile + 64.0) + 127) / 128 * 128);
   fill_force_params(s);
   return MD_OK;
 }
@@ -191,7 +210,6 @@ static size_t plan(md_system* s, char* base) {
   const size_t N = (size_t)s->N, C = (size_t)s->C;
   const size_t fsz = s->mixed ? sizeof(double) : sizeof(float);
   s->reps = (RepDev*)take(sizeof(RepDev) * s->n_reps);
-  s->tiles_lj = (Tile*)take(sizeof(Tile) * s->t_lj.size());
   s->tiles_int = (Tile*)take(sizeof(Tile) * s->t_int.size());
   s->x = take(3 * N * fsz);
   s->v = take(3 * N * fsz);
@@ -205,14 +223,14 @@ static size_t plan(md_system* s, char* base) {
   s->pos = (float4*)take(N * sizeof(float4));
   s->tag = (int*)take(N * sizeof(int));
   s->perm = (int*)take(N * sizeof(int));
-  s->nbr = (int*)take((size_t)s->cap * s->Npad * sizeof(int));
+  s->nbr = (uint4*)take((size_t)(s->cap / 8) * s->Npad * sizeof(uint4));
   s->ncount = (int*)take(N * sizeof(int));
   s->count = (int*)take(C * sizeof(int));
   s->cell_start = (int*)take((C + 1) * sizeof(int));
   s->cell_of = (int*)take(N * sizeof(int));
   s->slot = (int*)take(N * sizeof(int));
   s->tmp = (int*)take(N * sizeof(int));
-  s->lj_part = (double*)take(s->t_lj.size() * 8 * sizeof(double));
+  s->lj_part = (double*)take(C * 8 * sizeof(double));
   s->b_part = (double*)take(s->t_int.size() * 9 * sizeof(double));
   s->kepart = (double*)take(s->t_int.size() * sizeof(double));
   s->ke_out = (double*)take(s->n_reps * sizeof(double));
@@ -239,15 +257,15 @@ static void enqueue_rebin(md_system* s) {
   launch_cell_sort(s->mixed, s->x, (int)s->N, s->cell_start, s->tmp, s->cellc, s->site, s->reps, s->n_reps, s->C,
                    s->S, s->perm, s->inv_perm, s->pos, s->tag, s->ref, s->st);
   prof_mark(s);
-  launch_nbr_build(s->pos, s->tag, s->cell_start, s->reps, s->n_reps, s->C, s->fp.rlist2, s->nbr, s->ncount, s->cap,
-                   s->Npad, s->flags, s->st);
+  launch_nbr_tile(s->pos, s->tag, s->cell_start, s->reps, s->n_reps, s->C, s->nbr, s->ncount, s->cap, s->Npad,
+                  s->tile_cap, s->flags, s->st);
   prof_mark(s);
 }
 static const int kRebinLaunches = 6;   // memset counted as a launch
 
 static void enqueue_forces(md_system* s, bool energy) {
-  launch_lj(s->mixed, energy, s->pos, s->tag, s->nbr, s->ncount, s->Npad, s->tiles_lj, (int)s->t_lj.size(), s->reps,
-            s->fp, s->flj, s->lj_part, s->flags, kLjTile, s->st);
+  launch_lj_tile(s->mixed, energy, s->pos, s->tag, s->cell_start, s->nbr, s->ncount, s->Npad, s->tile_cap, s->reps,
+                 s->n_reps, s->C, s->fp, s->flj, s->lj_part, s->flags, s->st);
   prof_mark(s);
   launch_bonded(s->mixed, energy, s->x, s->site, s->inv_perm, s->flj, (int)s->N, s->tiles_int, (int)s->t_int.size(),
                 s->reps, s->fp, s->F, s->b_part, s->flags, s->st);
@@ -257,7 +275,7 @@ static void enqueue_forces(md_system* s, bool energy) {
 static void enqueue_integrate(md_system* s, IntegMode mode, bool ke) {
   launch_integrate(s->mixed, mode, ke, s->thermo, s->x, s->v, s->img, s->F, s->site, s->cellc,
                    s->inv_perm, s->ref, s->pos, (int)s->N, s->tiles_int, (int)s->t_int.size(), s->reps, s->n_reps,
-                   s->fp, s->kepart, s->done, s->ke_out, s->lam, s->tau, s->flags, s->st);
+                   s->fp, s->kepart, s->done, s->ke_out, s->lam, s->tau, s->flags, s->kt, s->st);
   prof_mark(s);
 }
 
@@ -409,6 +427,12 @@ int md_create(const md_desc* d, md_system** out) {
     }
     s->own_stream = true;
   }
+  s->kt = centre_table();
+  if (tile_kernels_init() != cudaSuccess) {
+    cudaGetLastError();
+    fail(s, MD_ECUDA, "cannot reserve shared memory for the neighbour-tile kernels");
+    return bail(MD_ECUDA);
+  }
   // static tables
   std::vector<uint16_t> site(s->N);
   for (int64_t i = 0; i < s->N; ++i) site[i] = 0;
@@ -421,7 +445,6 @@ int md_create(const md_desc* d, md_system** out) {
     return cudaMemcpyAsync(dst, src, b, cudaMemcpyHostToDevice, s->st) == cudaSuccess;
   };
   bool ok = up(s->reps, s->reps_h.data(), sizeof(RepDev) * s->n_reps) &&
-            up(s->tiles_lj, s->t_lj.data(), sizeof(Tile) * s->t_lj.size()) &&
             up(s->tiles_int, s->t_int.data(), sizeof(Tile) * s->t_int.size()) &&
             up(s->site, site.data(), sizeof(uint16_t) * s->N) &&
             up(s->lam, ones.data(), sizeof(double) * s->n_reps) &&
@@ -494,12 +517,12 @@ int md_energy(md_system* s, md_energy_t* out) {
   const bool p = s->profile;
   s->profile = false;
   enqueue_forces(s, true);
-  launch_energy_reduce(s->lj_part, s->b_part, s->tiles_lj, (int)s->t_lj.size(), s->tiles_int, (int)s->t_int.size(),
-                       s->n_reps, s->e_out, s->st);
+  launch_energy_reduce(s->lj_part, s->b_part, s->reps, s->tiles_int, (int)s->t_int.size(), s->n_reps, s->e_out,
+                       s->st);
   // kinetic energy of the current velocities (a pass that only reads v)
   launch_integrate(s->mixed, kKineticOnly, true, false, s->x, s->v, s->img, s->F, s->site, s->cellc, s->inv_perm,
                    s->ref, s->pos, (int)s->N, s->tiles_int, (int)s->t_int.size(), s->reps, s->n_reps, s->fp,
-                   s->kepart, s->done, s->ke_out, s->lam, s->tau, s->flags, s->st);
+                   s->kepart, s->done, s->ke_out, s->lam, s->tau, s->flags, s->kt, s->st);
   s->profile = p;
   CU(cudaGetLastError());
   std::vector<double> e((size_t)s->n_reps * 16), ke(s->n_reps);
@@ -620,16 +643,56 @@ int md_get_neighbors(md_system* s, int32_t* count, int32_t* entries) {
   if (!s) return fail(s, MD_EINVAL, "null system");
   CU(cudaStreamSynchronize(s->st));
   const size_t N = (size_t)s->N;
-  std::vector<int> cnt(N), pm(N), lst((size_t)s->cap * s->Npad);
+  std::vector<int> cnt(N), pm(N), cs(s->C + 1);
+  std::vector<uint16_t> lst((size_t)s->cap * s->Npad);   // blocks of 8 entries
   CU(cudaMemcpy(cnt.data(), s->ncount, N * sizeof(int), cudaMemcpyDeviceToHost));
   CU(cudaMemcpy(pm.data(), s->perm, N * sizeof(int), cudaMemcpyDeviceToHost));
-  if (entries) CU(cudaMemcpy(lst.data(), s->nbr, lst.size() * sizeof(int), cudaMemcpyDeviceToHost));
-  for (size_t sl = 0; sl < N; ++sl) {
-    const int i = pm[sl];
-    if (count) count[i] = cnt[sl];
-    if (entries)
-      for (int q = 0; q < cnt[sl]; ++q)
-        entries[(size_t)i * s->cap + q] = pm[(unsigned)lst[(size_t)q * s->Npad + sl] & kNbrIndexMask];
+  CU(cudaMemcpy(cs.data(), s->cell_start, (s->C + 1) * sizeof(int), cudaMemcpyDeviceToHost));
+  CU(cudaMemcpy(lst.data(), s->nbr, lst.size() * sizeof(uint16_t), cudaMemcpyDeviceToHost));
+  for (int r = 0; r < s->n_reps; ++r) {
+    const RepDev& q = s->reps_h[r];
+    const int M = q.M;
+    for (int lc = 0; lc < M * M * M; ++lc) {
+      const int c = q.cell_base + lc;
+      // the 27-cell tile of cell c, in the order the kernels stage it
+      int start[27], off[28];
+      off[0] = 0;
+      const int cx = lc % M, cy = (lc / M) % M, cz = lc / (M * M);
+      for (int k = 0; k < 27; ++k) {
+        const int ox = k % 3 - 1, oy = (k / 3) % 3 - 1, oz = k / 9 - 1;
+        const int nc = q.cell_base + (((cz + oz + M) % M) * M + ((cy + oy + M) % M)) * M + ((cx + ox + M) % M);
+        start[k] = cs[nc];
+        off[k + 1] = off[k] + cs[nc + 1] - cs[nc];
+      }
+      for (int sl = cs[c]; sl < cs[c + 1]; ++sl) {
+        const int i = pm[sl];
+        int m = 0;
+        for (int k2 = 0; k2 < 8 * cnt[sl]; ++k2) {      // cnt = blocks of 8; skip sentinel slots
+          const int t = lst[((size_t)(k2 >> 3) * s->Npad + sl) * 8 + (k2 & 7)] & 0x7fff;
+          if (t >= off[27]) continue;
+          int k = 0;
+          while (k < 26 && off[k + 1] <= t) ++k;
+          if (entries) entries[(size_t)i * s->cap + m] = pm[start[k] + (t - off[k])];
+          ++m;
+        }
+        if (count) count[i] = m;
+      }
+    }
+  }
+  return MD_OK;
+}
+
+int md_get_cell_units(md_system* s, float* u) {
+  if (!s || !u) return fail(s, MD_EINVAL, "bad arguments");
+  CU(cudaStreamSynchronize(s->st));
+  const size_t N = (size_t)s->N;
+  std::vector<float4> p(N);
+  std::vector<int> ip(N);
+  CU(cudaMemcpy(p.data(), s->pos, N * sizeof(float4), cudaMemcpyDeviceToHost));
+  CU(cudaMemcpy(ip.data(), s->inv_perm, N * sizeof(int), cudaMemcpyDeviceToHost));
+  for (size_t i = 0; i < N; ++i) {
+    const float4 q = p[ip[i]];
+    u[3 * i] = q.x; u[3 * i + 1] = q.y; u[3 * i + 2] = q.z;
   }
   return MD_OK;
 }

@@ -16,7 +16,8 @@
 //     tag        int32 [N]  chain*512 + site | type << 30
 //     perm       int32 [N]  original index of slot s
 //     Flj        AoS 32 B   LJ force on slot s
-//     nbr        int32 [cap][Npad] neighbour entries (column-major, coalesced)
+//     nbr        uint16 entries in blocks of 8 ([cap/8][Npad] of 16 B):
+//                index into the 27-cell tile of the atom's cell | type(j) << 15
 //     ncount     int32 [N]
 //   cells: count int32 [C], cell_start int32 [C+1]
 #pragma once
@@ -67,6 +68,29 @@ __device__ __forceinline__ float cell_unit(double x, int c, int w, const RepDev&
   const double k = (double)c + 0.5 - (double)w * (double)R.M;
   return __double2float_rn(fma(x, R.inv_h, -k));
 }
+// FP64 -> FP32 with round-to-nearest-even done on the integer pipe (FP64 <->
+// FP32 conversions share the slow FP64 pipe on this GPU).  From the IEEE 754
+// binary64/binary32 layouts: for a normal result, drop 29 mantissa bits with
+// round-half-even (add 2^28 - 1 + the lowest kept bit, then truncate; a carry
+// moves into the exponent) and rebias the exponent by 1023 - 127 = 896.
+// Zero keeps its sign; anything outside the normal FP32 range takes the
+// hardware conversion.
+__device__ __forceinline__ float d2f_rn_int(double d) {
+  const long long b = __double_as_longlong(d);
+  const unsigned long long a = (unsigned long long)b & 0x7fffffffffffffffull;
+  const unsigned sign = (unsigned)((unsigned long long)b >> 32) & 0x80000000u;
+  if (a == 0ull) return __uint_as_float(sign);
+  if (a < 0x3810000000000000ull || a >= 0x47efffffe0000000ull) return __double2float_rn(d);
+  const unsigned long long t = a + 0x0fffffffull + ((a >> 29) & 1ull);
+  return __uint_as_float(((unsigned)(t >> 29) - (896u << 23)) | sign);
+}
+
+// Same as cell_unit with the centre offset read from kt[c] = c + 1/2 (a
+// 1024-entry FP64 table: no integer-to-FP64 conversion) and the final
+// rounding on the integer pipe.
+__device__ __forceinline__ float cell_unit_t(double x, int c, const RepDev& R, const double* __restrict__ kt) {
+  return d2f_rn_int(fma(x, R.inv_h, -__ldg(kt + c)));
+}
 // FP32 master: x/h as p + e (exact product error by FMA, plus the low part of
 // 1/h), minus the exact integer-plus-half k; one final rounding.
 __device__ __forceinline__ float cell_unit(float x, int c, int w, const RepDev& R) {
@@ -86,9 +110,14 @@ struct ForceParams {
   int n_mult;
   int sites;                      // atoms per chain (NAOM)
   float half_skin2;               // (skin/2)^2
-  float pad;
+  float b0sq_hi, b0sq_lo;         // b0^2 as a two-float sum
+  double b0sq;                    // b0^2
   double mass[2], inv_mass[2];
   double dt;
+  float hdt_m_f[2], dt_f;         // FP32 copies for the plain form
+  float pad_f;
+  double hdt_m[2];                // dt / (2 m) per type
+  double hdt_m_fix[2];            // dt / (2 m) * 2^-32 (applied to int64 fixed-point forces)
 };
 
 struct F4i { long long x, y, z, w; };   // fixed-point force, 32 B
@@ -104,28 +133,32 @@ void launch_cell_sort(bool mixed, const void* x, int N, const int* cell_start, c
                       const int* cellc, const uint16_t* site, const RepDev* reps, int n_reps, int C,
                       int sites, int* perm, int* inv_perm, float4* pos, int* tag, float4* ref,
                       cudaStream_t st);
-void launch_nbr_build(const float4* pos, const int* tag, const int* cell_start, const RepDev* reps,
-                      int n_reps, int C, float rlist2, int* nbr, int* ncount, int cap, int Npad,
-                      unsigned* flags, cudaStream_t st);
-
 // ---------------------------------------------------------------- forces
-void launch_lj(bool mixed, bool energy, const float4* pos, const int* tag, const int* nbr, const int* ncount, int Npad,
-               const Tile* tiles, int n_tiles, const RepDev* reps, const ForceParams& fp,
-               void* flj, double* epart, unsigned* flags, int block, cudaStream_t st);
+// neighbour list and LJ over 27-cell shared-memory tiles (k_lj.cu).  The list
+// holds uint16 entries in blocks of 8: block q of slot s is nbr[q * Npad + s],
+// ncount[s] = number of blocks, unused slots hold the tile's sentinel index.
+// tile_cap = atoms a tile may hold (shared memory).
+void launch_nbr_tile(const float4* pos, const int* tag, const int* cell_start, const RepDev* reps, int n_reps, int C,
+                     uint4* nbr, int* ncount, int cap, int Npad, int tile_cap, unsigned* flags, cudaStream_t st);
+void launch_lj_tile(bool mixed, bool energy, const float4* pos, const int* tag, const int* cell_start,
+                    const uint4* nbr, const int* ncount, int Npad, int tile_cap, const RepDev* reps, int n_reps, int C,
+                    const ForceParams& fp, void* flj, double* epart, unsigned* flags, cudaStream_t st);
+cudaError_t tile_kernels_init();
+int tile_capacity_max();
 void launch_bonded(bool mixed, bool energy, const void* x, const uint16_t* site, const int* inv_perm,
                    const void* flj, int N, const Tile* tiles, int n_tiles, const RepDev* reps,
                    const ForceParams& fp, void* F, double* epart, unsigned* flags, cudaStream_t st);
 
 // ---------------------------------------------------------------- integration
 enum IntegMode { kKickDrift = 0, kKickKickDrift = 1, kKickOnly = 2, kKineticOnly = 3 };
+const double* centre_table();   // kt[c] = c + 1/2, c < 1024 (device memory, built once)
 void launch_integrate(bool mixed, IntegMode mode, bool ke, bool thermostat, void* x, void* v, int* img,
                       const void* F, const uint16_t* site, const int* cellc, const int* inv_perm,
                       const float4* ref, float4* pos, int N, const Tile* tiles, int n_tiles,
                       const RepDev* reps, int n_reps, const ForceParams& fp, double* kepart,
                       unsigned* done, double* ke_out, double* lam, double tau, unsigned* flags,
-                      cudaStream_t st);
-void launch_energy_reduce(const double* lj_part, const double* b_part, const Tile* lj_tiles,
-                          int n_lj_tiles, const Tile* b_tiles, int n_b_tiles, int n_reps,
-                          double* out, cudaStream_t st);
+                      const double* kt, cudaStream_t st);
+void launch_energy_reduce(const double* lj_part, const double* b_part, const RepDev* reps,
+                          const Tile* b_tiles, int n_b_tiles, int n_reps, double* out, cudaStream_t st);
 
 }  // namespace mdg

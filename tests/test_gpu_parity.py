@@ -286,3 +286,34 @@ def test_full_size_sampled_forces(precision):
     rel = np.sqrt(np.sum((f[sel] - f_orc)[clean] ** 2) / np.sum(f_orc[clean] ** 2))
     assert rel <= FORCE_TOL, rel
     s.close()
+
+
+@pytest.mark.parametrize("precision", [md.MD_MIXED, md.MD_PLAIN_FP32])
+def test_cell_unit_coordinates_are_correctly_rounded(precision):
+    """The FP32 positions the force kernels read, u = x/h - (c + 1/2) (+ a
+    whole box for atoms that crossed a face since the rebin), written by the
+    integrator after steps: mixed form = the exact value rounded once to FP64
+    (one FMA) and once to FP32 (round-half-even, integer-pipe rounding);
+    plain form within one FP32 ulp of the exact value."""
+    from fractions import Fraction
+    m = chaingen.melt(10, seed=17)
+    s = md.System(m, precision=precision, rebin_every=4)
+    s.step(3)
+    x, _, _ = s.state()
+    u = md.md_get_cell_units(s.h, s.n_atoms)
+    co, _, _ = s.bins()
+    M = s.info["cells_per_side"]
+    inv_h = Fraction(M / m["L"])                      # the library's (double) M / L
+    c = np.stack([co % M, (co // M) % M, co // (M * M)], 1)
+    rng = np.random.default_rng(1)
+    for i in rng.choice(s.n_atoms, 300, replace=False):
+        for a in range(3):
+            base = Fraction(float(x[i, a])) * inv_h - (int(c[i, a]) + Fraction(1, 2))
+            cands = [base + w * M for w in (-1, 0, 1)]
+            exact = min(cands, key=lambda q: abs(float(q) - float(u[i, a])))
+            if precision == md.MD_MIXED:
+                assert np.float32(float(exact)) == u[i, a], (i, a)
+            else:
+                ulp = np.spacing(np.float32(abs(float(exact))))
+                assert abs(Fraction(float(u[i, a])) - exact) <= Fraction(float(ulp))
+    s.close()
