@@ -61,8 +61,9 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* out) {
   }
 }
 
+// FP32 force -> int64 fixed point (2^-32 kJ/mol/nm); each part below 2^18
 __device__ __forceinline__ long long to_fix(float f, unsigned* flags) {
-  if (!(fabsf(f) < 2.0e9f)) { atomicOr(flags, kFlagFixOverflow); return 0; }
+  if (!(fabsf(f) < 262144.0f)) { atomicOr(flags, kFlagFixOverflow); return 0; }
   return __float2ll_rn(f * 4294967296.0f);
 }
 
@@ -150,8 +151,8 @@ __global__ void __launch_bounds__(kBondedBlock) k_bonded(const void* __restrict_
         const double dx = bond_diff((double)x[m], (double)x[m + 1], R.L, R.half_L);
         const double dy = bond_diff((double)x[N + m], (double)x[N + m + 1], R.L, R.half_L);
         const double dz = bond_diff((double)x[2 * N + m], (double)x[2 * N + m + 1], R.L, R.half_L);
-        b = mk(__double2float_rn(dx), __double2float_rn(dy), __double2float_rn(dz));
-        D = __double2float_rn(fma(dx, dx, fma(dy, dy, fma(dz, dz, -fp.b0sq))));
+        b = mk(d2f_rn_int(dx), d2f_rn_int(dy), d2f_rn_int(dz));
+        D = d2f_rn_int(fma(dx, dx, fma(dy, dy, fma(dz, dz, -fp.b0sq))));
       } else {
         b.x = bond_comp((float)x[m], (float)x[m + 1], R.Lf, R.half_Lf);
         b.y = bond_comp((float)x[N + m], (float)x[N + m + 1], R.Lf, R.half_Lf);

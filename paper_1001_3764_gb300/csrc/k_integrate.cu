@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(kIntBlock) k_integrate(void* __restrict__ xv, 
                                                          const ForceParams fp, double* __restrict__ kepart,
                                                          unsigned* __restrict__ done, double* __restrict__ ke_out,
                                                          double* __restrict__ lam, double tau,
-                                                         unsigned* __restrict__ flags, const double* __restrict__ kt) {
+                                                         unsigned* __restrict__ flags) {
   using T = typename std::conditional<MIXED, double, float>::type;
   T* x = reinterpret_cast<T*>(xv);
   T* v = reinterpret_cast<T*>(vv);
@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(kIntBlock) k_integrate(void* __restrict__ xv, 
     if (MODE == kKineticOnly) {
     } else if (MIXED) {
       const F4i f = reinterpret_cast<const F4i*>(Fv)[i];
-      F[0] = (T)(double)f.x; F[1] = (T)(double)f.y; F[2] = (T)(double)f.z;
+      F[0] = fix_to_double(f.x); F[1] = fix_to_double(f.y); F[2] = fix_to_double(f.z);
     } else {
       const float4 f = reinterpret_cast<const float4*>(Fv)[i];
       F[0] = f.x; F[1] = f.y; F[2] = f.z;
@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(kIntBlock) k_integrate(void* __restrict__ xv, 
         // face since the rebin is moved back by one box (M cell units)
         const int c = (cc >> (10 * a)) & 1023;
         float ua;
-        if constexpr (MIXED) ua = cell_unit_t(xa, c, R, kt); else ua = cell_unit(xa, c, 0, R);
+        if constexpr (MIXED) ua = cell_unit_t(xa, c, R); else ua = cell_unit(xa, c, 0, R);
         const float du = ua - r0a[a];
         if (du > halfM || du < -halfM) ua = cell_unit(xa, c, du > halfM ? -1 : 1, R);
         loc[a] = ua;
@@ -159,35 +159,16 @@ __global__ void __launch_bounds__(kIntBlock) k_integrate(void* __restrict__ xv, 
   }
 }
 
-// kt[c] = c + 1/2 for the FP64 cell-unit conversion; one copy per device
-__device__ double g_centre[1024];
-__global__ void k_fill_centre() {
-  for (int c = threadIdx.x; c < 1024; c += blockDim.x) g_centre[c] = (double)c + 0.5;
-}
-const double* centre_table() {
-  static int filled_on = -1;
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (filled_on != dev) {      // once per device (a process normally uses one)
-    k_fill_centre<<<1, 256>>>();
-    cudaDeviceSynchronize();
-    filled_on = dev;
-  }
-  void* p = nullptr;
-  cudaGetSymbolAddress(&p, g_centre);
-  return (const double*)p;
-}
-
 template <bool MIXED>
 static void launch_int_t(IntegMode mode, bool ke, bool th, void* x, void* v, int* img, const void* F,
                          const uint16_t* site, const int* cellc, const int* inv_perm, const float4* ref, float4* pos,
                          int N, const Tile* tiles, int n_tiles, const RepDev* reps, int n_reps,
                          const ForceParams& fp, double* kepart, unsigned* done, double* ke_out, double* lam,
-                         double tau, unsigned* flags, const double* kt, cudaStream_t st) {
+                         double tau, unsigned* flags, cudaStream_t st) {
 #define MDG_INT(MODE, KE, TH)                                                                                   \
   k_integrate<MIXED, MODE, KE, TH><<<n_tiles, kIntBlock, 0, st>>>(x, v, img, F, site, cellc, inv_perm, ref,     \
                                                                   pos, N, tiles, reps, n_reps, fp, kepart, done, \
-                                                                  ke_out, lam, tau, flags, kt)
+                                                                  ke_out, lam, tau, flags)
   // With the thermostat on, every step that starts (KD, KKD) takes the
   // temperature of the unscaled v(t_k), scales v(t_k) by the factor of the
   // previous step and leaves the factor of step k for the next one.  The
@@ -211,13 +192,13 @@ void launch_integrate(bool mixed, IntegMode mode, bool ke, bool thermostat, void
                       const void* F, const uint16_t* site, const int* cellc, const int* inv_perm, const float4* ref,
                       float4* pos, int N, const Tile* tiles, int n_tiles, const RepDev* reps, int n_reps,
                       const ForceParams& fp, double* kepart, unsigned* done, double* ke_out, double* lam,
-                      double tau, unsigned* flags, const double* kt, cudaStream_t st) {
+                      double tau, unsigned* flags, cudaStream_t st) {
   if (mixed)
     launch_int_t<true>(mode, ke, thermostat, x, v, img, F, site, cellc, inv_perm, ref, pos, N, tiles, n_tiles, reps,
-                       n_reps, fp, kepart, done, ke_out, lam, tau, flags, kt, st);
+                       n_reps, fp, kepart, done, ke_out, lam, tau, flags, st);
   else
     launch_int_t<false>(mode, ke, thermostat, x, v, img, F, site, cellc, inv_perm, ref, pos, N, tiles, n_tiles, reps,
-                        n_reps, fp, kepart, done, ke_out, lam, tau, flags, kt, st);
+                        n_reps, fp, kepart, done, ke_out, lam, tau, flags, st);
 }
 
 // ---------------------------------------------------------------- energy reduction

@@ -8,7 +8,7 @@
 // then u_i - w_j.  The paper's neighbour-search kernel also assigns a block to
 // a grid cell and stages the 27 cells (Sec. 3.1, last paragraph); here the
 // same staging serves the force kernel, and the list stores 16-bit indices
-// into the staged tile (bit 15 = type of j) instead of global atom ids.
+// into the staged tile instead of global atom ids.
 //
 // List build: every thread scans the whole tile for its home atom (cutoff
 // r_c + skin, 1-2 and 1-3 neighbours excluded, Sec. 3.1), keeps its entries
@@ -77,6 +77,8 @@ __device__ __forceinline__ void tile_setup(CellTile& T, int c, const RepDev& R, 
 // Copy the tile into shared memory, shifted into the home cell's frame: warp
 // w copies cells k = w, w + nwarps, ... (each cell is one contiguous run of
 // sorted atoms).
+// WITH_TAG: w = the atom's tag bits (list build); otherwise w = its LJ type
+// as 0.0 / 1.0 (force kernel).
 template <bool WITH_TAG>
 __device__ __forceinline__ void tile_load(const CellTile& T, const float4* __restrict__ pos, const int* __restrict__ tag,
                                           float4* __restrict__ sp) {
@@ -87,7 +89,8 @@ __device__ __forceinline__ void tile_load(const CellTile& T, const float4* __res
     for (int q = lane; q < n; q += 32) {
       float4 p = __ldg(pos + j0 + q);
       p.x += ox; p.y += oy; p.z += oz;
-      p.w = WITH_TAG ? __int_as_float(__ldg(tag + j0 + q)) : 0.f;
+      const int tg = __ldg(tag + j0 + q);
+      p.w = WITH_TAG ? __int_as_float(tg) : (float)((tg >> kTagTypeBit) & 1);
       sp[t0 + q] = p;
     }
   }
@@ -100,15 +103,65 @@ __device__ __forceinline__ void tile_load(const CellTile& T, const float4* __res
 // tile's sentinel index (= tile size): a staged atom placed far outside the
 // cutoff, so a padded slot adds exactly zero force and energy.
 //
-// TP adjacent threads share a home atom; thread p scans 32-atom words
-// p, p + TP, ... of the tile, forms the word's in-range bit mask in a register,
-// drops 1-2/1-3 neighbours and itself (tag test, Sec. 3.1) while turning the
-// set bits into entries, and writes its blocks at p, p + TP, ...; the TP
-// threads then pad to a common number of blocks.
+// TP adjacent threads share a home atom; in every 32-atom word of the tile
+// thread p takes atoms p, p + TP, ... (the lanes of a warp read neighbouring
+// 16-byte slots: one shared-memory wavefront), forms their in-range bit mask
+// in a register, drops 1-2/1-3 neighbours and itself (tag test, Sec. 3.1)
+// while turning the set bits into entries (plain tile indices), and writes
+// its blocks at p, p + TP, ...; the TP threads then pad to a common number of
+// blocks.
 constexpr int kBuildThreads = 128;
 
 __device__ __forceinline__ uint4 pack_block(unsigned long long lo, unsigned long long hi) {
   return make_uint4((unsigned)lo, (unsigned)(lo >> 32), (unsigned)hi, (unsigned)(hi >> 32));
+}
+
+template <int TP>
+__device__ __forceinline__ void build_atom(const float4* __restrict__ sp, int nwords, int total, float rl2, int s, int p,
+                                           const float4& pi, int ti, uint4* __restrict__ nbr, int Npad, int capb,
+                                           int& nb_out) {
+  const unsigned long long sent = (unsigned long long)total;
+  const unsigned long long sent4 = sent | (sent << 16) | (sent << 32) | (sent << 48);
+  constexpr int per = 32 / TP;                 // candidates of each word taken by this lane
+  int nb = 0, cnt = 0;
+  unsigned long long lo = 0ull, hi = 0ull;
+  for (int wd = 0; wd < nwords; ++wd) {
+    const float4* w32 = sp + wd * 32 + p;
+    unsigned m = 0u;
+#pragma unroll
+    for (int u = 0; u < per; ++u) {
+      const float4 w = w32[u * TP];
+      const float dx = pi.x - w.x, dy = pi.y - w.y, dz = pi.z - w.z;
+      m |= (dx * dx + dy * dy + dz * dz < rl2 ? 1u : 0u) << u;
+    }
+    while (m) {
+      const int u = __ffs(m) - 1;
+      m &= m - 1u;
+      const int t = wd * 32 + p + u * TP;
+      const int tj = __float_as_int(sp[t].w);
+      const int dtag = ti - (tj & (int)kTagMask);
+      if (dtag <= 2 && dtag >= -2) continue;          // itself, 1-2 and 1-3 neighbours
+      const unsigned long long e = (unsigned long long)t;
+      const int slot = cnt & 7;
+      if (slot < 4) lo |= e << (16 * slot); else hi |= e << (16 * (slot - 4));
+      if (slot == 7) {
+        const int q = p + TP * nb;
+        if (q < capb) nbr[(size_t)q * Npad + s] = pack_block(lo, hi);
+        ++nb;
+        lo = 0ull; hi = 0ull;
+      }
+      ++cnt;
+    }
+  }
+  const int rem = cnt & 7;
+  if (rem) {                                          // pad the open block with the sentinel
+    const unsigned long long fill = ~0ull << (16 * (rem < 4 ? rem : rem - 4));
+    if (rem < 4) { lo |= sent4 & fill; hi = sent4; } else { hi |= sent4 & fill; }
+    const int q = p + TP * nb;
+    if (q < capb) nbr[(size_t)q * Npad + s] = pack_block(lo, hi);
+    ++nb;
+  }
+  nb_out = nb;
 }
 
 __global__ void __launch_bounds__(kBuildThreads) k_nbr_tile(const float4* __restrict__ pos, const int* __restrict__ tag,
@@ -144,48 +197,13 @@ __global__ void __launch_bounds__(kBuildThreads) k_nbr_tile(const float4* __rest
     const int a = a0 + (int)threadIdx.x / TP, p = (int)threadIdx.x % TP;
     const bool active = a < n;
     const int s = b + a;
-    int nb = 0, cnt = 0;
+    int nb = 0;
     if (active) {
       const float4 pi = pos[s];
       const int ti = tag[s] & (int)kTagMask;
-      unsigned long long lo = 0ull, hi = 0ull;
-      for (int wd = p; wd < nwords; wd += TP) {
-        const float4* w32 = sp + wd * 32;
-        unsigned m = 0u;
-#pragma unroll
-        for (int u = 0; u < 32; ++u) {
-          const float4 w = w32[u];
-          const float dx = pi.x - w.x, dy = pi.y - w.y, dz = pi.z - w.z;
-          const float r2 = dx * dx + dy * dy + dz * dz;
-          m |= (r2 < rl2 ? 1u : 0u) << u;
-        }
-        while (m) {
-          const int u = __ffs(m) - 1;
-          m &= m - 1u;
-          const int t = wd * 32 + u;
-          const int tj = __float_as_int(w32[u].w);
-          const int dtag = ti - (tj & (int)kTagMask);
-          if (dtag <= 2 && dtag >= -2) continue;          // itself, 1-2 and 1-3 neighbours
-          const unsigned long long e = (unsigned long long)(t | (((unsigned)tj >> kTagTypeBit) << 15));
-          const int slot = cnt & 7;
-          if (slot < 4) lo |= e << (16 * slot); else hi |= e << (16 * (slot - 4));
-          if (slot == 7) {
-            const int q = p + TP * nb;
-            if (q < capb) nbr[(size_t)q * Npad + s] = pack_block(lo, hi);
-            ++nb;
-            lo = 0ull; hi = 0ull;
-          }
-          ++cnt;
-        }
-      }
-      const int rem = cnt & 7;
-      if (rem) {                                          // pad the open block with the sentinel
-        const unsigned long long fill = ~0ull << (16 * (rem < 4 ? rem : rem - 4));
-        if (rem < 4) { lo |= sent4 & fill; hi = sent4; } else { hi |= sent4 & fill; }
-        const int q = p + TP * nb;
-        if (q < capb) nbr[(size_t)q * Npad + s] = pack_block(lo, hi);
-        ++nb;
-      }
+      if (TP == 1) build_atom<1>(sp, nwords, total, rl2, s, p, pi, ti, nbr, Npad, capb, nb);
+      else if (TP == 2) build_atom<2>(sp, nwords, total, rl2, s, p, pi, ti, nbr, Npad, capb, nb);
+      else build_atom<4>(sp, nwords, total, rl2, s, p, pi, ti, nbr, Npad, capb, nb);
     }
     // common block count of the TP threads of an atom (adjacent lanes)
     int mb = nb;
@@ -216,21 +234,23 @@ void launch_nbr_tile(const float4* pos, const int* tag, const int* cell_start, c
 // ===================================================================== force
 constexpr int kEnergyVals = 8;   // lj, lj_shifted, vxx, vyy, vzz, vxy, vxz, vyz
 
+// FP32 force -> int64 fixed point (2^-32 kJ/mol/nm).  Each part (LJ, bonded)
+// is kept below 2^18 kJ/mol/nm so that their sum converts exactly to FP64.
 __device__ __forceinline__ long long fix_of(float f, unsigned* flags) {
-  if (!(fabsf(f) < 2.0e9f)) { atomicOr(flags, kFlagFixOverflow); return 0; }
+  if (!(fabsf(f) < 262144.0f)) { atomicOr(flags, kFlagFixOverflow); return 0; }
   return __float2ll_rn(f * 4294967296.0f);
 }
 
-// one pair of Eq. (2) in cell units (Sec. 3.2 listing: r2inv = 0 beyond r_c)
+// one pair of Eq. (2) in cell units (Sec. 3.2 listing: r2inv = 0 beyond r_c);
+// w.w is j's type (0/1), so the pair constants are a0 + t_j (a1 - a0)
 template <bool ENERGY>
-__device__ __forceinline__ void lj_pair(unsigned en, const float4* __restrict__ sp, const float4& pi, float rc2, float a0c,
-                                        float b0c, float a1c, float b1c, int ti, const RepDev& R, const ForceParams& fp,
+__device__ __forceinline__ void lj_pair(unsigned t, const float4* __restrict__ sp, const float4& pi, float rc2, float a0c,
+                                        float da, float b0c, float db, int ti, const RepDev& R, const ForceParams& fp,
                                         float& fx, float& fy, float& fz, float (&ev)[8]) {
-  const float4 w = sp[en & 0x7fffu];
-  const bool tj = (en >> 15) != 0;
+  const float4 w = sp[t];
   const float dx = pi.x - w.x, dy = pi.y - w.y, dz = pi.z - w.z;
   const float r2 = dx * dx + dy * dy + dz * dz;
-  const float A = tj ? a1c : a0c, B = tj ? b1c : b0c;
+  const float A = fmaf(w.w, da, a0c), B = fmaf(w.w, db, b0c);
   const float ir2 = r2 < rc2 ? rcp_approx(r2) : 0.f;
   const float ir6 = ir2 * ir2 * ir2;
   const float ff = ir2 * ir6 * (A * ir6 - B);
@@ -238,7 +258,8 @@ __device__ __forceinline__ void lj_pair(unsigned en, const float4* __restrict__ 
   fy += ff * dy;
   fz += ff * dz;
   if (ENERGY) {
-    const int tt = ti + (int)tj;
+    const int tj = w.w != 0.f ? 1 : 0;
+    const int tt = ti + tj;
     const float eij = ir6 * (R.C12u[tt] * ir6 - R.C6u[tt]);
     if (r2 < rc2) {
       ev[0] += eij;
@@ -287,22 +308,26 @@ __global__ void __launch_bounds__(kLjBlock) k_lj_tile(const float4* __restrict__
         const float4 pi = pos[s];
         const int ti = (tag[s] >> kTagTypeBit) & 1;
         const float a0c = 12.f * R.C12u[ti], b0c = 6.f * R.C6u[ti];
-        const float a1c = 12.f * R.C12u[ti + 1], b1c = 6.f * R.C6u[ti + 1];
+        const float da = 12.f * R.C12u[ti + 1] - a0c, db = 6.f * R.C6u[ti + 1] - b0c;
         const int nblk = ncount[s];
         const uint4* np = nbr + s;
+        const uint4 z4 = make_uint4(0u, 0u, 0u, 0u);
         int blk = p;
-        uint4 E = blk < nblk ? __ldg(np + (size_t)blk * Npad) : make_uint4(0u, 0u, 0u, 0u);
+        // two blocks in flight ahead of the one being processed
+        uint4 E = blk < nblk ? __ldg(np + (size_t)blk * Npad) : z4;
+        uint4 E1 = blk + TP < nblk ? __ldg(np + (size_t)(blk + TP) * Npad) : z4;
         while (blk < nblk) {
-          const int nb = blk + TP;
-          const uint4 En = nb < nblk ? __ldg(np + (size_t)nb * Npad) : make_uint4(0u, 0u, 0u, 0u);   // prefetch
+          const int n2 = blk + 2 * TP;
+          const uint4 E2 = n2 < nblk ? __ldg(np + (size_t)n2 * Npad) : z4;
           const unsigned ew[4] = {E.x, E.y, E.z, E.w};
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
-            lj_pair<ENERGY>(ew[u] & 0xffffu, sp, pi, rc2, a0c, b0c, a1c, b1c, ti, R, fp, fx, fy, fz, ev);
-            lj_pair<ENERGY>(ew[u] >> 16, sp, pi, rc2, a0c, b0c, a1c, b1c, ti, R, fp, gx, gy, gz, ev);
+            lj_pair<ENERGY>(ew[u] & 0xffffu, sp, pi, rc2, a0c, da, b0c, db, ti, R, fp, fx, fy, fz, ev);
+            lj_pair<ENERGY>(ew[u] >> 16, sp, pi, rc2, a0c, da, b0c, db, ti, R, fp, gx, gy, gz, ev);
           }
-          E = En;
-          blk = nb;
+          E = E1;
+          E1 = E2;
+          blk += TP;
         }
       }
       fx += gx; fy += gy; fz += gz;

@@ -57,7 +57,6 @@ struct md_system {
   double *lj_part = nullptr, *b_part = nullptr, *kepart = nullptr, *ke_out = nullptr, *lam = nullptr;
   double* e_out = nullptr;
   unsigned *done = nullptr, *flags = nullptr;
-  const double* kt = nullptr;
   // execution
   cudaStream_t st = nullptr;
   bool own_stream = false;
@@ -275,7 +274,7 @@ static void enqueue_forces(md_system* s, bool energy) {
 static void enqueue_integrate(md_system* s, IntegMode mode, bool ke) {
   launch_integrate(s->mixed, mode, ke, s->thermo, s->x, s->v, s->img, s->F, s->site, s->cellc,
                    s->inv_perm, s->ref, s->pos, (int)s->N, s->tiles_int, (int)s->t_int.size(), s->reps, s->n_reps,
-                   s->fp, s->kepart, s->done, s->ke_out, s->lam, s->tau, s->flags, s->kt, s->st);
+                   s->fp, s->kepart, s->done, s->ke_out, s->lam, s->tau, s->flags, s->st);
   prof_mark(s);
 }
 
@@ -330,7 +329,7 @@ static int check_flags(md_system* s) {
   if (!f) return MD_OK;
   CU(cudaMemset(s->flags, 0, sizeof(unsigned)));
   if (f & kFlagNbrOverflow) return fail(s, MD_EOVERFLOW, "neighbour list capacity exceeded (raise nbr_capacity)");
-  if (f & kFlagFixOverflow) return fail(s, MD_EOVERFLOW, "force beyond the fixed-point range (|F| >= 2^31 kJ/mol/nm)");
+  if (f & kFlagFixOverflow) return fail(s, MD_EOVERFLOW, "force beyond the fixed-point range (a part >= 2^18 kJ/mol/nm)");
   if (f & kFlagNaN) return fail(s, MD_EUNSTABLE, "non-finite position or velocity");
   if (f & kFlagDisplacement) return fail(s, MD_EUNSTABLE, "an atom moved more than skin/2 between rebins (raise skin or lower rebin_every)");
   if (f & kFlagTimeout) return fail(s, MD_ETIMEOUT, "a bounded device wait gave up");
@@ -427,7 +426,6 @@ int md_create(const md_desc* d, md_system** out) {
     }
     s->own_stream = true;
   }
-  s->kt = centre_table();
   if (tile_kernels_init() != cudaSuccess) {
     cudaGetLastError();
     fail(s, MD_ECUDA, "cannot reserve shared memory for the neighbour-tile kernels");
@@ -522,7 +520,7 @@ int md_energy(md_system* s, md_energy_t* out) {
   // kinetic energy of the current velocities (a pass that only reads v)
   launch_integrate(s->mixed, kKineticOnly, true, false, s->x, s->v, s->img, s->F, s->site, s->cellc, s->inv_perm,
                    s->ref, s->pos, (int)s->N, s->tiles_int, (int)s->t_int.size(), s->reps, s->n_reps, s->fp,
-                   s->kepart, s->done, s->ke_out, s->lam, s->tau, s->flags, s->kt, s->st);
+                   s->kepart, s->done, s->ke_out, s->lam, s->tau, s->flags, s->st);
   s->profile = p;
   CU(cudaGetLastError());
   std::vector<double> e((size_t)s->n_reps * 16), ke(s->n_reps);
@@ -668,7 +666,7 @@ int md_get_neighbors(md_system* s, int32_t* count, int32_t* entries) {
         const int i = pm[sl];
         int m = 0;
         for (int k2 = 0; k2 < 8 * cnt[sl]; ++k2) {      // cnt = blocks of 8; skip sentinel slots
-          const int t = lst[((size_t)(k2 >> 3) * s->Npad + sl) * 8 + (k2 & 7)] & 0x7fff;
+          const int t = lst[((size_t)(k2 >> 3) * s->Npad + sl) * 8 + (k2 & 7)];
           if (t >= off[27]) continue;
           int k = 0;
           while (k < 26 && off[k + 1] <= t) ++k;

@@ -17,7 +17,7 @@
 //     perm       int32 [N]  original index of slot s
 //     Flj        AoS 32 B   LJ force on slot s
 //     nbr        uint16 entries in blocks of 8 ([cap/8][Npad] of 16 B):
-//                index into the 27-cell tile of the atom's cell | type(j) << 15
+//                index into the 27-cell tile of the atom's cell
 //     ncount     int32 [N]
 //   cells: count int32 [C], cell_start int32 [C+1]
 #pragma once
@@ -37,7 +37,7 @@ constexpr double kFixInv = 1.0 / 4294967296.0;
 // Error flags (bitmask in device memory)
 enum : uint32_t {
   kFlagNbrOverflow = 1u,      // neighbour list capacity exceeded
-  kFlagFixOverflow = 2u,      // |F| too large for the fixed-point range
+  kFlagFixOverflow = 2u,      // a force part beyond 2^18 kJ/mol/nm (the fixed-point range)
   kFlagNaN = 4u,              // non-finite position or velocity
   kFlagDisplacement = 8u,     // an atom moved more than skin/2 since the rebin
   kFlagTimeout = 16u,         // a bounded device wait gave up
@@ -73,24 +73,41 @@ __device__ __forceinline__ float cell_unit(double x, int c, int w, const RepDev&
 // binary64/binary32 layouts: for a normal result, drop 29 mantissa bits with
 // round-half-even (add 2^28 - 1 + the lowest kept bit, then truncate; a carry
 // moves into the exponent) and rebias the exponent by 1023 - 127 = 896.
-// Zero keeps its sign; anything outside the normal FP32 range takes the
-// hardware conversion.
+// Zero and magnitudes below 2^-126 give a signed zero (no subnormal results),
+// magnitudes from 2^128 up give infinity, NaN stays NaN.
 __device__ __forceinline__ float d2f_rn_int(double d) {
   const long long b = __double_as_longlong(d);
   const unsigned long long a = (unsigned long long)b & 0x7fffffffffffffffull;
   const unsigned sign = (unsigned)((unsigned long long)b >> 32) & 0x80000000u;
-  if (a == 0ull) return __uint_as_float(sign);
-  if (a < 0x3810000000000000ull || a >= 0x47efffffe0000000ull) return __double2float_rn(d);
   const unsigned long long t = a + 0x0fffffffull + ((a >> 29) & 1ull);
-  return __uint_as_float(((unsigned)(t >> 29) - (896u << 23)) | sign);
+  unsigned f = (unsigned)(t >> 29) - (896u << 23);
+  f = a < 0x3810000000000000ull ? 0u : f;                              // below the normal range
+  f = (a >= 0x47effffff0000000ull && a <= 0x7ff0000000000000ull) ? 0x7f800000u : f;   // overflow, inf
+  f = a > 0x7ff0000000000000ull ? 0x7fc00000u : f;                     // NaN
+  return __uint_as_float(f | sign);
 }
 
-// Same as cell_unit with the centre offset read from kt[c] = c + 1/2 (a
-// 1024-entry FP64 table: no integer-to-FP64 conversion) and the final
-// rounding on the integer pipe.
-__device__ __forceinline__ float cell_unit_t(double x, int c, const RepDev& R, const double* __restrict__ kt) {
-  return d2f_rn_int(fma(x, R.inv_h, -__ldg(kt + c)));
+// c + 1/2 as an FP64 number built from its bits (no int -> FP64 conversion):
+// n = 2c + 1 is odd and below 2^12, c + 1/2 = n / 2 = 1.m * 2^(e-1), e = msb(n).
+__device__ __forceinline__ double half_plus(int c) {
+  const unsigned n = 2u * (unsigned)c + 1u;
+  const int e = 31 - __clz(n);
+  const unsigned long long m = ((unsigned long long)n << (52 - e)) & 0x000fffffffffffffull;
+  return __longlong_as_double(((unsigned long long)(e + 1022) << 52) | m);
 }
+
+// Same as cell_unit with the centre offset built on the integer pipe and the
+// final rounding on the integer pipe.
+__device__ __forceinline__ float cell_unit_t(double x, int c, const RepDev& R) {
+  return d2f_rn_int(fma(x, R.inv_h, -half_plus(c)));
+}
+
+// int64 fixed-point force -> FP64 by the 1.5 * 2^52 bias (one FP64 add, no
+// conversion instruction); exact for |n| < 2^51.
+__device__ __forceinline__ double fix_to_double(long long n) {
+  return __longlong_as_double(n + 0x4338000000000000ll) - 6755399441055744.0;
+}
+
 // FP32 master: x/h as p + e (exact product error by FMA, plus the low part of
 // 1/h), minus the exact integer-plus-half k; one final rounding.
 __device__ __forceinline__ float cell_unit(float x, int c, int w, const RepDev& R) {
@@ -151,13 +168,12 @@ void launch_bonded(bool mixed, bool energy, const void* x, const uint16_t* site,
 
 // ---------------------------------------------------------------- integration
 enum IntegMode { kKickDrift = 0, kKickKickDrift = 1, kKickOnly = 2, kKineticOnly = 3 };
-const double* centre_table();   // kt[c] = c + 1/2, c < 1024 (device memory, built once)
 void launch_integrate(bool mixed, IntegMode mode, bool ke, bool thermostat, void* x, void* v, int* img,
                       const void* F, const uint16_t* site, const int* cellc, const int* inv_perm,
                       const float4* ref, float4* pos, int N, const Tile* tiles, int n_tiles,
                       const RepDev* reps, int n_reps, const ForceParams& fp, double* kepart,
                       unsigned* done, double* ke_out, double* lam, double tau, unsigned* flags,
-                      const double* kt, cudaStream_t st);
+                      cudaStream_t st);
 void launch_energy_reduce(const double* lj_part, const double* b_part, const RepDev* reps,
                           const Tile* b_tiles, int n_b_tiles, int n_reps, double* out, cudaStream_t st);
 
