@@ -179,6 +179,34 @@ int md_profile_reset(md_system *sys);
 /* Kernel launches per call of md_step(n_steps) (all library kernels). */
 int64_t md_launches_per_call(md_system *sys, int64_t n_steps);
 
+/* Cell binning of one periodic box into caller-provided DEVICE arrays, with
+ * no device allocation.  (The paper has no counterpart: this exists for
+ * callers that may not allocate GPU memory themselves -- code running while
+ * another component owns all device memory, such as a framework's caching
+ * allocator or a fixed-budget real-time loop, where an extra cudaMalloc
+ * would fragment memory, stall on a device-wide synchronisation or exceed
+ * the budget.)
+ *   pos        [3 * n_atoms] FP64 positions, SoA (all x, then all y, then z)
+ *   box        cube side L; cells_per_side = M; cell side L / M
+ *   cell_of    [n_atoms] out: cell index (cz * M + cy) * M + cx of each atom
+ *   cell_start [M^3 + 1] out: first sorted slot of each cell, last = n_atoms
+ *   perm       [n_atoms] out: sorted slot -> atom index, atoms of a cell in
+ *              ascending index order
+ *   cuda_stream the stream to run on (NULL = legacy default stream)
+ * The same formulas as md_rebin, so the outputs equal md_get_bins for the
+ * same positions and M.  Limits: n_atoms <= 1,048,576 and M^3 <= 131,072;
+ * larger sizes return MD_EINVAL and run nothing.  Scratch memory is one
+ * fixed array of 8.9 MB per device inside this library, present on every
+ * device that loads it until the process exits; every call shares it and it
+ * keeps the last call's contents (the counters are cleared by each call), so
+ * calls whose work overlaps on the GPU (other streams, other host threads)
+ * race.  The first call on a device looks up the array's device address;
+ * make that first call before any stream capture.  Asynchronous: results are
+ * ready when the stream reaches them; errors are returned as MD_E* codes
+ * with md_last_error(NULL). */
+int md_bin_static(const double *pos, int32_t n_atoms, double box, int32_t cells_per_side, int32_t *cell_of,
+                  int32_t *cell_start, int32_t *perm, void *cuda_stream);
+
 void md_destroy(md_system *sys);
 
 /* Message of the last failure on this system (or of the last failed

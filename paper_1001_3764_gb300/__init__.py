@@ -65,7 +65,7 @@ class md_energy_t(ctypes.Structure):
 EXPORTS = ["md_workspace_size", "md_create", "md_step", "md_step_async", "md_sync", "md_forces", "md_energy",
            "md_rebin", "md_get_state", "md_set_state", "md_set_params", "md_set_temperature", "md_stream",
            "md_info", "md_get_bins", "md_get_neighbors", "md_get_cell_units", "md_profile_enable", "md_profile_read",
-           "md_profile_reset", "md_launches_per_call", "md_destroy", "md_last_error"]
+           "md_profile_reset", "md_launches_per_call", "md_bin_static", "md_destroy", "md_last_error"]
 
 _lib = None
 
@@ -102,6 +102,7 @@ def load(path: str = LIB_PATH):
         "md_profile_read": ([P, P, P], ctypes.c_int),
         "md_profile_reset": ([P], ctypes.c_int),
         "md_launches_per_call": ([P, i64], i64),
+        "md_bin_static": ([P, i32, ctypes.c_double, i32, P, P, P, P], ctypes.c_int),
         "md_destroy": ([P], None),
         "md_last_error": ([P], ctypes.c_char_p),
     }
@@ -248,6 +249,15 @@ def md_profile_reset(h):
 
 def md_launches_per_call(h, n: int) -> int:
     return int(load().md_launches_per_call(h, n))
+
+
+def md_bin_static(pos_dev: int, n_atoms: int, box: float, cells_per_side: int, cell_of_dev: int,
+                  cell_start_dev: int, perm_dev: int, stream: int = 0):
+    """Binning into caller DEVICE arrays (pointers as ints) with no device
+    allocation; see include/md.h for limits and the shared-scratch rules."""
+    _check(load().md_bin_static(ctypes.c_void_p(pos_dev), n_atoms, box, cells_per_side,
+                                ctypes.c_void_p(cell_of_dev), ctypes.c_void_p(cell_start_dev),
+                                ctypes.c_void_p(perm_dev), ctypes.c_void_p(stream)))
 
 
 def md_destroy(h):

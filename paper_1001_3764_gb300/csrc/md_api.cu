@@ -69,6 +69,8 @@ struct md_system {
   std::string err;
 };
 
+void md_set_global_error(const char* msg) { g_create_error = msg; }
+
 // ------------------------------------------------------------------ helpers
 static int fail(md_system* s, int code, const std::string& msg) {
   if (s) s->err = msg; else g_create_error = msg;
