@@ -269,7 +269,7 @@ def run_gpu(args):
     ns_day = md_steps / (m["ms"] * 1e-3) * DT_PS * 1e-3 * 86400
     lj_ms = m["prof_ms"][3] / max(m["prof_n"][3], 1)
     achieved = FLOP_PER_ATOM_LJ * n_atoms / (lj_ms * 1e-3) / 1e12
-    src = os.path.join(ROOT, "paper_1001_3764_gb300", "csrc", "k_force.cu")
+    src = os.path.join(ROOT, "paper_1001_3764_gb300", "csrc", "k_lj.cu")
     traffic = _traffic(src)
     e2e_val = ws * n_atoms * md_steps / m["e2e_s"]
     out = {
@@ -289,7 +289,7 @@ def run_gpu(args):
         "drift_detail": dr,
         "kernel_ms_per_launch": {g: float(t / max(n, 1)) for g, t, n in
                                  zip(md.PROFILE_GROUPS, m["prof_ms"], m["prof_n"])},
-        "roofline": {"kernel": "k_lj (LJ force, Eq. 2)", "bound": "alu", "achieved": achieved,
+        "roofline": {"kernel": "k_lj_tile (LJ force, Eq. 2)", "bound": "alu", "achieved": achieved,
                      "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
                      "flop_per_atom": FLOP_PER_ATOM_LJ, "traffic": traffic},
