@@ -23,7 +23,7 @@
 namespace mdg {
 
 constexpr int kStageCapMax = 6144;  // largest 27-cell tile (96 KB of float4); the staged index has 15 bits
-constexpr int kLjBlock = 128;
+constexpr int kLjBlock = 256;
 
 __device__ __forceinline__ int find_rep_cell(const RepDev* reps, int n_reps, int c) {
   int lo = 0, hi = n_reps - 1;
@@ -110,7 +110,7 @@ __device__ __forceinline__ void tile_load(const CellTile& T, const float4* __res
 // while turning the set bits into entries (plain tile indices), and writes
 // its blocks at p, p + TP, ...; the TP threads then pad to a common number of
 // blocks.
-constexpr int kBuildThreads = 128;
+constexpr int kBuildThreads = 256;
 
 __device__ __forceinline__ uint4 pack_block(unsigned long long lo, unsigned long long hi) {
   return make_uint4((unsigned)lo, (unsigned)(lo >> 32), (unsigned)hi, (unsigned)(hi >> 32));
@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(kBuildThreads) k_nbr_tile(const float4* __rest
   const float rl2 = R.rlist2u;
   const unsigned long long sent = (unsigned long long)total;
   const unsigned long long sent4 = sent | (sent << 16) | (sent << 32) | (sent << 48);
-  const int TP = n >= 64 ? 1 : (n >= 32 ? 2 : 4);
+  const int TP = n > kBuildThreads / 2 ? 1 : (n > kBuildThreads / 4 ? 2 : 4);
   const int per_pass = kBuildThreads / TP;
   const int capb = cap >> 3;
   for (int a0 = 0; a0 < n; a0 += per_pass) {
@@ -295,7 +295,7 @@ __global__ void __launch_bounds__(kLjBlock) k_lj_tile(const float4* __restrict__
     if (threadIdx.x == 0) sp[total] = make_float4(1e9f, 1e9f, 1e9f, 0.f);   // sentinel slot
     __syncthreads();
     // TP adjacent lanes share one home atom: entry blocks p, p + TP, ...
-    const int TP = n >= kLjBlock / 2 ? 1 : (n >= kLjBlock / 4 ? 2 : 4);
+    const int TP = n > kLjBlock / 2 ? 1 : (n > kLjBlock / 4 ? 2 : 4);
     const float rc2 = R.rc2u;
     const float ih = R.ih_hi;
     for (int a0 = 0; a0 < n; a0 += kLjBlock / TP) {
