@@ -114,6 +114,15 @@ def melt(n_chains: int, sites: int = 150, seed: int = 1, T: float = 500.0,
                 T=T, seed=seed, relaxed=int(relaxed))
 
 
+def maxwell(masses: np.ndarray, T: float, seed: int, stream: int = 1) -> np.ndarray:
+    """Fresh Maxwell-Boltzmann velocities (N,3) in nm/ps at T kelvin for the
+    given masses (amu), zero total momentum; stream 1 is the one melt() uses."""
+    masses = np.ascontiguousarray(masses, dtype=np.float64)
+    vel = np.empty((len(masses), 3), dtype=np.float64)
+    _load().cg_maxwell(len(masses), _ptr(masses), float(T), KB, ctypes.c_uint64(sub_seed(seed, stream)), _ptr(vel))
+    return vel
+
+
 def uniforms(seed: int, n: int) -> np.ndarray:
     out = np.empty(n, dtype=np.float64)
     _load().cg_uniforms(ctypes.c_uint64(sub_seed(seed, 7)), n, _ptr(out))

@@ -51,6 +51,9 @@ enum {
 
 enum { MD_PLAIN_FP32 = 0, MD_MIXED = 1 };   /* precision forms */
 enum { MD_NVE = 0, MD_VRESCALE = 1 };       /* thermostat */
+/* LJ work schedule: one thread block per cell, or a fixed grid (resident
+ * blocks x SMs) whose blocks take cells from a device counter */
+enum { MD_SCHED_GRID = 0, MD_SCHED_PERSISTENT = 1 };
 
 typedef struct md_system md_system;         /* opaque, owned by the library */
 
@@ -84,6 +87,8 @@ typedef struct {
   int32_t precision;           /* MD_PLAIN_FP32 or MD_MIXED */
   int32_t thermostat;          /* MD_NVE or MD_VRESCALE */
   int32_t nbr_capacity;        /* neighbour slots per atom; 0 = chosen from density */
+  int32_t lj_block;            /* threads per block of the LJ kernel: 128 or 256 (0 = 256) */
+  int32_t schedule;            /* MD_SCHED_GRID or MD_SCHED_PERSISTENT (see below) */
   void *cuda_stream;           /* cudaStream_t to run on; NULL = a stream the library creates */
   void *workspace;             /* optional DEVICE memory for all buffers (see md_workspace_size);
                                   NULL = the library allocates.  Must outlive the system. */
@@ -101,6 +106,29 @@ typedef struct {
   double virial[6];     /* sum r (x) f: xx, yy, zz, xy, xz, yz (kJ/mol) */
   double pressure;      /* (2 KE + tr virial) / (3 V), kJ/mol/nm^3 */
 } md_energy_t;
+
+/* Settings chosen by md_autotune. */
+typedef struct {
+  double skin;                 /* nm; sets the cell side (>= rc + skin) */
+  int32_t rebin_every;
+  int32_t lj_block;
+  int32_t schedule;
+  int32_t from_cache;          /* 1 if read from the cache file, 0 if measured now */
+  double us_per_step;          /* measured time per MD step of the winner */
+} md_tuning;
+
+/* Autotuner: times short runs of candidate settings on the system the
+ * descriptor describes -- LJ block shape (128, 256 threads) and schedule
+ * (grid, persistent), then cell size via (skin, rebin_every) in
+ * {(0.08, 6), (0.10, 10), (0.12, 12), (0.15, 16)} nm / steps -- and writes the
+ * fastest into desc->skin, rebin_every, lj_block and schedule.  Candidates that
+ * raise a device flag (e.g. an atom moving more than skin/2 between rebins)
+ * are rejected.  With cache_path != NULL the result is looked up in / appended
+ * to that text file, keyed by GPU, precision, replica count and atom-count and
+ * box-size buckets.  trial_cycles: rebin cycles timed per candidate (>= 1).
+ * Allocates and frees its own trial systems; the caller's state is only
+ * read.  out may be NULL. */
+int md_autotune(md_desc *desc, int32_t trial_cycles, const char *cache_path, md_tuning *out);
 
 /* Bytes of device memory md_create needs for this descriptor. */
 int md_workspace_size(const md_desc *desc, size_t *bytes);

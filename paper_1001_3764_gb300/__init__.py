@@ -20,6 +20,7 @@ LIB_PATH = _build.LIB
 MD_OK, MD_EINVAL, MD_ENOMEM, MD_ECUDA, MD_EOVERFLOW, MD_EUNSTABLE, MD_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
 MD_PLAIN_FP32, MD_MIXED = 0, 1
 MD_NVE, MD_VRESCALE = 0, 1
+MD_SCHED_GRID, MD_SCHED_PERSISTENT = 0, 1
 KB = 0.0083144626  # kJ/mol/K
 
 _ERRNAMES = {MD_EINVAL: "MD_EINVAL", MD_ENOMEM: "MD_ENOMEM", MD_ECUDA: "MD_ECUDA",
@@ -46,8 +47,14 @@ class md_desc(ctypes.Structure):
                 ("dt", ctypes.c_double), ("rc", ctypes.c_double), ("skin", ctypes.c_double),
                 ("tau_t", ctypes.c_double), ("rebin_every", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("thermostat", ctypes.c_int32), ("nbr_capacity", ctypes.c_int32),
+                ("lj_block", ctypes.c_int32), ("schedule", ctypes.c_int32),
                 ("cuda_stream", ctypes.c_void_p), ("workspace", ctypes.c_void_p),
                 ("workspace_bytes", ctypes.c_size_t)]
+
+
+class md_tuning(ctypes.Structure):
+    _fields_ = [("skin", ctypes.c_double), ("rebin_every", ctypes.c_int32), ("lj_block", ctypes.c_int32),
+                ("schedule", ctypes.c_int32), ("from_cache", ctypes.c_int32), ("us_per_step", ctypes.c_double)]
 
 
 class md_energy_t(ctypes.Structure):
@@ -62,7 +69,7 @@ class md_energy_t(ctypes.Structure):
         return d
 
 
-EXPORTS = ["md_workspace_size", "md_create", "md_step", "md_step_async", "md_sync", "md_forces", "md_energy",
+EXPORTS = ["md_autotune", "md_workspace_size", "md_create", "md_step", "md_step_async", "md_sync", "md_forces", "md_energy",
            "md_rebin", "md_get_state", "md_set_state", "md_set_params", "md_set_temperature", "md_stream",
            "md_info", "md_get_bins", "md_get_neighbors", "md_get_cell_units", "md_profile_enable", "md_profile_read",
            "md_profile_reset", "md_launches_per_call", "md_bin_static", "md_destroy", "md_last_error"]
@@ -81,6 +88,7 @@ def load(path: str = LIB_PATH):
     L = ctypes.CDLL(path)
     P, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
     sig = {
+        "md_autotune": ([P, i32, ctypes.c_char_p, P], ctypes.c_int),
         "md_workspace_size": ([P, P], ctypes.c_int),
         "md_create": ([P, P], ctypes.c_int),
         "md_step": ([P, i64], ctypes.c_int),
@@ -142,6 +150,13 @@ def make_params(p: dict) -> md_params:
 
 
 # ---------------------------------------------------------------- thin wrappers (C ABI names)
+
+def md_autotune(desc: md_desc, trial_cycles: int = 2, cache_path: str | None = None) -> dict:
+    t = md_tuning()
+    _check(load().md_autotune(ctypes.byref(desc), trial_cycles,
+                              None if cache_path is None else cache_path.encode(), ctypes.byref(t)))
+    return {k: getattr(t, k) for k, _ in t._fields_}
+
 
 def md_workspace_size(desc: md_desc) -> int:
     b = ctypes.c_size_t()
@@ -286,7 +301,8 @@ class System:
     def __init__(self, melts, precision: int = MD_MIXED, dt: float = 0.001, rc: float = 1.0,
                  skin: float = 0.1, rebin_every: int = 10, thermostat: int = MD_NVE, T_target=None,
                  tau_t: float = 0.1, params: dict | None = None, nbr_capacity: int = 0, device: int = 0,
-                 use_torch_memory: bool = True):
+                 use_torch_memory: bool = True, lj_block: int = 0, schedule: int = MD_SCHED_GRID,
+                 autotune: bool = False, tune_cycles: int = 2, tune_cache: str | None = None):
         import torch
         load()
         if isinstance(melts, dict):
@@ -314,6 +330,8 @@ class System:
         d.dt, d.rc, d.skin, d.tau_t = dt, rc, skin, tau_t
         d.rebin_every, d.precision, d.thermostat = rebin_every, precision, thermostat
         d.nbr_capacity = nbr_capacity
+        d.lj_block, d.schedule = lj_block, schedule
+        self.tuning = md_autotune(d, tune_cycles, tune_cache) if autotune else None
         d.cuda_stream = self.stream.cuda_stream
         self.workspace = None
         if use_torch_memory:
@@ -326,7 +344,7 @@ class System:
         torch.cuda.synchronize(self.device)
         self.h = md_create(d)
         self.info = md_info(self.h)
-        self.dt, self.rebin_every = dt, rebin_every
+        self.dt, self.rebin_every = dt, d.rebin_every
 
     def step(self, n: int, sync: bool = True):
         (md_step if sync else md_step_async)(self.h, n)

@@ -23,7 +23,6 @@
 namespace mdg {
 
 constexpr int kStageCapMax = 6144;  // largest 27-cell tile (96 KB of float4); the staged index has 15 bits
-constexpr int kLjBlock = 256;
 
 __device__ __forceinline__ int find_rep_cell(const RepDev* reps, int n_reps, int c) {
   int lo = 0, hi = n_reps - 1;
@@ -270,18 +269,14 @@ __device__ __forceinline__ void lj_pair(unsigned t, const float4* __restrict__ s
   }
 }
 
-template <bool MIXED, bool ENERGY>
-__global__ void __launch_bounds__(kLjBlock) k_lj_tile(const float4* __restrict__ pos, const int* __restrict__ tag,
-                                                      const int* __restrict__ cell_start,
-                                                      const uint4* __restrict__ nbr, const int* __restrict__ ncount,
-                                                      int Npad, int tile_cap, const RepDev* __restrict__ reps, int n_reps,
-                                                      const ForceParams fp, void* __restrict__ flj,
-                                                      double* __restrict__ epart, unsigned* __restrict__ flags) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  float4* sp = reinterpret_cast<float4*>(smem);      // the tile, tile_cap entries
-  __shared__ CellTile T;
-  __shared__ double red[kEnergyVals][kLjBlock / 32];
-  const int c = blockIdx.x;
+// Force on the home atoms of one cell (block-wide; all threads call it).
+template <bool MIXED, bool ENERGY, int NT>
+__device__ __forceinline__ void lj_cell(int c, const float4* __restrict__ pos, const int* __restrict__ tag,
+                                        const int* __restrict__ cell_start, const uint4* __restrict__ nbr,
+                                        const int* __restrict__ ncount, int Npad, int tile_cap,
+                                        const RepDev* __restrict__ reps, int n_reps, const ForceParams& fp,
+                                        void* __restrict__ flj, double* __restrict__ epart, unsigned* __restrict__ flags,
+                                        float4* sp, CellTile& T, double (&red)[kEnergyVals][NT / 32]) {
   const int b = cell_start[c], n = cell_start[c + 1] - b;
   float ev[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   const RepDev& R = reps[find_rep_cell(reps, n_reps, c)];
@@ -295,11 +290,11 @@ __global__ void __launch_bounds__(kLjBlock) k_lj_tile(const float4* __restrict__
     if (threadIdx.x == 0) sp[total] = make_float4(1e9f, 1e9f, 1e9f, 0.f);   // sentinel slot
     __syncthreads();
     // TP adjacent lanes share one home atom: entry blocks p, p + TP, ...
-    const int TP = n > kLjBlock / 2 ? 1 : (n > kLjBlock / 4 ? 2 : 4);
+    const int TP = n > NT / 2 ? 1 : (n > NT / 4 ? 2 : 4);
     const float rc2 = R.rc2u;
     const float ih = R.ih_hi;
-    for (int a0 = 0; a0 < n; a0 += kLjBlock / TP) {
-      const int na = min(kLjBlock / TP, n - a0);
+    for (int a0 = 0; a0 < n; a0 += NT / TP) {
+      const int na = min(NT / TP, n - a0);
       const int a = a0 + (int)threadIdx.x / TP, p = (int)threadIdx.x % TP;
       const bool active = a < a0 + na;
       float fx = 0.f, fy = 0.f, fz = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
@@ -369,21 +364,87 @@ __global__ void __launch_bounds__(kLjBlock) k_lj_tile(const float4* __restrict__
     if (threadIdx.x == 0) {
       for (int k = 0; k < kEnergyVals; ++k) {
         double sv = 0.0;
-        for (int q = 0; q < kLjBlock / 32; ++q) sv += red[k][q];
+        for (int q = 0; q < NT / 32; ++q) sv += red[k][q];
         epart[(size_t)c * kEnergyVals + k] = sv;
       }
     }
   }
+  __syncthreads();   // the tile and tables are reused by the next cell of this block
+}
+
+// One block per cell (grid schedule) or a fixed grid that takes cells from a
+// counter (persistent schedule).  work[0] hands out cells, work[1] counts
+// finished blocks; the last block to finish resets both for the next launch
+// (no block ever waits for another).
+template <bool MIXED, bool ENERGY, int NT, bool PERSIST>
+__global__ void __launch_bounds__(NT) k_lj_tile(const float4* __restrict__ pos, const int* __restrict__ tag,
+                                                const int* __restrict__ cell_start,
+                                                const uint4* __restrict__ nbr, const int* __restrict__ ncount,
+                                                int Npad, int tile_cap, const RepDev* __restrict__ reps, int n_reps,
+                                                int C, const ForceParams fp, void* __restrict__ flj,
+                                                double* __restrict__ epart, unsigned* __restrict__ flags,
+                                                int* __restrict__ work) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  float4* sp = reinterpret_cast<float4*>(smem);      // the tile, tile_cap entries
+  __shared__ CellTile T;
+  __shared__ double red[kEnergyVals][NT / 32];
+  if constexpr (!PERSIST) {
+    lj_cell<MIXED, ENERGY, NT>(blockIdx.x, pos, tag, cell_start, nbr, ncount, Npad, tile_cap, reps, n_reps, fp, flj,
+                               epart, flags, sp, T, red);
+  } else {
+    __shared__ int next;
+    for (;;) {
+      if (threadIdx.x == 0) next = atomicAdd(work, 1);
+      __syncthreads();
+      const int c = next;
+      __syncthreads();
+      if (c >= C) break;
+      lj_cell<MIXED, ENERGY, NT>(c, pos, tag, cell_start, nbr, ncount, Npad, tile_cap, reps, n_reps, fp, flj, epart,
+                                 flags, sp, T, red);
+    }
+    if (threadIdx.x == 0) {
+      __threadfence();
+      if (atomicAdd(work + 1, 1) == (int)gridDim.x - 1) { work[0] = 0; work[1] = 0; }
+    }
+  }
+}
+
+template <bool MIXED, bool ENERGY, int NT, bool PERSIST>
+static void lj_launch(int grid, size_t sm, cudaStream_t st, const float4* pos, const int* tag, const int* cell_start,
+                      const uint4* nbr, const int* ncount, int Npad, int tile_cap, const RepDev* reps, int n_reps, int C,
+                      const ForceParams& fp, void* flj, double* epart, unsigned* flags, int* work) {
+  k_lj_tile<MIXED, ENERGY, NT, PERSIST><<<grid, NT, sm, st>>>(pos, tag, cell_start, nbr, ncount, Npad, tile_cap, reps,
+                                                              n_reps, C, fp, flj, epart, flags, work);
 }
 
 void launch_lj_tile(bool mixed, bool energy, const float4* pos, const int* tag, const int* cell_start,
                     const uint4* nbr, const int* ncount, int Npad, int tile_cap, const RepDev* reps, int n_reps, int C,
-                    const ForceParams& fp, void* flj, double* epart, unsigned* flags, cudaStream_t st) {
+                    const ForceParams& fp, void* flj, double* epart, unsigned* flags, int block, int persistent_grid,
+                    int* work, cudaStream_t st) {
   const size_t sm = (size_t)tile_cap * sizeof(float4);
-#define MDG_LJ(M, E) k_lj_tile<M, E><<<C, kLjBlock, sm, st>>>(pos, tag, cell_start, nbr, ncount, Npad, tile_cap, reps, n_reps, fp, flj, epart, flags)
-  if (mixed) { if (energy) MDG_LJ(true, true); else MDG_LJ(true, false); }
-  else { if (energy) MDG_LJ(false, true); else MDG_LJ(false, false); }
+  const int grid = persistent_grid > 0 ? persistent_grid : C;
+#define MDG_LJ(M, E, NT, P) lj_launch<M, E, NT, P>(grid, sm, st, pos, tag, cell_start, nbr, ncount, Npad, tile_cap, reps, n_reps, C, fp, flj, epart, flags, work)
+#define MDG_LJ2(NT, P) \
+  if (mixed) { if (energy) MDG_LJ(true, true, NT, P); else MDG_LJ(true, false, NT, P); } \
+  else { if (energy) MDG_LJ(false, true, NT, P); else MDG_LJ(false, false, NT, P); }
+  if (block == 128) {
+    if (persistent_grid > 0) { MDG_LJ2(128, true) } else { MDG_LJ2(128, false) }
+  } else {
+    if (persistent_grid > 0) { MDG_LJ2(256, true) } else { MDG_LJ2(256, false) }
+  }
+#undef MDG_LJ2
 #undef MDG_LJ
+}
+
+// resident blocks per SM of the LJ kernel for a block size and tile
+int lj_blocks_per_sm(int block, int tile_cap) {
+  int nb = 0;
+  const size_t sm = (size_t)tile_cap * sizeof(float4);
+  if (block == 128)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_lj_tile<true, false, 128, true>, 128, sm);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_lj_tile<true, false, 256, true>, 256, sm);
+  return nb;
 }
 
 // Opt in to more than 48 KB of dynamic shared memory (once per device); the
@@ -391,10 +452,12 @@ void launch_lj_tile(bool mixed, bool energy, const float4* pos, const int* tag, 
 cudaError_t tile_kernels_init() {
   const int mx = kStageCapMax * sizeof(float4);
   cudaError_t e = cudaFuncSetAttribute(k_nbr_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_lj_tile<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_lj_tile<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_lj_tile<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_lj_tile<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+#define MDG_ATTR(M, E, NT, P) \
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_lj_tile<M, E, NT, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+#define MDG_ATTR4(NT, P) MDG_ATTR(true, true, NT, P) MDG_ATTR(true, false, NT, P) MDG_ATTR(false, true, NT, P) MDG_ATTR(false, false, NT, P)
+  MDG_ATTR4(128, false) MDG_ATTR4(128, true) MDG_ATTR4(256, false) MDG_ATTR4(256, true)
+#undef MDG_ATTR4
+#undef MDG_ATTR
   return e;
 }
 

@@ -52,6 +52,8 @@ struct md_system {
   float4 *ref = nullptr, *pos = nullptr;
   uint4* nbr = nullptr;
   int tile_cap = 0;
+  int lj_block = 256, persistent_grid = 0;   // persistent_grid > 0: fixed grid for the LJ kernel
+  int* work = nullptr;                       // LJ work counters (persistent schedule)
   int *ncount = nullptr, *count = nullptr, *cell_start = nullptr, *cell_of = nullptr;
   int *slot = nullptr, *tmp = nullptr;
   double *lj_part = nullptr, *b_part = nullptr, *kepart = nullptr, *ke_out = nullptr, *lam = nullptr;
@@ -149,6 +151,9 @@ static int configure(md_system* s, const md_desc* d) {
   s->mixed = d->precision == MD_MIXED;
   s->thermo = d->thermostat == MD_VRESCALE;
   s->dt = d->dt; s->rc = d->rc; s->skin = d->skin; s->tau = d->thermostat ? d->tau_t : 0.1;
+  if (d->lj_block != 0 && d->lj_block != 128 && d->lj_block != 256) return fail(s, MD_EINVAL, "lj_block must be 0, 128 or 256");
+  if (d->schedule != MD_SCHED_GRID && d->schedule != MD_SCHED_PERSISTENT) return fail(s, MD_EINVAL, "unknown schedule");
+  s->lj_block = d->lj_block ? d->lj_block : 256;
   s->params = d->params;
   const double rl = d->rc + d->skin;
   s->reps_h.assign(s->n_reps, RepDev{});
@@ -238,6 +243,7 @@ static size_t plan(md_system* s, char* base) {
   s->lam = (double*)take(s->n_reps * sizeof(double));
   s->e_out = (double*)take((size_t)s->n_reps * 16 * sizeof(double));
   s->done = (unsigned*)take(sizeof(unsigned));
+  s->work = (int*)take(2 * sizeof(int));
   s->flags = (unsigned*)take(sizeof(unsigned));
   return off;
 }
@@ -266,7 +272,7 @@ static const int kRebinLaunches = 6;   // memset counted as a launch
 
 static void enqueue_forces(md_system* s, bool energy) {
   launch_lj_tile(s->mixed, energy, s->pos, s->tag, s->cell_start, s->nbr, s->ncount, s->Npad, s->tile_cap, s->reps,
-                 s->n_reps, s->C, s->fp, s->flj, s->lj_part, s->flags, s->st);
+                 s->n_reps, s->C, s->fp, s->flj, s->lj_part, s->flags, s->lj_block, s->persistent_grid, s->work, s->st);
   prof_mark(s);
   launch_bonded(s->mixed, energy, s->x, s->site, s->inv_perm, s->flj, (int)s->N, s->tiles_int, (int)s->t_int.size(),
                 s->reps, s->fp, s->F, s->b_part, s->flags, s->st);
@@ -433,6 +439,13 @@ int md_create(const md_desc* d, md_system** out) {
     fail(s, MD_ECUDA, "cannot reserve shared memory for the neighbour-tile kernels");
     return bail(MD_ECUDA);
   }
+  if (d->schedule == MD_SCHED_PERSISTENT) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int per_sm = lj_blocks_per_sm(s->lj_block, s->tile_cap);
+    s->persistent_grid = std::max(1, std::min(s->C, sms * std::max(per_sm, 1)));
+  }
   // static tables
   std::vector<uint16_t> site(s->N);
   for (int64_t i = 0; i < s->N; ++i) site[i] = 0;
@@ -449,6 +462,7 @@ int md_create(const md_desc* d, md_system** out) {
             up(s->site, site.data(), sizeof(uint16_t) * s->N) &&
             up(s->lam, ones.data(), sizeof(double) * s->n_reps) &&
             cudaMemsetAsync(s->done, 0, sizeof(unsigned), s->st) == cudaSuccess &&
+            cudaMemsetAsync(s->work, 0, 2 * sizeof(int), s->st) == cudaSuccess &&
             cudaMemsetAsync(s->flags, 0, sizeof(unsigned), s->st) == cudaSuccess &&
             cudaStreamSynchronize(s->st) == cudaSuccess;
   if (!ok) { fail(s, MD_ECUDA, "initial upload failed"); return bail(MD_ECUDA); }
@@ -729,6 +743,118 @@ int64_t md_launches_per_call(md_system* s, int64_t n) {
   if (!s || n <= 0) return 0;
   const int64_t full = n / s->R, rem = n % s->R;
   return full * block_launches(s->R) + (rem ? block_launches((int)rem) : 0);
+}
+
+// ------------------------------------------------------------------ autotuner
+static std::string tune_key(const md_desc* d) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceProp prop;
+  std::string name = "gpu";
+  int sms = 0;
+  if (cudaGetDeviceProperties(&prop, dev) == cudaSuccess) { name = prop.name; sms = prop.multiProcessorCount; }
+  for (char& ch : name) if (ch == ' ') ch = '_';
+  long long N = 0;
+  double lmin = 1e300, lmax = 0.0;
+  for (int r = 0; r < d->n_replicas; ++r) {
+    N += (long long)d->n_chains[r] * d->sites_per_chain;
+    lmin = std::min(lmin, d->box[r]);
+    lmax = std::max(lmax, d->box[r]);
+  }
+  char buf[256];
+  snprintf(buf, sizeof buf, "%s:%d:p%d:t%d:r%d:n%d:L%.1f-%.1f", name.c_str(), sms, d->precision, d->thermostat,
+           d->n_replicas, (int)std::floor(2.0 * std::log2((double)std::max(N, 1LL))), std::round(2.0 * lmin) / 2.0,
+           std::round(2.0 * lmax) / 2.0);
+  return buf;
+}
+
+// time one candidate: create, one warm-up cycle, trial_cycles timed cycles
+static int tune_trial(md_desc cand, int cycles, double* us) {
+  cand.workspace = nullptr;
+  cand.workspace_bytes = 0;
+  cand.cuda_stream = nullptr;
+  md_system* s = nullptr;
+  int rc = md_create(&cand, &s);
+  if (rc) return rc;
+  rc = md_step(s, cand.rebin_every);
+  if (!rc) {
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, s->st);
+    rc = md_step_async(s, (int64_t)cand.rebin_every * cycles);
+    cudaEventRecord(b, s->st);
+    if (!rc) rc = md_sync(s);
+    float ms = 0.f;
+    cudaEventSynchronize(b);
+    cudaEventElapsedTime(&ms, a, b);
+    *us = 1000.0 * ms / ((double)cand.rebin_every * cycles);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+  }
+  md_destroy(s);
+  return rc;
+}
+
+extern "C" int md_autotune(md_desc* d, int32_t trial_cycles, const char* cache_path, md_tuning* out) {
+  if (!d || trial_cycles < 1) return fail(nullptr, MD_EINVAL, "autotune needs a descriptor and trial_cycles >= 1");
+  const std::string key = tune_key(d);
+  md_tuning best{d->skin, d->rebin_every, d->lj_block ? d->lj_block : 256, d->schedule, 0, 1e300};
+  if (cache_path) {
+    if (FILE* f = fopen(cache_path, "r")) {
+      char k[256];
+      double skin, us;
+      int R, blk, sch;
+      bool found = false;
+      while (fscanf(f, "%255s %lf %d %d %d %lf", k, &skin, &R, &blk, &sch, &us) == 6)
+        if (key == k) { best = md_tuning{skin, R, blk, sch, 1, us}; found = true; }
+      fclose(f);
+      if (found) {
+        d->skin = best.skin; d->rebin_every = best.rebin_every; d->lj_block = best.lj_block; d->schedule = best.schedule;
+        if (out) *out = best;
+        return MD_OK;
+      }
+    }
+  }
+  bool any = false;
+  // block shape x schedule at the descriptor's cell size
+  for (int blk : {128, 256})
+    for (int sch : {(int)MD_SCHED_GRID, (int)MD_SCHED_PERSISTENT}) {
+      md_desc c = *d;
+      c.lj_block = blk;
+      c.schedule = sch;
+      double us = 0.0;
+      if (tune_trial(c, trial_cycles, &us) == MD_OK && us < best.us_per_step) {
+        best = md_tuning{c.skin, c.rebin_every, blk, sch, 0, us};
+        any = true;
+      }
+    }
+  // cell size through (skin, rebin interval)
+  const double skins[4] = {0.08, 0.10, 0.12, 0.15};
+  const int reb[4] = {6, 10, 12, 16};
+  for (int k = 0; k < 4; ++k) {
+    if (skins[k] == best.skin && reb[k] == best.rebin_every) continue;
+    md_desc c = *d;
+    c.lj_block = best.lj_block;
+    c.schedule = best.schedule;
+    c.skin = skins[k];
+    c.rebin_every = reb[k];
+    double us = 0.0;
+    if (tune_trial(c, trial_cycles, &us) == MD_OK && us < best.us_per_step) {
+      best = md_tuning{skins[k], reb[k], best.lj_block, best.schedule, 0, us};
+      any = true;
+    }
+  }
+  if (!any) return fail(nullptr, MD_EUNSTABLE, "autotune: no candidate ran cleanly");
+  d->skin = best.skin; d->rebin_every = best.rebin_every; d->lj_block = best.lj_block; d->schedule = best.schedule;
+  if (cache_path)
+    if (FILE* f = fopen(cache_path, "a")) {
+      fprintf(f, "%s %.4f %d %d %d %.3f\n", key.c_str(), best.skin, best.rebin_every, best.lj_block, best.schedule,
+              best.us_per_step);
+      fclose(f);
+    }
+  if (out) *out = best;
+  return MD_OK;
 }
 
 void md_destroy(md_system* s) {

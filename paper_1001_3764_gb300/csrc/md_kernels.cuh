@@ -157,9 +157,13 @@ void launch_cell_sort(bool mixed, const void* x, int N, const int* cell_start, c
 // tile_cap = atoms a tile may hold (shared memory).
 void launch_nbr_tile(const float4* pos, const int* tag, const int* cell_start, const RepDev* reps, int n_reps, int C,
                      uint4* nbr, int* ncount, int cap, int Npad, int tile_cap, unsigned* flags, cudaStream_t st);
+// block = 128 or 256 threads; persistent_grid > 0 runs that many blocks that
+// take cells from work[0..1] (two ints, zero before the first launch)
 void launch_lj_tile(bool mixed, bool energy, const float4* pos, const int* tag, const int* cell_start,
                     const uint4* nbr, const int* ncount, int Npad, int tile_cap, const RepDev* reps, int n_reps, int C,
-                    const ForceParams& fp, void* flj, double* epart, unsigned* flags, cudaStream_t st);
+                    const ForceParams& fp, void* flj, double* epart, unsigned* flags, int block, int persistent_grid,
+                    int* work, cudaStream_t st);
+int lj_blocks_per_sm(int block, int tile_cap);
 cudaError_t tile_kernels_init();
 int tile_capacity_max();
 void launch_bonded(bool mixed, bool energy, const void* x, const uint16_t* site, const int* inv_perm,

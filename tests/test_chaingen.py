@@ -70,3 +70,18 @@ def test_replica_recipe():
     assert 50 < sorted(counts)[32] < 160
     assert abs(chaingen._load().cg_ln_export(10.0) - math.log(10.0)) < 1e-15
     assert abs(chaingen._load().cg_exp_export(2.5) - math.exp(2.5)) < 1e-14
+
+
+def test_maxwell_resample_temperature_and_momentum():
+    """Fresh Maxwell draws: zero total momentum, equipartition temperature
+    within 4 standard errors (3N-3 degrees of freedom), distinct streams."""
+    masses = np.tile(chaingen.site_masses(150), 200)
+    T = 437.0
+    v = chaingen.maxwell(masses, T, seed=5, stream=100)
+    assert np.abs((masses[:, None] * v).sum(0)).max() < 1e-9
+    dof = 3 * len(masses) - 3
+    t_meas = (masses[:, None] * v * v).sum() / (dof * chaingen.KB)
+    assert abs(t_meas / T - 1.0) < 4.0 * math.sqrt(2.0 / dof)
+    w = chaingen.maxwell(masses, T, seed=5, stream=101)
+    assert np.abs(v - w).max() > 0.1
+    assert np.array_equal(v, chaingen.maxwell(masses, T, seed=5, stream=100))

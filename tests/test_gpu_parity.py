@@ -317,3 +317,40 @@ def test_cell_unit_coordinates_are_correctly_rounded(precision):
                 ulp = np.spacing(np.float32(abs(float(exact))))
                 assert abs(Fraction(float(u[i, a])) - exact) <= Fraction(float(ulp))
     s.close()
+
+
+def test_schedules_and_block_shapes_agree():
+    """The persistent schedule gives the same bits as one block per cell (each
+    cell's forces do not depend on which block computes them); 128-thread
+    blocks split an atom's list differently, so they agree to FP32 rounding."""
+    m = chaingen.melt(30, seed=23)
+    runs = {}
+    for blk, sch in ((256, md.MD_SCHED_GRID), (256, md.MD_SCHED_PERSISTENT), (128, md.MD_SCHED_GRID),
+                     (128, md.MD_SCHED_PERSISTENT)):
+        s = md.System(m, precision=md.MD_MIXED, rebin_every=4, lj_block=blk, schedule=sch)
+        s.step(12)
+        runs[(blk, sch)] = (s.forces(), s.state()[0], s.energy()[0])
+        s.close()
+    for blk in (128, 256):
+        fa, xa, ea = runs[(blk, md.MD_SCHED_GRID)]
+        fb, xb, eb = runs[(blk, md.MD_SCHED_PERSISTENT)]
+        assert np.array_equal(fa, fb) and np.array_equal(xa, xb) and ea == eb
+    f1, x1, _ = runs[(128, md.MD_SCHED_GRID)]
+    f2, x2, _ = runs[(256, md.MD_SCHED_GRID)]
+    scale = np.sqrt(np.mean(np.sum(f2 ** 2, axis=1)))
+    assert np.abs(f1 - f2).max() < 1e-5 * scale
+    assert np.abs(x1 - x2).max() < 1e-7
+
+
+def test_autotune_picks_a_working_setting_and_caches_it(tmp_path):
+    m = chaingen.melt(20, seed=29)
+    cache = str(tmp_path / "tune.txt")
+    s = md.System(m, precision=md.MD_MIXED, autotune=True, tune_cycles=1, tune_cache=cache)
+    t = s.tuning
+    assert t["from_cache"] == 0 and t["lj_block"] in (128, 256) and t["schedule"] in (0, 1)
+    assert t["skin"] > 0 and t["rebin_every"] >= 1 and t["us_per_step"] > 0
+    s.step(2 * s.rebin_every)
+    s.close()
+    s2 = md.System(m, precision=md.MD_MIXED, autotune=True, tune_cycles=1, tune_cache=cache)
+    assert s2.tuning["from_cache"] == 1 and s2.tuning["skin"] == t["skin"]
+    s2.close()
