@@ -216,6 +216,29 @@ def batched(md, cycles=5):
             "T_final_range": [float(min(temps)), float(max(temps))]}
 
 
+def adjoint(md, n_chains=50, K=500, C=50, reps=3):
+    """Adjoint configuration: 50 chains x 150 sites (7,500 sites, L = 6.10
+    nm), 500 NVE steps in FP64, checkpoints every 50 steps; gradient of
+    (<U>, <R_ee^2>) with respect to (eps, sigma, k_phi).  Wall time of the
+    synchronous forward and reverse calls (median of `reps`)."""
+    import chaingen
+    melt = equilibrate(md, chaingen.melt(n_chains, SITES, seed=5, T=500.0))
+    adj = md.Adjoint(melt, n_steps=K, checkpoint_every=C)
+    adj.forward(); adj.backward((1.0, 0.0))          # warm-up
+    tf, tb = [], []
+    for _ in range(reps):
+        t0 = time.perf_counter(); obs = adj.forward(); t1 = time.perf_counter()
+        g = adj.backward((1.0, 0.0)); t2 = time.perf_counter()
+        tf.append(t1 - t0); tb.append(t2 - t1)
+    adj.close()
+    n = n_chains * SITES
+    f, b = float(np.median(tf)), float(np.median(tb))
+    return {"sites": n, "steps": K, "checkpoint_every": C, "forward_ms": f * 1e3, "backward_ms": b * 1e3,
+            "gradient_atom_steps_per_s": n * K / (f + b), "obs": [float(o) for o in obs],
+            "grad_U": dict(zip(md.THETA_NAMES, [float(x) for x in g])),
+            "note": "FP64 state and adjoint; backward recomputes each 50-step segment from its checkpoint"}
+
+
 def cpu_baseline(melt, steps=4):
     """FP64 oracle (cell list, OpenMP on every host core): `steps`
     velocity-Verlet steps of the same melt (steps + 1 force evaluations)."""
@@ -375,6 +398,8 @@ def run_gpu(args):
     }
     if not args.no_batched:
         out["batched"] = batched(md)
+    if not args.no_adjoint:
+        out["adjoint"] = adjoint(md)
     if ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(melt)
     print(json.dumps(out), flush=True)
@@ -395,6 +420,7 @@ def main():
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-batched", action="store_true", help="skip the 64-replica measurement")
+    p.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-gradient measurement")
     p.add_argument("--chains", type=int, default=N_CHAINS, help="chains of 150 sites (default 10,000 = 1.5M sites)")
     p.add_argument("--ncu-region", action="store_true",
                    help="profile only the timed loop of the mixed form (cudaProfilerStart/Stop); "

@@ -123,6 +123,16 @@ def maxwell(masses: np.ndarray, T: float, seed: int, stream: int = 1) -> np.ndar
     return vel
 
 
+def unwrapped(m: dict) -> np.ndarray:
+    """Positions (N,3) with every chain made continuous: site 0 as stored,
+    each later site one minimum-image bond vector on from the previous."""
+    p = m["pos"].reshape(m["n_chains"], m["sites"], 3)
+    d = np.diff(p, axis=1)
+    d -= m["L"] * np.round(d / m["L"])
+    out = np.concatenate([p[:, :1], p[:, :1] + np.cumsum(d, axis=1)], axis=1)
+    return out.reshape(-1, 3)
+
+
 def uniforms(seed: int, n: int) -> np.ndarray:
     out = np.empty(n, dtype=np.float64)
     _load().cg_uniforms(ctypes.c_uint64(sub_seed(seed, 7)), n, _ptr(out))

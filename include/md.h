@@ -237,6 +237,74 @@ int md_bin_static(const double *pos, int32_t n_atoms, double box, int32_t cells_
 
 void md_destroy(md_system *sys);
 
+/* ------------------------------------------------------------------------
+ * Adjoint: gradients of trajectory means with respect to the force-field
+ * parameters theta = (eps_C32, eps_C33, sigma_C32, sigma_C33, k_phi)
+ * (Table I, Eqs. 2 and 6).
+ *
+ * One melt of n_chains linear chains (atom = chain * sites + site, both ends
+ * C_33), run in FP64 on the GPU with NVE velocity Verlet (Sec. 3.4) for
+ * n_steps.  The pair set at every step is all non-excluded pairs (1-2 and 1-3
+ * neighbours left out, Sec. 3.1) with minimum-image r < rc, from cells of
+ * side >= rc rebuilt every step.  The observables are
+ *   J_U = 1/(K+1) sum_{k=0..K} U(x_k),  U = shifted LJ + bond + angle + dihedral
+ *   J_R = 1/(K+1) sum_{k=0..K} mean over chains |x_last - x_first|^2
+ * (the end-to-end vector of Sec. 4, Fig. 8) with x unwrapped.  The gradient
+ * is that of the discrete trajectory: the reverse pass steps the adjoint of
+ * velocity Verlet newest step first, with Hessian-vector products of the LJ,
+ * bond, angle and dihedral terms and the parameter derivatives of the forces,
+ * recomputing positions from (x, v) checkpoints taken every checkpoint_every
+ * steps.  Pairs crossing rc are invisible to it (the truncated force jumps
+ * there by F(rc)).
+ * Device memory: about 8 * 3N * (2 * ceil(K / C) + C + 8) bytes, allocated
+ * by md_adj_create.  Errors: MD_E* codes with md_last_error(NULL).
+ * ------------------------------------------------------------------------ */
+typedef struct md_adj md_adj;          /* opaque, owned by the library */
+
+typedef struct {
+  int32_t n_chains;            /* >= 1 */
+  int32_t sites_per_chain;     /* 2 .. 4096 */
+  double box;                  /* cube side L, nm */
+  md_params params;            /* theta is read from eps, sigma and kphi */
+  double rc;                   /* LJ cutoff, nm */
+  double dt;                   /* ps */
+  int32_t n_steps;             /* K, 0 .. 1e7 */
+  int32_t checkpoint_every;    /* C >= 1 */
+  int32_t lj_form;             /* 0: Eq. 2 truncated at rc (the paper's potential);
+                                  1: force-shifted E(r) - E(rc) - (r - rc) E'(rc), a
+                                     variant outside the paper whose force is continuous
+                                     at rc (for gradient checks) */
+  int32_t pad;
+  void *cuda_stream;           /* NULL = a stream the library creates */
+} md_adj_desc;
+
+int md_adj_create(const md_adj_desc *desc, md_adj **out);
+
+/* Replace theta (eps and sigma positive); invalidates the last forward run. */
+int md_adj_set_theta(md_adj *adj, const double theta[5]);
+
+/* Forward run from pos, vel ([3N] x,y,z per atom, unwrapped positions, host
+ * or device pointers, copied): stores the checkpoints and writes
+ * obs = (J_U, J_R).  Synchronous. */
+int md_adj_forward(md_adj *adj, const double *pos, const double *vel, double obs[2]);
+
+/* d(w0 J_U + w1 J_R)/dtheta of the last forward run at the current theta.
+ * Synchronous. */
+int md_adj_backward(md_adj *adj, const double weight[2], double grad[5]);
+
+/* One evaluation at pos along direction dir ([3N] each): grad_u = dU/dx,
+ * hvp = H dir (H the Hessian of U), dtheta[0..4] = dU/dtheta and
+ * dtheta[5..9] = d(dU/dx . dir)/dtheta.  grad_u, hvp or dtheta may be NULL.
+ * Synchronous; does not disturb the checkpoints of the last forward run. */
+int md_adj_tangent(md_adj *adj, const double *pos, const double *dir, double *grad_u, double *hvp,
+                   double dtheta[10]);
+
+/* Totals of the last evaluation: out = (shifted LJ, bond, angle, dihedral,
+ * sum over chains of R_ee^2, U).  Synchronous. */
+int md_adj_energy(md_adj *adj, double out[6]);
+
+void md_adj_destroy(md_adj *adj);
+
 /* Message of the last failure on this system (or of the last failed
  * md_create when sys is NULL).  Valid until the next call. */
 const char *md_last_error(const md_system *sys);

@@ -17,6 +17,10 @@ Readings of the paper taken here (the paper is garbled or silent):
   * Cutoff r_c = 1.0 nm, plain truncation (Sec. 3.2 listing).  The reported
     LJ energy is also given with the per-pair shift -E(r_c) ("shifted").
   * Dihedral angle phi in the IUPAC convention (trans = 180 deg).
+  * params["lj_form"] = 1 selects a force-shifted LJ, E(r) - E(r_c) -
+    (r - r_c) E'(r_c), whose force vanishes at r_c.  It is NOT the paper's
+    potential: the gradient checks use it to separate the force jump at r_c
+    (which no adjoint of the smooth branch sees) from the adjoint itself.
 
 Parity status: every routine here is pinned by tests in tests/test_oracle.py
 (finite differences, closed forms, brute force vs cells, the paper's worked
@@ -45,7 +49,7 @@ class FF(ctypes.Structure):
                 ("mass", ctypes.c_double * 2), ("kb", ctypes.c_double), ("b0", ctypes.c_double),
                 ("ka", ctypes.c_double), ("theta0", ctypes.c_double), ("kphi", ctypes.c_double),
                 ("phis", ctypes.c_double), ("n_mult", ctypes.c_int32), ("pad", ctypes.c_int32),
-                ("rc", ctypes.c_double)]
+                ("rc", ctypes.c_double), ("lj_form", ctypes.c_int32), ("pad2", ctypes.c_int32)]
 
 
 class Sys(ctypes.Structure):
@@ -68,6 +72,7 @@ def make_ff(p: dict) -> FF:
     ff.eps[:] = p["eps"]; ff.sigma[:] = p["sigma"]; ff.mass[:] = p["mass"]
     ff.kb, ff.b0, ff.ka, ff.theta0 = p["kb"], p["b0"], p["ka"], p["theta0"]
     ff.kphi, ff.phis, ff.n_mult, ff.rc = p["kphi"], p["phis"], int(p["n_mult"]), p["rc"]
+    ff.lj_form = int(p.get("lj_form", 0))   # 1: force-shifted variant (gradient checks only)
     return ff
 
 
@@ -100,6 +105,8 @@ def lib():
         L.orc_forces.argtypes = [P, P, P, P, P, P]
         L.orc_run.argtypes = [P, P, P, P, P, P, d, i64, i32, d, d, d, P, i64, P]
         L.orc_run.restype = ctypes.c_int
+        L.orc_traj_means.argtypes = [P, P, P, P, P, d, i64, P]
+        L.orc_traj_means.restype = ctypes.c_int
         L.orc_kinetic.argtypes = [i64, i32, P, P]
         L.orc_kinetic.restype = d
         _lib = L
@@ -234,6 +241,47 @@ class System:
                            _p(f), dt, n_steps, int(thermostat), T0, tau, KB, ctypes.byref(lam_c),
                            sample_every, _p(samples))
         return x, v, f, samples[:nr], lam_c.value
+
+    def traj_means(self, x, v, dt: float, n_steps: int):
+        """(mean U, mean R_ee^2) over steps 0..n_steps of an NVE velocity-Verlet
+        run; U = shifted LJ + bond + angle + dihedral, R_ee from unwrapped x."""
+        x = _c(x, np.float64).reshape(-1, 3)
+        v = _c(v, np.float64).reshape(-1, 3)
+        out = np.zeros(2)
+        lib().orc_traj_means(ctypes.byref(self.s), ctypes.byref(self.ff), _p(self.masses_m), _p(x), _p(v),
+                             dt, n_steps, _p(out))
+        return out
+
+    def theta(self):
+        """The differentiated parameters (eps_C32, eps_C33, sigma_C32, sigma_C33, k_phi)."""
+        p = self.params
+        return np.array([p["eps"][0], p["eps"][1], p["sigma"][0], p["sigma"][1], p["kphi"]])
+
+    def with_theta(self, th):
+        p = dict(self.params)
+        p["eps"] = (float(th[0]), float(th[1]))
+        p["sigma"] = (float(th[2]), float(th[3]))
+        p["kphi"] = float(th[4])
+        return p
+
+    def fd_gradient(self, x, v, dt: float, n_steps: int, rel_h: float = 1e-4):
+        """Central finite differences of traj_means in each of the five
+        parameters, step rel_h * |theta_i|: array (2, 5), row 0 d<U>, row 1
+        d<R_ee^2>.  The parameters are restored afterwards."""
+        th0 = self.theta()
+        p0 = dict(self.params)
+        g = np.zeros((2, 5))
+        try:
+            for i in range(5):
+                h = rel_h * abs(th0[i])
+                tp, tm = th0.copy(), th0.copy()
+                tp[i] += h; tm[i] -= h
+                self.set_params(self.with_theta(tp)); jp = self.traj_means(x, v, dt, n_steps)
+                self.set_params(self.with_theta(tm)); jm = self.traj_means(x, v, dt, n_steps)
+                g[:, i] = (jp - jm) / (tp[i] - tm[i])
+        finally:
+            self.set_params(p0)
+        return g
 
     def kinetic(self, v):
         v = _c(v, np.float64).reshape(-1, 3)

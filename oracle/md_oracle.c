@@ -11,7 +11,9 @@
  *   - Eq. (1)-(3): E = E_nb + E_b + E_a + E_d
  *   - Eq. (2): Lennard-Jones 4 eps [(s/r)^12 - (s/r)^6], truncated at r_c
  *     (pairs with r^2 >= r_c^2 contribute nothing, Sec. 3.2 listing), with
- *     1-2 and 1-3 bonded neighbours excluded (Sec. 3.1, Dreiding II)
+ *     1-2 and 1-3 bonded neighbours excluded (Sec. 3.1, Dreiding II);
+ *     lj_form = 1 selects a force-shifted variant (not the paper's) used
+ *     only by the gradient checks
  *   - Eq. (4): 1/2 k_b (r - b)^2
  *   - Eq. (5): 1/2 k_a (theta - theta0)^2, harmonic in theta
  *   - Eq. (6): k_phi (1 + cos(n phi - phi_s)), IUPAC phi (trans = 180 deg)
@@ -41,6 +43,8 @@ typedef struct {
     double kphi, phis;       /* Eq. (6): kJ/mol, rad */
     int32_t n_mult, pad;     /* Eq. (6): periodicity n */
     double rc;               /* LJ cutoff, nm */
+    int32_t lj_form, pad2;   /* 0: Eq. (2) truncated at r_c (the paper's);
+                                1: force-shifted variant for gradient checks */
 } orc_ff;
 
 /* ------------------------------------------------------------------ */
@@ -170,7 +174,11 @@ int orc_topo_home_view(int naom, int nterm, int width, const int32_t *terms, int
 /* ------------------------------------------------------------------ */
 /* Lennard-Jones (Eq. 2) with geometric mixing of eps and sigma.         */
 
-typedef struct { double c6, c12, e_rc; } lj_pair;
+/* e_rc = E(r_c); dphi_rc = dE/dr at r_c, used by the force-shifted variant
+ * E_sf(r) = E(r) - E(r_c) - (r - r_c) dE/dr(r_c), whose force vanishes at
+ * r_c (not part of the paper's method; it makes the trajectory a smooth
+ * function of the parameters for the gradient checks). */
+typedef struct { double c6, c12, e_rc, dphi_rc, rc; int form; } lj_pair;
 
 static void lj_table(const orc_ff *ff, lj_pair tab[2][2]) {
     for (int a = 0; a < 2; ++a)
@@ -182,6 +190,9 @@ static void lj_table(const orc_ff *ff, lj_pair tab[2][2]) {
             tab[a][b].c12 = 4.0 * eps * s6 * s6;
             double ir6 = 1.0 / (ff->rc * ff->rc * ff->rc * ff->rc * ff->rc * ff->rc);
             tab[a][b].e_rc = tab[a][b].c12 * ir6 * ir6 - tab[a][b].c6 * ir6;
+            tab[a][b].dphi_rc = (-12.0 * tab[a][b].c12 * ir6 * ir6 + 6.0 * tab[a][b].c6 * ir6) / ff->rc;
+            tab[a][b].rc = ff->rc;
+            tab[a][b].form = ff->lj_form;
         }
 }
 
@@ -200,9 +211,14 @@ static int lj_one(const lj_pair *P, double rc2, const double d[3], double fi[3],
     if (r2 >= rc2) return 0;
     double ir2 = 1.0 / r2, ir6 = ir2 * ir2 * ir2;
     double fr = ir2 * ir6 * (12.0 * P->c12 * ir6 - 6.0 * P->c6);   /* |F|/r */
-    for (int a = 0; a < 3; ++a) fi[a] = fr * d[a];
     *e = P->c12 * ir6 * ir6 - P->c6 * ir6;
     *es = *e - P->e_rc;
+    if (P->form == 1) {
+        double r = sqrt(r2);
+        fr += P->dphi_rc / r;
+        *es -= (r - P->rc) * P->dphi_rc;
+    }
+    for (int a = 0; a < 3; ++a) fi[a] = fr * d[a];
     return 1;
 }
 
@@ -574,4 +590,54 @@ double orc_kinetic(int64_t n, int32_t naom, const double *mass_m, const double *
     for (int64_t i = 0; i < n; ++i)
         for (int q = 0; q < 3; ++q) ke += 0.5 * mass_m[i % naom] * v[3 * i + q] * v[3 * i + q];
     return ke;
+}
+
+/*
+ * Trajectory means used by the gradient checks.  Two observables of an NVE
+ * velocity-Verlet run of n_steps from (x0, v0), x0 unwrapped:
+ *   out[0] = 1/(K+1) sum_{k=0..K} U(x_k), U = shifted LJ + bond + angle
+ *            + dihedral (Eqs. 1-6, each LJ pair shifted by -E(r_c));
+ *   out[1] = 1/(K+1) sum_{k=0..K} 1/n_mol sum_mol |x_last - x_first|^2,
+ *            the mean-square end-to-end distance of the chains (the
+ *            end-to-end vector of Sec. 4, Fig. 8), from the unwrapped
+ *            positions of MAIDX 0 and MAIDX naom-1.
+ * x0 and v0 are not modified.
+ */
+int orc_traj_means(const orc_sys *S, const orc_ff *ff, const double *mass_m, const double *x0, const double *v0,
+                   double dt, int64_t n_steps, double *out) {
+    int64_t n = S->n_mol * S->naom;
+    double *x = (double *)malloc(sizeof(double) * 3 * n);
+    double *v = (double *)malloc(sizeof(double) * 3 * n);
+    double *f = (double *)malloc(sizeof(double) * 3 * n);
+    memcpy(x, x0, sizeof(double) * 3 * n);
+    memcpy(v, v0, sizeof(double) * 3 * n);
+    double en[7], vir[6], sum_u = 0.0, sum_r2 = 0.0;
+    orc_forces(S, ff, x, f, en, vir);
+    for (int64_t k = 0; k <= n_steps; ++k) {
+        sum_u += en[1] + en[2] + en[3] + en[4];
+        double r2 = 0.0;
+        for (int64_t mol = 0; mol < S->n_mol; ++mol) {
+            const double *a = x + 3 * (mol * S->naom), *b = x + 3 * (mol * S->naom + S->naom - 1);
+            double e[3] = { b[0] - a[0], b[1] - a[1], b[2] - a[2] };
+            r2 += dot3(e, e);
+        }
+        sum_r2 += r2 / (double)S->n_mol;
+        if (k == n_steps) break;
+        for (int64_t i = 0; i < n; ++i) {
+            double m = mass_m[i % S->naom];
+            for (int q = 0; q < 3; ++q) {
+                v[3 * i + q] += 0.5 * dt * f[3 * i + q] / m;
+                x[3 * i + q] += dt * v[3 * i + q];
+            }
+        }
+        orc_forces(S, ff, x, f, en, vir);
+        for (int64_t i = 0; i < n; ++i) {
+            double m = mass_m[i % S->naom];
+            for (int q = 0; q < 3; ++q) v[3 * i + q] += 0.5 * dt * f[3 * i + q] / m;
+        }
+    }
+    out[0] = sum_u / (double)(n_steps + 1);
+    out[1] = sum_r2 / (double)(n_steps + 1);
+    free(x); free(v); free(f);
+    return 0;
 }

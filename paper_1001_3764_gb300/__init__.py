@@ -57,6 +57,13 @@ class md_tuning(ctypes.Structure):
                 ("schedule", ctypes.c_int32), ("from_cache", ctypes.c_int32), ("us_per_step", ctypes.c_double)]
 
 
+class md_adj_desc(ctypes.Structure):
+    _fields_ = [("n_chains", ctypes.c_int32), ("sites_per_chain", ctypes.c_int32), ("box", ctypes.c_double),
+                ("params", md_params), ("rc", ctypes.c_double), ("dt", ctypes.c_double),
+                ("n_steps", ctypes.c_int32), ("checkpoint_every", ctypes.c_int32),
+                ("lj_form", ctypes.c_int32), ("pad", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p)]
+
+
 class md_energy_t(ctypes.Structure):
     _fields_ = [("lj", ctypes.c_double), ("lj_shifted", ctypes.c_double), ("bond", ctypes.c_double),
                 ("angle", ctypes.c_double), ("dihedral", ctypes.c_double), ("kinetic", ctypes.c_double),
@@ -72,7 +79,9 @@ class md_energy_t(ctypes.Structure):
 EXPORTS = ["md_autotune", "md_workspace_size", "md_create", "md_step", "md_step_async", "md_sync", "md_forces", "md_energy",
            "md_rebin", "md_get_state", "md_set_state", "md_set_params", "md_set_temperature", "md_stream",
            "md_info", "md_get_bins", "md_get_neighbors", "md_get_cell_units", "md_profile_enable", "md_profile_read",
-           "md_profile_reset", "md_launches_per_call", "md_bin_static", "md_destroy", "md_last_error"]
+           "md_profile_reset", "md_launches_per_call", "md_bin_static", "md_destroy", "md_last_error",
+           "md_adj_create", "md_adj_set_theta", "md_adj_forward", "md_adj_backward", "md_adj_tangent",
+           "md_adj_energy", "md_adj_destroy"]
 
 _lib = None
 
@@ -113,6 +122,13 @@ def load(path: str = LIB_PATH):
         "md_bin_static": ([P, i32, ctypes.c_double, i32, P, P, P, P], ctypes.c_int),
         "md_destroy": ([P], None),
         "md_last_error": ([P], ctypes.c_char_p),
+        "md_adj_create": ([P, P], ctypes.c_int),
+        "md_adj_set_theta": ([P, P], ctypes.c_int),
+        "md_adj_forward": ([P, P, P, P], ctypes.c_int),
+        "md_adj_backward": ([P, P, P], ctypes.c_int),
+        "md_adj_tangent": ([P, P, P, P, P, P], ctypes.c_int),
+        "md_adj_energy": ([P, P], ctypes.c_int),
+        "md_adj_destroy": ([P], None),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -284,6 +300,49 @@ def md_last_error(h=None) -> str:
     return load().md_last_error(h).decode()
 
 
+def md_adj_create(desc: md_adj_desc):
+    h = ctypes.c_void_p()
+    _check(load().md_adj_create(ctypes.byref(desc), ctypes.byref(h)))
+    return h
+
+
+def md_adj_set_theta(h, theta):
+    th = np.ascontiguousarray(theta, np.float64).reshape(5)
+    _check(load().md_adj_set_theta(h, _p(th)))
+
+
+def md_adj_forward(h, pos, vel) -> np.ndarray:
+    pos = np.ascontiguousarray(pos, np.float64); vel = np.ascontiguousarray(vel, np.float64)
+    obs = np.zeros(2)
+    _check(load().md_adj_forward(h, _p(pos), _p(vel), _p(obs)))
+    return obs
+
+
+def md_adj_backward(h, weight) -> np.ndarray:
+    w = np.ascontiguousarray(weight, np.float64).reshape(2)
+    g = np.zeros(5)
+    _check(load().md_adj_backward(h, _p(w), _p(g)))
+    return g
+
+
+def md_adj_tangent(h, pos, direction):
+    pos = np.ascontiguousarray(pos, np.float64); d = np.ascontiguousarray(direction, np.float64)
+    gu = np.zeros_like(pos); hv = np.zeros_like(pos); dth = np.zeros(10)
+    _check(load().md_adj_tangent(h, _p(pos), _p(d), _p(gu), _p(hv), _p(dth)))
+    return gu, hv, dth[:5], dth[5:]
+
+
+def md_adj_energy(h) -> dict:
+    out = np.zeros(6)
+    _check(load().md_adj_energy(h, _p(out)))
+    return dict(lj_shifted=out[0], bond=out[1], angle=out[2], dihedral=out[3], r2_sum=out[4], U=out[5])
+
+
+def md_adj_destroy(h):
+    if h:
+        load().md_adj_destroy(h)
+
+
 # ---------------------------------------------------------------- convenience object
 
 PROFILE_GROUPS = ("rebin", "nbr_build", "integrate", "lj", "bonded")
@@ -390,3 +449,112 @@ class System:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------- adjoint
+
+THETA_NAMES = ("eps_C32", "eps_C33", "sigma_C32", "sigma_C33", "k_phi")
+
+
+class Adjoint:
+    """FP64 NVE run of one melt on the GPU and the gradient of its trajectory
+    means (<U>, <R_ee^2>) with respect to theta = (eps_C32, eps_C33,
+    sigma_C32, sigma_C33, k_phi) by the library's adjoint kernels.
+
+    `melt` is a chaingen-format dict; its positions are unwrapped chain by
+    chain (the end-to-end distance needs continuous chains)."""
+
+    def __init__(self, melt: dict, n_steps: int = 500, checkpoint_every: int = 50, dt: float = 0.001,
+                 rc: float = 1.0, params: dict | None = None, device: int | None = None, lj_form: int = 0):
+        import torch
+        if device is not None:
+            torch.cuda.set_device(device)
+        self.params = dict(default_params() if params is None else params)
+        n_chains, sites, L = int(melt["n_chains"]), int(melt["sites"]), float(melt["L"])
+        p = np.asarray(melt["pos"], np.float64).reshape(n_chains, sites, 3)
+        d = np.diff(p, axis=1)
+        if np.abs(d).max(initial=0.0) < 0.5 * L:      # chains already continuous: keep the bits
+            self.x0 = np.ascontiguousarray(p.reshape(-1, 3))
+        else:
+            d -= L * np.round(d / L)
+            self.x0 = np.ascontiguousarray(np.concatenate([p[:, :1], p[:, :1] + np.cumsum(d, axis=1)], axis=1)
+                                           .reshape(-1, 3))
+        self.v0 = np.ascontiguousarray(melt["vel"], np.float64).reshape(-1, 3)
+        self.n_atoms = n_chains * sites
+        desc = md_adj_desc()
+        desc.n_chains, desc.sites_per_chain, desc.box = n_chains, sites, L
+        desc.params = make_params(self.params)
+        desc.rc, desc.dt, desc.n_steps, desc.checkpoint_every = rc, dt, n_steps, checkpoint_every
+        desc.lj_form = int(lj_form)     # 1: force-shifted LJ, a variant outside the paper (gradient checks)
+        self.stream = torch.cuda.Stream()
+        desc.cuda_stream = self.stream.cuda_stream
+        self.h = md_adj_create(desc)
+        self.theta = np.array([*self.params["eps"], *self.params["sigma"], self.params["kphi"]], np.float64)
+        self._forward_theta = None
+
+    def forward(self, theta=None) -> np.ndarray:
+        """(<U>, <R_ee^2>) at theta (default: the current one)."""
+        if theta is not None:
+            self.theta = np.array(theta, np.float64).reshape(5)
+            md_adj_set_theta(self.h, self.theta)
+        obs = md_adj_forward(self.h, self.x0, self.v0)
+        self._forward_theta = self.theta.copy()
+        return obs
+
+    def backward(self, weight=(1.0, 0.0), theta=None) -> np.ndarray:
+        """d(w0 <U> + w1 <R_ee^2>)/dtheta; reruns the forward pass first if
+        the checkpoints are not those of theta."""
+        if theta is not None and not np.array_equal(np.asarray(theta, np.float64), self.theta):
+            self.forward(theta)
+        if self._forward_theta is None or not np.array_equal(self._forward_theta, self.theta):
+            self.forward()
+        return md_adj_backward(self.h, weight)
+
+    def tangent(self, pos, direction):
+        """(dU/dx, H dir, dU/dtheta, d(dU/dx . dir)/dtheta) at pos."""
+        return md_adj_tangent(self.h, pos, direction)
+
+    def energy(self) -> dict:
+        return md_adj_energy(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            md_adj_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _md_adjoint_function():
+    import torch
+
+    class MDAdjoint(torch.autograd.Function):
+        """theta (5,) float64 -> (<U>, <R_ee^2>) of an Adjoint's trajectory;
+        backward runs the reverse pass for the incoming weights."""
+
+        @staticmethod
+        def forward(ctx, theta, adj):
+            th = theta.detach().cpu().numpy().astype(np.float64)
+            obs = adj.forward(th)
+            ctx.adj, ctx.theta = adj, th
+            return torch.tensor(obs, dtype=torch.float64)
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            w = grad_out.detach().cpu().numpy().astype(np.float64)
+            g = ctx.adj.backward(w, theta=ctx.theta)
+            return torch.tensor(g, dtype=torch.float64), None
+
+    return MDAdjoint
+
+
+def __getattr__(name):
+    if name == "MDAdjoint":
+        fn = _md_adjoint_function()
+        globals()["MDAdjoint"] = fn
+        return fn
+    raise AttributeError(name)

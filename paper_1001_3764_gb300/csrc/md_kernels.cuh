@@ -144,6 +144,8 @@ void launch_bin_count(bool mixed, const void* x, int N, const Tile* tiles, int n
                       const RepDev* reps, int* cell_of, int* cellc, int* count, int* slot,
                       cudaStream_t st);
 void launch_scan(const int* count, int* cell_start, int C, cudaStream_t st);
+// stable order by atom index inside each of C cells: perm[cell_start[c] + rank] = atom
+void launch_cell_rank(const int* cell_start, const int* tmp, int* perm, int C, cudaStream_t st);
 void launch_bin_scatter(const int* cell_of, const int* slot, const int* cell_start, int* tmp, int N,
                         cudaStream_t st);
 void launch_cell_sort(bool mixed, const void* x, int N, const int* cell_start, const int* tmp,

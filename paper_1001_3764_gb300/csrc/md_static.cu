@@ -57,6 +57,10 @@ __global__ void __launch_bounds__(128) k_static_rank(const int* __restrict__ cel
   }
 }
 
+void launch_cell_rank(const int* cell_start, const int* tmp, int* perm, int C, cudaStream_t st) {
+  if (C > 0) k_static_rank<<<C, 128, 0, st>>>(cell_start, tmp, perm);
+}
+
 }  // namespace mdg
 
 using namespace mdg;
@@ -99,7 +103,7 @@ extern "C" int md_bin_static(const double* pos, int32_t n_atoms, double box, int
   k_static_count<<<(n_atoms + 255) / 256, 256, 0, st>>>(pos, n_atoms, box, inv_h, cells_per_side, cell_of, count, slot);
   launch_scan(count, cell_start, (int)C, st);
   launch_bin_scatter(cell_of, slot, cell_start, tmp, n_atoms, st);
-  k_static_rank<<<(int)C, 128, 0, st>>>(cell_start, tmp, perm);
+  launch_cell_rank(cell_start, tmp, perm, (int)C, st);
   if (cudaGetLastError() != cudaSuccess) return fail(MD_ECUDA, "a binning kernel failed to launch");
   return MD_OK;
 }

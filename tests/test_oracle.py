@@ -356,3 +356,104 @@ def test_thermostat_matches_hand_recurrence():
         lam_prev = lam_k
     assert np.allclose(smp[:, 7], T, rtol=1e-12)
     assert lam == pytest.approx(lam_prev, rel=1e-12)
+
+
+# ---------------------------------------------------------------- trajectory means (gradient checks)
+
+def test_traj_means_dimer_matches_exact_discrete_oscillator():
+    """One harmonic dimer (Eq. 4 only, no angles or LJ partners), released
+    at rest from b0 + delta along x.  Velocity Verlet on the relative
+    coordinate has the exact discrete solution delta cos(k W dt) with
+    cos(W dt) = 1 - (omega dt)^2 / 2, omega^2 = k_b / mu."""
+    p = oracle.default_params()
+    s = oracle.System(oracle.chain_topology(2), 1, 4.0, params=p)
+    mu = p["mass"][1] / 2.0                      # both ends are C_33
+    dt, K, delta = 0.001, 300, 0.004
+    x = np.array([[1.0, 1.5, 1.5], [1.0 + p["b0"] + delta, 1.5, 1.5]])
+    W = math.acos(1.0 - 0.5 * (p["kb"] / mu) * dt * dt) / dt
+    k = np.arange(K + 1)
+    q = delta * np.cos(k * W * dt)
+    want_u = np.mean(0.5 * p["kb"] * q * q)
+    want_r2 = np.mean((p["b0"] + q) ** 2)
+    got = s.traj_means(x, np.zeros_like(x), dt, K)
+    assert got[0] == pytest.approx(want_u, rel=1e-9)
+    assert got[1] == pytest.approx(want_r2, rel=1e-12)
+
+
+def test_traj_means_end_to_end_of_all_trans_chains():
+    """Planar all-trans zigzag of n bonds (length b, angle theta):
+    R^2 = b^2 (n^2 sin^2(theta/2) + (n mod 2) cos^2(theta/2))."""
+    p = oracle.default_params()
+    b, th, sites = p["b0"], p["theta0"], 150
+    k = np.arange(sites - 1)
+    bonds = b * np.stack([np.full(sites - 1, math.sin(th / 2)), (-1.0) ** k * math.cos(th / 2),
+                          np.zeros(sites - 1)], axis=1)
+    chain = np.concatenate([np.zeros((1, 3)), np.cumsum(bonds, axis=0)])
+    # two chains 3 nm apart in z, in a box much longer than a chain
+    x = np.concatenate([chain + [0.5, 1.0, 1.0], chain + [0.5, 1.0, 4.0]])
+    s = oracle.System(oracle.chain_topology(sites), 2, 40.0)
+    n = sites - 1
+    want = b * b * (n * n * math.sin(th / 2) ** 2 + math.cos(th / 2) ** 2)
+    assert s.traj_means(x, np.zeros_like(x), 0.001, 0)[1] == pytest.approx(want, rel=1e-12)
+
+
+def test_fd_gradient_at_zero_steps_against_closed_forms():
+    """With K = 0 the means are U(x0) and R_ee^2(x0).  E_d is linear in
+    k_phi (Eq. 6), the LJ energy is homogeneous of degree 1 in (eps_C32,
+    eps_C33) under the geometric mean, and R_ee^2 does not depend on any
+    parameter."""
+    m, s = _small_system()
+    x = chaingen.unwrapped(m)
+    _, en, _ = s.forces(x)
+    g = s.fd_gradient(x, m["vel"], 0.001, 0)
+    th = s.theta()
+    assert g[0, 4] == pytest.approx(en[4] / th[4], rel=1e-8)
+    assert th[0] * g[0, 0] + th[1] * g[0, 1] == pytest.approx(en[1], rel=1e-7)
+    assert np.abs(g[1]).max() < 1e-9
+
+
+def test_fd_gradient_sigma_of_an_isolated_pair():
+    """Two bond-free C_33 sites at r < r_c: U = 4 eps [(s/r)^12 - (s/r)^6]
+    minus the same at r_c, so dU/dsigma_C33 has a closed form."""
+    p = oracle.default_params()
+    topo = oracle.Topology(2, np.zeros((0, 2), np.int32), np.array([1, 1], np.int32))
+    s = oracle.System(topo, 1, 5.0, params=p)
+    r, rc, eps, sig = 0.41, p["rc"], p["eps"][1], p["sigma"][1]
+    x = np.array([[1.0, 1.0, 1.0], [1.0 + r, 1.0, 1.0]])
+    d = lambda q: 4 * eps * (12 * sig ** 11 / q ** 12 - 6 * sig ** 5 / q ** 6)
+    g = s.fd_gradient(x, np.zeros_like(x), 0.001, 0, rel_h=1e-5)
+    assert g[0, 3] == pytest.approx(d(r) - d(rc), rel=1e-7)
+    assert g[0, 1] == pytest.approx((4 * ((sig / r) ** 12 - (sig / r) ** 6 - (sig / rc) ** 12 + (sig / rc) ** 6)),
+                                    rel=1e-7)
+    assert abs(g[0, 0]) < 1e-9 and abs(g[0, 2]) < 1e-9
+
+
+def test_force_shifted_variant_closed_form_and_continuity():
+    """lj_form = 1: E_sf(r) = E(r) - E(r_c) - (r - r_c) E'(r_c) with
+    E = 4 eps [(s/r)^12 - (s/r)^6]; energy and force both vanish at r_c."""
+    p = dict(oracle.default_params(), lj_form=1)
+    topo = oracle.Topology(2, np.zeros((0, 2), np.int32), np.array([0, 0], np.int32))
+    s = oracle.System(topo, 1, 5.0, params=p)
+    eps, sig, rc = p["eps"][0], p["sigma"][0], p["rc"]
+    E = lambda r: 4 * eps * ((sig / r) ** 12 - (sig / r) ** 6)
+    dE = lambda r: 4 * eps * (-12 * sig ** 12 / r ** 13 + 6 * sig ** 6 / r ** 7)
+    for r in (0.35, 0.5, 0.8, rc - 1e-9):
+        x = np.array([[1.0, 1.0, 1.0], [1.0 + r, 1.0, 1.0]])
+        f, en, _ = s.lj(x)
+        assert en[0] == pytest.approx(E(r), rel=1e-12)
+        assert en[1] == pytest.approx(E(r) - E(rc) - (r - rc) * dE(rc), rel=1e-9, abs=1e-14)
+        assert f[1, 0] == pytest.approx(-(dE(r) - dE(rc)), rel=1e-9, abs=1e-12)
+    x = np.array([[1.0, 1.0, 1.0], [1.0 + rc - 1e-9, 1.0, 1.0]])
+    f, en, _ = s.lj(x)
+    assert abs(en[1]) < 1e-15 and abs(f[1, 0]) < 1e-9
+
+
+def test_force_shifted_variant_forces_are_minus_energy_gradient():
+    m = chaingen.melt(2, seed=4, L=3.3, T=300.0)
+    s = oracle.System(oracle.chain_topology(150), 2, m["L"], params=dict(oracle.default_params(), lj_form=1))
+    x = m["pos"]
+    f, _, _ = s.lj(x)
+    atoms = [5, 77, 160, 299]
+    fd = _fd_check(lambda y: s.lj(y)[1][1], x, atoms, h=1e-7)
+    an = np.concatenate([f[i] for i in atoms])
+    assert np.allclose(fd, an, rtol=1e-5, atol=1e-6 * np.abs(an).max())
