@@ -138,12 +138,12 @@ __global__ void __launch_bounds__(128) k_cell_sort(const T* __restrict__ x, int 
     p.x = cell_unit(x[id], cc & 1023, 0, R);
     p.y = cell_unit(x[N + id], (cc >> 10) & 1023, 0, R);
     p.z = cell_unit(x[2 * N + id], (cc >> 20) & 1023, 0, R);
-    p.w = 0.0f;
-    pos[s] = p;
-    ref[id] = p;
     const int st = site[id];
     const int chain = R.chain_off + (id - R.atom_off) / sites;
     const int type = (st == 0 || st == sites - 1) ? 1 : 0;
+    p.w = (float)type;   // LJ type: the pipelined force kernel copies positions as they are
+    pos[s] = p;
+    ref[id] = p;
     tag[s] = (chain << 9) | st | (type << kTagTypeBit);
   }
 }

@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(kIntBlock) k_integrate(void* __restrict__ xv, 
       }
       if (d2 > R.hs2u) atomicOr(flags, kFlagDisplacement);
       if (bad) atomicOr(flags, kFlagNaN);
-      pos[inv_perm[i]] = make_float4(loc[0], loc[1], loc[2], 0.f);
+      pos[inv_perm[i]] = make_float4(loc[0], loc[1], loc[2], (float)type);   // w: LJ type, as the sort writes it
     }
   }
   if (KE) {

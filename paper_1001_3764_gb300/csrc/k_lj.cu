@@ -372,78 +372,343 @@ __device__ __forceinline__ void lj_cell(int c, const float4* __restrict__ pos, c
   __syncthreads();   // the tile and tables are reused by the next cell of this block
 }
 
-// One block per cell (grid schedule) or a fixed grid that takes cells from a
-// counter (persistent schedule).  work[0] hands out cells, work[1] counts
-// finished blocks; the last block to finish resets both for the next launch
-// (no block ever waits for another).
-template <bool MIXED, bool ENERGY, int NT, bool PERSIST>
+// One block per cell.
+template <bool MIXED, bool ENERGY, int NT>
 __global__ void __launch_bounds__(NT) k_lj_tile(const float4* __restrict__ pos, const int* __restrict__ tag,
                                                 const int* __restrict__ cell_start,
                                                 const uint4* __restrict__ nbr, const int* __restrict__ ncount,
                                                 int Npad, int tile_cap, const RepDev* __restrict__ reps, int n_reps,
-                                                int C, const ForceParams fp, void* __restrict__ flj,
-                                                double* __restrict__ epart, unsigned* __restrict__ flags,
-                                                int* __restrict__ work) {
+                                                const ForceParams fp, void* __restrict__ flj,
+                                                double* __restrict__ epart, unsigned* __restrict__ flags) {
   extern __shared__ __align__(16) unsigned char smem[];
   float4* sp = reinterpret_cast<float4*>(smem);      // the tile, tile_cap entries
   __shared__ CellTile T;
   __shared__ double red[kEnergyVals][NT / 32];
-  if constexpr (!PERSIST) {
-    lj_cell<MIXED, ENERGY, NT>(blockIdx.x, pos, tag, cell_start, nbr, ncount, Npad, tile_cap, reps, n_reps, fp, flj,
-                               epart, flags, sp, T, red);
-  } else {
-    __shared__ int next;
-    for (;;) {
-      if (threadIdx.x == 0) next = atomicAdd(work, 1);
-      __syncthreads();
-      const int c = next;
-      __syncthreads();
-      if (c >= C) break;
-      lj_cell<MIXED, ENERGY, NT>(c, pos, tag, cell_start, nbr, ncount, Npad, tile_cap, reps, n_reps, fp, flj, epart,
-                                 flags, sp, T, red);
+  lj_cell<MIXED, ENERGY, NT>(blockIdx.x, pos, tag, cell_start, nbr, ncount, Npad, tile_cap, reps, n_reps, fp, flj,
+                             epart, flags, sp, T, red);
+}
+
+// ===================================================================== force, pipelined
+// Persistent blocks of NT/32 consumer warps and one producer warp.  The
+// producer takes the next cell from a counter, builds its 27-cell table, and
+// stages the cell's tile (27 runs of sorted positions, LJ type in w) and the
+// list rows of its home atoms in shared memory with bulk asynchronous copies
+// (cp.async.bulk, completion counted in bytes on an mbarrier), two stages
+// deep.  The consumers shift the staged tile into the home frame and evaluate
+// the pairs of one cell while the next is in flight; they hand a stage back
+// through a second mbarrier.  Pair arithmetic, thread split and summation
+// order are those of k_lj_tile, so both give the same bits.  Every wait is
+// bounded: a wait that gives up raises kFlagTimeout and the block returns.
+constexpr int kPipeStages = 2;
+constexpr int kPipeHomeCap = 256;           // home atoms whose list counts are staged
+constexpr unsigned kPipeSpin = 1u << 22;    // try_wait rounds before a wait gives up
+
+struct PipeMeta {
+  int c, b, n, total, qmax, tile_ok, staged, ri;
+  int start[27];
+  int off[28];
+  int nc[kPipeHomeCap];
+};
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+// wait for the completion of the phase with this parity; false if it gave up
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+  const unsigned a = smem_u32(bar);
+  for (unsigned k = 0; k < kPipeSpin; ++k) {
+    unsigned done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+// global -> shared bulk copy (16-byte aligned addresses, size a multiple of 16)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void consumer_sync(int nthreads) {
+  asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
+}
+
+template <bool MIXED, bool ENERGY, int NT>
+__global__ void __launch_bounds__(NT + 32) k_lj_pipe(const float4* __restrict__ pos, const int* __restrict__ cell_start,
+                                                     const uint4* __restrict__ nbr, const int* __restrict__ ncount,
+                                                     int Npad, int tile_cap, int list_cap,
+                                                     const RepDev* __restrict__ reps, int n_reps, int C,
+                                                     const ForceParams fp, void* __restrict__ flj,
+                                                     double* __restrict__ epart, unsigned* __restrict__ flags,
+                                                     int* __restrict__ work) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  float4* tiles = reinterpret_cast<float4*>(smem);
+  uint4* lists = reinterpret_cast<uint4*>(smem + (size_t)kPipeStages * tile_cap * sizeof(float4));
+  __shared__ __align__(8) unsigned long long full[kPipeStages], empty[kPipeStages];
+  __shared__ PipeMeta meta[kPipeStages];
+  __shared__ double red[kEnergyVals][NT / 32];
+  __shared__ int abort_all;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    abort_all = 0;
+    for (int k = 0; k < kPipeStages; ++k) {
+      mbar_init(&full[k], 32);
+      mbar_init(&empty[k], NT / 32);
     }
-    if (threadIdx.x == 0) {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  if (warp == NT / 32) {
+    // ------------------------------------------------------------ producer
+    for (int i = 0;; ++i) {
+      const int s = i % kPipeStages;
+      if (i >= kPipeStages && !mbar_wait(&empty[s], ((i / kPipeStages) - 1) & 1)) {
+        if (lane == 0) atomicOr(flags, kFlagTimeout);
+        break;
+      }
+      int c = 0;
+      if (lane == 0) c = atomicAdd(work, 1);
+      c = __shfl_sync(0xffffffffu, c, 0);
+      PipeMeta& M = meta[s];
+      if (c >= C) {
+        if (lane == 0) M.c = -1;
+        mbar_arrive(&full[s]);
+        break;
+      }
+      const int ri = find_rep_cell(reps, n_reps, c);
+      const RepDev& R = reps[ri];
+      int len = 0, st = 0;
+      if (lane < 27) {
+        const int M3 = R.M, lc = c - R.cell_base;
+        const int cx = lc % M3, cy = (lc / M3) % M3, cz = lc / (M3 * M3);
+        const int ox = lane % 3 - 1, oy = (lane / 3) % 3 - 1, oz = lane / 9 - 1;
+        const int nc = R.cell_base + (((cz + oz + M3) % M3) * M3 + ((cy + oy + M3) % M3)) * M3 + ((cx + ox + M3) % M3);
+        st = cell_start[nc];
+        len = cell_start[nc + 1] - st;
+        M.start[lane] = st;
+      }
+      int incl = len;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+      }
+      if (lane < 27) M.off[lane] = incl - len;
+      const int total = __shfl_sync(0xffffffffu, incl, 26);
+      if (lane == 0) M.off[27] = total;
+      const int b = __shfl_sync(0xffffffffu, st, 13), n = __shfl_sync(0xffffffffu, len, 13);
+      int qmax = 0;
+      for (int a = lane; a < n && a < kPipeHomeCap; a += 32) {
+        const int v = ncount[b + a];
+        M.nc[a] = v;
+        qmax = max(qmax, v);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) qmax = max(qmax, __shfl_xor_sync(0xffffffffu, qmax, o));
+      const bool tile_ok = ((total + 32) & ~31) <= tile_cap;
+      const bool staged = tile_ok && n <= kPipeHomeCap && n * qmax <= list_cap;
+      const unsigned bytes = (tile_ok ? (unsigned)total * 16u : 0u) + (staged ? (unsigned)(n * qmax) * 16u : 0u);
+      if (lane == 0) {
+        M.c = c; M.b = b; M.n = n; M.total = total; M.qmax = qmax;
+        M.tile_ok = tile_ok; M.staged = staged; M.ri = ri;
+        if (bytes) mbar_expect_tx(&full[s], bytes);
+      }
+      __syncwarp();
+      if (tile_ok && lane < 27 && len > 0)
+        bulk_g2s(tiles + (size_t)s * tile_cap + (incl - len), pos + st, (unsigned)len * 16u, &full[s]);
+      if (staged && n > 0)
+        for (int q = lane; q < qmax; q += 32)
+          bulk_g2s(lists + (size_t)s * list_cap + (size_t)q * n, nbr + (size_t)q * Npad + b, (unsigned)n * 16u,
+                   &full[s]);
+      mbar_arrive(&full[s]);
+    }
+    if (lane == 0) {
       __threadfence();
-      if (atomicAdd(work + 1, 1) == (int)gridDim.x - 1) { work[0] = 0; work[1] = 0; }
+      if (atomicAdd(work + 1, 1) == (int)gridDim.x - 1) {   // last block: reset for the next launch
+        work[0] = 0;
+        work[1] = 0;
+      }
     }
+    return;
+  }
+
+  // -------------------------------------------------------------- consumers
+  // Every consumer warp passes the same named barriers in every round, and a
+  // warp whose wait gave up (twice) raises abort_all before the first one, so
+  // all consumer warps leave together.
+  const int tid = threadIdx.x;
+  for (int i = 0;; ++i) {
+    const int s = i % kPipeStages;
+    const unsigned par = (i / kPipeStages) & 1;
+    if (!mbar_wait(&full[s], par)) {
+      if (lane == 0) atomicOr(flags, kFlagTimeout);
+      if (!mbar_wait(&full[s], par) && lane == 0) atomicExch(&abort_all, 1);
+    }
+    consumer_sync(NT);
+    if (*(volatile int*)&abort_all) break;
+    const PipeMeta& M = meta[s];
+    const int c = M.c;
+    if (c < 0) break;
+    const int n = M.n, b = M.b, total = M.total;
+    const RepDev& R = reps[M.ri];
+    float4* sp = tiles + (size_t)s * tile_cap;
+    const uint4* lst = lists + (size_t)s * list_cap;
+    float ev[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (n > 0 && M.tile_ok) {
+      // move the staged runs into the home cell's frame
+      for (int k = warp; k < 27; k += NT / 32) {
+        if (k == 13) continue;
+        const float ox = (float)(k % 3 - 1), oy = (float)((k / 3) % 3 - 1), oz = (float)(k / 9 - 1);
+        for (int t = M.off[k] + lane; t < M.off[k + 1]; t += 32) {
+          float4 q = sp[t];
+          q.x += ox; q.y += oy; q.z += oz;
+          sp[t] = q;
+        }
+      }
+      if (tid == 0) sp[total] = make_float4(1e9f, 1e9f, 1e9f, 0.f);   // sentinel slot
+    }
+    consumer_sync(NT);
+    if (n > 0 && M.tile_ok) {
+      const float4* home = sp + M.off[13];
+      const bool staged = M.staged;
+      const int TP = n > NT / 2 ? 1 : (n > NT / 4 ? 2 : 4);
+      const float rc2 = R.rc2u;
+      const float ih = R.ih_hi;
+      for (int a0 = 0; a0 < n; a0 += NT / TP) {
+        const int na = min(NT / TP, n - a0);
+        const int a = a0 + tid / TP, p = tid % TP;
+        const bool active = a < a0 + na;
+        float fx = 0.f, fy = 0.f, fz = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+        if (active) {
+          const float4 pi = home[a];
+          const int ti = pi.w != 0.f ? 1 : 0;
+          const float a0c = 12.f * R.C12u[ti], b0c = 6.f * R.C6u[ti];
+          const float da = 12.f * R.C12u[ti + 1] - a0c, db = 6.f * R.C6u[ti + 1] - b0c;
+          const int nblk = a < kPipeHomeCap ? M.nc[a] : ncount[b + a];
+          const uint4* np = nbr + b + a;
+          for (int blk = p; blk < nblk; blk += TP) {
+            const uint4 E = staged ? lst[(size_t)blk * n + a] : __ldg(np + (size_t)blk * Npad);
+            const unsigned ew[4] = {E.x, E.y, E.z, E.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              lj_pair<ENERGY>(ew[u] & 0xffffu, sp, pi, rc2, a0c, da, b0c, db, ti, R, fp, fx, fy, fz, ev);
+              lj_pair<ENERGY>(ew[u] >> 16, sp, pi, rc2, a0c, da, b0c, db, ti, R, fp, gx, gy, gz, ev);
+            }
+          }
+        }
+        fx += gx; fy += gy; fz += gz;
+        // sum the TP partial forces of an atom (adjacent lanes, fixed order)
+        if (TP >= 2) {
+          fx += __shfl_down_sync(0xffffffffu, fx, 1); fy += __shfl_down_sync(0xffffffffu, fy, 1); fz += __shfl_down_sync(0xffffffffu, fz, 1);
+        }
+        if (TP >= 4) {
+          fx += __shfl_down_sync(0xffffffffu, fx, 2); fy += __shfl_down_sync(0xffffffffu, fy, 2); fz += __shfl_down_sync(0xffffffffu, fz, 2);
+        }
+        if (active && p == 0) {
+          fx *= ih; fy *= ih; fz *= ih;             // back from cell units
+          const int sa = b + a;
+          if (MIXED) {
+            F4i o;
+            o.x = fix_of(fx, flags); o.y = fix_of(fy, flags); o.z = fix_of(fz, flags); o.w = 0;
+            reinterpret_cast<F4i*>(flj)[sa] = o;
+          } else {
+            reinterpret_cast<float4*>(flj)[sa] = make_float4(fx, fy, fz, 0.f);
+          }
+        }
+      }
+    } else if (n > 0 && tid == 0) {
+      atomicOr(flags, kFlagNbrOverflow);
+    }
+    if (ENERGY) {
+      double v[kEnergyVals];
+#pragma unroll
+      for (int k = 0; k < kEnergyVals; ++k) v[k] = 0.5 * (double)ev[k];   // full list: every pair twice
+#pragma unroll
+      for (int k = 0; k < kEnergyVals; ++k) {
+        double sv = v[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sv += __shfl_down_sync(0xffffffffu, sv, o);
+        if (lane == 0) red[k][warp] = sv;
+      }
+      consumer_sync(NT);
+      if (tid == 0) {
+        for (int k = 0; k < kEnergyVals; ++k) {
+          double sv = 0.0;
+          for (int q = 0; q < NT / 32; ++q) sv += red[k][q];
+          epart[(size_t)c * kEnergyVals + k] = sv;
+        }
+      }
+    }
+    // hand the stage back: order this thread's shared-memory writes before
+    // the producer's next bulk copy into it
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    consumer_sync(NT);
+    if (lane == 0) mbar_arrive(&empty[s]);
   }
 }
 
-template <bool MIXED, bool ENERGY, int NT, bool PERSIST>
-static void lj_launch(int grid, size_t sm, cudaStream_t st, const float4* pos, const int* tag, const int* cell_start,
-                      const uint4* nbr, const int* ncount, int Npad, int tile_cap, const RepDev* reps, int n_reps, int C,
-                      const ForceParams& fp, void* flj, double* epart, unsigned* flags, int* work) {
-  k_lj_tile<MIXED, ENERGY, NT, PERSIST><<<grid, NT, sm, st>>>(pos, tag, cell_start, nbr, ncount, Npad, tile_cap, reps,
-                                                              n_reps, C, fp, flj, epart, flags, work);
+// list rows staged per stage: two blocks per SM when the tile leaves room for
+// 1,024 rows, else one block per SM
+int lj_pipe_list_cap(int tile_cap) {
+  const int two = 3400 - tile_cap;
+  return two >= 1024 ? two : 7000 - tile_cap;
 }
 
+size_t lj_pipe_smem(int tile_cap) {
+  return (size_t)kPipeStages * (tile_cap + lj_pipe_list_cap(tile_cap)) * sizeof(float4);
+}
+
+template <bool MIXED, bool ENERGY, int NT>
+static void lj_launch(bool pipe, int grid, int tile_cap, cudaStream_t st, const float4* pos, const int* tag,
+                      const int* cell_start, const uint4* nbr, const int* ncount, int Npad, const RepDev* reps,
+                      int n_reps, int C, const ForceParams& fp, void* flj, double* epart, unsigned* flags, int* work) {
+  if (pipe)
+    k_lj_pipe<MIXED, ENERGY, NT><<<grid, NT + 32, lj_pipe_smem(tile_cap), st>>>(
+        pos, cell_start, nbr, ncount, Npad, tile_cap, lj_pipe_list_cap(tile_cap), reps, n_reps, C, fp, flj, epart,
+        flags, work);
+  else
+    k_lj_tile<MIXED, ENERGY, NT><<<C, NT, (size_t)tile_cap * sizeof(float4), st>>>(
+        pos, tag, cell_start, nbr, ncount, Npad, tile_cap, reps, n_reps, fp, flj, epart, flags);
+}
+
+// persistent_grid > 0: the pipelined kernel on that many blocks; else one
+// block per cell
 void launch_lj_tile(bool mixed, bool energy, const float4* pos, const int* tag, const int* cell_start,
                     const uint4* nbr, const int* ncount, int Npad, int tile_cap, const RepDev* reps, int n_reps, int C,
                     const ForceParams& fp, void* flj, double* epart, unsigned* flags, int block, int persistent_grid,
                     int* work, cudaStream_t st) {
-  const size_t sm = (size_t)tile_cap * sizeof(float4);
-  const int grid = persistent_grid > 0 ? persistent_grid : C;
-#define MDG_LJ(M, E, NT, P) lj_launch<M, E, NT, P>(grid, sm, st, pos, tag, cell_start, nbr, ncount, Npad, tile_cap, reps, n_reps, C, fp, flj, epart, flags, work)
-#define MDG_LJ2(NT, P) \
-  if (mixed) { if (energy) MDG_LJ(true, true, NT, P); else MDG_LJ(true, false, NT, P); } \
-  else { if (energy) MDG_LJ(false, true, NT, P); else MDG_LJ(false, false, NT, P); }
-  if (block == 128) {
-    if (persistent_grid > 0) { MDG_LJ2(128, true) } else { MDG_LJ2(128, false) }
-  } else {
-    if (persistent_grid > 0) { MDG_LJ2(256, true) } else { MDG_LJ2(256, false) }
-  }
+  const bool pipe = persistent_grid > 0;
+#define MDG_LJ(M, E, NT) lj_launch<M, E, NT>(pipe, persistent_grid, tile_cap, st, pos, tag, cell_start, nbr, ncount, Npad, reps, n_reps, C, fp, flj, epart, flags, work)
+#define MDG_LJ2(NT) \
+  if (mixed) { if (energy) MDG_LJ(true, true, NT); else MDG_LJ(true, false, NT); } \
+  else { if (energy) MDG_LJ(false, true, NT); else MDG_LJ(false, false, NT); }
+  if (block == 128) { MDG_LJ2(128) } else { MDG_LJ2(256) }
 #undef MDG_LJ2
 #undef MDG_LJ
 }
 
-// resident blocks per SM of the LJ kernel for a block size and tile
+// resident blocks per SM of the pipelined LJ kernel for a block size and tile
 int lj_blocks_per_sm(int block, int tile_cap) {
   int nb = 0;
-  const size_t sm = (size_t)tile_cap * sizeof(float4);
+  const size_t sm = lj_pipe_smem(tile_cap);
   if (block == 128)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_lj_tile<true, false, 128, true>, 128, sm);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_lj_pipe<true, false, 128>, 128 + 32, sm);
   else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_lj_tile<true, false, 256, true>, 256, sm);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_lj_pipe<true, false, 256>, 256 + 32, sm);
   return nb;
 }
 
@@ -451,11 +716,13 @@ int lj_blocks_per_sm(int block, int tile_cap) {
 // attribute is an upper bound, set for the largest tile accepted.
 cudaError_t tile_kernels_init() {
   const int mx = kStageCapMax * sizeof(float4);
+  const int mp = (int)lj_pipe_smem(kStageCapMax);
   cudaError_t e = cudaFuncSetAttribute(k_nbr_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-#define MDG_ATTR(M, E, NT, P) \
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_lj_tile<M, E, NT, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-#define MDG_ATTR4(NT, P) MDG_ATTR(true, true, NT, P) MDG_ATTR(true, false, NT, P) MDG_ATTR(false, true, NT, P) MDG_ATTR(false, false, NT, P)
-  MDG_ATTR4(128, false) MDG_ATTR4(128, true) MDG_ATTR4(256, false) MDG_ATTR4(256, true)
+#define MDG_ATTR(M, E, NT) \
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_lj_tile<M, E, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx); \
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_lj_pipe<M, E, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, mp);
+#define MDG_ATTR4(NT) MDG_ATTR(true, true, NT) MDG_ATTR(true, false, NT) MDG_ATTR(false, true, NT) MDG_ATTR(false, false, NT)
+  MDG_ATTR4(128) MDG_ATTR4(256)
 #undef MDG_ATTR4
 #undef MDG_ATTR
   return e;
