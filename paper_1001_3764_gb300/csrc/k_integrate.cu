@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(kIntBlock) k_integrate(void* __restrict__ xv, 
     if (MODE == kKineticOnly) {
     } else if (MIXED) {
       const F4i f = reinterpret_cast<const F4i*>(Fv)[i];
-      F[0] = fix_to_double(f.x); F[1] = fix_to_double(f.y); F[2] = fix_to_double(f.z);
+      F[0] = fix_to_double_i(f.x); F[1] = fix_to_double_i(f.y); F[2] = fix_to_double_i(f.z);   // integer pipe
     } else {
       const float4 f = reinterpret_cast<const float4*>(Fv)[i];
       F[0] = f.x; F[1] = f.y; F[2] = f.z;

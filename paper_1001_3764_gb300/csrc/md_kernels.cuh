@@ -102,6 +102,18 @@ __device__ __forceinline__ float cell_unit_t(double x, int c, const RepDev& R) {
   return d2f_rn_int(fma(x, R.inv_h, -half_plus(c)));
 }
 
+// int64 -> FP64 on the integer pipe, exact for |n| < 2^53: the binary64
+// fields are built directly (exponent from the leading-zero count, the
+// mantissa by a left shift, no rounding needed).
+__device__ __forceinline__ double fix_to_double_i(long long n) {
+  const unsigned long long sgn = (unsigned long long)n & 0x8000000000000000ull;
+  const unsigned long long a = n < 0 ? 0ull - (unsigned long long)n : (unsigned long long)n;
+  const int e = 63 - __clzll((long long)a);                 // msb of a (a != 0)
+  const unsigned long long m = (a << (52 - e)) & 0x000fffffffffffffull;
+  const unsigned long long bits = sgn | ((unsigned long long)(e + 1023) << 52) | m;
+  return a == 0ull ? 0.0 : __longlong_as_double((long long)bits);
+}
+
 // int64 fixed-point force -> FP64 by the 1.5 * 2^52 bias (one FP64 add, no
 // conversion instruction); exact for |n| < 2^51.
 __device__ __forceinline__ double fix_to_double(long long n) {
