@@ -108,9 +108,31 @@ def _traffic(kernel_src: str):
         return None
 
 
+def replica_seed(rank: int) -> int:
+    """Seed of rank r's replica melt: every rank steps an independent system."""
+    return 3 + 1000 * rank
+
+
 def make_workload(rank: int, chains: int = N_CHAINS):
     import chaingen
-    return chaingen.melt(chains, SITES, seed=3 + 1000 * rank, T=500.0)
+    return chaingen.melt(chains, SITES, seed=replica_seed(rank), T=500.0)
+
+
+def max_over_ranks(x: float, ws: int) -> float:
+    """The largest of x over all ranks (the slowest rank sets the time)."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(ws: int, n_atoms_per_rank: int, md_steps: int, seconds: float) -> float:
+    """Whole-job atom-steps/s: the units all ranks processed over the slowest rank's time."""
+    return ws * n_atoms_per_rank * md_steps / seconds
 
 
 def equilibrate(md, melts, rounds=6, steps=250, seed=11):
@@ -221,26 +243,40 @@ def batched(md, cycles=5):
     temps = [e["temperature"] for e in s.energy()]
     tuning = dict(s.tuning)
     s.close()
-    # the same replicas, one system at a time, same settings
-    t_seq = 0.0
-    for m, T in zip(ms, T0):
-        q = md.System(m, precision=md.MD_MIXED, thermostat=md.MD_VRESCALE, T_target=T, tau_t=0.1,
-                      skin=tuning["skin"], rebin_every=R, lj_block=tuning["lj_block"], schedule=tuning["schedule"])
-        q.step(R)
-        qs = torch.cuda.ExternalStream(md.md_stream(q.h))
+    def timed(system):
+        system.step(R)
+        qs = torch.cuda.ExternalStream(md.md_stream(system.h))
         torch.cuda.synchronize()
         a.record(qs)
-        q.step(cycles * R, sync=False)
+        system.step(cycles * R, sync=False)
         b.record(qs)
-        q.sync()
+        system.sync()
         torch.cuda.synchronize()
-        t_seq += a.elapsed_time(b) * 1e-3
-        q.close()
+        return a.elapsed_time(b) * 1e-3
+
+    # the same replicas one system at a time (mixed, same settings; and plain FP32)
+    t_seq = {md.MD_MIXED: 0.0, md.MD_PLAIN_FP32: 0.0}
+    for prec in t_seq:
+        for m, T in zip(ms, T0):
+            q = md.System(m, precision=prec, thermostat=md.MD_VRESCALE, T_target=T, tau_t=0.1,
+                          skin=tuning["skin"], rebin_every=R, lj_block=tuning["lj_block"],
+                          schedule=tuning["schedule"])
+            t_seq[prec] += timed(q)
+            q.close()
+    # one plain FP32 melt with the same total number of chains
+    big = equilibrate(md, chaingen.melt(sum(m["n_chains"] for m in ms), SITES, seed=4, T=400.0), rounds=2)
+    q = md.System(big, precision=md.MD_PLAIN_FP32, skin=tuning["skin"], rebin_every=R,
+                  lj_block=tuning["lj_block"], schedule=tuning["schedule"])
+    t_big = timed(q)
+    n_big = len(big["pos"])
+    q.close()
     steps = cycles * R
     return {"value": n_atoms * steps / t_batched, "unit": "atom-steps/s", "replicas": len(ms), "sites": n_atoms,
-            "md_steps": steps, "sequential_value": n_atoms * steps / t_seq,
-            "speedup_vs_sequential": t_seq / t_batched, "tuning": tuning,
-            "T_final_range": [float(min(temps)), float(max(temps))]}
+            "md_steps": steps, "sequential_value": n_atoms * steps / t_seq[md.MD_MIXED],
+            "speedup_vs_sequential": t_seq[md.MD_MIXED] / t_batched,
+            "sequential_plain_fp32_value": n_atoms * steps / t_seq[md.MD_PLAIN_FP32],
+            "one_plain_fp32_melt_value": n_big * steps / t_big, "one_plain_fp32_melt_sites": n_big,
+            "tuning": tuning, "T_final_range": [float(min(temps)), float(max(temps))]}
 
 
 def adjoint(md, n_chains=50, K=500, C=50, reps=3):
@@ -347,11 +383,7 @@ def run_gpu(args):
             torch.cuda.profiler.stop()
         torch.cuda.synchronize()
         ck = clocks.stop()
-        ms = a.elapsed_time(b)
-        if ws > 1:
-            t = torch.tensor([ms], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(a.elapsed_time(b), ws)
         prof_ms, prof_n = md.md_profile_read(s.h)
         md.md_profile_enable(s.h, False)
         launches = md.md_launches_per_call(s.h, MD_STEPS_PER_BENCH_STEP) * args.steps
@@ -368,7 +400,7 @@ def run_gpu(args):
                 s.set_state(pos_h, vel_h)
                 s.step(MD_STEPS_PER_BENCH_STEP)
                 s.energy()
-            e2e_s = time.perf_counter() - t0
+            e2e_s = max_over_ranks(time.perf_counter() - t0, ws)
             results[name]["e2e_s"] = e2e_s
             results[name]["e2e_h2d"] = pos_h.nbytes + vel_h.nbytes
             results[name]["e2e_d2h"] = ctypes_size_energy(md)
@@ -381,23 +413,22 @@ def run_gpu(args):
                               "launches": int(m["launches"])}), flush=True)
         return
     # energy drift of both forms (outside the timed region)
-    # energy drift of both forms on the 150k-site melt (outside the timed region)
-    dr = drift(md)
-
     if rank != 0:
         if ws > 1:
             torch.distributed.destroy_process_group()
         return
+    # energy drift of both forms on the 150k-site melt (outside the timed region, rank 0)
+    dr = drift(md)
     m = results["mixed"]
     md_steps = MD_STEPS_PER_BENCH_STEP * args.steps
-    value = ws * n_atoms * md_steps / (m["ms"] * 1e-3)
-    plain_value = ws * n_atoms * md_steps / (results["plain"]["ms"] * 1e-3)
+    value = aggregate_rate(ws, n_atoms, md_steps, m["ms"] * 1e-3)
+    plain_value = aggregate_rate(ws, n_atoms, md_steps, results["plain"]["ms"] * 1e-3)
     ns_day = md_steps / (m["ms"] * 1e-3) * DT_PS * 1e-3 * 86400
     lj_ms = m["prof_ms"][3] / max(m["prof_n"][3], 1)
     achieved = FLOP_PER_ATOM_LJ * n_atoms / (lj_ms * 1e-3) / 1e12
     src = os.path.join(ROOT, "paper_1001_3764_gb300", "csrc", "k_lj.cu")
     traffic = _traffic(src)
-    e2e_val = ws * n_atoms * md_steps / m["e2e_s"]
+    e2e_val = aggregate_rate(ws, n_atoms, md_steps, m["e2e_s"])
     out = {
         "metric": "atom-steps/s", "value": value, "unit": "atom-steps/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": m["ms"] / args.steps,

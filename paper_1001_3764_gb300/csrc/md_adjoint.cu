@@ -501,7 +501,7 @@ struct md_adj {
   int C_cells;
   // device buffers (one allocation)
   void* mem;
-  double *x, *v, *gv, *gt, *alpha, *beta, *rec, *part, *acc, *totals, *ckx, *ckv, *seg;
+  double *x, *v, *gv, *gt, *alpha, *beta, *rec, *part, *acc, *totals, *ckx, *ckv, *seg, *xk;
   int *count, *cell_start, *cell_of, *slot, *tmp, *perm;
   bool have_forward;
   double obs[2];
@@ -575,6 +575,30 @@ void chain_rule(const md_adj* a, const double* acc, double* grad) {
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
+// Record the launches `body` enqueues on the adjoint's stream as one CUDA
+// graph (the per-step launch sequence is replayed instead of re-launched).
+template <class F>
+bool capture(md_adj* a, cudaGraphExec_t* exec, F&& body) {
+  *exec = nullptr;
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(a->st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return false;
+  const int rc = body();
+  const cudaError_t e = cudaStreamEndCapture(a->st, &g);
+  if (rc != MD_OK || e != cudaSuccess || !g) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return false;
+  }
+  const cudaError_t ie = cudaGraphInstantiate(exec, g, 0);
+  cudaGraphDestroy(g);
+  if (ie != cudaSuccess) {
+    *exec = nullptr;
+    cudaGetLastError();
+    return false;
+  }
+  return true;
+}
+
 }  // namespace
 
 extern "C" int md_adj_create(const md_adj_desc* d, md_adj** out) {
@@ -643,7 +667,7 @@ extern "C" int md_adj_create(const md_adj_desc* d, md_adj** out) {
                           sizeof(double) * kRec * kRedBlocks, sizeof(double) * kAccN, sizeof(double) * kRec,
                           n3 * a->S, n3 * a->S, n3 * (size_t)(a->C + 1), sizeof(int) * a->C_cells,
                           sizeof(int) * (a->C_cells + 1), sizeof(int) * (size_t)N, sizeof(int) * (size_t)N,
-                          sizeof(int) * (size_t)N, sizeof(int) * (size_t)N};
+                          sizeof(int) * (size_t)N, sizeof(int) * (size_t)N, n3};
   const int nbuf = sizeof(sizes) / sizeof(sizes[0]);
   size_t total = 0;
   for (int k = 0; k < nbuf; ++k) total += align256(sizes[k]);
@@ -661,6 +685,7 @@ extern "C" int md_adj_create(const md_adj_desc* d, md_adj** out) {
   a->acc = (double*)ptrs[8]; a->totals = (double*)ptrs[9]; a->ckx = (double*)ptrs[10]; a->ckv = (double*)ptrs[11];
   a->seg = (double*)ptrs[12]; a->count = (int*)ptrs[13]; a->cell_start = (int*)ptrs[14];
   a->cell_of = (int*)ptrs[15]; a->slot = (int*)ptrs[16]; a->tmp = (int*)ptrs[17]; a->perm = (int*)ptrs[18];
+  a->xk = (double*)ptrs[19];
   a->have_forward = false;
   *out = a;
   return MD_OK;
@@ -686,16 +711,26 @@ extern "C" int md_adj_forward(md_adj* a, const double* pos, const double* vel, d
     return adj_fail(MD_ECUDA, "upload of the initial state failed");
   const int nb = (a->P.N + 255) / 256;
   if (evaluate(a, a->x, nullptr, 0.0, 0, 0.0) != MD_OK) return adj_fail(MD_ECUDA, "force evaluation failed");
-  for (int k = 0; k < a->K; ++k) {
+  // one velocity-Verlet step (kick-drift, forces and sums, kick) as a graph
+  cudaGraphExec_t step = nullptr;
+  if (a->K > 0 && !capture(a, &step, [&]() {
+        k_adj_kick_drift<<<nb, 256, 0, st>>>(a->x, a->v, a->gv, a->P, a->dt, nullptr);
+        const int rc = evaluate(a, a->x, nullptr, 0.0, 0, 0.0);
+        k_adj_kick<<<nb, 256, 0, st>>>(a->v, a->gv, a->P, a->dt);
+        return rc;
+      }))
+    return adj_fail(MD_ECUDA, "capturing the forward step failed");
+  int grc = MD_OK;
+  for (int k = 0; k < a->K && grc == MD_OK; ++k) {
     if (k % a->C == 0) {
       const size_t s = (size_t)(k / a->C);
       cudaMemcpyAsync(a->ckx + s * 3 * a->P.N, a->x, n3, cudaMemcpyDeviceToDevice, st);
       cudaMemcpyAsync(a->ckv + s * 3 * a->P.N, a->v, n3, cudaMemcpyDeviceToDevice, st);
     }
-    k_adj_kick_drift<<<nb, 256, 0, st>>>(a->x, a->v, a->gv, a->P, a->dt, nullptr);
-    if (evaluate(a, a->x, nullptr, 0.0, 0, 0.0) != MD_OK) return adj_fail(MD_ECUDA, "force evaluation failed");
-    k_adj_kick<<<nb, 256, 0, st>>>(a->v, a->gv, a->P, a->dt);
+    if (cudaGraphLaunch(step, st) != cudaSuccess) grc = MD_ECUDA;
   }
+  if (step) cudaGraphExecDestroy(step);
+  if (grc != MD_OK) return adj_fail(MD_ECUDA, "forward step launch failed");
   if (a->K == 0) {
     cudaMemcpyAsync(a->ckx, a->x, n3, cudaMemcpyDeviceToDevice, st);
     cudaMemcpyAsync(a->ckv, a->v, n3, cudaMemcpyDeviceToDevice, st);
@@ -725,6 +760,30 @@ extern "C" int md_adj_backward(md_adj* a, const double weight[2], double grad[5]
   if (cudaMemsetAsync(a->alpha, 0, n3, st) != cudaSuccess || cudaMemsetAsync(a->beta, 0, n3, st) != cudaSuccess ||
       cudaMemsetAsync(a->acc, 0, sizeof(double) * kAccN, st) != cudaSuccess)
     return adj_fail(MD_ECUDA, "clearing the adjoint state failed");
+  // graphs: a recomputed forward step, and a reverse step with c_k = dt at
+  // positions copied to xk (the steps k = K and k = 0 are launched directly)
+  cudaGraphExec_t rec_step = nullptr, rev_step = nullptr;
+  const bool have_graphs =
+      capture(a, &rec_step, [&]() {
+        k_adj_kick_drift<<<nb, 256, 0, st>>>(a->x, a->v, a->gv, P, a->dt, nullptr);
+        const int rc = evaluate(a, a->x, nullptr, 0.0, 2, 0.0);
+        k_adj_kick<<<nb, 256, 0, st>>>(a->v, a->gv, P, a->dt);
+        return rc;
+      }) &&
+      capture(a, &rev_step, [&]() {
+        const int rc = evaluate(a, a->xk, a->beta, a->dt, 1, wu);
+        k_adj_update<<<nb, 256, 0, st>>>(a->xk, a->gv, a->gt, P, wu, wr, a->dt, 1, a->alpha, a->beta);
+        return rc;
+      });
+  if (!have_graphs) {
+    if (rec_step) cudaGraphExecDestroy(rec_step);
+    if (rev_step) cudaGraphExecDestroy(rev_step);
+    return adj_fail(MD_ECUDA, "capturing the adjoint steps failed");
+  }
+  struct GraphGuard {
+    cudaGraphExec_t a, b;
+    ~GraphGuard() { cudaGraphExecDestroy(a); cudaGraphExecDestroy(b); }
+  } guard{rec_step, rev_step};
   for (int s = a->S - 1; s >= 0; --s) {
     const int k0 = s * a->C, k1 = (k0 + a->C < a->K) ? k0 + a->C : a->K;
     // recompute the segment's positions from its checkpoint
@@ -734,17 +793,23 @@ extern "C" int md_adj_backward(md_adj* a, const double weight[2], double grad[5]
     if (k1 > k0 && evaluate(a, a->x, nullptr, 0.0, 2, 0.0) != MD_OK)
       return adj_fail(MD_ECUDA, "force evaluation failed");
     for (int k = k0; k < k1; ++k) {
-      k_adj_kick_drift<<<nb, 256, 0, st>>>(a->x, a->v, a->gv, P, a->dt, a->seg + (size_t)(k - k0 + 1) * stride);
       if (k + 1 < k1) {
-        if (evaluate(a, a->x, nullptr, 0.0, 2, 0.0) != MD_OK) return adj_fail(MD_ECUDA, "force evaluation failed");
-        k_adj_kick<<<nb, 256, 0, st>>>(a->v, a->gv, P, a->dt);
+        if (cudaGraphLaunch(rec_step, st) != cudaSuccess) return adj_fail(MD_ECUDA, "recompute step launch failed");
+        cudaMemcpyAsync(a->seg + (size_t)(k - k0 + 1) * stride, a->x, n3, cudaMemcpyDeviceToDevice, st);
+      } else {
+        k_adj_kick_drift<<<nb, 256, 0, st>>>(a->x, a->v, a->gv, P, a->dt, a->seg + (size_t)(k - k0 + 1) * stride);
       }
     }
     // reverse steps k1 .. k0 + 1 (and 0 in the first segment)
     const int k_lo = s == 0 ? 0 : k0 + 1;
     for (int k = k1; k >= k_lo; --k) {
-      const double ck = k == a->K ? 0.0 : (k == 0 ? 0.5 * a->dt : a->dt);
       const double* xk = a->seg + (size_t)(k - k0) * stride;
+      if (k != a->K && k != 0) {
+        cudaMemcpyAsync(a->xk, xk, n3, cudaMemcpyDeviceToDevice, st);
+        if (cudaGraphLaunch(rev_step, st) != cudaSuccess) return adj_fail(MD_ECUDA, "reverse step launch failed");
+        continue;
+      }
+      const double ck = k == a->K ? 0.0 : 0.5 * a->dt;
       if (evaluate(a, xk, a->beta, ck, 1, wu) != MD_OK) return adj_fail(MD_ECUDA, "tangent evaluation failed");
       k_adj_update<<<nb, 256, 0, st>>>(xk, a->gv, a->gt, P, wu, wr, a->dt, k >= 1 ? 1 : 0, a->alpha, a->beta);
     }

@@ -222,7 +222,7 @@ def test_replicas_equal_separate_runs_and_oracle():
     both.close()
 
 
-@pytest.mark.parametrize("sites", [4, 7, 150])
+@pytest.mark.parametrize("sites", [4, 7, 150, 511])
 def test_short_chains_and_rebin_every_step(sites):
     n_chains = max(1, 1500 // sites)
     m = chaingen.melt(n_chains, sites=sites, seed=3, L=3.6)
@@ -317,6 +317,23 @@ def test_cell_unit_coordinates_are_correctly_rounded(precision):
                 ulp = np.spacing(np.float32(abs(float(exact))))
                 assert abs(Fraction(float(u[i, a])) - exact) <= Fraction(float(ulp))
     s.close()
+
+
+def test_full_size_pipelined_schedule_gives_the_same_bits():
+    """1.5M sites as benchmarked: the pipelined persistent LJ kernel (tile and
+    list rows staged by bulk copies; a cell whose rows exceed a stage reads
+    them from global memory) gives the same forces and energies, bit for bit,
+    as one block per cell."""
+    m = chaingen.melt(10000, seed=3)
+    out = []
+    for sch in (md.MD_SCHED_GRID, md.MD_SCHED_PERSISTENT):
+        s = md.System(m, precision=md.MD_MIXED, schedule=sch)
+        out.append((s.forces(), s.energy()[0]))
+        s.close()
+    assert np.array_equal(out[0][0], out[1][0])
+    for k in ("lj", "lj_shifted", "bond", "angle", "dihedral"):
+        assert out[0][1][k] == out[1][1][k], k
+    assert out[0][1]["virial"] == out[1][1]["virial"]
 
 
 def test_schedules_and_block_shapes_agree():
