@@ -116,6 +116,7 @@ struct AdjDev {
   double rc, rc2, irc6, irc12;   // cutoff and the shift terms (1/r_c)^6, (1/r_c)^12
   double irc7, irc13;            // force-shifted variant: (1/r_c)^7, (1/r_c)^13
   int sf;                        // 1 = force-shifted variant (not the paper's potential)
+  float pre2;                    // FP32 prefilter: (r_c + 1e-4 nm)^2; a candidate beyond it is out in FP64 too
   double c6[3], c12[3];       // pair types 0 = C32-C32, 1 = C32-C33, 2 = C33-C33
   double kb, b0, ka, theta0, kphi, phis;
   int n_mult;
@@ -168,13 +169,21 @@ constexpr int kR2 = 18;      // |x_last - x_first|^2 on each chain's first atom
 constexpr int kFields = 19;
 
 // ------------------------------------------------------------------ binning (stable counting sort)
+// wrapped coordinate in [0, L) (FP64), as the cell test takes it
+__device__ __forceinline__ double wrapped(double xv, const AdjDev& P) { return xv - P.L * floor(xv * P.inv_L); }
+
+// cell of every atom, its slot in the cell, and an FP32 copy of its wrapped
+// position for the pair prefilter
 __global__ void __launch_bounds__(256) k_adj_count(const double* __restrict__ x, AdjDev P, int* __restrict__ cell_of,
-                                                   int* __restrict__ count, int* __restrict__ slot) {
+                                                   int* __restrict__ count, int* __restrict__ slot,
+                                                   float4* __restrict__ x32) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= P.N) return;
   const int c = (cell_coord(x[3 * i + 2], P) * P.M + cell_coord(x[3 * i + 1], P)) * P.M + cell_coord(x[3 * i], P);
   cell_of[i] = c;
   slot[i] = atomicAdd(count + c, 1);
+  x32[i] = make_float4((float)wrapped(x[3 * i], P), (float)wrapped(x[3 * i + 1], P), (float)wrapped(x[3 * i + 2], P),
+                       0.f);
 }
 
 // ------------------------------------------------------------------ LJ, Eq. (2): one warp per atom
@@ -184,6 +193,7 @@ template <class T>
 __global__ void __launch_bounds__(32 * kLjWarps) k_adj_lj(const double* __restrict__ x, const double* __restrict__ beta,
                                                           double cu, const int* __restrict__ cell_start,
                                                           const int* __restrict__ perm, AdjDev P,
+                                                          const float4* __restrict__ x32,
                                                           double* __restrict__ gv, double* __restrict__ gt,
                                                           double* __restrict__ rec) {
   __shared__ int s_beg[kLjWarps][27];
@@ -193,6 +203,8 @@ __global__ void __launch_bounds__(32 * kLjWarps) k_adj_lj(const double* __restri
   if (i >= P.N) return;   // the whole warp leaves together
   const int si = i % P.sites, ci = i / P.sites, ti = site_type(si, P.sites);
   const V3<T> xi = load_pos<T>(x, beta, cu, i, P);
+  const float4 xf = x32[i];
+  const float Lf = (float)P.L, iLf = (float)P.inv_L;
   // candidate cells and the prefix of their sizes
   if (lane < P.n_off) {
     int cell = 0;
@@ -223,6 +235,13 @@ __global__ void __launch_bounds__(32 * kLjWarps) k_adj_lj(const double* __restri
     if (j == i) continue;
     const int sj = j % P.sites;
     if (j / P.sites == ci && abs(sj - si) <= 2) continue;   // 1-2 and 1-3 neighbours (Sec. 3.1)
+    {
+      // FP32 prefilter on the wrapped copies (error ~1e-6 nm against a 1e-4 nm margin)
+      const float4 w = x32[j];
+      float ex = xf.x - w.x, ey = xf.y - w.y, ez = xf.z - w.z;
+      ex -= Lf * rintf(ex * iLf); ey -= Lf * rintf(ey * iLf); ez -= Lf * rintf(ez * iLf);
+      if (ex * ex + ey * ey + ez * ez > P.pre2) continue;
+    }
     // the cutoff test on values only, as the definition reads
     const double dx = min_image(x[3 * i] - x[3 * j], P), dy = min_image(x[3 * i + 1] - x[3 * j + 1], P),
                  dz = min_image(x[3 * i + 2] - x[3 * j + 2], P);
@@ -502,6 +521,7 @@ struct md_adj {
   // device buffers (one allocation)
   void* mem;
   double *x, *v, *gv, *gt, *alpha, *beta, *rec, *part, *acc, *totals, *ckx, *ckv, *seg, *xk;
+  float4* x32;
   int *count, *cell_start, *cell_of, *slot, *tmp, *perm;
   bool have_forward;
   double obs[2];
@@ -533,18 +553,18 @@ int evaluate(md_adj* a, const double* xp, const double* beta, double cu, int mod
   cudaStream_t st = a->st;
   const int N = P.N;
   if (cudaMemsetAsync(a->count, 0, sizeof(int) * a->C_cells, st) != cudaSuccess) return MD_ECUDA;
-  k_adj_count<<<(N + 255) / 256, 256, 0, st>>>(xp, P, a->cell_of, a->count, a->slot);
+  k_adj_count<<<(N + 255) / 256, 256, 0, st>>>(xp, P, a->cell_of, a->count, a->slot, a->x32);
   launch_scan(a->count, a->cell_start, a->C_cells, st);
   launch_bin_scatter(a->cell_of, a->slot, a->cell_start, a->tmp, N, st);
   launch_cell_rank(a->cell_start, a->tmp, a->perm, a->C_cells, st);
   const int lj_blocks = (N + kLjWarps - 1) / kLjWarps;
   if (beta) {
-    k_adj_lj<Dual><<<lj_blocks, 32 * kLjWarps, 0, st>>>(xp, beta, cu, a->cell_start, a->perm, P, a->gv, a->gt,
-                                                          a->rec);
+    k_adj_lj<Dual><<<lj_blocks, 32 * kLjWarps, 0, st>>>(xp, beta, cu, a->cell_start, a->perm, P, a->x32, a->gv,
+                                                          a->gt, a->rec);
     k_adj_bonded<Dual><<<(N + 127) / 128, 128, 0, st>>>(xp, beta, cu, P, a->gv, a->gt, a->rec);
   } else {
-    k_adj_lj<double><<<lj_blocks, 32 * kLjWarps, 0, st>>>(xp, nullptr, 0.0, a->cell_start, a->perm, P, a->gv,
-                                                            nullptr, a->rec);
+    k_adj_lj<double><<<lj_blocks, 32 * kLjWarps, 0, st>>>(xp, nullptr, 0.0, a->cell_start, a->perm, P, a->x32,
+                                                            a->gv, nullptr, a->rec);
     k_adj_bonded<double><<<(N + 127) / 128, 128, 0, st>>>(xp, nullptr, 0.0, P, a->gv, nullptr, a->rec);
   }
   const int nb = N < kRedBlocks ? 1 : kRedBlocks;
@@ -642,6 +662,7 @@ extern "C" int md_adj_create(const md_adj_desc* d, md_adj** out) {
     return adj_fail(MD_EINVAL, "lj_form must be 0 or 1");
   }
   P.sf = d->lj_form;
+  P.pre2 = (float)((d->rc + 1e-4) * (d->rc + 1e-4));
   P.kb = p.kb; P.b0 = p.b0; P.ka = p.ka; P.theta0 = p.theta0; P.phis = p.phis; P.n_mult = p.n_mult;
   P.inv_mass[0] = 1.0 / p.mass[0];
   P.inv_mass[1] = 1.0 / p.mass[1];
@@ -667,7 +688,7 @@ extern "C" int md_adj_create(const md_adj_desc* d, md_adj** out) {
                           sizeof(double) * kRec * kRedBlocks, sizeof(double) * kAccN, sizeof(double) * kRec,
                           n3 * a->S, n3 * a->S, n3 * (size_t)(a->C + 1), sizeof(int) * a->C_cells,
                           sizeof(int) * (a->C_cells + 1), sizeof(int) * (size_t)N, sizeof(int) * (size_t)N,
-                          sizeof(int) * (size_t)N, sizeof(int) * (size_t)N, n3};
+                          sizeof(int) * (size_t)N, sizeof(int) * (size_t)N, n3, sizeof(float4) * (size_t)N};
   const int nbuf = sizeof(sizes) / sizeof(sizes[0]);
   size_t total = 0;
   for (int k = 0; k < nbuf; ++k) total += align256(sizes[k]);
@@ -686,6 +707,7 @@ extern "C" int md_adj_create(const md_adj_desc* d, md_adj** out) {
   a->seg = (double*)ptrs[12]; a->count = (int*)ptrs[13]; a->cell_start = (int*)ptrs[14];
   a->cell_of = (int*)ptrs[15]; a->slot = (int*)ptrs[16]; a->tmp = (int*)ptrs[17]; a->perm = (int*)ptrs[18];
   a->xk = (double*)ptrs[19];
+  a->x32 = (float4*)ptrs[20];
   a->have_forward = false;
   *out = a;
   return MD_OK;
