@@ -148,8 +148,9 @@ int md_step_async(md_system *sys, int64_t n_steps);
 /* Wait for queued work and report device flags (then clear them). */
 int md_sync(md_system *sys);
 
-/* Total force on every atom at the current positions, [3 * N] host doubles,
- * original order, kJ/mol/nm. */
+/* Total force on every atom at the current positions, [3 * N] doubles (host
+ * or device pointer), original order, kJ/mol/nm.  Converted on the GPU and
+ * copied in one DMA.  Synchronous. */
 int md_forces(md_system *sys, double *f_out);
 
 /* Energies of every replica at the current state, out[n_replicas]. */
@@ -160,11 +161,16 @@ int md_rebin(md_system *sys);
 
 /* Current state: positions wrapped into [0, L) ([3 * N]), velocities
  * ([3 * N]) and periodic image counters ([3 * N], may be NULL); any output
- * may be NULL.  Unwrapped position = pos + images * L. */
+ * may be NULL; host or device pointers (one DMA each, after an in-GPU
+ * transpose).  Unwrapped position = pos + images * L.  Synchronous. */
 int md_get_state(md_system *sys, double *pos, double *vel, int32_t *images);
 
-/* Replace positions and velocities ([3 * N] each, original order), reset the
- * image counters, re-bin and recompute the forces. */
+/* Replace positions and velocities ([3 * N] each, original order, host or
+ * device pointers, read before the call returns), reset the image counters,
+ * re-bin and recompute the forces.  The arrays are copied to the GPU as they
+ * are (one DMA each) and checked, wrapped and transposed there.  A non-finite
+ * value gives MD_EINVAL; the system's state is then undefined until the next
+ * successful md_set_state. */
 int md_set_state(md_system *sys, const double *pos, const double *vel);
 
 /* Replace the force-field parameters and recompute the forces. */

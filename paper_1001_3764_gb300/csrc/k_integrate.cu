@@ -205,31 +205,137 @@ void launch_integrate(bool mixed, IntegMode mode, bool ke, bool thermostat, void
 // LJ partials are per cell (replica r owns cells [cell_base, cell_base + M^3)),
 // bonded partials per integrator tile.  Fixed summation order.
 // out[r*16 + k]: k = 0 lj, 1 lj_shifted, 2 bond, 3 angle, 4 dihedral, 5..10 virial
-__global__ void k_energy_reduce(const double* __restrict__ lj_part, const double* __restrict__ b_part,
-                                const RepDev* __restrict__ reps, const Tile* __restrict__ b_tiles, int n_b_tiles,
-                                int n_reps, double* __restrict__ out) {
-  for (int r = threadIdx.x; r < n_reps; r += blockDim.x) {
-    double acc[11] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-    const RepDev& R = reps[r];
-    const int c0 = R.cell_base, c1 = R.cell_base + R.M * R.M * R.M;
-    for (int c = c0; c < c1; ++c) {
-      const double* p = lj_part + (size_t)c * 8;
-      acc[0] += p[0]; acc[1] += p[1];
-      for (int k = 0; k < 6; ++k) acc[5 + k] += p[2 + k];
-    }
-    for (int q = R.tile_off; q < R.tile_off + R.n_tiles; ++q) {
-      const double* p = b_part + (size_t)q * 9;
-      acc[2] += p[0]; acc[3] += p[1]; acc[4] += p[2];
-      for (int k = 0; k < 6; ++k) acc[5 + k] += p[3 + k];
-    }
-    for (int k = 0; k < 11; ++k) out[r * 16 + k] = acc[k];
+// One block per replica: thread t sums cells t, t + 256, ... and bonded
+// tiles t, t + 256, ...; the block then adds the 256 partials in a fixed tree
+// (warp shuffles, then the warps in order), so the sums are deterministic.
+constexpr int kRedThreads = 256;
+
+__global__ void __launch_bounds__(kRedThreads) k_energy_reduce(const double* __restrict__ lj_part,
+                                                               const double* __restrict__ b_part,
+                                                               const RepDev* __restrict__ reps,
+                                                               double* __restrict__ out) {
+  __shared__ double sh[11][kRedThreads / 32];
+  const int r = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const RepDev& R = reps[r];
+  double acc[11] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  const int c0 = R.cell_base, c1 = R.cell_base + R.M * R.M * R.M;
+  for (int c = c0 + tid; c < c1; c += kRedThreads) {
+    const double* p = lj_part + (size_t)c * 8;
+    acc[0] += p[0]; acc[1] += p[1];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) acc[5 + k] += p[2 + k];
   }
-  (void)b_tiles; (void)n_b_tiles;
+  for (int q = R.tile_off + tid; q < R.tile_off + R.n_tiles; q += kRedThreads) {
+    const double* p = b_part + (size_t)q * 9;
+    acc[2] += p[0]; acc[3] += p[1]; acc[4] += p[2];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) acc[5 + k] += p[3 + k];
+  }
+#pragma unroll
+  for (int k = 0; k < 11; ++k) {
+    double v = acc[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) sh[k][w] = v;
+  }
+  __syncthreads();
+  if (tid < 11) {
+    double v = 0.0;
+    for (int q = 0; q < kRedThreads / 32; ++q) v += sh[tid][q];
+    out[r * 16 + tid] = v;
+  }
 }
 
 void launch_energy_reduce(const double* lj_part, const double* b_part, const RepDev* reps, const Tile* b_tiles,
                           int n_b_tiles, int n_reps, double* out, cudaStream_t st) {
-  k_energy_reduce<<<1, 256, 0, st>>>(lj_part, b_part, reps, b_tiles, n_b_tiles, n_reps, out);
+  (void)b_tiles; (void)n_b_tiles;
+  if (n_reps > 0) k_energy_reduce<<<n_reps, kRedThreads, 0, st>>>(lj_part, b_part, reps, out);
+}
+
+// ------------------------------------------------------------------ output state
+// SoA state -> AoS FP64 positions, velocities and image counters in the
+// staging buffer (one DMA each to the caller afterwards).
+template <bool MIXED>
+__global__ void __launch_bounds__(256) k_egress_state(const void* __restrict__ xv, const void* __restrict__ vv,
+                                                      const int* __restrict__ img, int N, double* __restrict__ pos,
+                                                      double* __restrict__ vel, int* __restrict__ im) {
+  using T = typename std::conditional<MIXED, double, float>::type;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const T* x = reinterpret_cast<const T*>(xv);
+  const T* v = reinterpret_cast<const T*>(vv);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    pos[3 * (size_t)i + a] = (double)x[a * N + i];
+    vel[3 * (size_t)i + a] = (double)v[a * N + i];
+    im[3 * (size_t)i + a] = img[a * N + i];
+  }
+}
+
+// total force (int64 fixed point or FP32) -> AoS FP64 kJ/mol/nm
+template <bool MIXED>
+__global__ void __launch_bounds__(256) k_egress_forces(const void* __restrict__ Fv, int N, double scale,
+                                                       double* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  if constexpr (MIXED) {
+    const F4i f = reinterpret_cast<const F4i*>(Fv)[i];
+    out[3 * (size_t)i] = fix_to_double_i(f.x) * scale;
+    out[3 * (size_t)i + 1] = fix_to_double_i(f.y) * scale;
+    out[3 * (size_t)i + 2] = fix_to_double_i(f.z) * scale;
+  } else {
+    const float4 f = reinterpret_cast<const float4*>(Fv)[i];
+    out[3 * (size_t)i] = f.x; out[3 * (size_t)i + 1] = f.y; out[3 * (size_t)i + 2] = f.z;
+  }
+}
+
+void launch_egress_state(bool mixed, const void* x, const void* v, const int* img, int N, double* pos, double* vel,
+                         int* im, cudaStream_t st) {
+  if (N <= 0) return;
+  if (mixed) k_egress_state<true><<<(N + 255) / 256, 256, 0, st>>>(x, v, img, N, pos, vel, im);
+  else k_egress_state<false><<<(N + 255) / 256, 256, 0, st>>>(x, v, img, N, pos, vel, im);
+}
+
+void launch_egress_forces(bool mixed, const void* F, int N, double scale, double* out, cudaStream_t st) {
+  if (N <= 0) return;
+  if (mixed) k_egress_forces<true><<<(N + 255) / 256, 256, 0, st>>>(F, N, scale, out);
+  else k_egress_forces<false><<<(N + 255) / 256, 256, 0, st>>>(F, N, scale, out);
+}
+
+// ------------------------------------------------------------------ input state
+template <bool MIXED>
+__global__ void __launch_bounds__(kIntBlock) k_ingest(const double* __restrict__ stage, int N,
+                                                      const Tile* __restrict__ tiles, const RepDev* __restrict__ reps,
+                                                      void* __restrict__ xv, void* __restrict__ vv,
+                                                      int* __restrict__ img, unsigned* __restrict__ flags) {
+  using T = typename std::conditional<MIXED, double, float>::type;
+  const Tile t = tiles[blockIdx.x];
+  if ((int)threadIdx.x >= t.len) return;
+  const RepDev& R = reps[t.rep];
+  const int i = t.start + threadIdx.x;
+  T* x = reinterpret_cast<T*>(xv);
+  T* v = reinterpret_cast<T*>(vv);
+  bool bad = false;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    double xa = stage[3 * (size_t)i + a];
+    const double va = stage[3 * (size_t)N + 3 * (size_t)i + a];
+    bad |= !isfinite(xa) || !isfinite(va);
+    xa -= R.L * floor(xa / R.L);
+    if (!(xa < R.L) || xa < 0.0) xa = 0.0;
+    if (!MIXED && (float)xa >= R.Lf) xa = 0.0;
+    x[a * N + i] = (T)xa;
+    v[a * N + i] = (T)va;
+    img[a * N + i] = 0;
+  }
+  if (bad) atomicOr(flags, kFlagBadInput);
+}
+
+void launch_ingest(bool mixed, const double* stage, int N, const Tile* tiles, int n_tiles, const RepDev* reps,
+                   void* x, void* v, int* img, unsigned* flags, cudaStream_t st) {
+  if (n_tiles <= 0) return;
+  if (mixed) k_ingest<true><<<n_tiles, kIntBlock, 0, st>>>(stage, N, tiles, reps, x, v, img, flags);
+  else k_ingest<false><<<n_tiles, kIntBlock, 0, st>>>(stage, N, tiles, reps, x, v, img, flags);
 }
 
 }  // namespace mdg

@@ -58,6 +58,7 @@ struct md_system {
   int *slot = nullptr, *tmp = nullptr;
   double *lj_part = nullptr, *b_part = nullptr, *kepart = nullptr, *ke_out = nullptr, *lam = nullptr;
   double* e_out = nullptr;
+  double* stage = nullptr;                   // input staging (6N doubles)
   unsigned *done = nullptr, *flags = nullptr;
   // execution
   cudaStream_t st = nullptr;
@@ -245,6 +246,7 @@ static size_t plan(md_system* s, char* base) {
   s->done = (unsigned*)take(sizeof(unsigned));
   s->work = (int*)take(2 * sizeof(int));
   s->flags = (unsigned*)take(sizeof(unsigned));
+  s->stage = (double*)take(6 * N * sizeof(double) + 3 * N * sizeof(int));   // staging: x, v (FP64), images
   return off;
 }
 
@@ -340,40 +342,23 @@ static int check_flags(md_system* s) {
   if (f & kFlagFixOverflow) return fail(s, MD_EOVERFLOW, "force beyond the fixed-point range (a part >= 2^18 kJ/mol/nm)");
   if (f & kFlagNaN) return fail(s, MD_EUNSTABLE, "non-finite position or velocity");
   if (f & kFlagDisplacement) return fail(s, MD_EUNSTABLE, "an atom moved more than skin/2 between rebins (raise skin or lower rebin_every)");
+  if (f & kFlagBadInput) return fail(s, MD_EINVAL, "non-finite input position or velocity");
   if (f & kFlagTimeout) return fail(s, MD_ETIMEOUT, "a bounded device wait gave up");
   return fail(s, MD_ECUDA, "unknown device flag");
 }
 
 // upload positions (wrapped) and velocities, reset images
+// Caller's arrays (host or device, x,y,z per atom) -> one DMA each into the
+// staging buffer -> k_ingest checks, wraps and transposes them on the GPU.  A
+// non-finite value raises kFlagBadInput, reported by the next check_flags
+// (refresh() runs one before md_create / md_set_state return).
 static int upload_state(md_system* s, const double* pos, const double* vel) {
   const size_t N = (size_t)s->N;
-  std::vector<double> xd(3 * N), vd(3 * N);
-  for (int r = 0; r < s->n_reps; ++r) {
-    const RepDev& q = s->reps_h[r];
-    for (int i = q.atom_off; i < q.atom_off + q.n_atoms; ++i)
-      for (int a = 0; a < 3; ++a) {
-        double xa = pos[3 * (size_t)i + a];
-        if (!std::isfinite(xa) || !std::isfinite(vel[3 * (size_t)i + a]))
-          return fail(s, MD_EINVAL, "non-finite input position or velocity");
-        xa -= q.L * std::floor(xa / q.L);
-        if (xa >= q.L || xa < 0) xa = 0.0;
-        if (!s->mixed && (float)xa >= (float)q.L) xa = 0.0;
-        xd[a * N + i] = xa;
-        vd[a * N + i] = vel[3 * (size_t)i + a];
-      }
-  }
-  if (s->mixed) {
-    CU(cudaMemcpyAsync(s->x, xd.data(), 3 * N * sizeof(double), cudaMemcpyHostToDevice, s->st));
-    CU(cudaMemcpyAsync(s->v, vd.data(), 3 * N * sizeof(double), cudaMemcpyHostToDevice, s->st));
-    CU(cudaStreamSynchronize(s->st));
-  } else {
-    std::vector<float> xf(3 * N), vf(3 * N);
-    for (size_t k = 0; k < 3 * N; ++k) { xf[k] = (float)xd[k]; vf[k] = (float)vd[k]; }
-    CU(cudaMemcpyAsync(s->x, xf.data(), 3 * N * sizeof(float), cudaMemcpyHostToDevice, s->st));
-    CU(cudaMemcpyAsync(s->v, vf.data(), 3 * N * sizeof(float), cudaMemcpyHostToDevice, s->st));
-    CU(cudaStreamSynchronize(s->st));
-  }
-  CU(cudaMemsetAsync(s->img, 0, 3 * N * sizeof(int), s->st));
+  CU(cudaMemcpyAsync(s->stage, pos, 3 * N * sizeof(double), cudaMemcpyDefault, s->st));
+  CU(cudaMemcpyAsync(s->stage + 3 * N, vel, 3 * N * sizeof(double), cudaMemcpyDefault, s->st));
+  launch_ingest(s->mixed, s->stage, (int)N, s->tiles_int, (int)s->t_int.size(), s->reps, s->x, s->v, s->img,
+                s->flags, s->st);
+  CU(cudaGetLastError());
   return MD_OK;
 }
 
@@ -508,21 +493,11 @@ int md_sync(md_system* s) {
 
 int md_forces(md_system* s, double* f_out) {
   if (!s || !f_out) return fail(s, MD_EINVAL, "bad arguments");
-  CU(cudaStreamSynchronize(s->st));
   const size_t N = (size_t)s->N;
-  if (s->mixed) {
-    std::vector<F4i> h(N);
-    CU(cudaMemcpy(h.data(), s->F, N * sizeof(F4i), cudaMemcpyDeviceToHost));
-    for (size_t i = 0; i < N; ++i) {
-      f_out[3 * i] = (double)h[i].x * kFixInv;
-      f_out[3 * i + 1] = (double)h[i].y * kFixInv;
-      f_out[3 * i + 2] = (double)h[i].z * kFixInv;
-    }
-  } else {
-    std::vector<float4> h(N);
-    CU(cudaMemcpy(h.data(), s->F, N * sizeof(float4), cudaMemcpyDeviceToHost));
-    for (size_t i = 0; i < N; ++i) { f_out[3 * i] = h[i].x; f_out[3 * i + 1] = h[i].y; f_out[3 * i + 2] = h[i].z; }
-  }
+  launch_egress_forces(s->mixed, s->F, (int)N, kFixInv, s->stage, s->st);
+  CU(cudaGetLastError());
+  CU(cudaMemcpyAsync(f_out, s->stage, 3 * N * sizeof(double), cudaMemcpyDefault, s->st));
+  CU(cudaStreamSynchronize(s->st));
   return MD_OK;
 }
 
@@ -569,33 +544,16 @@ int md_rebin(md_system* s) {
 
 int md_get_state(md_system* s, double* pos, double* vel, int32_t* images) {
   if (!s) return fail(s, MD_EINVAL, "null system");
-  CU(cudaStreamSynchronize(s->st));
   const size_t N = (size_t)s->N;
-  auto fetch = [&](const void* src, double* dst) -> int {
-    if (!dst) return MD_OK;
-    if (s->mixed) {
-      std::vector<double> h(3 * N);
-      CU(cudaMemcpy(h.data(), src, 3 * N * sizeof(double), cudaMemcpyDeviceToHost));
-      for (size_t i = 0; i < N; ++i)
-        for (int a = 0; a < 3; ++a) dst[3 * i + a] = h[a * N + i];
-    } else {
-      std::vector<float> h(3 * N);
-      CU(cudaMemcpy(h.data(), src, 3 * N * sizeof(float), cudaMemcpyDeviceToHost));
-      for (size_t i = 0; i < N; ++i)
-        for (int a = 0; a < 3; ++a) dst[3 * i + a] = h[a * N + i];
-    }
-    return MD_OK;
-  };
-  int rc = fetch(s->x, pos);
-  if (rc) return rc;
-  rc = fetch(s->v, vel);
-  if (rc) return rc;
-  if (images) {
-    std::vector<int> h(3 * N);
-    CU(cudaMemcpy(h.data(), s->img, 3 * N * sizeof(int), cudaMemcpyDeviceToHost));
-    for (size_t i = 0; i < N; ++i)
-      for (int a = 0; a < 3; ++a) images[3 * i + a] = h[a * N + i];
-  }
+  double* sp = s->stage;
+  double* sv = s->stage + 3 * N;
+  int* si = reinterpret_cast<int*>(s->stage + 6 * N);
+  launch_egress_state(s->mixed, s->x, s->v, s->img, (int)N, sp, sv, si, s->st);
+  CU(cudaGetLastError());
+  if (pos) CU(cudaMemcpyAsync(pos, sp, 3 * N * sizeof(double), cudaMemcpyDefault, s->st));
+  if (vel) CU(cudaMemcpyAsync(vel, sv, 3 * N * sizeof(double), cudaMemcpyDefault, s->st));
+  if (images) CU(cudaMemcpyAsync(images, si, 3 * N * sizeof(int), cudaMemcpyDefault, s->st));
+  CU(cudaStreamSynchronize(s->st));
   return MD_OK;
 }
 

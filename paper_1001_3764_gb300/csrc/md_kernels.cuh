@@ -41,6 +41,7 @@ enum : uint32_t {
   kFlagNaN = 4u,              // non-finite position or velocity
   kFlagDisplacement = 8u,     // an atom moved more than skin/2 since the rebin
   kFlagTimeout = 16u,         // a bounded device wait gave up
+  kFlagBadInput = 32u,        // a non-finite input position or velocity (md_create / md_set_state)
 };
 
 struct RepDev {
@@ -186,6 +187,15 @@ void launch_bonded(bool mixed, bool energy, const void* x, const uint16_t* site,
 
 // ---------------------------------------------------------------- integration
 enum IntegMode { kKickDrift = 0, kKickKickDrift = 1, kKickOnly = 2, kKineticOnly = 3 };
+// Input state from a staging copy of the caller's arrays (x,y,z per atom:
+// positions, then velocities): check, wrap into [0, L), write the SoA state
+// and clear the image counters, on the integrator's tiles.
+void launch_ingest(bool mixed, const double* stage, int N, const Tile* tiles, int n_tiles, const RepDev* reps,
+                   void* x, void* v, int* img, unsigned* flags, cudaStream_t st);
+// AoS FP64 copies of the state / total force in device memory (for one DMA to the caller)
+void launch_egress_state(bool mixed, const void* x, const void* v, const int* img, int N, double* pos, double* vel,
+                         int* im, cudaStream_t st);
+void launch_egress_forces(bool mixed, const void* F, int N, double scale, double* out, cudaStream_t st);
 void launch_integrate(bool mixed, IntegMode mode, bool ke, bool thermostat, void* x, void* v, int* img,
                       const void* F, const uint16_t* site, const int* cellc, const int* inv_perm,
                       const float4* ref, float4* pos, int N, const Tile* tiles, int n_tiles,

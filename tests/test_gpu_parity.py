@@ -336,6 +336,37 @@ def test_full_size_pipelined_schedule_gives_the_same_bits():
     assert out[0][1]["virial"] == out[1][1]["virial"]
 
 
+@pytest.mark.parametrize("precision", [md.MD_MIXED, md.MD_PLAIN_FP32])
+def test_set_state_round_trip_and_non_finite_input(precision):
+    """md_set_state copies the arrays to the GPU as they are and wraps them
+    there: positions come back wrapped into [0, L) with image counters 0,
+    velocities unchanged; a NaN is reported as MD_EINVAL and a good state
+    afterwards works again."""
+    m = chaingen.melt(6, seed=31, L=3.6)
+    L = m["L"]
+    s = md.System(m, precision=precision)
+    rng = np.random.default_rng(3)
+    x_in = m["pos"] + L * rng.integers(-3, 4, size=m["pos"].shape)     # any image
+    v_in = m["vel"] * 0.5
+    s.set_state(x_in, v_in)
+    x, v, img = s.state()
+    want = x_in - L * np.floor(x_in / L)
+    tol = 1e-14 * L if precision == md.MD_MIXED else 4e-7 * L    # the GPU may fuse L * floor() into the subtraction
+    assert np.abs(x - want).max() <= tol
+    assert np.abs(v - v_in).max() <= (0.0 if precision == md.MD_MIXED else 1e-6 * np.abs(v_in).max())
+    assert not img.any()
+    bad = v_in.copy()
+    bad[17, 1] = np.nan
+    with pytest.raises(md.MDError) as e:
+        s.set_state(x_in, bad)
+    assert e.value.code == md.MD_EINVAL
+    s.set_state(m["pos"], m["vel"])
+    f = s.forces()
+    f_orc, _, _ = _oracle(m).forces(s.state()[0])
+    check_forces(f, f_orc, s.state()[0], L)
+    s.close()
+
+
 def test_schedules_and_block_shapes_agree():
     """The persistent schedule gives the same bits as one block per cell (each
     cell's forces do not depend on which block computes them); 128-thread
