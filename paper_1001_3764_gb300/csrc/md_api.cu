@@ -64,6 +64,8 @@ struct md_system {
   cudaStream_t st = nullptr;
   bool own_stream = false;
   cudaGraphExec_t cycle = nullptr;
+  cudaGraphExec_t cycle_fresh = nullptr;     // the same cycle without its leading rebin + list
+  bool fresh = false;                        // bins, list and forces are those of the current positions
   bool profile = false;
   std::vector<cudaEvent_t> ev;
   int ev_used = 0;
@@ -252,9 +254,15 @@ static size_t plan(md_system* s, char* base) {
 
 // ------------------------------------------------------------------ enqueue helpers
 static void prof_mark(md_system* s) {
-  // external records: inside a stream capture they become event-record nodes
-  if (s->profile && s->ev_used < (int)s->ev.size())
+  if (!s->profile || s->ev_used >= (int)s->ev.size()) return;
+  // inside a stream capture an external record becomes an event-record node;
+  // outside one (a remainder block launched directly) a plain record
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s->st, &cs);
+  if (cs == cudaStreamCaptureStatusActive)
     cudaEventRecordWithFlags(s->ev[s->ev_used++], s->st, cudaEventRecordExternal);
+  else
+    cudaEventRecord(s->ev[s->ev_used++], s->st);
 }
 
 static void enqueue_rebin(md_system* s) {
@@ -288,11 +296,12 @@ static void enqueue_integrate(md_system* s, IntegMode mode, bool ke) {
   prof_mark(s);
 }
 
-// one block of k steps: rebin + list, k velocity-Verlet steps
-static void enqueue_block(md_system* s, int k) {
+// one block of k steps: rebin + list (unless the bins and list are already
+// those of the current positions), k velocity-Verlet steps
+static void enqueue_block(md_system* s, int k, bool rebin = true) {
   s->ev_used = 0;
   prof_mark(s);
-  enqueue_rebin(s);
+  if (rebin) enqueue_rebin(s);
   enqueue_integrate(s, kKickDrift, false);
   enqueue_forces(s, false);
   for (int j = 1; j < k; ++j) {
@@ -319,16 +328,25 @@ static void prof_collect(md_system* s, int k) {
   cudaEventElapsedTime(&ms, s->ev[e], s->ev[e + 1]); s->prof_ms[2] += ms; s->prof_n[2] += 1;
 }
 
+// the rebin cycle as a graph, and the same without its leading rebin + list
+// (used for the first cycle after md_set_state / md_rebin, which just did
+// them; never while profiling, so that the event layout stays fixed)
 static int capture_cycle(md_system* s) {
   if (s->cycle) { cudaGraphExecDestroy(s->cycle); s->cycle = nullptr; }
-  cudaGraph_t g;
-  CU(cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal));
-  enqueue_block(s, s->R);
-  cudaError_t e = cudaStreamEndCapture(s->st, &g);
-  if (e != cudaSuccess) return fail(s, MD_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-  e = cudaGraphInstantiate(&s->cycle, g, 0);
-  cudaGraphDestroy(g);
-  if (e != cudaSuccess) return fail(s, MD_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  if (s->cycle_fresh) { cudaGraphExecDestroy(s->cycle_fresh); s->cycle_fresh = nullptr; }
+  for (int pass = 0; pass < 2; ++pass) {
+    const bool prof = s->profile;
+    if (pass == 1) s->profile = false;
+    cudaGraph_t g;
+    CU(cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal));
+    enqueue_block(s, s->R, pass == 0);
+    cudaError_t e = cudaStreamEndCapture(s->st, &g);
+    s->profile = prof;
+    if (e != cudaSuccess) return fail(s, MD_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(pass == 0 ? &s->cycle : &s->cycle_fresh, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(s, MD_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  }
   return MD_OK;
 }
 
@@ -368,7 +386,9 @@ static int refresh(md_system* s) {
   enqueue_rebin(s);
   enqueue_forces(s, false);
   s->profile = p;
-  return check_flags(s);
+  const int rc = check_flags(s);
+  s->fresh = rc == MD_OK;
+  return rc;
 }
 
 // ------------------------------------------------------------------ C ABI
@@ -465,7 +485,9 @@ int md_step_async(md_system* s, int64_t n) {
   if (!s || n < 0) return fail(s, MD_EINVAL, "bad arguments");
   const int64_t full = n / s->R, rem = n % s->R;
   for (int64_t c = 0; c < full; ++c) {
-    CU(cudaGraphLaunch(s->cycle, s->st));
+    const bool skip_rebin = c == 0 && s->fresh && !s->profile;
+    s->fresh = false;
+    CU(cudaGraphLaunch(skip_rebin ? s->cycle_fresh : s->cycle, s->st));
     if (s->profile) {
       s->ev_used = (int)std::min<int64_t>(s->ev.size(), 3 + 3 * s->R + 1);
       CU(cudaStreamSynchronize(s->st));
@@ -473,6 +495,7 @@ int md_step_async(md_system* s, int64_t n) {
     }
   }
   if (rem) {
+    s->fresh = false;
     enqueue_block(s, (int)rem);
     CU(cudaGetLastError());
     if (s->profile) { CU(cudaStreamSynchronize(s->st)); prof_collect(s, (int)rem); }
@@ -539,7 +562,9 @@ int md_rebin(md_system* s) {
   s->profile = false;
   enqueue_rebin(s);
   s->profile = p;
-  return check_flags(s);
+  const int rc = check_flags(s);
+  s->fresh = rc == MD_OK;   // the forces already belong to these positions
+  return rc;
 }
 
 int md_get_state(md_system* s, double* pos, double* vel, int32_t* images) {
@@ -819,6 +844,7 @@ void md_destroy(md_system* s) {
   if (!s) return;
   if (s->st) cudaStreamSynchronize(s->st);
   if (s->cycle) cudaGraphExecDestroy(s->cycle);
+  if (s->cycle_fresh) cudaGraphExecDestroy(s->cycle_fresh);
   for (cudaEvent_t e : s->ev) cudaEventDestroy(e);
   if (s->own_mem && s->base) cudaFree(s->base);
   if (s->own_stream && s->st) cudaStreamDestroy(s->st);

@@ -367,6 +367,23 @@ def test_set_state_round_trip_and_non_finite_input(precision):
     s.close()
 
 
+def test_first_cycle_after_set_state_skips_the_rebin_with_the_same_bits():
+    """After md_set_state the bins, list and forces belong to the current
+    positions, so the first cycle runs without its leading rebin; with
+    profiling on the full cycle runs.  Both give the same trajectory."""
+    m = chaingen.melt(10, seed=33)
+    out = []
+    for prof in (False, True):
+        s = md.System(m, precision=md.MD_MIXED)
+        s.set_state(m["pos"], m["vel"])
+        md.md_profile_enable(s.h, prof)
+        s.step(25)
+        out.append(s.state())
+        s.close()
+    for a, b in zip(out[0], out[1]):
+        assert np.array_equal(a, b)
+
+
 def test_schedules_and_block_shapes_agree():
     """The persistent schedule gives the same bits as one block per cell (each
     cell's forces do not depend on which block computes them); 128-thread
