@@ -244,7 +244,7 @@ __device__ __forceinline__ long long fix_of(float f, unsigned* flags) {
 // w.w is j's type (0/1), so the pair constants are a0 + t_j (a1 - a0)
 template <bool ENERGY>
 __device__ __forceinline__ void lj_pair(unsigned t, const float4* __restrict__ sp, const float4& pi, float rc2, float a0c,
-                                        float da, float b0c, float db, int ti, const RepDev& R, const ForceParams& fp,
+                                        float da, float b0c, float db, const float (&ec)[6],
                                         float& fx, float& fy, float& fz, float (&ev)[8]) {
   const float4 w = sp[t];
   const float dx = pi.x - w.x, dy = pi.y - w.y, dz = pi.z - w.z;
@@ -257,13 +257,12 @@ __device__ __forceinline__ void lj_pair(unsigned t, const float4* __restrict__ s
   fy += ff * dy;
   fz += ff * dz;
   if (ENERGY) {
-    const int tj = w.w != 0.f ? 1 : 0;
-    const int tt = ti + tj;
-    const float eij = ir6 * (R.C12u[tt] * ir6 - R.C6u[tt]);
-    if (r2 < rc2) {
-      ev[0] += eij;
-      ev[1] += eij - fp.erc[ti][tj];
-    }
+    // the partner's type blends the home atom's two coefficient pairs (ec);
+    // beyond r_c ir6 is 0, so only the shift needs the cutoff test
+    const float c12 = fmaf(w.w, ec[1], ec[0]), c6 = fmaf(w.w, ec[3], ec[2]);
+    const float eij = ir6 * (c12 * ir6 - c6);
+    ev[0] += eij;
+    ev[1] += eij - (r2 < rc2 ? fmaf(w.w, ec[5], ec[4]) : 0.f);
     ev[2] += dx * dx * ff; ev[3] += dy * dy * ff; ev[4] += dz * dz * ff;
     ev[5] += dx * dy * ff; ev[6] += dx * dz * ff; ev[7] += dy * dz * ff;
   }
@@ -304,6 +303,12 @@ __device__ __forceinline__ void lj_cell(int c, const float4* __restrict__ pos, c
         const int ti = (tag[s] >> kTagTypeBit) & 1;
         const float a0c = 12.f * R.C12u[ti], b0c = 6.f * R.C6u[ti];
         const float da = 12.f * R.C12u[ti + 1] - a0c, db = 6.f * R.C6u[ti + 1] - b0c;
+        float ec[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};     // energy coefficients (ENERGY only)
+        if (ENERGY) {
+          ec[0] = R.C12u[ti]; ec[1] = R.C12u[ti + 1] - ec[0];
+          ec[2] = R.C6u[ti]; ec[3] = R.C6u[ti + 1] - ec[2];
+          ec[4] = fp.erc[ti][0]; ec[5] = fp.erc[ti][1] - ec[4];
+        }
         const int nblk = ncount[s];
         const uint4* np = nbr + s;
         const uint4 z4 = make_uint4(0u, 0u, 0u, 0u);
@@ -317,8 +322,8 @@ __device__ __forceinline__ void lj_cell(int c, const float4* __restrict__ pos, c
           const unsigned ew[4] = {E.x, E.y, E.z, E.w};
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
-            lj_pair<ENERGY>(ew[u] & 0xffffu, sp, pi, rc2, a0c, da, b0c, db, ti, R, fp, fx, fy, fz, ev);
-            lj_pair<ENERGY>(ew[u] >> 16, sp, pi, rc2, a0c, da, b0c, db, ti, R, fp, gx, gy, gz, ev);
+            lj_pair<ENERGY>(ew[u] & 0xffffu, sp, pi, rc2, a0c, da, b0c, db, ec, fx, fy, fz, ev);
+            lj_pair<ENERGY>(ew[u] >> 16, sp, pi, rc2, a0c, da, b0c, db, ec, gx, gy, gz, ev);
           }
           E = E1;
           E1 = E2;
@@ -598,6 +603,12 @@ __global__ void __launch_bounds__(NT + 32) k_lj_pipe(const float4* __restrict__ 
           const int ti = pi.w != 0.f ? 1 : 0;
           const float a0c = 12.f * R.C12u[ti], b0c = 6.f * R.C6u[ti];
           const float da = 12.f * R.C12u[ti + 1] - a0c, db = 6.f * R.C6u[ti + 1] - b0c;
+          float ec[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // energy coefficients (ENERGY only)
+          if (ENERGY) {
+            ec[0] = R.C12u[ti]; ec[1] = R.C12u[ti + 1] - ec[0];
+            ec[2] = R.C6u[ti]; ec[3] = R.C6u[ti + 1] - ec[2];
+            ec[4] = fp.erc[ti][0]; ec[5] = fp.erc[ti][1] - ec[4];
+          }
           const int nblk = a < kPipeHomeCap ? M.nc[a] : ncount[b + a];
           const uint4* np = nbr + b + a;
           for (int blk = p; blk < nblk; blk += TP) {
@@ -605,8 +616,8 @@ __global__ void __launch_bounds__(NT + 32) k_lj_pipe(const float4* __restrict__ 
             const unsigned ew[4] = {E.x, E.y, E.z, E.w};
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-              lj_pair<ENERGY>(ew[u] & 0xffffu, sp, pi, rc2, a0c, da, b0c, db, ti, R, fp, fx, fy, fz, ev);
-              lj_pair<ENERGY>(ew[u] >> 16, sp, pi, rc2, a0c, da, b0c, db, ti, R, fp, gx, gy, gz, ev);
+              lj_pair<ENERGY>(ew[u] & 0xffffu, sp, pi, rc2, a0c, da, b0c, db, ec, fx, fy, fz, ev);
+              lj_pair<ENERGY>(ew[u] >> 16, sp, pi, rc2, a0c, da, b0c, db, ec, gx, gy, gz, ev);
             }
           }
         }
