@@ -256,21 +256,11 @@ def test_workspace_and_library_allocation_agree():
 
 
 @pytest.mark.parametrize("precision", [md.MD_MIXED, md.MD_PLAIN_FP32])
-def test_full_size_sampled_forces(precision):
-    """1.5M sites (10,000 chains, L = 35.68 nm), as benchmarked: forces of
-    sampled atoms against the oracle's all-atom sums."""
-    m = chaingen.melt(10000, seed=3)
-    s = md.System(m, precision=precision)
-    x, _, _ = s.state()
-    f = s.forces()
-    rng = np.random.default_rng(0)
-    sel = np.sort(rng.choice(len(x), 48, replace=False))
-    ref = _oracle(m)
-    f_lj = ref.lj_atoms(x, sel)
-    f_b, _, _ = ref.bonded(x)
-    f_orc = f_lj + f_b[sel]
+def _check_sampled(f, x, sel, f_orc, L):
+    """Sampled atoms against the oracle's all-atom sums, with the same bar as
+    check_forces (an atom with a pair within 2e-6 nm of r_c gets |F(r_c)| per
+    such pair on top)."""
     scale = np.sqrt(np.mean(np.sum(f ** 2, axis=1)))
-    L = m["L"]
     tr = cKDTree(np.mod(x, L), boxsize=L)
     amb = np.zeros(len(sel), int)
     for k, i in enumerate(sel):
@@ -285,37 +275,21 @@ def test_full_size_sampled_forces(precision):
     clean = amb == 0
     rel = np.sqrt(np.sum((f[sel] - f_orc)[clean] ** 2) / np.sum(f_orc[clean] ** 2))
     assert rel <= FORCE_TOL, rel
-    s.close()
 
 
 @pytest.mark.parametrize("precision", [md.MD_MIXED, md.MD_PLAIN_FP32])
-def test_cell_unit_coordinates_are_correctly_rounded(precision):
-    """The FP32 positions the force kernels read, u = x/h - (c + 1/2) (+ a
-    whole box for atoms that crossed a face since the rebin), written by the
-    integrator after steps: mixed form = the exact value rounded once to FP64
-    (one FMA) and once to FP32 (round-half-even, integer-pipe rounding);
-    plain form within one FP32 ulp of the exact value."""
-    from fractions import Fraction
-    m = chaingen.melt(10, seed=17)
-    s = md.System(m, precision=precision, rebin_every=4)
-    s.step(3)
+def test_full_size_sampled_forces(precision):
+    """1.5M sites (10,000 chains, L = 35.68 nm), as benchmarked: forces of
+    sampled atoms against the oracle's all-atom sums."""
+    m = chaingen.melt(10000, seed=3)
+    s = md.System(m, precision=precision)
     x, _, _ = s.state()
-    u = md.md_get_cell_units(s.h, s.n_atoms)
-    co, _, _ = s.bins()
-    M = s.info["cells_per_side"]
-    inv_h = Fraction(M / m["L"])                      # the library's (double) M / L
-    c = np.stack([co % M, (co // M) % M, co // (M * M)], 1)
-    rng = np.random.default_rng(1)
-    for i in rng.choice(s.n_atoms, 300, replace=False):
-        for a in range(3):
-            base = Fraction(float(x[i, a])) * inv_h - (int(c[i, a]) + Fraction(1, 2))
-            cands = [base + w * M for w in (-1, 0, 1)]
-            exact = min(cands, key=lambda q: abs(float(q) - float(u[i, a])))
-            if precision == md.MD_MIXED:
-                assert np.float32(float(exact)) == u[i, a], (i, a)
-            else:
-                ulp = np.spacing(np.float32(abs(float(exact))))
-                assert abs(Fraction(float(u[i, a])) - exact) <= Fraction(float(ulp))
+    f = s.forces()
+    rng = np.random.default_rng(0)
+    sel = np.sort(rng.choice(len(x), 48, replace=False))
+    ref = _oracle(m)
+    f_orc = ref.lj_atoms(x, sel) + ref.bonded(x)[0][sel]
+    _check_sampled(f, x, sel, f_orc, m["L"])
     s.close()
 
 
@@ -419,3 +393,74 @@ def test_autotune_picks_a_working_setting_and_caches_it(tmp_path):
     s2 = md.System(m, precision=md.MD_MIXED, autotune=True, tune_cycles=1, tune_cache=cache)
     assert s2.tuning["from_cache"] == 1 and s2.tuning["skin"] == t["skin"]
     s2.close()
+
+
+def _oracle_relaxed(n_chains, seed, L=None, T=500.0, rounds=3, steps=300):
+    """Generator melt relaxed by the oracle (thermostat rounds with Maxwell
+    redraws), so that long GPU runs start from the same well-behaved state."""
+    m = chaingen.melt(n_chains, seed=seed, L=L, T=T)
+    s = oracle.System(oracle.chain_topology(m["sites"]), n_chains, m["L"], use_cells=True)
+    x, v = chaingen.unwrapped(m), m["vel"]
+    for r in range(rounds):
+        x, v, _, _, _ = s.run(x, v, 0.001, steps, thermostat=True, T0=T, tau=0.05, sample_every=0)
+        v = chaingen.maxwell(m["masses"], T, seed, stream=100 + r)
+    x, v, _, _, _ = s.run(x, v, 0.001, steps, thermostat=True, T0=T, tau=0.05, sample_every=0)
+    return dict(m, pos=x, vel=v), s
+
+
+@pytest.mark.parametrize("precision", [md.MD_MIXED, md.MD_PLAIN_FP32])
+def test_config1_small_box_1000_nve_steps(precision):
+    """Config 1: 10 chains (1,500 sites) in L = 3.568 nm (M = 3: the 27 cells
+    are the whole box), 1,000 NVE steps at 500 K.  Trajectories part by chaos
+    after a few hundred steps, so the run is compared through what it must
+    share with the oracle's: the total energy stays within the oracle's own
+    excursion (x3 and a 1 kJ/mol floor; plain FP32 within 10 kJ/mol), and the
+    mean potential energy over the run agrees within 2 %."""
+    m, ref = _oracle_relaxed(10, seed=41, L=3.568)
+    s = md.System(m, precision=precision)
+    assert s.info["cells_per_side"] == 3
+    e_gpu, u_gpu = [], []
+    for k in range(21):
+        e = s.energy()[0]
+        e_gpu.append(e["total"]); u_gpu.append(e["total"] - e["kinetic"])
+        if k < 20:
+            s.step(50)
+    s.close()
+    _, _, _, smp, _ = ref.run(m["pos"], m["vel"], 0.001, 1000, sample_every=50)
+    e_orc = smp[:, 2] + smp[:, 3] + smp[:, 4] + smp[:, 5] + smp[:, 6]
+    u_orc = e_orc - smp[:, 6]
+    assert abs(e_gpu[0] - e_orc[0]) < 1e-4 * abs(e_orc[0]) + 1e-2
+    exc_orc = np.abs(e_orc - e_orc[0]).max()
+    exc_gpu = np.abs(np.array(e_gpu) - e_gpu[0]).max()
+    floor = 1.0 if precision == md.MD_MIXED else 10.0
+    assert exc_gpu <= 3.0 * exc_orc + floor, (exc_gpu, exc_orc)
+    assert abs(np.mean(u_gpu) - np.mean(u_orc)) <= 0.02 * abs(np.mean(u_orc)) + 5.0
+
+
+def test_config2_quench_plain_fp32():
+    """Config 2: 1,000 chains (150,000 sites, L = 16.56 nm) in plain FP32,
+    with the weak-coupling thermostat set to 300 K (the quench): sampled
+    forces at the start against the oracle's all-atom sums, and the
+    temperature series of the first 30 steps against the oracle's run."""
+    m = chaingen.melt(1000, seed=2, T=500.0)
+    assert abs(m["L"] - 16.56) < 0.01
+    # straight from the generator: its hottest contacts move atoms faster than
+    # skin/2 per 10 steps with the default 0.1 nm skin, so a wider skin here
+    # (the pair set inside r_c does not depend on it)
+    s = md.System(m, precision=md.MD_PLAIN_FP32, thermostat=md.MD_VRESCALE, T_target=300.0, tau_t=0.1,
+                  skin=0.25, rebin_every=10)
+    x0, v0, _ = s.state()
+    f = s.forces()
+    rng = np.random.default_rng(2)
+    sel = np.sort(rng.choice(len(x0), 64, replace=False))
+    ref = _oracle(m)
+    _check_sampled(f, x0, sel, ref.lj_atoms(x0, sel) + ref.bonded(x0)[0][sel], m["L"])
+    temps = [s.energy()[0]["temperature"]]
+    for _ in range(3):
+        s.step(10)
+        temps.append(s.energy()[0]["temperature"])
+    s.close()
+    _, _, _, smp, _ = ref.run(x0, v0, 0.001, 30, thermostat=True, T0=300.0, tau=0.1, sample_every=10)
+    # (from the generator's hot start the contacts heat the melt faster than
+    # the 0.1 ps coupling removes it over 30 steps; the oracle does the same)
+    assert np.allclose(temps, smp[:, 7], rtol=2e-4), (temps, smp[:, 7])
