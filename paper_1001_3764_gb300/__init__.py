@@ -81,7 +81,7 @@ EXPORTS = ["md_autotune", "md_workspace_size", "md_create", "md_step", "md_step_
            "md_info", "md_get_bins", "md_get_neighbors", "md_get_cell_units", "md_profile_enable", "md_profile_read",
            "md_profile_reset", "md_launches_per_call", "md_bin_static", "md_destroy", "md_last_error",
            "md_adj_create", "md_adj_set_theta", "md_adj_forward", "md_adj_backward", "md_adj_tangent",
-           "md_adj_energy", "md_adj_destroy"]
+           "md_adj_energy", "md_adj_destroy", "md_wait_selftest"]
 
 _lib = None
 
@@ -129,6 +129,7 @@ def load(path: str = LIB_PATH):
         "md_adj_tangent": ([P, P, P, P, P, P], ctypes.c_int),
         "md_adj_energy": ([P, P], ctypes.c_int),
         "md_adj_destroy": ([P], None),
+        "md_wait_selftest": ([i32], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -298,6 +299,11 @@ def md_destroy(h):
 
 def md_last_error(h=None) -> str:
     return load().md_last_error(h).decode()
+
+
+def md_wait_selftest(spins: int = 1000) -> int:
+    """Return code of the bounded-wait self-test (MD_ETIMEOUT when it works)."""
+    return int(load().md_wait_selftest(int(spins)))
 
 
 def md_adj_create(desc: md_adj_desc):

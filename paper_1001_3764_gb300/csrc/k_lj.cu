@@ -410,7 +410,6 @@ constexpr unsigned kPipeSpin = 1u << 22;    // try_wait rounds before a wait giv
 
 struct PipeMeta {
   int c, b, n, total, qmax, tile_ok, staged, ri;
-  int start[27];
   int off[28];
   int nc[kPipeHomeCap];
 };
@@ -427,9 +426,10 @@ __device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 // wait for the completion of the phase with this parity; false if it gave up
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+// after `spins` try_wait rounds
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, unsigned spins = kPipeSpin) {
   const unsigned a = smem_u32(bar);
-  for (unsigned k = 0; k < kPipeSpin; ++k) {
+  for (unsigned k = 0; k < spins; ++k) {
     unsigned done;
     asm volatile(
         "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}\n"
@@ -504,7 +504,6 @@ __global__ void __launch_bounds__(NT + 32) k_lj_pipe(const float4* __restrict__ 
         const int nc = R.cell_base + (((cz + oz + M3) % M3) * M3 + ((cy + oy + M3) % M3)) * M3 + ((cx + ox + M3) % M3);
         st = cell_start[nc];
         len = cell_start[nc + 1] - st;
-        M.start[lane] = st;
       }
       int incl = len;
 #pragma unroll
@@ -670,6 +669,22 @@ __global__ void __launch_bounds__(NT + 32) k_lj_pipe(const float4* __restrict__ 
     consumer_sync(NT);
     if (lane == 0) mbar_arrive(&empty[s]);
   }
+}
+
+// Self-test of the bounded wait: one thread waits on an mbarrier that nothing
+// arrives on, gives up after `spins` rounds and raises kFlagTimeout.
+__global__ void __launch_bounds__(32) k_wait_selftest(unsigned spins, unsigned* __restrict__ flags) {
+  __shared__ __align__(8) unsigned long long bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !mbar_wait(&bar, 0, spins)) atomicOr(flags, kFlagTimeout);
+}
+
+void launch_wait_selftest(unsigned spins, unsigned* flags, cudaStream_t st) {
+  k_wait_selftest<<<1, 32, 0, st>>>(spins, flags);
 }
 
 // list rows staged per stage: two blocks per SM when the tile leaves room for

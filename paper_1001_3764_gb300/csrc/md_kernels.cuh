@@ -181,6 +181,8 @@ void launch_lj_tile(bool mixed, bool energy, const float4* pos, const int* tag, 
 int lj_blocks_per_sm(int block, int tile_cap);
 cudaError_t tile_kernels_init();
 int tile_capacity_max();
+// one block waits on an mbarrier nothing arrives on, `spins` rounds, then raises kFlagTimeout
+void launch_wait_selftest(unsigned spins, unsigned* flags, cudaStream_t st);
 void launch_bonded(bool mixed, bool energy, const void* x, const uint16_t* site, const int* inv_perm,
                    const void* flj, int N, const Tile* tiles, int n_tiles, const RepDev* reps,
                    const ForceParams& fp, void* F, double* epart, unsigned* flags, cudaStream_t st);

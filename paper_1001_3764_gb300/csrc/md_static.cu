@@ -107,3 +107,30 @@ extern "C" int md_bin_static(const double* pos, int32_t n_atoms, double box, int
   if (cudaGetLastError() != cudaSuccess) return fail(MD_ECUDA, "a binning kernel failed to launch");
   return MD_OK;
 }
+
+extern "C" int md_wait_selftest(int32_t spins) {
+  if (spins < 1 || spins > 100000) {
+    md_set_global_error("spins must be 1 .. 100000");
+    return MD_EINVAL;
+  }
+  unsigned* flag = nullptr;
+  if (cudaMalloc(&flag, sizeof(unsigned)) != cudaSuccess) {
+    cudaGetLastError();
+    md_set_global_error("device allocation failed");
+    return MD_ENOMEM;
+  }
+  unsigned f = 0;
+  const bool ok = cudaMemset(flag, 0, sizeof(unsigned)) == cudaSuccess &&
+                  (launch_wait_selftest((unsigned)spins, flag, 0), cudaGetLastError() == cudaSuccess) &&
+                  cudaMemcpy(&f, flag, sizeof f, cudaMemcpyDeviceToHost) == cudaSuccess;
+  cudaFree(flag);
+  if (!ok) {
+    md_set_global_error("the wait self-test failed to run");
+    return MD_ECUDA;
+  }
+  if (f & kFlagTimeout) {
+    md_set_global_error("a bounded device wait gave up (expected in this self-test)");
+    return MD_ETIMEOUT;
+  }
+  return MD_OK;
+}

@@ -464,3 +464,15 @@ def test_config2_quench_plain_fp32():
     # (from the generator's hot start the contacts heat the melt faster than
     # the 0.1 ps coupling removes it over 30 steps; the oracle does the same)
     assert np.allclose(temps, smp[:, 7], rtol=2e-4), (temps, smp[:, 7])
+
+
+def test_bounded_device_wait_gives_up_and_reports_timeout():
+    """A device wait on an mbarrier that nothing arrives on gives up after its
+    round limit and reports MD_ETIMEOUT; the context stays usable."""
+    assert md.md_wait_selftest(1000) == md.MD_ETIMEOUT
+    assert "gave up" in md.md_last_error(None)
+    m = chaingen.melt(2, seed=7, L=3.4)
+    s = md.System(m, precision=md.MD_MIXED)
+    s.step(10)
+    assert np.isfinite(s.forces()).all()
+    s.close()
