@@ -476,3 +476,39 @@ def test_bounded_device_wait_gives_up_and_reports_timeout():
     s.step(10)
     assert np.isfinite(s.forces()).all()
     s.close()
+
+
+def test_list_capacity_overflow_is_reported():
+    """A neighbour list capacity far below the ~184 entries an atom needs is
+    reported as MD_EOVERFLOW (list writes stop at the capacity)."""
+    m = chaingen.melt(10, seed=34)
+    with pytest.raises(md.MDError) as e:
+        md.System(m, precision=md.MD_MIXED, nbr_capacity=16)
+    assert e.value.code == md.MD_EOVERFLOW
+
+
+def _with_contact(m, gap):
+    """Site 10 of chain 1 placed `gap` nm from site 10 of chain 0 (non-bonded)."""
+    x = m["pos"].copy()
+    x[150 + 10] = x[10] + np.array([gap, 0.0, 0.0])
+    return dict(m, pos=x)
+
+
+def test_fixed_point_range_is_reported():
+    """A force part beyond 2^18 kJ/mol/nm (two sites 0.05 nm apart) cannot be
+    held in the 2^-32 fixed point: the mixed form reports MD_EOVERFLOW."""
+    m = _with_contact(chaingen.melt(4, seed=35, L=3.6), 0.05)
+    with pytest.raises(md.MDError) as e:
+        md.System(m, precision=md.MD_MIXED)
+    assert e.value.code == md.MD_EOVERFLOW
+
+
+def test_non_finite_state_is_reported():
+    """Two sites on the same spot give a non-finite FP32 force; after one
+    rebin cycle the plain form reports MD_EUNSTABLE."""
+    m = _with_contact(chaingen.melt(4, seed=36, L=3.6), 0.0)
+    s = md.System(m, precision=md.MD_PLAIN_FP32)
+    with pytest.raises(md.MDError) as e:
+        s.step(10)
+    assert e.value.code == md.MD_EUNSTABLE
+    s.close()
