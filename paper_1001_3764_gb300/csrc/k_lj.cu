@@ -76,8 +76,9 @@ __device__ __forceinline__ void tile_setup(CellTile& T, int c, const RepDev& R, 
 // Copy the tile into shared memory, shifted into the home cell's frame: warp
 // w copies cells k = w, w + nwarps, ... (each cell is one contiguous run of
 // sorted atoms).
-// WITH_TAG: w = the atom's tag bits (list build); otherwise w = its LJ type
-// as 0.0 / 1.0 (force kernel).
+// WITH_TAG: w = the atom's chain and site bits (tag without the type bit;
+// list build); otherwise w keeps the LJ type (0.0 / 1.0) that binning and
+// integration store in the sorted positions (force kernel).
 template <bool WITH_TAG>
 __device__ __forceinline__ void tile_load(const CellTile& T, const float4* __restrict__ pos, const int* __restrict__ tag,
                                           float4* __restrict__ sp) {
@@ -88,8 +89,7 @@ __device__ __forceinline__ void tile_load(const CellTile& T, const float4* __res
     for (int q = lane; q < n; q += 32) {
       float4 p = __ldg(pos + j0 + q);
       p.x += ox; p.y += oy; p.z += oz;
-      const int tg = __ldg(tag + j0 + q);
-      p.w = WITH_TAG ? __int_as_float(tg) : (float)((tg >> kTagTypeBit) & 1);
+      if (WITH_TAG) p.w = __int_as_float(__ldg(tag + j0 + q) & (int)kTagMask);
       sp[t0 + q] = p;
     }
   }
@@ -104,60 +104,67 @@ __device__ __forceinline__ void tile_load(const CellTile& T, const float4* __res
 //
 // TP adjacent threads share a home atom; in every 32-atom word of the tile
 // thread p takes atoms p, p + TP, ... (the lanes of a warp read neighbouring
-// 16-byte slots: one shared-memory wavefront), forms their in-range bit mask
-// in a register, drops 1-2/1-3 neighbours and itself (tag test, Sec. 3.1)
-// while turning the set bits into entries (plain tile indices), and writes
-// its blocks at p, p + TP, ...; the TP threads then pad to a common number of
-// blocks.
+// 16-byte slots: one shared-memory wavefront) and keeps those within r_c +
+// skin that are not itself or a 1-2/1-3 neighbour (tag test, Sec. 3.1).  The
+// test and the keep are branch-free: a kept index goes to the thread's
+// 16-slot ring in shared memory (a predicated store) and the ring is written
+// out as a block of 8 whenever it holds 8, so no lane waits on another's set
+// bits.  Thread p writes its blocks at p, p + TP, ..., entries in increasing
+// tile order; the TP threads then pad to a common number of blocks.
 constexpr int kBuildThreads = 256;
+constexpr int kRingRow = 2 * kBuildThreads;   // bytes of one ring slot row (slot k of every thread)
 
 __device__ __forceinline__ uint4 pack_block(unsigned long long lo, unsigned long long hi) {
   return make_uint4((unsigned)lo, (unsigned)(lo >> 32), (unsigned)hi, (unsigned)(hi >> 32));
 }
 
+// entries r0 .. r0+7 of this thread's ring (byte offset `base` of slot r0),
+// slots k >= nk replaced by the sentinel
+__device__ __forceinline__ uint4 ring_block(const unsigned char* ring, unsigned base, int nk, unsigned sent) {
+  unsigned e[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+    e[k] = k < nk ? *reinterpret_cast<const unsigned short*>(ring + base + k * kRingRow) : sent;
+  return make_uint4(e[0] | (e[1] << 16), e[2] | (e[3] << 16), e[4] | (e[5] << 16), e[6] | (e[7] << 16));
+}
+
 template <int TP>
 __device__ __forceinline__ void build_atom(const float4* __restrict__ sp, int nwords, int total, float rl2, int s, int p,
-                                           const float4& pi, int ti, uint4* __restrict__ nbr, int Npad, int capb,
-                                           int& nb_out) {
-  const unsigned long long sent = (unsigned long long)total;
-  const unsigned long long sent4 = sent | (sent << 16) | (sent << 32) | (sent << 48);
-  constexpr int per = 32 / TP;                 // candidates of each word taken by this lane
-  int nb = 0, cnt = 0;
-  unsigned long long lo = 0ull, hi = 0ull;
+                                           const float4& pi, int ti, unsigned char* ring, uint4* __restrict__ nbr,
+                                           int Npad, int capb, int& nb_out) {
+  constexpr int per = 32 / TP;                 // candidates of each word taken by this lane (8, 16 or 32)
+  const unsigned me = 2u * threadIdx.x;        // this thread's column in the ring
+  const unsigned tip2 = (unsigned)ti + 2u;
+  unsigned kept = 0u, done = 0u;               // entries kept / written out, x kRingRow
+  int nb = 0;
   for (int wd = 0; wd < nwords; ++wd) {
     const float4* w32 = sp + wd * 32 + p;
-    unsigned m = 0u;
+    const unsigned t0 = (unsigned)(wd * 32 + p);
 #pragma unroll
-    for (int u = 0; u < per; ++u) {
-      const float4 w = w32[u * TP];
-      const float dx = pi.x - w.x, dy = pi.y - w.y, dz = pi.z - w.z;
-      m |= (dx * dx + dy * dy + dz * dz < rl2 ? 1u : 0u) << u;
-    }
-    while (m) {
-      const int u = __ffs(m) - 1;
-      m &= m - 1u;
-      const int t = wd * 32 + p + u * TP;
-      const int tj = __float_as_int(sp[t].w);
-      const int dtag = ti - (tj & (int)kTagMask);
-      if (dtag <= 2 && dtag >= -2) continue;          // itself, 1-2 and 1-3 neighbours
-      const unsigned long long e = (unsigned long long)t;
-      const int slot = cnt & 7;
-      if (slot < 4) lo |= e << (16 * slot); else hi |= e << (16 * (slot - 4));
-      if (slot == 7) {
-        const int q = p + TP * nb;
-        if (q < capb) nbr[(size_t)q * Npad + s] = pack_block(lo, hi);
-        ++nb;
-        lo = 0ull; hi = 0ull;
+    for (int c0 = 0; c0 < per; c0 += 8) {
+#pragma unroll
+      for (int u = c0; u < c0 + 8; ++u) {
+        const float4 w = w32[u * TP];
+        const float dx = pi.x - w.x, dy = pi.y - w.y, dz = pi.z - w.z;
+        // |i - j| <= 2 within one chain: itself, 1-2 and 1-3 neighbours
+        const bool keep = (dx * dx + dy * dy + dz * dz < rl2) & (tip2 - (unsigned)__float_as_int(w.w) > 4u);
+        if (keep) *reinterpret_cast<unsigned short*>(ring + ((kept & (15u * kRingRow)) | me)) =
+            (unsigned short)(t0 + u * TP);
+        kept += keep ? (unsigned)kRingRow : 0u;
       }
-      ++cnt;
+      // at most 8 + 7 entries pending here, so one block of 8 drains it below 8
+      if (kept - done >= 8u * kRingRow) {
+        const int q = p + TP * nb;
+        if (q < capb) nbr[(size_t)q * Npad + s] = ring_block(ring, (done & (8u * kRingRow)) | me, 8, 0u);
+        ++nb;
+        done += 8u * kRingRow;
+      }
     }
   }
-  const int rem = cnt & 7;
+  const int rem = (int)((kept - done) / kRingRow);
   if (rem) {                                          // pad the open block with the sentinel
-    const unsigned long long fill = ~0ull << (16 * (rem < 4 ? rem : rem - 4));
-    if (rem < 4) { lo |= sent4 & fill; hi = sent4; } else { hi |= sent4 & fill; }
     const int q = p + TP * nb;
-    if (q < capb) nbr[(size_t)q * Npad + s] = pack_block(lo, hi);
+    if (q < capb) nbr[(size_t)q * Npad + s] = ring_block(ring, (done & (8u * kRingRow)) | me, rem, (unsigned)total);
     ++nb;
   }
   nb_out = nb;
@@ -171,6 +178,7 @@ __global__ void __launch_bounds__(kBuildThreads) k_nbr_tile(const float4* __rest
   extern __shared__ __align__(16) unsigned char smem[];
   float4* sp = reinterpret_cast<float4*>(smem);
   __shared__ CellTile T;
+  __shared__ __align__(16) unsigned char ring[16 * kRingRow];
   const int c = blockIdx.x;
   const int b = cell_start[c], n = cell_start[c + 1] - b;
   if (n == 0) return;
@@ -200,9 +208,9 @@ __global__ void __launch_bounds__(kBuildThreads) k_nbr_tile(const float4* __rest
     if (active) {
       const float4 pi = pos[s];
       const int ti = tag[s] & (int)kTagMask;
-      if (TP == 1) build_atom<1>(sp, nwords, total, rl2, s, p, pi, ti, nbr, Npad, capb, nb);
-      else if (TP == 2) build_atom<2>(sp, nwords, total, rl2, s, p, pi, ti, nbr, Npad, capb, nb);
-      else build_atom<4>(sp, nwords, total, rl2, s, p, pi, ti, nbr, Npad, capb, nb);
+      if (TP == 1) build_atom<1>(sp, nwords, total, rl2, s, p, pi, ti, ring, nbr, Npad, capb, nb);
+      else if (TP == 2) build_atom<2>(sp, nwords, total, rl2, s, p, pi, ti, ring, nbr, Npad, capb, nb);
+      else build_atom<4>(sp, nwords, total, rl2, s, p, pi, ti, ring, nbr, Npad, capb, nb);
     }
     // common block count of the TP threads of an atom (adjacent lanes)
     int mb = nb;
@@ -300,7 +308,7 @@ __device__ __forceinline__ void lj_cell(int c, const float4* __restrict__ pos, c
       if (active) {
         const int s = b + a;
         const float4 pi = pos[s];
-        const int ti = (tag[s] >> kTagTypeBit) & 1;
+        const int ti = (int)pi.w;                   // LJ type, kept in w by binning and integration
         const float a0c = 12.f * R.C12u[ti], b0c = 6.f * R.C6u[ti];
         const float da = 12.f * R.C12u[ti + 1] - a0c, db = 6.f * R.C6u[ti + 1] - b0c;
         float ec[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};     // energy coefficients (ENERGY only)
@@ -377,9 +385,13 @@ __device__ __forceinline__ void lj_cell(int c, const float4* __restrict__ pos, c
   __syncthreads();   // the tile and tables are reused by the next cell of this block
 }
 
-// One block per cell.
+// One block per cell.  Six blocks of 256 threads per SM (40 registers) for
+// the force-only form: the tile's shared memory allows six, and 2 of a
+// block's 8 warps often have no home atom, so more resident blocks keep more
+// warps at work.  The energy form needs more registers and keeps its own
+// allocation.
 template <bool MIXED, bool ENERGY, int NT>
-__global__ void __launch_bounds__(NT) k_lj_tile(const float4* __restrict__ pos, const int* __restrict__ tag,
+__global__ void __launch_bounds__(NT, ENERGY ? 1 : 1536 / NT) k_lj_tile(const float4* __restrict__ pos, const int* __restrict__ tag,
                                                 const int* __restrict__ cell_start,
                                                 const uint4* __restrict__ nbr, const int* __restrict__ ncount,
                                                 int Npad, int tile_cap, const RepDev* __restrict__ reps, int n_reps,
