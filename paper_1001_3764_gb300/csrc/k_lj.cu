@@ -385,13 +385,14 @@ __device__ __forceinline__ void lj_cell(int c, const float4* __restrict__ pos, c
   __syncthreads();   // the tile and tables are reused by the next cell of this block
 }
 
-// One block per cell.  Six blocks of 256 threads per SM (40 registers) for
-// the force-only form: the tile's shared memory allows six, and 2 of a
-// block's 8 warps often have no home atom, so more resident blocks keep more
-// warps at work.  The energy form needs more registers and keeps its own
-// allocation.
-template <bool MIXED, bool ENERGY, int NT>
-__global__ void __launch_bounds__(NT, ENERGY ? 1 : 1536 / NT) k_lj_tile(const float4* __restrict__ pos, const int* __restrict__ tag,
+// One block per cell.  TPS > 0 asks the compiler for TPS / NT resident
+// blocks per SM (TPS = 1536: 40 registers; 1024: 64).  The force-only form
+// is launched with the largest TPS whose block count the tile's shared
+// memory also allows: 2 of a block's 8 warps often have no home atom, so
+// more resident blocks keep more warps at work.  The energy form, and tiles
+// too large for 1024 threads per SM, use the unconstrained allocation.
+template <bool MIXED, bool ENERGY, int NT, int TPS>
+__global__ void __launch_bounds__(NT, TPS > 0 ? TPS / NT : 1) k_lj_tile(const float4* __restrict__ pos, const int* __restrict__ tag,
                                                 const int* __restrict__ cell_start,
                                                 const uint4* __restrict__ nbr, const int* __restrict__ ncount,
                                                 int Npad, int tile_cap, const RepDev* __restrict__ reps, int n_reps,
@@ -710,6 +711,17 @@ size_t lj_pipe_smem(int tile_cap) {
   return (size_t)kPipeStages * (tile_cap + lj_pipe_list_cap(tile_cap)) * sizeof(float4);
 }
 
+// true if the force kernel compiled for TPS threads per SM keeps TPS / NT
+// blocks resident with this tile (shared memory is the other limit)
+template <bool MIXED, int NT, int TPS>
+static bool lj_tile_fits(int tile_cap) {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_lj_tile<MIXED, false, NT, TPS>, NT,
+                                                    (size_t)tile_cap * sizeof(float4)) != cudaSuccess)
+    return false;
+  return nb >= TPS / NT;
+}
+
 template <bool MIXED, bool ENERGY, int NT>
 static void lj_launch(bool pipe, int grid, int tile_cap, cudaStream_t st, const float4* pos, const int* tag,
                       const int* cell_start, const uint4* nbr, const int* ncount, int Npad, const RepDev* reps,
@@ -718,9 +730,23 @@ static void lj_launch(bool pipe, int grid, int tile_cap, cudaStream_t st, const 
     k_lj_pipe<MIXED, ENERGY, NT><<<grid, NT + 32, lj_pipe_smem(tile_cap), st>>>(
         pos, cell_start, nbr, ncount, Npad, tile_cap, lj_pipe_list_cap(tile_cap), reps, n_reps, C, fp, flj, epart,
         flags, work);
-  else
-    k_lj_tile<MIXED, ENERGY, NT><<<C, NT, (size_t)tile_cap * sizeof(float4), st>>>(
+  else {
+    const size_t sm = (size_t)tile_cap * sizeof(float4);
+    if constexpr (!ENERGY) {
+      if (lj_tile_fits<MIXED, NT, 1536>(tile_cap)) {
+        k_lj_tile<MIXED, false, NT, 1536><<<C, NT, sm, st>>>(pos, tag, cell_start, nbr, ncount, Npad, tile_cap, reps,
+                                                             n_reps, fp, flj, epart, flags);
+        return;
+      }
+      if (lj_tile_fits<MIXED, NT, 1024>(tile_cap)) {
+        k_lj_tile<MIXED, false, NT, 1024><<<C, NT, sm, st>>>(pos, tag, cell_start, nbr, ncount, Npad, tile_cap, reps,
+                                                             n_reps, fp, flj, epart, flags);
+        return;
+      }
+    }
+    k_lj_tile<MIXED, ENERGY, NT, 0><<<C, NT, (size_t)tile_cap * sizeof(float4), st>>>(
         pos, tag, cell_start, nbr, ncount, Npad, tile_cap, reps, n_reps, fp, flj, epart, flags);
+  }
 }
 
 // persistent_grid > 0: the pipelined kernel on that many blocks; else one
@@ -757,7 +783,9 @@ cudaError_t tile_kernels_init() {
   const int mp = (int)lj_pipe_smem(kStageCapMax);
   cudaError_t e = cudaFuncSetAttribute(k_nbr_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
 #define MDG_ATTR(M, E, NT) \
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_lj_tile<M, E, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx); \
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_lj_tile<M, E, NT, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx); \
+  if (e == cudaSuccess && !E) e = cudaFuncSetAttribute(k_lj_tile<M, false, NT, 1536>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx); \
+  if (e == cudaSuccess && !E) e = cudaFuncSetAttribute(k_lj_tile<M, false, NT, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx); \
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_lj_pipe<M, E, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, mp);
 #define MDG_ATTR4(NT) MDG_ATTR(true, true, NT) MDG_ATTR(true, false, NT) MDG_ATTR(false, true, NT) MDG_ATTR(false, false, NT)
   MDG_ATTR4(128) MDG_ATTR4(256)
