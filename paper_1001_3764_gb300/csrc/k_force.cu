@@ -33,22 +33,21 @@ __device__ __forceinline__ float rcp_approx(float x) {
   return y;
 }
 
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// Block reduction of NV doubles into out[NV] (thread 0 holds the result).
+// Block reduction of NV FP32 per-thread values into out[NV] (FP64; thread 0
+// holds the result): each warp adds its 32 lanes in FP32 by a fixed shuffle
+// tree (an FP64 tree per lane would load this GPU's narrow FP64 pipe), lane 0
+// converts the warp sum to FP64 and the warps are added in FP64 in order.
 // Fixed shape, so the summation order is the same on every run.
 template <int NV, int NT>
-__device__ __forceinline__ void block_sum(double (&v)[NV], double* out) {
+__device__ __forceinline__ void block_sum(const float (&v)[NV], double* out) {
   __shared__ double red[NV][NT / 32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
   for (int k = 0; k < NV; ++k) {
-    double s = warp_sum(v[k]);
-    if (lane == 0) red[k][w] = s;
+    float s = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) red[k][w] = (double)s;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -64,7 +63,7 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* out) {
 // FP32 force -> int64 fixed point (2^-32 kJ/mol/nm); each part below 2^18
 __device__ __forceinline__ long long to_fix(float f, unsigned* flags) {
   if (!(fabsf(f) < 262144.0f)) { atomicOr(flags, kFlagFixOverflow); return 0; }
-  return __float2ll_rn(f * 4294967296.0f);
+  return fix_round_int(f);   // = __float2ll_rn(f * 2^32), on the integer pipe
 }
 
 // ======================================================================= bonded
@@ -250,7 +249,7 @@ __global__ void __launch_bounds__(kBondedBlock) k_bonded(const void* __restrict_
     }
   }
   if (ENERGY) {
-    double v[kBondedVals] = {Eb, Ea, Ed, W[0], W[1], W[2], W[3], W[4], W[5]};
+    const float v[kBondedVals] = {Eb, Ea, Ed, W[0], W[1], W[2], W[3], W[4], W[5]};
     block_sum<kBondedVals, kBondedBlock>(v, epart + (size_t)blockIdx.x * kBondedVals);
   }
 }

@@ -11,8 +11,9 @@
 // The paper's Nose-Hoover coupling needs the whole-system kinetic energy,
 // which it sums through a per-atom array and a tree reduction (Sec. 3.4).
 // Here each block writes one FP64 partial; the last block to finish (ticket
-// counter, no waiting) sums the partials of each replica in tile order, so
-// the sum has a fixed order, and computes that replica's rescaling factor.
+// counter, no waiting) sums the partials of each replica in a fixed order
+// (one warp per replica, see below) and computes that replica's rescaling
+// factor.
 // The factor computed at step k is applied at step k+1 (one-step lag).
 //
 // The drift also refreshes the FP32 cell-unit positions in sorted order for
@@ -144,14 +145,32 @@ __global__ void __launch_bounds__(kIntBlock) k_integrate(void* __restrict__ xv, 
     __syncthreads();
     if (last) {
       __threadfence();
-      for (int r = threadIdx.x; r < n_reps; r += blockDim.x) {
+      // one warp per replica: lane l keeps eight chains P_m (m = 0..7), P_m
+      // adding the replica's partials l + 32 m, l + 32 m + 256, ... in order
+      // (eight loads in flight); then each P_m is summed over the lanes by a
+      // fixed tree and the eight results in m order.  The order depends only
+      // on the replica's own tile count.
+      const int lane = threadIdx.x & 31;
+      for (int r = threadIdx.x >> 5; r < n_reps; r += kIntBlock / 32) {
         const RepDev& Q = reps[r];
+        const double* kp = kepart + Q.tile_off;
+        double P[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        for (int k0 = 0; k0 < Q.n_tiles; k0 += 256) {
+#pragma unroll
+          for (int m = 0; m < 8; ++m) {
+            const int q = k0 + lane + 32 * m;
+            if (q < Q.n_tiles) P[m] += __ldcg(kp + q);
+          }
+        }
         double sum = 0.0;
-        for (int q = 0; q < Q.n_tiles; ++q) sum += __ldcg(kepart + Q.tile_off + q);
-        ke_out[r] = sum;
-        if (THERMO) {
-          const double T_inst = 2.0 * sum / (Q.dof * 0.0083144626);
-          lam[r] = sqrt(1.0 + fp.dt / tau * (Q.T0 / T_inst - 1.0));
+#pragma unroll
+        for (int m = 0; m < 8; ++m) sum += warp_sum_i(P[m]);
+        if (lane == 0) {
+          ke_out[r] = sum;
+          if (THERMO) {
+            const double T_inst = 2.0 * sum / (Q.dof * 0.0083144626);
+            lam[r] = sqrt(1.0 + fp.dt / tau * (Q.T0 / T_inst - 1.0));
+          }
         }
       }
       if (threadIdx.x == 0) *done = 0u;
@@ -205,27 +224,39 @@ void launch_integrate(bool mixed, IntegMode mode, bool ke, bool thermostat, void
 // LJ partials are per cell (replica r owns cells [cell_base, cell_base + M^3)),
 // bonded partials per integrator tile.  Fixed summation order.
 // out[r*16 + k]: k = 0 lj, 1 lj_shifted, 2 bond, 3 angle, 4 dihedral, 5..10 virial
-// One block per replica: thread t sums cells t, t + 256, ... and bonded
-// tiles t, t + 256, ...; the block then adds the 256 partials in a fixed tree
-// (warp shuffles, then the warps in order), so the sums are deterministic.
+// Two passes, spread over the GPU (FP64 adds are slow on one SM):
+//  1. slice j of replica r covers its cells [j*1024, (j+1)*1024) and the same
+//     share of its bonded tiles; thread t adds every 256th entry in order,
+//     then a fixed tree over the block (warp shuffles, then the warps in
+//     order) gives the slice's 11 sums;
+//  2. one warp per replica adds its slices in slice order.
+// The slices of a replica depend only on its own size, so a replica gets the
+// same bits alone or batched with others.
 constexpr int kRedThreads = 256;
 
-__global__ void __launch_bounds__(kRedThreads) k_energy_reduce(const double* __restrict__ lj_part,
+__host__ __device__ inline int energy_slices(int n_cells) { return (n_cells + kEnergySliceCells - 1) / kEnergySliceCells; }
+
+__global__ void __launch_bounds__(kRedThreads) k_energy_slices(const double* __restrict__ lj_part,
                                                                const double* __restrict__ b_part,
-                                                               const RepDev* __restrict__ reps,
-                                                               double* __restrict__ out) {
+                                                               const RepDev* __restrict__ reps, int max_slices,
+                                                               double* __restrict__ slices) {
   __shared__ double sh[11][kRedThreads / 32];
-  const int r = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int r = blockIdx.x / max_slices, j = blockIdx.x % max_slices;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const RepDev& R = reps[r];
+  const int nc = R.M * R.M * R.M, ns = energy_slices(nc);
+  if (j >= ns) return;
+  const int lt = (R.n_tiles + ns - 1) / ns;
   double acc[11] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-  const int c0 = R.cell_base, c1 = R.cell_base + R.M * R.M * R.M;
+  const int c0 = R.cell_base + j * kEnergySliceCells, c1 = R.cell_base + min(nc, (j + 1) * kEnergySliceCells);
   for (int c = c0 + tid; c < c1; c += kRedThreads) {
     const double* p = lj_part + (size_t)c * 8;
     acc[0] += p[0]; acc[1] += p[1];
 #pragma unroll
     for (int k = 0; k < 6; ++k) acc[5 + k] += p[2 + k];
   }
-  for (int q = R.tile_off + tid; q < R.tile_off + R.n_tiles; q += kRedThreads) {
+  const int q0 = R.tile_off + j * lt, q1 = R.tile_off + min(R.n_tiles, (j + 1) * lt);
+  for (int q = q0 + tid; q < q1; q += kRedThreads) {
     const double* p = b_part + (size_t)q * 9;
     acc[2] += p[0]; acc[3] += p[1]; acc[4] += p[2];
 #pragma unroll
@@ -242,14 +273,27 @@ __global__ void __launch_bounds__(kRedThreads) k_energy_reduce(const double* __r
   if (tid < 11) {
     double v = 0.0;
     for (int q = 0; q < kRedThreads / 32; ++q) v += sh[tid][q];
-    out[r * 16 + tid] = v;
+    slices[(size_t)blockIdx.x * 11 + tid] = v;
   }
 }
 
-void launch_energy_reduce(const double* lj_part, const double* b_part, const RepDev* reps, const Tile* b_tiles,
-                          int n_b_tiles, int n_reps, double* out, cudaStream_t st) {
-  (void)b_tiles; (void)n_b_tiles;
-  if (n_reps > 0) k_energy_reduce<<<n_reps, kRedThreads, 0, st>>>(lj_part, b_part, reps, out);
+__global__ void __launch_bounds__(32) k_energy_reduce(const double* __restrict__ slices, const RepDev* __restrict__ reps,
+                                                      int max_slices, double* __restrict__ out) {
+  const int r = blockIdx.x, k = threadIdx.x;
+  if (k >= 11) return;
+  const int ns = energy_slices(reps[r].M * reps[r].M * reps[r].M);
+  double v = 0.0;
+  for (int j = 0; j < ns; ++j) v += slices[((size_t)r * max_slices + j) * 11 + k];
+  out[r * 16 + k] = v;
+}
+
+int energy_slice_count(int n_cells) { return energy_slices(n_cells); }
+
+void launch_energy_reduce(const double* lj_part, const double* b_part, const RepDev* reps, int n_reps, int max_slices,
+                          double* slices, double* out, cudaStream_t st) {
+  if (n_reps <= 0) return;
+  k_energy_slices<<<n_reps * max_slices, kRedThreads, 0, st>>>(lj_part, b_part, reps, max_slices, slices);
+  k_energy_reduce<<<n_reps, 32, 0, st>>>(slices, reps, max_slices, out);
 }
 
 // ------------------------------------------------------------------ output state

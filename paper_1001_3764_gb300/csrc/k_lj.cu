@@ -248,6 +248,23 @@ __device__ __forceinline__ long long fix_of(float f, unsigned* flags) {
   return __float2ll_rn(f * 4294967296.0f);
 }
 
+// Energy and virial sums of one warp: the 32 lanes' FP32 partials are added
+// in FP32 by a fixed shuffle tree, and lane 0 stores the warp sum as FP64
+// (halved: a full list counts every pair twice).  The block then adds its
+// warps in FP64, and all later sums are FP64.  A per-lane FP64 tree would
+// cost 8 conversions and 40 FP64 adds per thread on this GPU's narrow FP64
+// pipe, more than the pair loop of the energy kernel.
+template <int NW>
+__device__ __forceinline__ void warp_energy_sums(const float (&ev)[8], int lane, double (&red)[8][NW], int w) {
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    float sv = ev[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sv += __shfl_down_sync(0xffffffffu, sv, o);
+    if (lane == 0) red[k][w] = 0.5 * (double)sv;
+  }
+}
+
 // one pair of Eq. (2) in cell units (Sec. 3.2 listing: r2inv = 0 beyond r_c);
 // w.w is j's type (0/1), so the pair constants are a0 + t_j (a1 - a0)
 template <bool ENERGY>
@@ -362,17 +379,8 @@ __device__ __forceinline__ void lj_cell(int c, const float4* __restrict__ pos, c
     atomicOr(flags, kFlagNbrOverflow);
   }
   if (ENERGY) {
-    double v[kEnergyVals];
-#pragma unroll
-    for (int k = 0; k < kEnergyVals; ++k) v[k] = 0.5 * (double)ev[k];   // full list: every pair twice
     const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
-#pragma unroll
-    for (int k = 0; k < kEnergyVals; ++k) {
-      double sv = v[k];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) sv += __shfl_down_sync(0xffffffffu, sv, o);
-      if (lane == 0) red[k][wi] = sv;
-    }
+    warp_energy_sums(ev, lane, red, wi);
     __syncthreads();
     if (threadIdx.x == 0) {
       for (int k = 0; k < kEnergyVals; ++k) {
@@ -389,10 +397,12 @@ __device__ __forceinline__ void lj_cell(int c, const float4* __restrict__ pos, c
 // blocks per SM (TPS = 1536: 40 registers; 1024: 64).  The force-only form
 // is launched with the largest TPS whose block count the tile's shared
 // memory also allows: 2 of a block's 8 warps often have no home atom, so
-// more resident blocks keep more warps at work.  The energy form, and tiles
-// too large for 1024 threads per SM, use the unconstrained allocation.
+// more resident blocks keep more warps at work.  Tiles too large for 1024
+// threads per SM use the unconstrained allocation.  The energy form (eight
+// more accumulators) is compiled for 1024 threads per SM (64 registers, no
+// spills) instead of the 2 blocks its unconstrained allocation would allow.
 template <bool MIXED, bool ENERGY, int NT, int TPS>
-__global__ void __launch_bounds__(NT, TPS > 0 ? TPS / NT : 1) k_lj_tile(const float4* __restrict__ pos, const int* __restrict__ tag,
+__global__ void __launch_bounds__(NT, TPS > 0 ? TPS / NT : (ENERGY ? 1024 / NT : 1)) k_lj_tile(const float4* __restrict__ pos, const int* __restrict__ tag,
                                                 const int* __restrict__ cell_start,
                                                 const uint4* __restrict__ nbr, const int* __restrict__ ncount,
                                                 int Npad, int tile_cap, const RepDev* __restrict__ reps, int n_reps,
@@ -657,16 +667,7 @@ __global__ void __launch_bounds__(NT + 32) k_lj_pipe(const float4* __restrict__ 
       atomicOr(flags, kFlagNbrOverflow);
     }
     if (ENERGY) {
-      double v[kEnergyVals];
-#pragma unroll
-      for (int k = 0; k < kEnergyVals; ++k) v[k] = 0.5 * (double)ev[k];   // full list: every pair twice
-#pragma unroll
-      for (int k = 0; k < kEnergyVals; ++k) {
-        double sv = v[k];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) sv += __shfl_down_sync(0xffffffffu, sv, o);
-        if (lane == 0) red[k][warp] = sv;
-      }
+      warp_energy_sums(ev, lane, red, warp);
       consumer_sync(NT);
       if (tid == 0) {
         for (int k = 0; k < kEnergyVals; ++k) {

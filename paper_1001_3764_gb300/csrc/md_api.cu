@@ -58,6 +58,8 @@ struct md_system {
   int *slot = nullptr, *tmp = nullptr;
   double *lj_part = nullptr, *b_part = nullptr, *kepart = nullptr, *ke_out = nullptr, *lam = nullptr;
   double* e_out = nullptr;
+  double* e_slices = nullptr;   // first-pass energy sums, n_reps * max_slices * 11
+  int max_slices = 1;
   double* stage = nullptr;                   // input staging (6N doubles)
   unsigned *done = nullptr, *flags = nullptr;
   // execution
@@ -193,6 +195,7 @@ static int configure(md_system* s, const md_desc* d) {
     max_expected = std::max(max_expected, 4.0 / 3.0 * M_PI * rl * rl * rl * rho);
     max_tile = std::max(max_tile, 27.0 * std::max(q.n_atoms / (L * L * L), 33.0) * q.h * q.h * q.h);
     atoms += q.n_atoms; cells += (int64_t)M * M * M; chains += nc;
+    s->max_slices = std::max(s->max_slices, energy_slice_count(M * M * M));
     if (atoms >= (int64_t)kNbrIndexMask) return fail(s, MD_EINVAL, "too many atoms (limit 2^26)");
     if (chains >= (1 << 21)) return fail(s, MD_EINVAL, "too many chains (limit 2^21)");
     if (cells >= (1 << 26)) return fail(s, MD_EINVAL, "too many cells");
@@ -245,6 +248,7 @@ static size_t plan(md_system* s, char* base) {
   s->ke_out = (double*)take(s->n_reps * sizeof(double));
   s->lam = (double*)take(s->n_reps * sizeof(double));
   s->e_out = (double*)take((size_t)s->n_reps * 16 * sizeof(double));
+  s->e_slices = (double*)take((size_t)s->n_reps * s->max_slices * 11 * sizeof(double));
   s->done = (unsigned*)take(sizeof(unsigned));
   s->work = (int*)take(2 * sizeof(int));
   s->flags = (unsigned*)take(sizeof(unsigned));
@@ -529,8 +533,7 @@ int md_energy(md_system* s, md_energy_t* out) {
   const bool p = s->profile;
   s->profile = false;
   enqueue_forces(s, true);
-  launch_energy_reduce(s->lj_part, s->b_part, s->reps, s->tiles_int, (int)s->t_int.size(), s->n_reps, s->e_out,
-                       s->st);
+  launch_energy_reduce(s->lj_part, s->b_part, s->reps, s->n_reps, s->max_slices, s->e_slices, s->e_out, s->st);
   // kinetic energy of the current velocities (a pass that only reads v)
   launch_integrate(s->mixed, kKineticOnly, true, false, s->x, s->v, s->img, s->F, s->site, s->cellc, s->inv_perm,
                    s->ref, s->pos, (int)s->N, s->tiles_int, (int)s->t_int.size(), s->reps, s->n_reps, s->fp,

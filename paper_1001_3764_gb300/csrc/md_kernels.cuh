@@ -71,20 +71,23 @@ __device__ __forceinline__ float cell_unit(double x, int c, int w, const RepDev&
 }
 // FP64 -> FP32 with round-to-nearest-even done on the integer pipe (FP64 <->
 // FP32 conversions share the slow FP64 pipe on this GPU).  From the IEEE 754
-// binary64/binary32 layouts: for a normal result, drop 29 mantissa bits with
-// round-half-even (add 2^28 - 1 + the lowest kept bit, then truncate; a carry
-// moves into the exponent) and rebias the exponent by 1023 - 127 = 896.
-// Zero and magnitudes below 2^-126 give a signed zero (no subnormal results),
-// magnitudes from 2^128 up give infinity, NaN stays NaN.
+// binary64/binary32 layouts, on the two 32-bit words of the double: for a
+// normal result, keep the sign, the 11-bit exponent and the top 23 mantissa
+// bits (the kept word, taken modulo 2^32), drop the low 29 mantissa bits with
+// round-half-even (add 2^28 - 1 + the lowest kept bit; a carry moves into the
+// exponent) and rebias the exponent by 1023 - 127 = 896.  Zero and magnitudes
+// below 2^-126 give a signed zero (no subnormal results), magnitudes from
+// 2^128 up give infinity, NaN stays NaN.  32-bit words rather than 64-bit
+// integer arithmetic: fewer instructions on this GPU.
 __device__ __forceinline__ float d2f_rn_int(double d) {
-  const long long b = __double_as_longlong(d);
-  const unsigned long long a = (unsigned long long)b & 0x7fffffffffffffffull;
-  const unsigned sign = (unsigned)((unsigned long long)b >> 32) & 0x80000000u;
-  const unsigned long long t = a + 0x0fffffffull + ((a >> 29) & 1ull);
-  unsigned f = (unsigned)(t >> 29) - (896u << 23);
-  f = a < 0x3810000000000000ull ? 0u : f;                              // below the normal range
-  f = (a >= 0x47effffff0000000ull && a <= 0x7ff0000000000000ull) ? 0x7f800000u : f;   // overflow, inf
-  f = a > 0x7ff0000000000000ull ? 0x7fc00000u : f;                     // NaN
+  const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+  const unsigned ha = hi & 0x7fffffffu, sign = hi & 0x80000000u;
+  const unsigned kept = (ha << 3) | (lo >> 29);
+  const unsigned inc = ((lo & 0x1fffffffu) + 0x0fffffffu + (kept & 1u)) >> 29;
+  unsigned f = kept + inc - (896u << 23);
+  f = ha < 0x38100000u ? 0u : f;                                          // below the normal range
+  f = (ha > 0x47efffffu || (ha == 0x47efffffu && lo >= 0xf0000000u)) ? 0x7f800000u : f;   // overflow, inf
+  f = (ha > 0x7ff00000u || (ha == 0x7ff00000u && lo != 0u)) ? 0x7fc00000u : f;            // NaN
   return __uint_as_float(f | sign);
 }
 
@@ -128,6 +131,32 @@ __device__ __forceinline__ float cell_unit(float x, int c, int w, const RepDev& 
   const float p = x * R.ih_hi;
   const float e = fmaf(x, R.ih_hi, -p);
   return __fadd_rn(__fsub_rn(p, k), fmaf(x, R.ih_lo, e));
+}
+
+// round-half-even(f * 2^32) as int64 (the 2^-32 fixed point of the forces)
+// on the integer pipe, from the binary32 fields: f * 2^32 = m * 2^s with m
+// the 24-bit significand and s = e - 118; a left shift for s >= 0 (s <= 26
+// for |f| < 2^18, the range the callers check), else a right shift by -s
+// with round-half-even (nothing is left for -s >= 25).  Gives the bits of
+// __float2ll_rn(f * 2^32) without the conversion instruction, which runs on
+// the narrow FP64 pipe of this GPU.
+__device__ __forceinline__ long long fix_round_int(float f) {
+  const unsigned u = __float_as_uint(f);
+  const int e = (int)((u >> 23) & 0xffu);
+  const unsigned m = (u & 0x007fffffu) | (e ? 0x00800000u : 0u);
+  const int s = e - 118;
+  unsigned hi = 0u, lo;
+  if (s >= 0) {
+    hi = s ? m >> (32 - s) : 0u;
+    lo = m << s;
+  } else {
+    const int r = -s;
+    const unsigned q = r >= 25 ? 0u : m >> r;
+    const unsigned rem = r >= 25 ? 0u : m & ((1u << r) - 1u), half = r >= 25 ? 1u : 1u << (r - 1);
+    lo = q + ((rem > half || (rem == half && (q & 1u))) ? 1u : 0u);
+  }
+  const long long v = (long long)(((unsigned long long)hi << 32) | lo);
+  return (u >> 31) ? -v : v;
 }
 
 // Per-system constants passed by value to kernels.
@@ -204,7 +233,11 @@ void launch_integrate(bool mixed, IntegMode mode, bool ke, bool thermostat, void
                       const RepDev* reps, int n_reps, const ForceParams& fp, double* kepart,
                       unsigned* done, double* ke_out, double* lam, double tau, unsigned* flags,
                       cudaStream_t st);
-void launch_energy_reduce(const double* lj_part, const double* b_part, const RepDev* reps,
-                          const Tile* b_tiles, int n_b_tiles, int n_reps, double* out, cudaStream_t st);
+// cells per slice of the first energy-reduction pass
+constexpr int kEnergySliceCells = 1024;
+int energy_slice_count(int n_cells);
+// slices: n_reps * max_slices * 11 doubles of scratch
+void launch_energy_reduce(const double* lj_part, const double* b_part, const RepDev* reps, int n_reps, int max_slices,
+                          double* slices, double* out, cudaStream_t st);
 
 }  // namespace mdg
