@@ -135,9 +135,15 @@ __global__ void __launch_bounds__(128) k_cell_sort(const T* __restrict__ x, int 
     inv_perm[id] = s;
     const int cc = cellc[id];
     float4 p;
-    p.x = cell_unit(x[id], cc & 1023, 0, R);
-    p.y = cell_unit(x[N + id], (cc >> 10) & 1023, 0, R);
-    p.z = cell_unit(x[2 * N + id], (cc >> 20) & 1023, 0, R);
+    if constexpr (sizeof(T) == 8) {      // FP64 master: integer-pipe offset and rounding, same value
+      p.x = cell_unit_t(x[id], cc & 1023, R);
+      p.y = cell_unit_t(x[N + id], (cc >> 10) & 1023, R);
+      p.z = cell_unit_t(x[2 * N + id], (cc >> 20) & 1023, R);
+    } else {
+      p.x = cell_unit(x[id], cc & 1023, 0, R);
+      p.y = cell_unit(x[N + id], (cc >> 10) & 1023, 0, R);
+      p.z = cell_unit(x[2 * N + id], (cc >> 20) & 1023, 0, R);
+    }
     const int st = site[id];
     const int chain = R.chain_off + (id - R.atom_off) / sites;
     const int type = (st == 0 || st == sites - 1) ? 1 : 0;

@@ -118,7 +118,10 @@ __global__ void __launch_bounds__(kIntBlock) k_integrate(void* __restrict__ xv, 
         float ua;
         if constexpr (MIXED) ua = cell_unit_t(xa, c, R); else ua = cell_unit(xa, c, 0, R);
         const float du = ua - r0a[a];
-        if (du > halfM || du < -halfM) ua = cell_unit(xa, c, du > halfM ? -1 : 1, R);
+        if (du > halfM || du < -halfM) {
+          if constexpr (MIXED) ua = cell_unit_tw(xa, c, du > halfM ? -1 : 1, R);
+          else ua = cell_unit(xa, c, du > halfM ? -1 : 1, R);
+        }
         loc[a] = ua;
         const float d = ua - r0a[a];
         d2 += d * d;

@@ -284,12 +284,15 @@ static void enqueue_rebin(md_system* s) {
 }
 static const int kRebinLaunches = 6;   // memset counted as a launch
 
-static void enqueue_forces(md_system* s, bool energy) {
+// F_out: where the total force goes (the dynamics' s->F, or scratch for an
+// energy read-out, whose kernels need not reproduce the force bits of the
+// force-only kernels: the compiler may fuse their arithmetic differently)
+static void enqueue_forces(md_system* s, bool energy, void* F_out = nullptr) {
   launch_lj_tile(s->mixed, energy, s->pos, s->tag, s->cell_start, s->nbr, s->ncount, s->Npad, s->tile_cap, s->reps,
                  s->n_reps, s->C, s->fp, s->flj, s->lj_part, s->flags, s->lj_block, s->persistent_grid, s->work, s->st);
   prof_mark(s);
   launch_bonded(s->mixed, energy, s->x, s->site, s->inv_perm, s->flj, (int)s->N, s->tiles_int, (int)s->t_int.size(),
-                s->reps, s->fp, s->F, s->b_part, s->flags, s->st);
+                s->reps, s->fp, F_out ? F_out : s->F, s->b_part, s->flags, s->st);
   prof_mark(s);
 }
 
@@ -532,7 +535,10 @@ int md_energy(md_system* s, md_energy_t* out) {
   if (!s || !out) return fail(s, MD_EINVAL, "bad arguments");
   const bool p = s->profile;
   s->profile = false;
-  enqueue_forces(s, true);
+  // energies and virial of the current state; the forces of this pass go to
+  // the staging buffer (6N doubles + 3N ints, room for either force layout),
+  // so reading energies never changes the forces the dynamics use
+  enqueue_forces(s, true, s->stage);
   launch_energy_reduce(s->lj_part, s->b_part, s->reps, s->n_reps, s->max_slices, s->e_slices, s->e_out, s->st);
   // kinetic energy of the current velocities (a pass that only reads v)
   launch_integrate(s->mixed, kKineticOnly, true, false, s->x, s->v, s->img, s->F, s->site, s->cellc, s->inv_perm,

@@ -100,6 +100,25 @@ __device__ __forceinline__ double half_plus(int c) {
   return __longlong_as_double(((unsigned long long)(e + 1022) << 52) | m);
 }
 
+// k + 1/2 for any int k with |2k + 1| < 2^21 (cell indices shifted by a box,
+// k = c - w M), from its bits like half_plus, with the sign bit.
+__device__ __forceinline__ double half_plus_s(int k) {
+  const int m = 2 * k + 1;
+  const unsigned a = (unsigned)(m < 0 ? -m : m);
+  const unsigned sgn = m < 0 ? 0x80000000u : 0u;
+  const int e = 31 - __clz(a);
+  const unsigned mh = (a << (20 - e)) & 0x000fffffu;
+  return __hiloint2double((int)(sgn | ((unsigned)(e + 1022) << 20) | mh), 0);
+}
+
+// cell_unit(x, c, w, R) on the integer pipe: the centre offset c + 1/2 - w M
+// built from bits and the FP32 rounding done with integer operations (same
+// value).  Evaluating the conversions of cell_unit for every atom, as a
+// compiler may do for a branch taken by few, would load the FP64 pipe.
+__device__ __forceinline__ float cell_unit_tw(double x, int c, int w, const RepDev& R) {
+  return d2f_rn_int(fma(x, R.inv_h, -half_plus_s(c - w * R.M)));
+}
+
 // Same as cell_unit with the centre offset built on the integer pipe and the
 // final rounding on the integer pipe.
 __device__ __forceinline__ float cell_unit_t(double x, int c, const RepDev& R) {

@@ -222,6 +222,52 @@ def test_replicas_equal_separate_runs_and_oracle():
     both.close()
 
 
+def test_thermostatted_replicas_equal_separate_runs_including_energies():
+    # Each replica's kinetic-energy sum (which sets its rescaling factor) and
+    # its energy/virial sums have an order fixed by the replica's own size, so
+    # a replica stepped with others gives the same bits as alone.  The
+    # 400-chain replica has 11^3 cells: its energy sums take two slices.
+    melts = [chaingen.melt(c, seed=70 + c) for c in (10, 400, 25)]
+    T0 = [300.0, 450.0, 380.0]
+    kw = dict(precision=md.MD_MIXED, thermostat=md.MD_VRESCALE, tau_t=0.05, rebin_every=5)
+    both = md.System(melts, T_target=T0, **kw)
+    both.step(30)
+    xb, vb, _ = both.state()
+    eb = both.energy()
+    off = 0
+    for m, T, e in zip(melts, T0, eb):
+        alone = md.System(m, T_target=T, **kw)
+        alone.step(30)
+        xa, va, _ = alone.state()
+        n = len(xa)
+        assert np.array_equal(xb[off:off + n], xa) and np.array_equal(vb[off:off + n], va)
+        ea = alone.energy()[0]
+        for k in ("lj", "lj_shifted", "bond", "angle", "dihedral", "kinetic", "temperature"):
+            assert e[k] == ea[k], k
+        assert np.array_equal(np.asarray(e["virial"]), np.asarray(ea["virial"]))
+        off += n
+        alone.close()
+    both.close()
+
+
+def test_energy_call_leaves_forces_and_trajectory_unchanged():
+    # md_energy recomputes the forces with the energy-form kernels; they must
+    # be the bits the force-only kernels give, or reading energies would
+    # perturb the dynamics
+    m = chaingen.melt(30, seed=8)
+    a = md.System(m, precision=md.MD_MIXED, rebin_every=5)
+    b = md.System(m, precision=md.MD_MIXED, rebin_every=5)
+    for _ in range(3):
+        a.step(7)
+        b.step(7)
+        f = a.forces()
+        a.energy()
+        assert np.array_equal(a.forces(), f)
+    assert np.array_equal(a.state()[0], b.state()[0]) and np.array_equal(a.state()[1], b.state()[1])
+    a.close()
+    b.close()
+
+
 @pytest.mark.parametrize("sites", [4, 7, 150, 511])
 def test_short_chains_and_rebin_every_step(sites):
     n_chains = max(1, 1500 // sites)
