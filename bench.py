@@ -296,12 +296,22 @@ def adjoint(md, n_chains=50, K=500, C=50, reps=3):
         g = adj.backward((1.0, 0.0)); t2 = time.perf_counter()
         tf.append(t1 - t0); tb.append(t2 - t1)
     adj.close()
+    # the same with FP32 Hessian-vector products in the reverse pass
+    adj32 = md.Adjoint(melt, n_steps=K, checkpoint_every=C, hvp_fp32=True)
+    adj32.forward(); adj32.backward((1.0, 0.0))
+    tb32 = []
+    for _ in range(reps):
+        t1 = time.perf_counter(); g32 = adj32.backward((1.0, 0.0)); tb32.append(time.perf_counter() - t1)
+    adj32.close()
     n = n_chains * SITES
-    f, b = float(np.median(tf)), float(np.median(tb))
+    f, b, b32 = float(np.median(tf)), float(np.median(tb)), float(np.median(tb32))
     return {"sites": n, "steps": K, "checkpoint_every": C, "forward_ms": f * 1e3, "backward_ms": b * 1e3,
             "gradient_atom_steps_per_s": n * K / (f + b), "obs": [float(o) for o in obs],
             "grad_U": dict(zip(md.THETA_NAMES, [float(x) for x in g])),
-            "note": "FP64 state and adjoint; backward recomputes each 50-step segment from its checkpoint"}
+            "backward_ms_fp32_hvp": b32 * 1e3,
+            "fp32_hvp_max_rel_diff": float(np.max(np.abs(g32 - g)) / np.max(np.abs(g))),
+            "note": "FP64 state and adjoint; backward recomputes each 50-step segment from its checkpoint; "
+                    "the fp32_hvp figures run the reverse pass's Hessian-vector products in FP32"}
 
 
 def cpu_baseline(melt, steps=4):

@@ -288,7 +288,10 @@ typedef struct {
                                   1: force-shifted E(r) - E(rc) - (r - rc) E'(rc), a
                                      variant outside the paper whose force is continuous
                                      at rc (for gradient checks) */
-  int32_t pad;
+  int32_t hvp_precision;       /* 0: Hessian-vector products and parameter terms of the reverse
+                                  pass in FP64 dual numbers; 1: in FP32 dual numbers (pair set,
+                                  separations, records, reductions and the forward run stay
+                                  FP64).  Affects md_adj_backward and md_adj_tangent. */
   void *cuda_stream;           /* NULL = a stream the library creates */
 } md_adj_desc;
 

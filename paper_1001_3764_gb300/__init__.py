@@ -61,7 +61,7 @@ class md_adj_desc(ctypes.Structure):
     _fields_ = [("n_chains", ctypes.c_int32), ("sites_per_chain", ctypes.c_int32), ("box", ctypes.c_double),
                 ("params", md_params), ("rc", ctypes.c_double), ("dt", ctypes.c_double),
                 ("n_steps", ctypes.c_int32), ("checkpoint_every", ctypes.c_int32),
-                ("lj_form", ctypes.c_int32), ("pad", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p)]
+                ("lj_form", ctypes.c_int32), ("hvp_precision", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p)]
 
 
 class md_energy_t(ctypes.Structure):
@@ -471,7 +471,8 @@ class Adjoint:
     chain (the end-to-end distance needs continuous chains)."""
 
     def __init__(self, melt: dict, n_steps: int = 500, checkpoint_every: int = 50, dt: float = 0.001,
-                 rc: float = 1.0, params: dict | None = None, device: int | None = None, lj_form: int = 0):
+                 rc: float = 1.0, params: dict | None = None, device: int | None = None, lj_form: int = 0,
+                 hvp_fp32: bool = False):
         import torch
         if device is not None:
             torch.cuda.set_device(device)
@@ -492,6 +493,7 @@ class Adjoint:
         desc.params = make_params(self.params)
         desc.rc, desc.dt, desc.n_steps, desc.checkpoint_every = rc, dt, n_steps, checkpoint_every
         desc.lj_form = int(lj_form)     # 1: force-shifted LJ, a variant outside the paper (gradient checks)
+        desc.hvp_precision = 1 if hvp_fp32 else 0   # FP32 Hessian-vector products in the reverse pass
         self.stream = torch.cuda.Stream()
         desc.cuda_stream = self.stream.cuda_stream
         self.h = md_adj_create(desc)

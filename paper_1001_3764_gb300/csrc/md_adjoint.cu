@@ -31,6 +31,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <type_traits>
 
 #include "../../include/md.h"
 #include "md_kernels.cuh"
@@ -91,6 +92,53 @@ __device__ __forceinline__ double value(Dual a) { return a.v; }
 __device__ __forceinline__ double tangent(double) { return 0.0; }
 __device__ __forceinline__ double tangent(Dual a) { return a.t; }
 
+// FP32 dual numbers for the reverse pass's Hessian-vector products (the
+// optional FP32 HVP): separations still come from FP64 positions and the pair
+// set from an FP64 cutoff test; only the term arithmetic runs in FP32, and its
+// per-atom results are added into the FP64 records.  FP64 constants are
+// rounded to FP32 where they meet an FP32 dual.
+struct DualF {
+  float v, t;
+};
+__device__ __forceinline__ DualF operator+(DualF a, DualF b) { return {a.v + b.v, a.t + b.t}; }
+__device__ __forceinline__ DualF operator-(DualF a, DualF b) { return {a.v - b.v, a.t - b.t}; }
+__device__ __forceinline__ DualF operator-(DualF a) { return {-a.v, -a.t}; }
+__device__ __forceinline__ DualF operator*(DualF a, DualF b) { return {a.v * b.v, a.v * b.t + a.t * b.v}; }
+__device__ __forceinline__ DualF operator*(double s, DualF a) { const float f = (float)s; return {f * a.v, f * a.t}; }
+__device__ __forceinline__ DualF operator*(DualF a, double s) { const float f = (float)s; return {f * a.v, f * a.t}; }
+__device__ __forceinline__ DualF operator+(DualF a, double s) { return {a.v + (float)s, a.t}; }
+__device__ __forceinline__ DualF operator+(double s, DualF a) { return {a.v + (float)s, a.t}; }
+__device__ __forceinline__ DualF operator-(DualF a, double s) { return {a.v - (float)s, a.t}; }
+__device__ __forceinline__ DualF operator-(double s, DualF a) { return {(float)s - a.v, -a.t}; }
+__device__ __forceinline__ DualF operator/(DualF a, DualF b) {
+  const float q = a.v / b.v;
+  return {q, (a.t - q * b.t) / b.v};
+}
+__device__ __forceinline__ DualF operator/(double s, DualF b) {
+  const float q = (float)s / b.v;
+  return {q, -q * b.t / b.v};
+}
+__device__ __forceinline__ DualF& operator+=(DualF& a, DualF b) { a = a + b; return a; }
+__device__ __forceinline__ DualF gsqrt(DualF a) {
+  const float r = sqrtf(a.v);
+  return {r, 0.5f * a.t / r};
+}
+__device__ __forceinline__ DualF gatan2(DualF y, DualF x) {
+  return {atan2f(y.v, x.v), (x.v * y.t - y.v * x.t) / (x.v * x.v + y.v * y.v)};
+}
+__device__ __forceinline__ DualF gcos(DualF a) {
+  float s, c;
+  sincosf(a.v, &s, &c);
+  return {c, -s * a.t};
+}
+__device__ __forceinline__ DualF gsin(DualF a) {
+  float s, c;
+  sincosf(a.v, &s, &c);
+  return {s, c * a.t};
+}
+__device__ __forceinline__ double value(DualF a) { return (double)a.v; }
+__device__ __forceinline__ double tangent(DualF a) { return (double)a.t; }
+
 template <class T>
 struct V3 {
   T x, y, z;
@@ -127,29 +175,38 @@ __device__ __forceinline__ int site_type(int site, int sites) { return (site == 
 
 __device__ __forceinline__ double min_image(double d, const AdjDev& P) { return d - P.L * rint(d * P.inv_L); }
 
+// separation x_b - x_a (minimum image, FP64 value) with the tangent
+// u_b - u_a, u_k = cu * beta_k / m_k the direction of atom k, in the scalar
+// type T of the evaluation
 template <class T>
-__device__ __forceinline__ void wrap_value(V3<T>& d, const AdjDev& P);
+__device__ __forceinline__ V3<T> make_sep(double dx, double dy, double dz, const double* beta, double cu, int a,
+                                          int b, const AdjDev& P);
 template <>
-__device__ __forceinline__ void wrap_value<double>(V3<double>& d, const AdjDev& P) {
-  d.x = min_image(d.x, P); d.y = min_image(d.y, P); d.z = min_image(d.z, P);
+__device__ __forceinline__ V3<double> make_sep<double>(double dx, double dy, double dz, const double*, double, int,
+                                                       int, const AdjDev&) {
+  return {dx, dy, dz};
 }
 template <>
-__device__ __forceinline__ void wrap_value<Dual>(V3<Dual>& d, const AdjDev& P) {
-  d.x.v = min_image(d.x.v, P); d.y.v = min_image(d.y.v, P); d.z.v = min_image(d.z.v, P);
+__device__ __forceinline__ V3<Dual> make_sep<Dual>(double dx, double dy, double dz, const double* beta, double cu,
+                                                   int a, int b, const AdjDev& P) {
+  const double sa = cu * P.inv_mass[site_type(a % P.sites, P.sites)];
+  const double sb = cu * P.inv_mass[site_type(b % P.sites, P.sites)];
+  return {{dx, sb * beta[3 * b] - sa * beta[3 * a]}, {dy, sb * beta[3 * b + 1] - sa * beta[3 * a + 1]},
+          {dz, sb * beta[3 * b + 2] - sa * beta[3 * a + 2]}};
 }
-
-// position of atom k with its direction u_k = cu * beta_k / m_k as tangent
+template <>
+__device__ __forceinline__ V3<DualF> make_sep<DualF>(double dx, double dy, double dz, const double* beta, double cu,
+                                                     int a, int b, const AdjDev& P) {
+  const double sa = cu * P.inv_mass[site_type(a % P.sites, P.sites)];
+  const double sb = cu * P.inv_mass[site_type(b % P.sites, P.sites)];
+  return {{(float)dx, (float)(sb * beta[3 * b] - sa * beta[3 * a])},
+          {(float)dy, (float)(sb * beta[3 * b + 1] - sa * beta[3 * a + 1])},
+          {(float)dz, (float)(sb * beta[3 * b + 2] - sa * beta[3 * a + 2])}};
+}
 template <class T>
-__device__ __forceinline__ V3<T> load_pos(const double* x, const double* beta, double cu, int k, const AdjDev& P);
-template <>
-__device__ __forceinline__ V3<double> load_pos<double>(const double* x, const double*, double, int k, const AdjDev&) {
-  return {x[3 * k], x[3 * k + 1], x[3 * k + 2]};
-}
-template <>
-__device__ __forceinline__ V3<Dual> load_pos<Dual>(const double* x, const double* beta, double cu, int k,
-                                                   const AdjDev& P) {
-  const double s = cu * P.inv_mass[site_type(k % P.sites, P.sites)];
-  return {{x[3 * k], s * beta[3 * k]}, {x[3 * k + 1], s * beta[3 * k + 1]}, {x[3 * k + 2], s * beta[3 * k + 2]}};
+__device__ __forceinline__ V3<T> sep(const double* x, const double* beta, double cu, int a, int b, const AdjDev& P) {
+  return make_sep<T>(min_image(x[3 * b] - x[3 * a], P), min_image(x[3 * b + 1] - x[3 * a + 1], P),
+                     min_image(x[3 * b + 2] - x[3 * a + 2], P), beta, cu, a, b, P);
 }
 
 __device__ __forceinline__ int cell_coord(double xv, const AdjDev& P) {
@@ -202,7 +259,6 @@ __global__ void __launch_bounds__(32 * kLjWarps) k_adj_lj(const double* __restri
   const int i = blockIdx.x * kLjWarps + w;
   if (i >= P.N) return;   // the whole warp leaves together
   const int si = i % P.sites, ci = i / P.sites, ti = site_type(si, P.sites);
-  const V3<T> xi = load_pos<T>(x, beta, cu, i, P);
   const float4 xf = x32[i];
   const float Lf = (float)P.L, iLf = (float)P.inv_L;
   // candidate cells and the prefix of their sizes
@@ -228,6 +284,7 @@ __global__ void __launch_bounds__(32 * kLjWarps) k_adj_lj(const double* __restri
   T gx = T{}, gy = T{}, gz = T{};
   T A0 = T{}, B0 = T{}, A1 = T{}, B1 = T{};   // partners of type 0 / type 1
   double e = 0.0;
+  float ef = 0.f;                               // the same in the FP32 evaluation
   int o = 0;
   for (int q = lane; q < total; q += 32) {
     while (q >= s_pre[w][o + 1]) ++o;
@@ -248,8 +305,7 @@ __global__ void __launch_bounds__(32 * kLjWarps) k_adj_lj(const double* __restri
     const double r2v = dx * dx + dy * dy + dz * dz;
     if (r2v >= P.rc2) continue;
     const int tj = site_type(sj, P.sites), t = ti + tj;
-    V3<T> d = xi - load_pos<T>(x, beta, cu, j, P);
-    wrap_value<T>(d, P);
+    const V3<T> d = make_sep<T>(dx, dy, dz, beta, cu, j, i, P);   // x_i - x_j
     const T r2 = dot(d, d);
     const T ir2 = 1.0 / r2;
     const T ir6 = ir2 * ir2 * ir2;
@@ -264,16 +320,32 @@ __global__ void __launch_bounds__(32 * kLjWarps) k_adj_lj(const double* __restri
     }
     gx += s * d.x; gy += s * d.y; gz += s * d.z;
     if (tj) { A1 += 0.5 * A; B1 += 0.5 * B; } else { A0 += 0.5 * A; B0 += 0.5 * B; }
-    e += 0.5 * (P.c12[t] * value(A) - P.c6[t] * value(B));
+    if constexpr (std::is_same<T, DualF>::value) ef += 0.5f * ((float)P.c12[t] * A.v - (float)P.c6[t] * B.v);
+    else e += 0.5 * (P.c12[t] * value(A) - P.c6[t] * value(B));
   }
-  // fixed-order butterfly: every lane ends with the same sums
-  double r[17] = {value(gx), value(gy), value(gz), tangent(gx), tangent(gy), tangent(gz),
-                  value(A0), tangent(A0), value(B0), tangent(B0), value(A1), tangent(A1), value(B1), tangent(B1), e,
-                  0.0, 0.0};
+  // fixed-order butterfly: every lane ends with the same sums (the tangent
+  // fields only where there is a tangent; FP32 sums for the FP32 evaluation)
+  double r[15];
+  if constexpr (std::is_same<T, DualF>::value) {
+    float f[15] = {gx.v, gy.v, gz.v, gx.t, gy.t, gz.t, A0.v, A0.t, B0.v, B0.t, A1.v, A1.t, B1.v, B1.t, ef};
 #pragma unroll
-  for (int k = 0; k < 15; ++k)
+    for (int k = 0; k < 15; ++k) {
 #pragma unroll
-    for (int m = 16; m >= 1; m >>= 1) r[k] += __shfl_xor_sync(0xffffffffu, r[k], m);
+      for (int m = 16; m >= 1; m >>= 1) f[k] += __shfl_xor_sync(0xffffffffu, f[k], m);
+      r[k] = (double)f[k];
+    }
+  } else {
+    r[0] = value(gx); r[1] = value(gy); r[2] = value(gz); r[3] = tangent(gx); r[4] = tangent(gy); r[5] = tangent(gz);
+    r[6] = value(A0); r[7] = tangent(A0); r[8] = value(B0); r[9] = tangent(B0);
+    r[10] = value(A1); r[11] = tangent(A1); r[12] = value(B1); r[13] = tangent(B1); r[14] = e;
+    constexpr bool kTan = std::is_same<T, Dual>::value;
+#pragma unroll
+    for (int k = 0; k < 15; ++k) {
+      if (!kTan && (k == 3 || k == 4 || k == 5 || k == 7 || k == 9 || k == 11 || k == 13)) continue;   // zero
+#pragma unroll
+      for (int m = 16; m >= 1; m >>= 1) r[k] += __shfl_xor_sync(0xffffffffu, r[k], m);
+    }
+  }
   if (lane == 0) {
     gv[3 * i] = r[0]; gv[3 * i + 1] = r[1]; gv[3 * i + 2] = r[2];
     if (gt) { gt[3 * i] = r[3]; gt[3 * i + 1] = r[4]; gt[3 * i + 2] = r[5]; }
@@ -289,10 +361,9 @@ __global__ void __launch_bounds__(32 * kLjWarps) k_adj_lj(const double* __restri
 
 // ------------------------------------------------------------------ bonded, Eqs. (4)-(6)
 // gradient of each term's energy with respect to its atoms (not the force)
+// d = x_b - x_a (minimum image)
 template <class T>
-__device__ __forceinline__ T bond_grad(V3<T> xa, V3<T> xb, const AdjDev& P, V3<T>* g) {
-  V3<T> d = xb - xa;
-  wrap_value<T>(d, P);
+__device__ __forceinline__ T bond_grad(V3<T> d, const AdjDev& P, V3<T>* g) {
   const T r = gsqrt(dot(d, d));
   const T dr = r - P.b0;
   const T s = P.kb * dr / r;
@@ -304,10 +375,7 @@ __device__ __forceinline__ T bond_grad(V3<T> xa, V3<T> xb, const AdjDev& P, V3<T
 // theta = angle(u, w), u = x_a - x_b, w = x_c - x_b:
 // dtheta/du = ((u.w / u.u) u - w) / |u x w|, likewise for w
 template <class T>
-__device__ __forceinline__ T angle_grad(V3<T> xa, V3<T> xb, V3<T> xc, const AdjDev& P, V3<T>* g) {
-  V3<T> u = xa - xb, w = xc - xb;
-  wrap_value<T>(u, P);
-  wrap_value<T>(w, P);
+__device__ __forceinline__ T angle_grad(V3<T> u, V3<T> w, const AdjDev& P, V3<T>* g) {
   const T c = dot(u, w);
   const T s = gsqrt(dot(cross(u, w), cross(u, w)));
   const T th = gatan2(s, c);
@@ -324,11 +392,7 @@ __device__ __forceinline__ T angle_grad(V3<T> xa, V3<T> xb, V3<T> xc, const AdjD
 // G_c = p G_a - (1+q) G_d, p = b1.b2/|b2|^2, q = b3.b2/|b2|^2.
 // Returns D = 1 + cos(n phi - phi_s); the energy is k_phi D (Eq. 6).
 template <class T>
-__device__ __forceinline__ T dihedral_grad(V3<T> xa, V3<T> xb, V3<T> xc, V3<T> xd, const AdjDev& P, V3<T>* g) {
-  V3<T> b1 = xb - xa, b2 = xc - xb, b3 = xd - xc;
-  wrap_value<T>(b1, P);
-  wrap_value<T>(b2, P);
-  wrap_value<T>(b3, P);
+__device__ __forceinline__ T dihedral_grad(V3<T> b1, V3<T> b2, V3<T> b3, const AdjDev& P, V3<T>* g) {
   const V3<T> m = cross(b1, b2), n = cross(b2, b3);
   const T bb = dot(b2, b2);
   const T lb2 = gsqrt(bb);
@@ -362,22 +426,21 @@ __global__ void __launch_bounds__(128) k_adj_bonded(const double* __restrict__ x
   V3<T> gt4[4];
   for (int q = si - 1; q <= si; ++q) {
     if (q < 0 || q + 1 >= P.sites) continue;
-    const T en = bond_grad<T>(load_pos<T>(x, beta, cu, o + q, P), load_pos<T>(x, beta, cu, o + q + 1, P), P, gt4);
+    const T en = bond_grad<T>(sep<T>(x, beta, cu, o + q, o + q + 1, P), P, gt4);
     g = g + gt4[si - q];
     if (q == si) eb = value(en);
   }
   for (int q = si - 2; q <= si; ++q) {
     if (q < 0 || q + 2 >= P.sites) continue;
-    const T en = angle_grad<T>(load_pos<T>(x, beta, cu, o + q, P), load_pos<T>(x, beta, cu, o + q + 1, P),
-                               load_pos<T>(x, beta, cu, o + q + 2, P), P, gt4);
+    const T en = angle_grad<T>(sep<T>(x, beta, cu, o + q + 1, o + q, P), sep<T>(x, beta, cu, o + q + 1, o + q + 2, P),
+                               P, gt4);
     g = g + gt4[si - q];
     if (q == si) ea = value(en);
   }
   for (int q = si - 3; q <= si; ++q) {
     if (q < 0 || q + 3 >= P.sites) continue;
-    const T dd = dihedral_grad<T>(load_pos<T>(x, beta, cu, o + q, P), load_pos<T>(x, beta, cu, o + q + 1, P),
-                                  load_pos<T>(x, beta, cu, o + q + 2, P), load_pos<T>(x, beta, cu, o + q + 3, P),
-                                  P, gt4);
+    const T dd = dihedral_grad<T>(sep<T>(x, beta, cu, o + q, o + q + 1, P), sep<T>(x, beta, cu, o + q + 1, o + q + 2, P),
+                                  sep<T>(x, beta, cu, o + q + 2, o + q + 3, P), P, gt4);
     g = g + gt4[si - q];
     if (q == si) D = dd;
   }
@@ -518,6 +581,7 @@ struct md_adj {
   cudaStream_t st;
   bool own_stream;
   int C_cells;
+  bool hvp32;                  // Hessian-vector products in FP32 (md_adj_desc.hvp_precision = 1)
   // device buffers (one allocation)
   void* mem;
   double *x, *v, *gv, *gt, *alpha, *beta, *rec, *part, *acc, *totals, *ckx, *ckv, *seg, *xk;
@@ -558,7 +622,11 @@ int evaluate(md_adj* a, const double* xp, const double* beta, double cu, int mod
   launch_bin_scatter(a->cell_of, a->slot, a->cell_start, a->tmp, N, st);
   launch_cell_rank(a->cell_start, a->tmp, a->perm, a->C_cells, st);
   const int lj_blocks = (N + kLjWarps - 1) / kLjWarps;
-  if (beta) {
+  if (beta && a->hvp32) {
+    k_adj_lj<DualF><<<lj_blocks, 32 * kLjWarps, 0, st>>>(xp, beta, cu, a->cell_start, a->perm, P, a->x32, a->gv,
+                                                           a->gt, a->rec);
+    k_adj_bonded<DualF><<<(N + 127) / 128, 128, 0, st>>>(xp, beta, cu, P, a->gv, a->gt, a->rec);
+  } else if (beta) {
     k_adj_lj<Dual><<<lj_blocks, 32 * kLjWarps, 0, st>>>(xp, beta, cu, a->cell_start, a->perm, P, a->x32, a->gv,
                                                           a->gt, a->rec);
     k_adj_bonded<Dual><<<(N + 127) / 128, 128, 0, st>>>(xp, beta, cu, P, a->gv, a->gt, a->rec);
@@ -662,6 +730,11 @@ extern "C" int md_adj_create(const md_adj_desc* d, md_adj** out) {
     return adj_fail(MD_EINVAL, "lj_form must be 0 or 1");
   }
   P.sf = d->lj_form;
+  if (d->hvp_precision != 0 && d->hvp_precision != 1) {
+    delete a;
+    return adj_fail(MD_EINVAL, "hvp_precision must be 0 (FP64) or 1 (FP32)");
+  }
+  a->hvp32 = d->hvp_precision == 1;
   P.pre2 = (float)((d->rc + 1e-4) * (d->rc + 1e-4));
   P.kb = p.kb; P.b0 = p.b0; P.ka = p.ka; P.theta0 = p.theta0; P.phis = p.phis; P.n_mult = p.n_mult;
   P.inv_mass[0] = 1.0 / p.mass[0];

@@ -157,10 +157,10 @@ def melt_1500():
 CASES = [(1, 500, 1e-3, 1e-3, 5), (0, 50, 1e-3, 1e-3, 5), (0, 500, 2e-2, 1e-1, 0)]
 
 
-def _fd_case(md, melt, lj_form, K, rtol_u, rtol_r, min_sharp, checkpoint_every=50):
+def _fd_case(md, melt, lj_form, K, rtol_u, rtol_r, min_sharp, checkpoint_every=50, hvp_fp32=False):
     s = oracle.System(oracle.chain_topology(SITES), melt["n_chains"], melt["L"], use_cells=True,
                       params=dict(oracle.default_params(), lj_form=lj_form))
-    adj = md.Adjoint(melt, n_steps=K, checkpoint_every=checkpoint_every, lj_form=lj_form)
+    adj = md.Adjoint(melt, n_steps=K, checkpoint_every=checkpoint_every, lj_form=lj_form, hvp_fp32=hvp_fp32)
     obs = adj.forward()
     assert obs == pytest.approx(s.traj_means(melt["pos"], melt["vel"], 0.001, K), rel=1e-7)
     g = np.stack([adj.backward((1.0, 0.0)), adj.backward((0.0, 1.0))])
@@ -191,3 +191,55 @@ def test_gradient_matches_oracle_finite_differences_7500_sites_500_steps(md):
     differences resolve the gradient."""
     melt, _ = _equilibrated(50, seed=5)
     _fd_case(md, melt, 1, 500, 1e-3, 1e-3, 5)
+
+
+# ---------------------------------------------------------------- FP32 Hessian-vector products
+def test_fp32_hvp_tangent_matches_oracle_differences(md):
+    """The FP32 evaluation of the reverse pass (FP64 separations and pair set,
+    FP32 dual arithmetic) against the same central differences; the bars are
+    those of FP32 sums over ~100 pairs per atom."""
+    m = chaingen.melt(4, seed=21, L=3.4)
+    s = _oracle_system(m)
+    x = chaingen.unwrapped(m)
+    adj = md.Adjoint(m, n_steps=0, hvp_fp32=True)
+    d = _direction(len(x), 1)
+    gu, hv, dth, dmix = adj.tangent(x, d)
+    f0, en, _ = s.forces(x)
+    assert np.linalg.norm(gu + f0) <= 1e-5 * np.linalg.norm(f0)
+    assert adj.energy()["U"] == pytest.approx(en[1] + en[2] + en[3] + en[4], rel=1e-5)
+    h = 1e-6
+    fd = -(s.forces(x + h * d)[0] - s.forces(x - h * d)[0]) / (2 * h)
+    err = np.linalg.norm(hv - fd) / np.linalg.norm(fd)
+    assert err < 1e-4, err
+    g = s.fd_gradient(x, m["vel"], 0.001, 0, rel_h=1e-5)[0]
+    assert np.allclose(dth, g, rtol=1e-5, atol=1e-7 * np.abs(g).max())
+    th0 = s.theta()
+    want = np.zeros(5)
+    for i in range(5):
+        hp = 1e-5 * th0[i]
+        tp, tm = th0.copy(), th0.copy()
+        tp[i] += hp; tm[i] -= hp
+        s.set_params(s.with_theta(tp)); fp = s.forces(x)[0]
+        s.set_params(s.with_theta(tm)); fm = s.forces(x)[0]
+        want[i] = -((fp - fm) * d).sum() / (2 * hp)
+    s.set_params(s.with_theta(th0))
+    assert np.allclose(dmix, want, rtol=1e-4, atol=1e-6 * np.abs(want).max())
+    adj.close()
+
+
+def test_fp32_hvp_gradient_matches_oracle_finite_differences_1500_sites(md, melt_1500):
+    """500 force-shifted steps with FP32 Hessian-vector products: the same
+    1e-3 bar against the oracle's finite differences as the FP64 reverse pass."""
+    _fd_case(md, melt_1500[0], 1, 500, 1e-3, 1e-3, 5, hvp_fp32=True)
+
+
+def test_fp32_hvp_gradient_close_to_fp64(md, melt_1500):
+    """Same forward run, reverse pass in FP64 and in FP32 dual numbers."""
+    out = []
+    for fp32 in (False, True):
+        adj = md.Adjoint(melt_1500[0], n_steps=200, checkpoint_every=50, lj_form=1, hvp_fp32=fp32)
+        adj.forward()
+        out.append(np.stack([adj.backward((1.0, 0.0)), adj.backward((0.0, 1.0))]))
+        adj.close()
+    rel = np.abs(out[1] - out[0]) / np.abs(out[0]).max(axis=1, keepdims=True)
+    assert rel.max() < 1e-4, rel
