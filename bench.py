@@ -369,6 +369,25 @@ def run_gpu(args):
     melt = equilibrate(md, make_workload(rank, args.chains))
     n_atoms = len(melt["pos"])
 
+    if args.ncu_energy:
+        # the kernels of md_energy (energy-form forces, reductions, kinetic
+        # energy) inside cudaProfilerStart/Stop, for a launch list
+        s = md.System(melt, precision=md.MD_MIXED)
+        s.step(MD_STEPS_PER_BENCH_STEP)
+        s.energy()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        torch.cuda.profiler.start()
+        for _ in range(args.steps):
+            s.energy()
+        torch.cuda.profiler.stop()
+        el = time.perf_counter() - t0
+        s.close()
+        if rank == 0:
+            print(json.dumps({"ncu_energy": True, "calls": args.steps, "ms_per_call": el / args.steps * 1e3,
+                              "sites": n_atoms}), flush=True)
+        return
+
     results = {}
     forms = (("mixed", md.MD_MIXED),) if args.ncu_region else (("mixed", md.MD_MIXED), ("plain", md.MD_PLAIN_FP32))
     for name, prec in forms:
@@ -497,6 +516,9 @@ def main():
     p.add_argument("--ncu-region", action="store_true",
                    help="profile only the timed loop of the mixed form (cudaProfilerStart/Stop); "
                         "skips the plain form, e2e, drift and CPU baseline")
+    p.add_argument("--ncu-energy", action="store_true",
+                   help="profile only `steps` md_energy calls on the mixed form (cudaProfilerStart/Stop), "
+                        "then exit")
     args = p.parse_args()
     if args.warmup < 3:
         args.warmup = 3
