@@ -85,3 +85,24 @@ def test_thermostat_needs_targets(lib):
     d, keep = _desc(m, thermostat=md.MD_VRESCALE)
     with pytest.raises(md.MDError):
         md.md_workspace_size(d)
+
+
+def _adj_desc(**kw):
+    d = md.md_adj_desc()
+    d.n_chains, d.sites_per_chain, d.box = 4, 150, 3.4
+    d.params = md.make_params(md.default_params())
+    d.rc, d.dt, d.n_steps, d.checkpoint_every = 1.0, 0.001, 10, 5
+    d.lj_form, d.hvp_precision = 0, 0
+    for k, v in kw.items():
+        setattr(d, k, v)
+    return d
+
+
+@pytest.mark.parametrize("field,value", [("hvp_precision", 2), ("hvp_precision", -1), ("lj_form", 3),
+                                         ("n_chains", 0), ("n_steps", -1), ("checkpoint_every", 0),
+                                         ("box", 0.0)])
+def test_bad_adjoint_descriptors_are_rejected(lib, field, value):
+    # validated before any CUDA call
+    with pytest.raises(md.MDError) as e:
+        md.md_adj_create(_adj_desc(**{field: value}))
+    assert e.value.code == md.MD_EINVAL
