@@ -137,12 +137,6 @@ __device__ __forceinline__ double fix_to_double_i(long long n) {
   return a == 0ull ? 0.0 : __longlong_as_double((long long)bits);
 }
 
-// int64 fixed-point force -> FP64 by the 1.5 * 2^52 bias (one FP64 add, no
-// conversion instruction); exact for |n| < 2^51.
-__device__ __forceinline__ double fix_to_double(long long n) {
-  return __longlong_as_double(n + 0x4338000000000000ll) - 6755399441055744.0;
-}
-
 // FP32 master: x/h as p + e (exact product error by FMA, plus the low part of
 // 1/h), minus the exact integer-plus-half k; one final rounding.
 __device__ __forceinline__ float cell_unit(float x, int c, int w, const RepDev& R) {
