@@ -42,6 +42,19 @@ def _oracle(melt, params=None):
                          use_cells=n * melt["sites"] > 3000)
 
 
+def _uploaded(melt, precision=md.MD_MIXED):
+    """The state a system holds right after creation, computed on the host
+    from the generator's output (its positions are already in [0, L)): FP64
+    as given, or rounded to FP32 (nearest even) for the plain form.  Oracle
+    inputs come from here, never from the GPU."""
+    x = np.array(melt["pos"], np.float64)
+    v = np.array(melt["vel"], np.float64)
+    if precision == md.MD_PLAIN_FP32:
+        x = x.astype(np.float32).astype(np.float64)
+        v = v.astype(np.float32).astype(np.float64)
+    return x, v
+
+
 def _ambiguous_pairs(x, L, rc, tol=2e-6):
     tr = cKDTree(np.mod(x, L), boxsize=L)
     pairs = tr.query_pairs(rc + tol, output_type="ndarray")
@@ -78,7 +91,7 @@ def check_forces(f_gpu, f_orc, x, L, params=None):
 def test_binning_is_bit_exact(precision, n_chains, L):
     m = chaingen.melt(n_chains, seed=21, L=L)
     s = md.System(m, precision=precision)
-    x, _, _ = s.state()
+    x, _ = _uploaded(m, precision)
     M = s.info["cells_per_side"]
     assert M == int(m["L"] // 1.1)
     co, cs, pm = s.bins()
@@ -93,7 +106,7 @@ def test_binning_is_bit_exact(precision, n_chains, L):
 def test_neighbour_pairs(precision):
     m = chaingen.melt(20, seed=5, L=4.6)
     s = md.System(m, precision=precision)
-    x, _, _ = s.state()
+    x, _ = _uploaded(m, precision)
     L = m["L"]
     cnt, ent = s.neighbors()
     listed = set()
@@ -122,7 +135,7 @@ def test_neighbour_pairs(precision):
 def test_forces_match_oracle(precision, n_chains, seed, L):
     m = chaingen.melt(n_chains, seed=seed, L=L)
     s = md.System(m, precision=precision)
-    x, _, _ = s.state()
+    x, _ = _uploaded(m, precision)
     f = s.forces()
     f_orc, _, _ = _oracle(m).forces(x)
     check_forces(f, f_orc, x, m["L"])
@@ -133,7 +146,7 @@ def test_forces_match_oracle(precision, n_chains, seed, L):
 def test_energies_match_oracle(precision):
     m = chaingen.melt(10, seed=4)
     s = md.System(m, precision=precision)
-    x, v, _ = s.state()
+    x, v = _uploaded(m, precision)
     e = s.energy()[0]
     ref = _oracle(m)
     _, en, vir = ref.forces(x)
@@ -149,7 +162,7 @@ def test_energies_match_oracle(precision):
 def test_short_trajectory_matches_oracle(precision, tol):
     m = chaingen.melt(4, seed=12, L=3.6, T=300.0)
     s = md.System(m, precision=precision, rebin_every=5)
-    x0, v0, _ = s.state()
+    x0, v0 = _uploaded(m, precision)
     s.step(50)
     x, v, img = s.state()
     xo, vo, _, _, _ = _oracle(m).run(x0, v0, 0.001, 50, sample_every=0)
@@ -184,7 +197,7 @@ def test_net_force_vanishes():
 def test_thermostat_temperature_series_matches_oracle():
     m = chaingen.melt(4, seed=8, L=3.6, T=450.0)
     s = md.System(m, precision=md.MD_MIXED, thermostat=md.MD_VRESCALE, T_target=300.0, tau_t=0.02)
-    x0, v0, _ = s.state()
+    x0, v0 = _uploaded(m)
     temps = [s.energy()[0]["temperature"]]
     for _ in range(30):
         s.step(1)
@@ -205,7 +218,7 @@ def test_replicas_equal_separate_runs_and_oracle():
         fa = alone.forces()
         n = len(m["pos"])
         assert np.array_equal(fb[off:off + n], fa)
-        x, _, _ = alone.state()
+        x, _ = _uploaded(m)
         check_forces(fa, _oracle(m).forces(x)[0], x, m["L"])
         alone.close()
         off += n
@@ -274,12 +287,14 @@ def test_short_chains_and_rebin_every_step(sites):
     m = chaingen.melt(n_chains, sites=sites, seed=3, L=3.6)
     params = oracle.default_params()
     s = md.System(m, precision=md.MD_MIXED, rebin_every=1)
-    x, _, _ = s.state()
+    x, v = _uploaded(m)
     ref = oracle.System(oracle.chain_topology(sites), n_chains, m["L"], use_cells=False)
     check_forces(s.forces(), ref.forces(x)[0], x, m["L"], params)
+    # after 7 steps (a rebin before every step): the forces at the end of the
+    # oracle's own 7-step run from the same state
     s.step(7)
-    x, _, _ = s.state()
-    check_forces(s.forces(), ref.forces(x)[0], x, m["L"], params)
+    xo, _, fo, _, _ = ref.run(x, v, 0.001, 7, sample_every=0)
+    check_forces(s.forces(), fo, xo, m["L"], params)
     s.close()
 
 
@@ -329,13 +344,40 @@ def test_full_size_sampled_forces(precision):
     sampled atoms against the oracle's all-atom sums."""
     m = chaingen.melt(10000, seed=3)
     s = md.System(m, precision=precision)
-    x, _, _ = s.state()
+    x, _ = _uploaded(m, precision)
     f = s.forces()
     rng = np.random.default_rng(0)
     sel = np.sort(rng.choice(len(x), 48, replace=False))
     ref = _oracle(m)
     f_orc = ref.lj_atoms(x, sel) + ref.bonded(x)[0][sel]
     _check_sampled(f, x, sel, f_orc, m["L"])
+    s.close()
+
+
+def test_batched_replicas_full_size_sampled_forces():
+    """64 replicas of 20..400 chains (chain counts log-uniform, seed 4;
+    ~1.07M sites) in one system, in the launch configuration the benchmark
+    tunes to (skin 0.12 nm, list every 12 steps, 256 threads, grid schedule),
+    thermostatted at each replica's T0: sampled forces of every replica against
+    the oracle's all-atom sums at the generator's state.  (Straight from the
+    generator, atoms at the hottest contacts move more than skin/2 within 12
+    steps; the benchmark equilibrates first.)"""
+    melts = chaingen.replicas(64, seed=4)
+    T0 = [m["T"] for m in melts]
+    s = md.System(melts, precision=md.MD_MIXED, thermostat=md.MD_VRESCALE, T_target=T0, tau_t=0.1, skin=0.12,
+                  rebin_every=12, lj_block=256, schedule=md.MD_SCHED_GRID)
+    rng = np.random.default_rng(4)
+    f = s.forces()
+    off = 0
+    for m in melts:
+        n = len(m["pos"])
+        xr, _ = _uploaded(m)
+        fr = f[off:off + n]
+        sel = np.sort(rng.choice(n, 3, replace=False))
+        ref = _oracle(m)
+        _check_sampled(fr, xr, sel, ref.lj_atoms(xr, sel) + ref.bonded(xr)[0][sel], m["L"])
+        off += n
+    assert off == len(f)
     s.close()
 
 
@@ -382,8 +424,9 @@ def test_set_state_round_trip_and_non_finite_input(precision):
     assert e.value.code == md.MD_EINVAL
     s.set_state(m["pos"], m["vel"])
     f = s.forces()
-    f_orc, _, _ = _oracle(m).forces(s.state()[0])
-    check_forces(f, f_orc, s.state()[0], L)
+    xu, _ = _uploaded(m, precision)
+    f_orc, _, _ = _oracle(m).forces(xu)
+    check_forces(f, f_orc, xu, L)
     s.close()
 
 
@@ -495,7 +538,7 @@ def test_config2_quench_plain_fp32():
     # (the pair set inside r_c does not depend on it)
     s = md.System(m, precision=md.MD_PLAIN_FP32, thermostat=md.MD_VRESCALE, T_target=300.0, tau_t=0.1,
                   skin=0.25, rebin_every=10)
-    x0, v0, _ = s.state()
+    x0, v0 = _uploaded(m, md.MD_PLAIN_FP32)
     f = s.forces()
     rng = np.random.default_rng(2)
     sel = np.sort(rng.choice(len(x0), 64, replace=False))
