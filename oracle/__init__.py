@@ -105,6 +105,8 @@ def lib():
         L.orc_forces.argtypes = [P, P, P, P, P, P]
         L.orc_run.argtypes = [P, P, P, P, P, P, d, i64, i32, d, d, d, P, i64, P]
         L.orc_run.restype = ctypes.c_int
+        L.orc_run_nh.argtypes = [P, P, P, P, P, P, d, i64, d, d, d, P, i64, P]
+        L.orc_run_nh.restype = ctypes.c_int
         L.orc_traj_means.argtypes = [P, P, P, P, P, d, i64, P]
         L.orc_traj_means.restype = ctypes.c_int
         L.orc_kinetic.argtypes = [i64, i32, P, P]
@@ -241,6 +243,29 @@ class System:
                            _p(f), dt, n_steps, int(thermostat), T0, tau, KB, ctypes.byref(lam_c),
                            sample_every, _p(samples))
         return x, v, f, samples[:nr], lam_c.value
+
+    def run_nh(self, x, v, dt: float, n_steps: int, T0: float, tau: float, xi: float = 0.0, sample_every: int = 1):
+        """Leap-Frog with Nose-Hoover coupling and centre-of-mass translation
+        removal (Sec. 2, Sec. 3.4), Q = tau^2 T0 / (4 pi^2); v is the on-step
+        velocity.  Returns x, v, f, samples[(step, lj, lj_s, bond, angle, dih,
+        ke, T, xi, eta)], xi."""
+        x = _c(x, np.float64).reshape(-1, 3).copy()
+        v = _c(v, np.float64).reshape(-1, 3).copy()
+        f = np.zeros_like(x)
+        rows = n_steps // max(sample_every, 1) + 2
+        samples = np.zeros((rows, 10))
+        xi_c = ctypes.c_double(xi)
+        nr = lib().orc_run_nh(ctypes.byref(self.s), ctypes.byref(self.ff), _p(self.masses_m), _p(x), _p(v),
+                              _p(f), dt, n_steps, T0, tau, KB, ctypes.byref(xi_c), sample_every, _p(samples))
+        return x, v, f, samples[:nr], xi_c.value
+
+    def nh_extended_energy(self, samples, T0: float, tau: float):
+        """H = K + U + g kB Q xi^2 / 2 + g kB T0 eta per sample row of run_nh
+        (U with the shifted LJ energy; g = 3N - 3)."""
+        g = 3.0 * self.n - 3.0
+        Q = tau * tau * T0 / (4.0 * np.pi ** 2)
+        U = samples[:, 2] + samples[:, 3] + samples[:, 4] + samples[:, 5]
+        return samples[:, 6] + U + 0.5 * g * KB * Q * samples[:, 8] ** 2 + g * KB * T0 * samples[:, 9]
 
     def traj_means(self, x, v, dt: float, n_steps: int):
         """(mean U, mean R_ee^2) over steps 0..n_steps of an NVE velocity-Verlet

@@ -584,6 +584,82 @@ int orc_run(const orc_sys *S, const orc_ff *ff, const double *mass_m, double *x,
     return rows;
 }
 
+/*
+ * NVT run with the paper's integrator and thermostat: Leap-Frog (Sec. 2,
+ * Sec. 3.4) with Nose-Hoover coupling (the extended-ensemble method of
+ * Sec. 2), and removal of the centre-of-mass translation (Sec. 2).  The paper
+ * prints no formulas; this is the standard leap-frog Nose-Hoover scheme for
+ *   dv/dt = F/m - xi v,   dxi/dt = (T - T0) / Q,   Q = tau^2 T0 / (4 pi^2):
+ *   v_{k+1/2} = [v_{k-1/2} (1 - c_k) + dt F_k / m] / (1 + c_k),  c_k = dt xi_k / 2,
+ *   x_{k+1}   = x_k + dt v_{k+1/2},
+ *   xi_{k+1}  = xi_k + dt (T_{k+1/2} - T0) / Q    (midpoint rule),
+ * T_{k+1/2} the temperature (3N - 3 degrees of freedom) of v_{k+1/2}.  The
+ * step goes through the on-step velocity
+ *   v_k = (v_{k-1/2} + dt F_k / (2m)) / (1 + c_k),
+ * from which v_{k+1/2} = (1 - c_k) v_k + dt F_k / (2m) is the same update.
+ * After the drift and T_{k+1/2}, the centre-of-mass velocity of v_{k+1/2} is
+ * subtracted.
+ * In: v = v_0 (on step), *xi_io = xi_0.  Out: x_K, v_K, F_K, *xi_io = xi_K.
+ * Sample rows (10 values): k, lj, lj_shifted, bond, angle, dihedral, kinetic,
+ * T, xi_k, eta_k with eta the trapezoidal integral of xi; with them
+ *   H = K + U + g kB Q xi^2 / 2 + g kB T0 eta,  g = 3N - 3,
+ * is the conserved energy of the extended system.
+ */
+int orc_run_nh(const orc_sys *S, const orc_ff *ff, const double *mass_m, double *x, double *v, double *f,
+               double dt, int64_t n_steps, double T0, double tau, double kB, double *xi_io, int64_t sample_every,
+               double *samples) {
+    int64_t n = S->n_mol * S->naom;
+    double *m = (double *)malloc(sizeof(double) * n);
+    double M = 0.0;
+    for (int64_t i = 0; i < n; ++i) { m[i] = mass_m[i % S->naom]; M += m[i]; }
+    const double pi = 3.14159265358979323846;
+    const double dof = 3.0 * (double)n - 3.0;
+    const double Q = tau * tau * T0 / (4.0 * pi * pi);
+    double xi = *xi_io, eta = 0.0;
+    double en[7], vir[6];
+    orc_forces(S, ff, x, f, en, vir);
+    int rows = 0;
+    for (int64_t k = 0; k <= n_steps; ++k) {
+        const double c = 0.5 * dt * xi;
+        if (k > 0)                                   /* v holds v_{k-1/2}: the on-step velocity */
+            for (int64_t i = 0; i < n; ++i)
+                for (int q = 0; q < 3; ++q) v[3 * i + q] = (v[3 * i + q] + 0.5 * dt * f[3 * i + q] / m[i]) / (1.0 + c);
+        double ke = 0.0;
+        for (int64_t i = 0; i < n; ++i)
+            for (int q = 0; q < 3; ++q) ke += 0.5 * m[i] * v[3 * i + q] * v[3 * i + q];
+        const double T = 2.0 * ke / (dof * kB);       /* on-step T_k, reported */
+        if (sample_every > 0 && (k % sample_every == 0)) {
+            double *r = samples + 10 * rows++;
+            r[0] = (double)k; r[1] = en[0]; r[2] = en[1]; r[3] = en[2]; r[4] = en[3]; r[5] = en[4];
+            r[6] = ke; r[7] = T; r[8] = xi; r[9] = eta;
+        }
+        if (k == n_steps) break;
+        /* v_{k+1/2} and the drift */
+        for (int64_t i = 0; i < n; ++i)
+            for (int q = 0; q < 3; ++q) {
+                v[3 * i + q] = (1.0 - c) * v[3 * i + q] + 0.5 * dt * f[3 * i + q] / m[i];
+                x[3 * i + q] += dt * v[3 * i + q];
+            }
+        /* T_{k+1/2}, then the centre-of-mass translation of v_{k+1/2} removed */
+        double ke_h = 0.0, P[3] = { 0.0, 0.0, 0.0 };
+        for (int64_t i = 0; i < n; ++i)
+            for (int q = 0; q < 3; ++q) {
+                ke_h += 0.5 * m[i] * v[3 * i + q] * v[3 * i + q];
+                P[q] += m[i] * v[3 * i + q];
+            }
+        for (int64_t i = 0; i < n; ++i)
+            for (int q = 0; q < 3; ++q) v[3 * i + q] -= P[q] / M;
+        const double T_h = 2.0 * ke_h / (dof * kB);
+        const double xi_next = xi + dt * (T_h - T0) / Q;
+        eta += 0.5 * dt * (xi + xi_next);
+        xi = xi_next;
+        orc_forces(S, ff, x, f, en, vir);
+    }
+    *xi_io = xi;
+    free(m);
+    return rows;
+}
+
 /* Kinetic energy and instantaneous temperature (3N-3 dof). */
 double orc_kinetic(int64_t n, int32_t naom, const double *mass_m, const double *v) {
     double ke = 0.0;

@@ -457,3 +457,60 @@ def test_force_shifted_variant_forces_are_minus_energy_gradient():
     fd = _fd_check(lambda y: s.lj(y)[1][1], x, atoms, h=1e-7)
     an = np.concatenate([f[i] for i in atoms])
     assert np.allclose(fd, an, rtol=1e-5, atol=1e-6 * np.abs(an).max())
+
+
+# ------------------------------------------------------------------ Leap-Frog + Nose-Hoover (Sec. 2, 3.4)
+def _nh_system(T=450.0, seed=12):
+    m = chaingen.melt(4, seed=seed, L=3.4, T=T)
+    return m, oracle.System(oracle.chain_topology(150), 4, m["L"], use_cells=False)
+
+
+def test_nose_hoover_extended_energy_error_is_second_order():
+    """The extended energy K + U + g kB Q xi^2/2 + g kB T0 int(xi) is
+    conserved by the continuous equations; the leap-frog scheme keeps it to
+    O(dt^2) over a fixed time (a quench from 450 K to 300 K with tau = 0.1
+    ps, so xi moves far from 0)."""
+    m, s = _nh_system()
+    err = []
+    for dt, K in ((0.001, 200), (0.0005, 400), (0.00025, 800)):
+        _, _, _, smp, _ = s.run_nh(m["pos"], m["vel"], dt, K, T0=300.0, tau=0.1, sample_every=K // 50)
+        H = s.nh_extended_energy(smp, 300.0, 0.1)
+        err.append(np.abs(H - H[0]).max())
+    assert 3.3 < err[0] / err[1] < 4.7 and 3.3 < err[1] / err[2] < 4.7, err
+
+
+def test_nose_hoover_without_coupling_is_velocity_verlet():
+    """Q -> infinity: xi stays 0 and the run is NVE velocity Verlet (the
+    centre-of-mass velocity of the generator's input is already zero)."""
+    m, s = _nh_system()
+    xa, va, _, _, xi = s.run_nh(m["pos"], m["vel"], 0.001, 40, T0=300.0, tau=1e9, sample_every=0)
+    xb, vb, _, _, _ = s.run(m["pos"], m["vel"], 0.001, 40, sample_every=0)
+    assert abs(xi) < 1e-12
+    assert np.abs(xa - xb).max() < 1e-12 and np.abs(va - vb).max() < 1e-9
+
+
+def test_nose_hoover_removes_centre_of_mass_translation():
+    m, s = _nh_system()
+    masses = np.asarray(m["masses"])                       # per atom
+    v = m["vel"] + np.array([0.3, -0.2, 0.1])              # a drifting input
+    _, v1, _, _, _ = s.run_nh(m["pos"], v, 0.001, 1, T0=300.0, tau=0.1, sample_every=0)
+    p = (masses[:, None] * v1).sum(0)
+    assert np.abs(p).max() < 1e-10 * np.abs(masses[:, None] * v1).sum()
+
+
+def test_nose_hoover_run_splits_at_any_step():
+    """Two runs of 7 and 13 steps, the second from the first's on-step state
+    and xi, give the 20-step run bit for bit (what a GPU call boundary must
+    reproduce)."""
+    m, s = _nh_system()
+    x20, v20, _, _, xi20 = s.run_nh(m["pos"], m["vel"], 0.001, 20, T0=300.0, tau=0.1, sample_every=0)
+    x7, v7, _, _, xi7 = s.run_nh(m["pos"], m["vel"], 0.001, 7, T0=300.0, tau=0.1, sample_every=0)
+    x, v, _, _, xi = s.run_nh(x7, v7, 0.001, 13, T0=300.0, tau=0.1, xi=xi7, sample_every=0)
+    assert np.array_equal(x, x20) and np.array_equal(v, v20) and xi == xi20
+
+
+def test_nose_hoover_cools_a_hot_melt_towards_the_target():
+    m, s = _nh_system()
+    _, _, _, smp, _ = s.run_nh(m["pos"], m["vel"], 0.001, 400, T0=300.0, tau=0.1, sample_every=100)
+    assert smp[0, 7] > 400.0
+    assert abs(smp[-1, 7] - 300.0) < 10.0
