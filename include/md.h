@@ -50,7 +50,7 @@ enum {
 };
 
 enum { MD_PLAIN_FP32 = 0, MD_MIXED = 1 };   /* precision forms */
-enum { MD_NVE = 0, MD_VRESCALE = 1 };       /* thermostat */
+enum { MD_NVE = 0, MD_VRESCALE = 1, MD_NOSE_HOOVER = 2 };   /* thermostat */
 /* LJ work schedule: one thread block per cell, or a fixed grid (resident
  * blocks x SMs) whose blocks take cells from a device counter */
 enum { MD_SCHED_GRID = 0, MD_SCHED_PERSISTENT = 1 };
@@ -85,7 +85,15 @@ typedef struct {
   double tau_t;                /* thermostat coupling time, ps */
   int32_t rebin_every;         /* steps between rebin + list builds (paper: 10) */
   int32_t precision;           /* MD_PLAIN_FP32 or MD_MIXED */
-  int32_t thermostat;          /* MD_NVE or MD_VRESCALE */
+  int32_t thermostat;          /* MD_NVE; MD_VRESCALE (weak coupling, lambda =
+                                  sqrt(1 + dt/tau (T0/T - 1)) from the previous step's T);
+                                  or MD_NOSE_HOOVER, the paper's NVT ensemble (Leap-Frog with
+                                  Nose-Hoover coupling, Sec. 2 and 3.4): per replica
+                                  v_{k+1/2} = [v_{k-1/2}(1 - dt xi_k/2) + dt F/m]/(1 + dt xi_k/2),
+                                  xi_{k+1} = xi_k + dt (T_{k+1/2} - T0)/Q, Q = tau^2 T0/(4 pi^2),
+                                  T_{k+1/2} from v_{k+1/2} (3N - 3 dof), and the centre-of-mass
+                                  velocity of v_{k+1/2} removed before the next step.  xi starts
+                                  at 0 and persists across md_step and md_set_state calls. */
   int32_t nbr_capacity;        /* neighbour slots per atom; 0 = chosen from density */
   int32_t lj_block;            /* threads per block of the LJ kernel: 128 or 256 (0 = 256) */
   int32_t schedule;            /* MD_SCHED_GRID or MD_SCHED_PERSISTENT (see below) */
@@ -178,6 +186,10 @@ int md_set_params(md_system *sys, const md_params *params);
 
 /* Thermostat targets per replica ([n_replicas] kelvin). */
 int md_set_temperature(md_system *sys, const double *T_target);
+
+/* Nose-Hoover friction xi (1/ps) of each replica, [n_replicas]; zeros for
+ * the other thermostats.  Synchronous. */
+int md_get_thermostat(md_system *sys, double *xi);
 
 /* The cudaStream_t the system runs on (for events and ordering). */
 void *md_stream(md_system *sys);

@@ -19,7 +19,7 @@ LIB_PATH = _build.LIB
 
 MD_OK, MD_EINVAL, MD_ENOMEM, MD_ECUDA, MD_EOVERFLOW, MD_EUNSTABLE, MD_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
 MD_PLAIN_FP32, MD_MIXED = 0, 1
-MD_NVE, MD_VRESCALE = 0, 1
+MD_NVE, MD_VRESCALE, MD_NOSE_HOOVER = 0, 1, 2
 MD_SCHED_GRID, MD_SCHED_PERSISTENT = 0, 1
 KB = 0.0083144626  # kJ/mol/K
 
@@ -77,7 +77,7 @@ class md_energy_t(ctypes.Structure):
 
 
 EXPORTS = ["md_autotune", "md_workspace_size", "md_create", "md_step", "md_step_async", "md_sync", "md_forces", "md_energy",
-           "md_rebin", "md_get_state", "md_set_state", "md_set_params", "md_set_temperature", "md_stream",
+           "md_rebin", "md_get_state", "md_set_state", "md_set_params", "md_set_temperature", "md_get_thermostat", "md_stream",
            "md_info", "md_get_bins", "md_get_neighbors", "md_get_cell_units", "md_profile_enable", "md_profile_read",
            "md_profile_reset", "md_launches_per_call", "md_bin_static", "md_destroy", "md_last_error",
            "md_adj_create", "md_adj_set_theta", "md_adj_forward", "md_adj_backward", "md_adj_tangent",
@@ -110,6 +110,7 @@ def load(path: str = LIB_PATH):
         "md_set_state": ([P, P, P], ctypes.c_int),
         "md_set_params": ([P, P], ctypes.c_int),
         "md_set_temperature": ([P, P], ctypes.c_int),
+        "md_get_thermostat": ([P, P], ctypes.c_int),
         "md_stream": ([P], P),
         "md_info": ([P, P, P, P, P], ctypes.c_int),
         "md_get_bins": ([P, P, P, P], ctypes.c_int),
@@ -234,6 +235,12 @@ def md_set_params(h, p: dict):
 def md_set_temperature(h, T):
     T = np.ascontiguousarray(T, np.float64)
     _check(load().md_set_temperature(h, _p(T)), h)
+
+
+def md_get_thermostat(h, n_replicas: int) -> np.ndarray:
+    xi = np.zeros(n_replicas, np.float64)
+    _check(load().md_get_thermostat(h, xi.ctypes.data), h)
+    return xi
 
 
 def md_stream(h) -> int:
@@ -438,6 +445,11 @@ class System:
 
     def set_temperature(self, T):
         md_set_temperature(self.h, np.broadcast_to(np.asarray(T, np.float64), (self.n_replicas,)))
+
+    def thermostat_xi(self) -> np.ndarray:
+        """Nose-Hoover friction xi (1/ps) of each replica (zeros for the
+        other thermostats)."""
+        return md_get_thermostat(self.h, self.n_replicas)
 
     def bins(self):
         return md_get_bins(self.h, self.n_atoms, self.info["n_cells"])

@@ -16,6 +16,15 @@
 // factor.
 // The factor computed at step k is applied at step k+1 (one-step lag).
 //
+// Nose-Hoover (TH = 2; the paper's NVT ensemble with Leap-Frog, Sec. 2 and
+// 3.4): per replica, lam[6r..6r+5] = (xi_k, 1 - c_k, 1/(1 + c_k), V_com),
+// c_k = dt xi_k / 2.  A step closes v_k = (v_{k-1/2} - V_com + dt F/(2m)) /
+// (1 + c_k), opens v_{k+1/2} = (1 - c_k) v_k + dt F/(2m) and drifts; the
+// last block takes T_{k+1/2} and the momentum of v_{k+1/2} and leaves
+// xi_{k+1} = xi_k + dt (T_{k+1/2} - T0)/Q, Q = tau^2 T0/(4 pi^2), and the
+// centre-of-mass velocity that the next step subtracts.  This is the
+// leap-frog update v_{k+1/2} = [v_{k-1/2}(1 - c_k) + dt F/m]/(1 + c_k).
+//
 // The drift also refreshes the FP32 cell-unit positions in sorted order for
 // the force kernels, wraps positions into [0, L) with image counters, and
 // flags atoms that moved more than skin/2 since the last rebin.
@@ -38,7 +47,7 @@ __device__ __forceinline__ bool past_box(float x, float L) { return __float_as_i
 __device__ __forceinline__ bool negative(double x) { return __double_as_longlong(x) < 0; }
 __device__ __forceinline__ bool negative(float x) { return __float_as_int(x) < 0; }
 
-template <bool MIXED, int MODE, bool KE, bool THERMO>
+template <bool MIXED, int MODE, bool KE, int TH>
 __global__ void __launch_bounds__(kIntBlock) k_integrate(void* __restrict__ xv, void* __restrict__ vv,
                                                          int* __restrict__ img, const void* __restrict__ Fv,
                                                          const uint16_t* __restrict__ site,
@@ -58,6 +67,7 @@ __global__ void __launch_bounds__(kIntBlock) k_integrate(void* __restrict__ xv, 
   const RepDev& R = reps[t.rep];
   const int i = t.start + threadIdx.x;
   double ke = 0.0;
+  double mom[3] = {0.0, 0.0, 0.0};   // Nose-Hoover: momentum of v_{k+1/2}
   if ((int)threadIdx.x < t.len) {
     const int sm = site[i];
     const int type = (sm == 0 || sm == fp.sites - 1) ? 1 : 0;
@@ -79,17 +89,24 @@ __global__ void __launch_bounds__(kIntBlock) k_integrate(void* __restrict__ xv, 
     // kick of dt F/m (the full-step velocity is never needed in between).
     constexpr bool kMerged = MODE == kKickKickDrift && !KE;
     if ((MODE == kKickKickDrift && KE) || MODE == kKickOnly) {
+      if constexpr (TH == 2) {
+        const double* nh = lam + 6 * t.rep;
+        const T fc = (T)nh[2];
 #pragma unroll
-      for (int a = 0; a < 3; ++a) vi[a] += hdt_m * F[a];   // v(t): close the previous step
+        for (int a = 0; a < 3; ++a) vi[a] = (vi[a] - (T)nh[3 + a] + hdt_m * F[a]) * fc;   // v_k
+      } else {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) vi[a] += hdt_m * F[a];   // v(t): close the previous step
+      }
     }
-    if (KE) {
+    if (KE && TH != 2) {
       const double m = fp.mass[type];
       ke = 0.5 * m * ((double)vi[0] * vi[0] + (double)vi[1] * vi[1] + (double)vi[2] * vi[2]);
     }
     if (MODE == kKickOnly) {
       v[i] = vi[0]; v[N + i] = vi[1]; v[2 * N + i] = vi[2];
     } else if (MODE == kKickDrift || MODE == kKickKickDrift) {
-      if (THERMO) {
+      if (TH == 1) {
         const T l = (T)lam[t.rep];
 #pragma unroll
         for (int a = 0; a < 3; ++a) vi[a] *= l;
@@ -102,9 +119,12 @@ __global__ void __launch_bounds__(kIntBlock) k_integrate(void* __restrict__ xv, 
       const float halfM = 0.5f * R.Mf;
       float loc[3], d2 = 0.f;
       bool bad = false;
+      T fo = (T)1;
+      if constexpr (TH == 2) fo = (T)lam[6 * t.rep + 1];
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        vi[a] = kMerged ? vi[a] + (hdt_m + hdt_m) * F[a] : vi[a] + hdt_m * F[a];
+        if constexpr (TH == 2) vi[a] = vi[a] * fo + hdt_m * F[a];   // v_{k+1/2}
+        else vi[a] = kMerged ? vi[a] + (hdt_m + hdt_m) * F[a] : vi[a] + hdt_m * F[a];
         T xa = x[a * N + i] + dt * vi[a];
         // wrap into [0, L): for non-negative IEEE numbers the bit patterns
         // order like the values, so the tests run on the integer pipe
@@ -129,19 +149,40 @@ __global__ void __launch_bounds__(kIntBlock) k_integrate(void* __restrict__ xv, 
       }
       if (d2 > R.hs2u) atomicOr(flags, kFlagDisplacement);
       if (bad) atomicOr(flags, kFlagNaN);
+      if constexpr (TH == 2) {
+        const double m = fp.mass[type];
+        ke = 0.5 * m * ((double)vi[0] * vi[0] + (double)vi[1] * vi[1] + (double)vi[2] * vi[2]);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) mom[a] = m * (double)vi[a];
+      }
       pos[inv_perm[i]] = make_float4(loc[0], loc[1], loc[2], (float)type);   // w: LJ type, as the sort writes it
     }
   }
   if (KE) {
-    __shared__ double red[kIntBlock / 32];
+    __shared__ double red[4][kIntBlock / 32];
     __shared__ bool last;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     double s = warp_sum_i(ke);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    if (lane == 0) red[0][w] = s;
+    if constexpr (TH == 2) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const double sm = warp_sum_i(mom[a]);
+        if (lane == 0) red[1 + a][w] = sm;
+      }
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
       double b = 0.0;
-      for (int q = 0; q < kIntBlock / 32; ++q) b += red[q];
+      for (int q = 0; q < kIntBlock / 32; ++q) b += red[0][q];
       kepart[blockIdx.x] = b;
+      if constexpr (TH == 2) {
+        for (int a = 0; a < 3; ++a) {
+          double bm = 0.0;
+          for (int q = 0; q < kIntBlock / 32; ++q) bm += red[1 + a][q];
+          kepart[gridDim.x + 3 * blockIdx.x + a] = bm;   // momentum partials follow the energy partials
+        }
+      }
       __threadfence();
       last = atomicAdd(done, 1u) == gridDim.x - 1;
     }
@@ -153,26 +194,41 @@ __global__ void __launch_bounds__(kIntBlock) k_integrate(void* __restrict__ xv, 
       // (eight loads in flight); then each P_m is summed over the lanes by a
       // fixed tree and the eight results in m order.  The order depends only
       // on the replica's own tile count.
-      const int lane = threadIdx.x & 31;
-      for (int r = threadIdx.x >> 5; r < n_reps; r += kIntBlock / 32) {
-        const RepDev& Q = reps[r];
-        const double* kp = kepart + Q.tile_off;
+      auto replica_sum = [&](const double* base, int stride, int n) {
         double P[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-        for (int k0 = 0; k0 < Q.n_tiles; k0 += 256) {
+        for (int k0 = 0; k0 < n; k0 += 256) {
 #pragma unroll
           for (int m = 0; m < 8; ++m) {
             const int q = k0 + lane + 32 * m;
-            if (q < Q.n_tiles) P[m] += __ldcg(kp + q);
+            if (q < n) P[m] += __ldcg(base + (size_t)q * stride);
           }
         }
         double sum = 0.0;
 #pragma unroll
         for (int m = 0; m < 8; ++m) sum += warp_sum_i(P[m]);
+        return sum;
+      };
+      for (int r = threadIdx.x >> 5; r < n_reps; r += kIntBlock / 32) {
+        const RepDev& Q = reps[r];
+        const double sum = replica_sum(kepart + Q.tile_off, 1, Q.n_tiles);
+        double P[3] = {0.0, 0.0, 0.0};
+        if constexpr (TH == 2)
+          for (int a = 0; a < 3; ++a) P[a] = replica_sum(kepart + gridDim.x + 3 * Q.tile_off + a, 3, Q.n_tiles);
         if (lane == 0) {
           ke_out[r] = sum;
-          if (THERMO) {
+          if (TH == 1) {
             const double T_inst = 2.0 * sum / (Q.dof * 0.0083144626);
             lam[r] = sqrt(1.0 + fp.dt / tau * (Q.T0 / T_inst - 1.0));
+          }
+          if constexpr (TH == 2) {
+            const double T_half = 2.0 * sum / (Q.dof * 0.0083144626);
+            const double Qm = tau * tau * Q.T0 / (4.0 * 3.14159265358979323846 * 3.14159265358979323846);
+            double* nh = lam + 6 * r;
+            const double xi = nh[0] + fp.dt * (T_half - Q.T0) / Qm;
+            const double c = 0.5 * fp.dt * xi;
+            const double M = (double)Q.n_chains * ((double)(fp.sites - 2) * fp.mass[0] + 2.0 * fp.mass[1]);
+            nh[0] = xi; nh[1] = 1.0 - c; nh[2] = 1.0 / (1.0 + c);
+            nh[3] = P[0] / M; nh[4] = P[1] / M; nh[5] = P[2] / M;
           }
         }
       }
@@ -182,7 +238,7 @@ __global__ void __launch_bounds__(kIntBlock) k_integrate(void* __restrict__ xv, 
 }
 
 template <bool MIXED>
-static void launch_int_t(IntegMode mode, bool ke, bool th, void* x, void* v, int* img, const void* F,
+static void launch_int_t(IntegMode mode, bool ke, int th, void* x, void* v, int* img, const void* F,
                          const uint16_t* site, const int* cellc, const int* inv_perm, const float4* ref, float4* pos,
                          int N, const Tile* tiles, int n_tiles, const RepDev* reps, int n_reps,
                          const ForceParams& fp, double* kepart, unsigned* done, double* ke_out, double* lam,
@@ -191,26 +247,33 @@ static void launch_int_t(IntegMode mode, bool ke, bool th, void* x, void* v, int
   k_integrate<MIXED, MODE, KE, TH><<<n_tiles, kIntBlock, 0, st>>>(x, v, img, F, site, cellc, inv_perm, ref,     \
                                                                   pos, N, tiles, reps, n_reps, fp, kepart, done, \
                                                                   ke_out, lam, tau, flags)
-  // With the thermostat on, every step that starts (KD, KKD) takes the
-  // temperature of the unscaled v(t_k), scales v(t_k) by the factor of the
-  // previous step and leaves the factor of step k for the next one.  The
-  // closing kick (K) only completes v; the next call's KD picks up from there.
+  // With the weak-coupling thermostat (th = 1), every step that starts (KD,
+  // KKD) takes the temperature of the unscaled v(t_k), scales v(t_k) by the
+  // factor of the previous step and leaves the factor of step k for the next
+  // one.  With Nose-Hoover (th = 2) every KD and KKD sums the kinetic energy
+  // and momentum of v_{k+1/2} for xi_{k+1} and the centre-of-mass velocity.
+  // The closing kick (K) only completes v; the next call's KD picks up from
+  // there.
   if (mode == kKickDrift) {
-    if (th) MDG_INT(kKickDrift, true, true); else MDG_INT(kKickDrift, false, false);
+    if (th == 2) MDG_INT(kKickDrift, true, 2);
+    else if (th == 1) MDG_INT(kKickDrift, true, 1);
+    else MDG_INT(kKickDrift, false, 0);
   } else if (mode == kKickKickDrift) {
-    if (th) MDG_INT(kKickKickDrift, true, true);
-    else if (ke) MDG_INT(kKickKickDrift, true, false);
-    else MDG_INT(kKickKickDrift, false, false);
+    if (th == 2) MDG_INT(kKickKickDrift, true, 2);
+    else if (th == 1) MDG_INT(kKickKickDrift, true, 1);
+    else if (ke) MDG_INT(kKickKickDrift, true, 0);
+    else MDG_INT(kKickKickDrift, false, 0);
   } else if (mode == kKickOnly) {
-    if (ke) MDG_INT(kKickOnly, true, false);
-    else MDG_INT(kKickOnly, false, false);
+    if (th == 2) MDG_INT(kKickOnly, false, 2);
+    else if (ke) MDG_INT(kKickOnly, true, 0);
+    else MDG_INT(kKickOnly, false, 0);
   } else {
-    MDG_INT(kKineticOnly, true, false);
+    MDG_INT(kKineticOnly, true, 0);
   }
 #undef MDG_INT
 }
 
-void launch_integrate(bool mixed, IntegMode mode, bool ke, bool thermostat, void* x, void* v, int* img,
+void launch_integrate(bool mixed, IntegMode mode, bool ke, int thermostat, void* x, void* v, int* img,
                       const void* F, const uint16_t* site, const int* cellc, const int* inv_perm, const float4* ref,
                       float4* pos, int N, const Tile* tiles, int n_tiles, const RepDev* reps, int n_reps,
                       const ForceParams& fp, double* kepart, unsigned* done, double* ke_out, double* lam,

@@ -32,7 +32,8 @@ struct md_system {
   int n_reps = 0, S = 0, R = 10;
   int64_t N = 0;
   int C = 0, Npad = 0, cap = 0;
-  bool mixed = false, thermo = false;
+  bool mixed = false;
+  int thermo = 0;                 // MD_NVE, MD_VRESCALE or MD_NOSE_HOOVER
   double dt = 0, rc = 0, skin = 0, tau = 0.1;
   md_params params{};
   ForceParams fp{};
@@ -143,8 +144,9 @@ static int configure(md_system* s, const md_desc* d) {
   if (!(d->dt > 0) || !(d->rc > 0) || !(d->skin >= 0) || d->rebin_every < 1)
     return fail(s, MD_EINVAL, "dt, rc must be > 0, skin >= 0, rebin_every >= 1");
   if (d->precision != MD_PLAIN_FP32 && d->precision != MD_MIXED) return fail(s, MD_EINVAL, "unknown precision");
-  if (d->thermostat != MD_NVE && d->thermostat != MD_VRESCALE) return fail(s, MD_EINVAL, "unknown thermostat");
-  if (d->thermostat == MD_VRESCALE && (!d->T_target || !(d->tau_t > 0)))
+  if (d->thermostat != MD_NVE && d->thermostat != MD_VRESCALE && d->thermostat != MD_NOSE_HOOVER)
+    return fail(s, MD_EINVAL, "unknown thermostat");
+  if (d->thermostat != MD_NVE && (!d->T_target || !(d->tau_t > 0)))
     return fail(s, MD_EINVAL, "thermostat needs T_target and tau_t > 0");
   for (int a = 0; a < 2; ++a)
     if (!(d->params.mass[a] > 0) || !(d->params.sigma[a] > 0) || !(d->params.eps[a] >= 0))
@@ -154,7 +156,7 @@ static int configure(md_system* s, const md_desc* d) {
   s->S = d->sites_per_chain;
   s->R = d->rebin_every;
   s->mixed = d->precision == MD_MIXED;
-  s->thermo = d->thermostat == MD_VRESCALE;
+  s->thermo = d->thermostat;
   s->dt = d->dt; s->rc = d->rc; s->skin = d->skin; s->tau = d->thermostat ? d->tau_t : 0.1;
   if (d->lj_block != 0 && d->lj_block != 128 && d->lj_block != 256) return fail(s, MD_EINVAL, "lj_block must be 0, 128 or 256");
   if (d->schedule != MD_SCHED_GRID && d->schedule != MD_SCHED_PERSISTENT) return fail(s, MD_EINVAL, "unknown schedule");
@@ -244,9 +246,9 @@ static size_t plan(md_system* s, char* base) {
   s->tmp = (int*)take(N * sizeof(int));
   s->lj_part = (double*)take(C * 8 * sizeof(double));
   s->b_part = (double*)take(s->t_int.size() * 9 * sizeof(double));
-  s->kepart = (double*)take(s->t_int.size() * sizeof(double));
+  s->kepart = (double*)take(4 * s->t_int.size() * sizeof(double));   // kinetic energy, then momentum (x, y, z) per tile
   s->ke_out = (double*)take(s->n_reps * sizeof(double));
-  s->lam = (double*)take(s->n_reps * sizeof(double));
+  s->lam = (double*)take(6 * s->n_reps * sizeof(double));   // rescale factor, or the Nose-Hoover state (6 per replica)
   s->e_out = (double*)take((size_t)s->n_reps * 16 * sizeof(double));
   s->e_slices = (double*)take((size_t)s->n_reps * s->max_slices * 11 * sizeof(double));
   s->done = (unsigned*)take(sizeof(unsigned));
@@ -465,14 +467,19 @@ int md_create(const md_desc* d, md_system** out) {
     const RepDev& q = s->reps_h[r];
     for (int i = 0; i < q.n_atoms; ++i) site[q.atom_off + i] = (uint16_t)(i % s->S);
   }
-  std::vector<double> ones(s->n_reps, 1.0);
+  // thermostat state: the weak-coupling factor lam[r] = 1, or per replica the
+  // Nose-Hoover (xi, 1 - c, 1/(1 + c), V_com) = (0, 1, 1, 0, 0, 0)
+  std::vector<double> ones(6 * s->n_reps, 1.0);
+  if (s->thermo == MD_NOSE_HOOVER)
+    for (int r = 0; r < s->n_reps; ++r)
+      for (int k = 0; k < 6; ++k) ones[6 * r + k] = (k == 1 || k == 2) ? 1.0 : 0.0;
   auto up = [&](void* dst, const void* src, size_t b) {
     return cudaMemcpyAsync(dst, src, b, cudaMemcpyHostToDevice, s->st) == cudaSuccess;
   };
   bool ok = up(s->reps, s->reps_h.data(), sizeof(RepDev) * s->n_reps) &&
             up(s->tiles_int, s->t_int.data(), sizeof(Tile) * s->t_int.size()) &&
             up(s->site, site.data(), sizeof(uint16_t) * s->N) &&
-            up(s->lam, ones.data(), sizeof(double) * s->n_reps) &&
+            up(s->lam, ones.data(), sizeof(double) * 6 * s->n_reps) &&
             cudaMemsetAsync(s->done, 0, sizeof(unsigned), s->st) == cudaSuccess &&
             cudaMemsetAsync(s->work, 0, 2 * sizeof(int), s->st) == cudaSuccess &&
             cudaMemsetAsync(s->flags, 0, sizeof(unsigned), s->st) == cudaSuccess &&
@@ -622,6 +629,15 @@ int md_set_temperature(md_system* s, const double* T) {
   CU(cudaStreamSynchronize(s->st));
   for (int r = 0; r < s->n_reps; ++r) { s->reps_h[r].T0 = T[r]; s->T0[r] = T[r]; }
   CU(cudaMemcpy(s->reps, s->reps_h.data(), sizeof(RepDev) * s->n_reps, cudaMemcpyHostToDevice));
+  return MD_OK;
+}
+
+int md_get_thermostat(md_system* s, double* xi) {
+  if (!s || !xi) return fail(s, MD_EINVAL, "bad arguments");
+  CU(cudaStreamSynchronize(s->st));
+  std::vector<double> h(6 * (size_t)s->n_reps);
+  CU(cudaMemcpy(h.data(), s->lam, h.size() * sizeof(double), cudaMemcpyDeviceToHost));
+  for (int r = 0; r < s->n_reps; ++r) xi[r] = s->thermo == MD_NOSE_HOOVER ? h[6 * r] : 0.0;
   return MD_OK;
 }
 

@@ -240,7 +240,8 @@ void launch_ingest(bool mixed, const double* stage, int N, const Tile* tiles, in
 void launch_egress_state(bool mixed, const void* x, const void* v, const int* img, int N, double* pos, double* vel,
                          int* im, cudaStream_t st);
 void launch_egress_forces(bool mixed, const void* F, int N, double scale, double* out, cudaStream_t st);
-void launch_integrate(bool mixed, IntegMode mode, bool ke, bool thermostat, void* x, void* v, int* img,
+// thermostat: 0 none, 1 weak coupling, 2 Nose-Hoover
+void launch_integrate(bool mixed, IntegMode mode, bool ke, int thermostat, void* x, void* v, int* img,
                       const void* F, const uint16_t* site, const int* cellc, const int* inv_perm,
                       const float4* ref, float4* pos, int N, const Tile* tiles, int n_tiles,
                       const RepDev* reps, int n_reps, const ForceParams& fp, double* kepart,

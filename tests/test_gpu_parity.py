@@ -281,6 +281,67 @@ def test_energy_call_leaves_forces_and_trajectory_unchanged():
     b.close()
 
 
+@pytest.mark.parametrize("precision,tol_x,tol_t", [(md.MD_MIXED, 1e-5, 2e-5), (md.MD_PLAIN_FP32, 2e-4, 2e-4)])
+def test_nose_hoover_matches_oracle(precision, tol_x, tol_t):
+    """The paper's NVT ensemble (Leap-Frog + Nose-Hoover + centre-of-mass
+    removal), a 450 K melt coupled to 300 K: temperature and xi after every
+    step of 30, and positions after 50 steps, against the oracle's run."""
+    m = chaingen.melt(4, seed=12, L=3.6, T=450.0)
+    s = md.System(m, precision=precision, thermostat=md.MD_NOSE_HOOVER, T_target=300.0, tau_t=0.1,
+                  rebin_every=5)
+    x0, v0 = _uploaded(m, precision)
+    temps, xis = [s.energy()[0]["temperature"]], [s.thermostat_xi()[0]]
+    for _ in range(30):
+        s.step(1)
+        temps.append(s.energy()[0]["temperature"])
+        xis.append(s.thermostat_xi()[0])
+    s.step(20)
+    x, _, img = s.state()
+    ref = _oracle(m)
+    _, _, _, smp, _ = ref.run_nh(x0, v0, 0.001, 30, T0=300.0, tau=0.1)
+    assert np.allclose(temps, smp[:, 7], rtol=tol_t)
+    assert np.allclose(xis, smp[:, 8], rtol=10 * tol_t, atol=10 * tol_t * np.abs(smp[:, 8]).max())
+    assert abs(xis[-1]) > 0.1                       # the coupling has acted
+    xo, _, _, _, _ = ref.run_nh(x0, v0, 0.001, 50, T0=300.0, tau=0.1, sample_every=0)
+    d = x + img * m["L"] - xo
+    d -= m["L"] * np.round(d / m["L"])
+    assert np.abs(d).max() < tol_x, np.abs(d).max()
+    s.close()
+
+
+def test_nose_hoover_replicas_equal_separate_runs():
+    melts = [chaingen.melt(c, seed=80 + c, T=420.0) for c in (10, 15, 12)]
+    T0 = [300.0, 500.0, 380.0]
+    kw = dict(precision=md.MD_MIXED, thermostat=md.MD_NOSE_HOOVER, tau_t=0.1, rebin_every=5)
+    both = md.System(melts, T_target=T0, **kw)
+    both.step(23)
+    xb, vb, _ = both.state()
+    xib = both.thermostat_xi()
+    off = 0
+    for k, (m, T) in enumerate(zip(melts, T0)):
+        alone = md.System(m, T_target=T, **kw)
+        alone.step(23)
+        xa, va, _ = alone.state()
+        n = len(xa)
+        assert np.array_equal(xb[off:off + n], xa) and np.array_equal(vb[off:off + n], va)
+        assert xib[k] == alone.thermostat_xi()[0]
+        off += n
+        alone.close()
+    both.close()
+
+
+def test_nose_hoover_removes_centre_of_mass_drift():
+    m = chaingen.melt(6, seed=13, L=3.6, T=350.0)
+    masses = np.asarray(m["masses"])[:, None]
+    s = md.System(m, precision=md.MD_MIXED, thermostat=md.MD_NOSE_HOOVER, T_target=350.0, tau_t=0.2)
+    s.set_state(m["pos"], m["vel"] + np.array([0.2, -0.1, 0.3]))
+    s.step(2)
+    _, v, _ = s.state()
+    # left: the net force (zero only to FP32 rounding) over the closing half step
+    assert np.abs((masses * v).sum(0)).max() < 1e-7 * np.abs(masses * v).sum()
+    s.close()
+
+
 @pytest.mark.parametrize("sites", [4, 7, 150, 511])
 def test_short_chains_and_rebin_every_step(sites):
     n_chains = max(1, 1500 // sites)
