@@ -187,6 +187,15 @@ int md_set_params(md_system *sys, const md_params *params);
 /* Thermostat targets per replica ([n_replicas] kelvin). */
 int md_set_temperature(md_system *sys, const double *T_target);
 
+/* Structural observables of the current state (the quantities of Sec. 5,
+ * Fig. 8), computed on the GPU with each chain made continuous by
+ * minimum-image bond vectors: r_ee[3c..3c+2] = x_last - x_first of chain c
+ * (nm), rg2[c] = mass-weighted squared radius of gyration (nm^2), and
+ * trans_fraction[r] = fraction of backbone dihedrals of replica r with
+ * |phi| > 120 deg (IUPAC, trans = 180).  Chains are numbered over all
+ * replicas; host or device pointers, any may be NULL.  Synchronous. */
+int md_observables(md_system *sys, double *r_ee, double *rg2, double *trans_fraction);
+
 /* Nose-Hoover friction xi (1/ps) of each replica, [n_replicas]; zeros for
  * the other thermostats.  Synchronous. */
 int md_get_thermostat(md_system *sys, double *xi);

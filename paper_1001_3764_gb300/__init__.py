@@ -77,7 +77,7 @@ class md_energy_t(ctypes.Structure):
 
 
 EXPORTS = ["md_autotune", "md_workspace_size", "md_create", "md_step", "md_step_async", "md_sync", "md_forces", "md_energy",
-           "md_rebin", "md_get_state", "md_set_state", "md_set_params", "md_set_temperature", "md_get_thermostat", "md_stream",
+           "md_rebin", "md_get_state", "md_set_state", "md_set_params", "md_set_temperature", "md_get_thermostat", "md_observables", "md_stream",
            "md_info", "md_get_bins", "md_get_neighbors", "md_get_cell_units", "md_profile_enable", "md_profile_read",
            "md_profile_reset", "md_launches_per_call", "md_bin_static", "md_destroy", "md_last_error",
            "md_adj_create", "md_adj_set_theta", "md_adj_forward", "md_adj_backward", "md_adj_tangent",
@@ -111,6 +111,7 @@ def load(path: str = LIB_PATH):
         "md_set_params": ([P, P], ctypes.c_int),
         "md_set_temperature": ([P, P], ctypes.c_int),
         "md_get_thermostat": ([P, P], ctypes.c_int),
+        "md_observables": ([P, P, P, P], ctypes.c_int),
         "md_stream": ([P], P),
         "md_info": ([P, P, P, P, P], ctypes.c_int),
         "md_get_bins": ([P, P, P, P], ctypes.c_int),
@@ -445,6 +446,17 @@ class System:
 
     def set_temperature(self, T):
         md_set_temperature(self.h, np.broadcast_to(np.asarray(T, np.float64), (self.n_replicas,)))
+
+    def observables(self) -> dict:
+        """Per chain: end-to-end vectors r_ee [n_chains, 3] and squared radii
+        of gyration rg2 [n_chains]; per replica: trans_fraction, computed on
+        the GPU from the current state."""
+        n_ch = int(self._n_chains.sum())
+        ree = np.zeros((n_ch, 3), np.float64)
+        rg2 = np.zeros(n_ch, np.float64)
+        tf = np.zeros(self.n_replicas, np.float64)
+        _check(load().md_observables(self.h, ree.ctypes.data, rg2.ctypes.data, tf.ctypes.data), self.h)
+        return {"r_ee": ree, "rg2": rg2, "trans_fraction": tf}
 
     def thermostat_xi(self) -> np.ndarray:
         """Nose-Hoover friction xi (1/ps) of each replica (zeros for the

@@ -362,6 +362,82 @@ void launch_energy_reduce(const double* lj_part, const double* b_part, const Rep
   k_energy_reduce<<<n_reps, 32, 0, st>>>(slices, reps, max_slices, out);
 }
 
+// ------------------------------------------------------------ chain observables
+// One thread per chain (the structural observables of the paper's Sec. 5):
+// the chain is made continuous by adding minimum-image bond vectors from site
+// 0; R_ee = x_last - x_first (Fig. 8), R_g^2 = sum m |x - x_cm|^2 / sum m
+// (mass-weighted, from sums relative to site 0), and the number of backbone
+// dihedrals in the trans state, |phi| > 120 deg, i.e. cos(phi) =
+// n1.n2 / (|n1||n2|) < -1/2 with n1 = b1 x b2, n2 = b2 x b3 (IUPAC, trans at
+// 180 deg).  The trans counts of a replica are added as integers.
+template <class T>
+__global__ void __launch_bounds__(128) k_chain_observables(const T* __restrict__ x, int N,
+                                                           const RepDev* __restrict__ reps, int n_reps,
+                                                           const ForceParams fp, int n_chains_total,
+                                                           double* __restrict__ ree, double* __restrict__ rg2,
+                                                           unsigned long long* __restrict__ trans) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n_chains_total) return;
+  int r = 0;
+  while (r + 1 < n_reps && reps[r + 1].chain_off <= c) ++r;
+  const RepDev& R = reps[r];
+  const int S = fp.sites;
+  const int o = R.atom_off + (c - R.chain_off) * S;
+  const double L = R.L;
+  double p[3] = {0.0, 0.0, 0.0};                       // site position relative to site 0
+  double m_sum = 0.0, s1[3] = {0.0, 0.0, 0.0}, s2 = 0.0;
+  double b[3][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};   // the last three bond vectors
+  unsigned long long nt = 0;
+  for (int k = 0; k < S; ++k) {
+    if (k > 0) {
+      double d[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        double e = (double)x[a * N + o + k] - (double)x[a * N + o + k - 1];
+        e -= L * rint(e / L);
+        d[a] = e;
+        p[a] += e;
+      }
+#pragma unroll
+      for (int a = 0; a < 3; ++a) { b[0][a] = b[1][a]; b[1][a] = b[2][a]; b[2][a] = d[a]; }
+      if (k >= 3) {
+        const double n1[3] = {b[0][1] * b[1][2] - b[0][2] * b[1][1], b[0][2] * b[1][0] - b[0][0] * b[1][2],
+                              b[0][0] * b[1][1] - b[0][1] * b[1][0]};
+        const double n2[3] = {b[1][1] * b[2][2] - b[1][2] * b[2][1], b[1][2] * b[2][0] - b[1][0] * b[2][2],
+                              b[1][0] * b[2][1] - b[1][1] * b[2][0]};
+        const double dn = n1[0] * n2[0] + n1[1] * n2[1] + n1[2] * n2[2];
+        const double l1 = n1[0] * n1[0] + n1[1] * n1[1] + n1[2] * n1[2];
+        const double l2 = n2[0] * n2[0] + n2[1] * n2[1] + n2[2] * n2[2];
+        // cos(phi) < -1/2  <=>  n1.n2 < 0 and (n1.n2)^2 > |n1|^2 |n2|^2 / 4
+        nt += (dn < 0.0 && 4.0 * dn * dn > l1 * l2) ? 1ull : 0ull;
+      }
+    }
+    const double m = fp.mass[(k == 0 || k == S - 1) ? 1 : 0];
+    m_sum += m;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) s1[a] += m * p[a];
+    s2 += m * (p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) ree[3 * c + a] = p[a];
+  const double cx = s1[0] / m_sum, cy = s1[1] / m_sum, cz = s1[2] / m_sum;
+  rg2[c] = s2 / m_sum - (cx * cx + cy * cy + cz * cz);
+  atomicAdd(trans + r, nt);
+}
+
+void launch_chain_observables(bool mixed, const void* x, int N, const RepDev* reps, int n_reps,
+                              const ForceParams& fp, int n_chains_total, double* ree, double* rg2,
+                              unsigned long long* trans, cudaStream_t st) {
+  const int blocks = (n_chains_total + 127) / 128;
+  if (blocks == 0) return;
+  if (mixed)
+    k_chain_observables<double><<<blocks, 128, 0, st>>>((const double*)x, N, reps, n_reps, fp, n_chains_total,
+                                                        ree, rg2, trans);
+  else
+    k_chain_observables<float><<<blocks, 128, 0, st>>>((const float*)x, N, reps, n_reps, fp, n_chains_total,
+                                                       ree, rg2, trans);
+}
+
 // ------------------------------------------------------------------ output state
 // SoA state -> AoS FP64 positions, velocities and image counters in the
 // staging buffer (one DMA each to the caller afterwards).

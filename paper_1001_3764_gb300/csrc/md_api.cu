@@ -632,6 +632,30 @@ int md_set_temperature(md_system* s, const double* T) {
   return MD_OK;
 }
 
+int md_observables(md_system* s, double* r_ee, double* rg2, double* trans_fraction) {
+  if (!s) return fail(s, MD_EINVAL, "null system");
+  int chains = 0;
+  for (int r = 0; r < s->n_reps; ++r) chains += s->reps_h[r].n_chains;
+  // scratch in the staging buffer (6N doubles + 3N ints >= 4 doubles per chain + counts)
+  double* ree_d = s->stage;
+  double* rg_d = s->stage + 3 * (size_t)chains;
+  unsigned long long* tr_d = reinterpret_cast<unsigned long long*>(s->stage + 4 * (size_t)chains);
+  CU(cudaMemsetAsync(tr_d, 0, sizeof(unsigned long long) * s->n_reps, s->st));
+  launch_chain_observables(s->mixed, s->x, (int)s->N, s->reps, s->n_reps, s->fp, chains, ree_d, rg_d, tr_d, s->st);
+  CU(cudaGetLastError());
+  std::vector<unsigned long long> tr(s->n_reps);
+  if (r_ee) CU(cudaMemcpyAsync(r_ee, ree_d, 3 * (size_t)chains * sizeof(double), cudaMemcpyDefault, s->st));
+  if (rg2) CU(cudaMemcpyAsync(rg2, rg_d, (size_t)chains * sizeof(double), cudaMemcpyDefault, s->st));
+  CU(cudaMemcpyAsync(tr.data(), tr_d, sizeof(unsigned long long) * s->n_reps, cudaMemcpyDeviceToHost, s->st));
+  CU(cudaStreamSynchronize(s->st));
+  if (trans_fraction)
+    for (int r = 0; r < s->n_reps; ++r) {
+      const double nd = (double)s->reps_h[r].n_chains * (double)(s->S > 3 ? s->S - 3 : 0);
+      trans_fraction[r] = nd > 0 ? (double)tr[r] / nd : 0.0;
+    }
+  return MD_OK;
+}
+
 int md_get_thermostat(md_system* s, double* xi) {
   if (!s || !xi) return fail(s, MD_EINVAL, "bad arguments");
   CU(cudaStreamSynchronize(s->st));

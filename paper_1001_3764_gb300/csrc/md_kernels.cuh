@@ -240,6 +240,11 @@ void launch_ingest(bool mixed, const double* stage, int N, const Tile* tiles, in
 void launch_egress_state(bool mixed, const void* x, const void* v, const int* img, int N, double* pos, double* vel,
                          int* im, cudaStream_t st);
 void launch_egress_forces(bool mixed, const void* F, int N, double scale, double* out, cudaStream_t st);
+// per chain: end-to-end vector ree[3c..3c+2], R_g^2 rg2[c]; per replica the
+// number of trans dihedrals added into trans[r] (zeroed by the caller)
+void launch_chain_observables(bool mixed, const void* x, int N, const RepDev* reps, int n_reps,
+                              const ForceParams& fp, int n_chains_total, double* ree, double* rg2,
+                              unsigned long long* trans, cudaStream_t st);
 // thermostat: 0 none, 1 weak coupling, 2 Nose-Hoover
 void launch_integrate(bool mixed, IntegMode mode, bool ke, int thermostat, void* x, void* v, int* img,
                       const void* F, const uint16_t* site, const int* cellc, const int* inv_perm,

@@ -662,3 +662,29 @@ def test_non_finite_state_is_reported():
         s.step(10)
     assert e.value.code == md.MD_EUNSTABLE
     s.close()
+
+
+@pytest.mark.parametrize("precision", [md.MD_MIXED, md.MD_PLAIN_FP32])
+def test_chain_observables_match_oracle(precision):
+    """End-to-end vectors, radii of gyration and the trans fraction computed
+    on the GPU against oracle/observables.py on the same (uploaded) state,
+    two replicas; the generator's chains cross the box walls."""
+    from oracle import observables as ob
+    melts = [chaingen.melt(12, seed=41), chaingen.melt(20, seed=42)]
+    s = md.System(melts, precision=precision)
+    got = s.observables()
+    off = 0
+    for r, m in enumerate(melts):
+        x, _ = _uploaded(m, precision)
+        xu = chaingen.unwrapped(dict(m, pos=x))
+        n = m["n_chains"]
+        ree, rg2 = ob.end_to_end(xu, m["sites"]), ob.radius_of_gyration_sq(xu, m["sites"], m["masses"])
+        tol = 1e-12 if precision == md.MD_MIXED else 1e-9
+        assert np.allclose(got["r_ee"][off:off + n], ree, rtol=tol, atol=tol)
+        assert np.allclose(got["rg2"][off:off + n], rg2, rtol=tol * 100)
+        phi = ob.dihedral_angles(xu, m["sites"])
+        want = np.mean(np.abs(phi) > 120.0)
+        near = np.sum(np.abs(np.abs(phi) - 120.0) < 1e-6)      # classification ties the precisions may split
+        assert abs(got["trans_fraction"][r] - want) <= near / phi.size + 1e-15
+        off += n
+    s.close()
