@@ -554,7 +554,7 @@ def main():
                         "then exit")
     args = p.parse_args()
     if args.warmup < 3:
-        args.warmup = 3
+        p.error("--warmup must be at least 3 (untimed warm-up steps before the timed region)")
     if args.impl == "reference":
         run_reference(args)
     else:

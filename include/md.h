@@ -72,7 +72,7 @@ typedef struct {
 
 typedef struct {
   int32_t n_replicas;          /* independent systems stepped together (>= 1) */
-  int32_t sites_per_chain;     /* NAOM (Table II), 4 .. 511 */
+  int32_t sites_per_chain;     /* NAOM (Table II), 4 .. 511; at most 2^20 - 1 chains in all */
   const int32_t *n_chains;     /* [n_replicas] */
   const double *box;           /* [n_replicas] cube side L, nm; L >= 3 (rc + skin) */
   const double *pos;           /* [3 * N] x,y,z per atom, original order (any image) */
@@ -142,7 +142,11 @@ int md_autotune(md_desc *desc, int32_t trial_cycles, const char *cache_path, md_
 int md_workspace_size(const md_desc *desc, size_t *bytes);
 
 /* Validate, copy the initial state to the GPU, bin, build the neighbour list,
- * evaluate F(t0) and capture the per-cycle CUDA graph.  Sets *out. */
+ * evaluate F(t0) and capture the per-cycle CUDA graph.  Sets *out.  This is
+ * the "input initial conditions" step of the paper's MD procedure (Sec. 3,
+ * Fig. 1): the topology and parameters go to the GPU once (Sec. 3.3, last
+ * paragraph), after which the step loop needs no host copy; the first
+ * binning and list build follow Sec. 3.1. */
 int md_create(const md_desc *desc, md_system **out);
 
 /* Advance n_steps time steps (velocity Verlet; Leap-Frog positions, Sec. 3.4).
@@ -156,9 +160,11 @@ int md_step_async(md_system *sys, int64_t n_steps);
 /* Wait for queued work and report device flags (then clear them). */
 int md_sync(md_system *sys);
 
-/* Total force on every atom at the current positions, [3 * N] doubles (host
- * or device pointer), original order, kJ/mol/nm.  Converted on the GPU and
- * copied in one DMA.  Synchronous. */
+/* Total force on every atom at the current positions, F = -grad E with E of
+ * Eq. 1 (LJ of Eq. 2 over the Sec. 3.1 pair set, bonded terms of Eqs. 4-6,
+ * Sec. 3.2-3.3): the force the integrator of Sec. 3.4 uses.  [3 * N] doubles
+ * (host or device pointer), original order, kJ/mol/nm.  Converted on the GPU
+ * and copied in one DMA.  Synchronous. */
 int md_forces(md_system *sys, double *f_out);
 
 /* Energies of every replica at the current state, out[n_replicas]. */
@@ -167,18 +173,21 @@ int md_energy(md_system *sys, md_energy_t *out);
 /* Re-bin the current positions and rebuild the neighbour list (Sec. 3.1). */
 int md_rebin(md_system *sys);
 
-/* Current state: positions wrapped into [0, L) ([3 * N]), velocities
- * ([3 * N]) and periodic image counters ([3 * N], may be NULL); any output
- * may be NULL; host or device pointers (one DMA each, after an in-GPU
- * transpose).  Unwrapped position = pos + images * L.  Synchronous. */
+/* Current state: the positions and velocities that the update of Sec. 3.4
+ * advances, with positions wrapped into the periodic cube [0, L) that the
+ * cells of Sec. 3.1 tile ([3 * N]), velocities ([3 * N]) and periodic image
+ * counters ([3 * N], may be NULL); any output may be NULL; host or device
+ * pointers (one DMA each, after an in-GPU transpose).  Unwrapped position =
+ * pos + images * L.  Synchronous. */
 int md_get_state(md_system *sys, double *pos, double *vel, int32_t *images);
 
 /* Replace positions and velocities ([3 * N] each, original order, host or
  * device pointers, read before the call returns), reset the image counters,
  * re-bin and recompute the forces.  The arrays are copied to the GPU as they
- * are (one DMA each) and checked, wrapped and transposed there.  A non-finite
- * value gives MD_EINVAL; the system's state is then undefined until the next
- * successful md_set_state. */
+ * are (one DMA each) and checked, wrapped and transposed there: a position
+ * x is stored as x - L floor(x / L), and a result that rounds to L (a tiny
+ * negative x) is stored as 0.  A non-finite value gives MD_EINVAL; the
+ * system's state is then undefined until the next successful md_set_state. */
 int md_set_state(md_system *sys, const double *pos, const double *vel);
 
 /* Replace the force-field parameters and recompute the forces. */
@@ -250,13 +259,18 @@ int64_t md_launches_per_call(md_system *sys, int64_t n_steps);
  *   cuda_stream the stream to run on (NULL = legacy default stream)
  * The same formulas as md_rebin, so the outputs equal md_get_bins for the
  * same positions and M.  Limits: n_atoms <= 1,048,576 and M^3 <= 131,072;
- * larger sizes return MD_EINVAL and run nothing.  Scratch memory is one
- * fixed array of 8.9 MB per device inside this library, present on every
- * device that loads it until the process exits; every call shares it and it
- * keeps the last call's contents (the counters are cleared by each call), so
- * calls whose work overlaps on the GPU (other streams, other host threads)
- * race.  The first call on a device looks up the array's device address;
- * make that first call before any stream capture.  Asynchronous: results are
+ * larger sizes return MD_EINVAL and run nothing.  Cost: the order inside a
+ * cell of m atoms takes O(m log m) work (runs of 256 ordered in shared
+ * memory, then merge passes), whatever the positions; the worst legal call
+ * (all 2^20 atoms in one cell) runs 4,096 runs on one block and 12 merge
+ * passes over the atoms, a few milliseconds.  Scratch memory is one fixed
+ * array of 13.1 MB per device inside this library, present on every device
+ * that loads it until the process exits; every call shares it and it keeps
+ * the last call's contents (the counters are cleared by each call), so calls
+ * whose work overlaps on the GPU (other streams, other host threads) race.
+ * Every call looks up the array's device address on the current device (so
+ * a reset context is followed); the first call on a device also loads it,
+ * so make that first call before any stream capture.  Asynchronous: results are
  * ready when the stream reaches them; errors are returned as MD_E* codes
  * with md_last_error(NULL). */
 int md_bin_static(const double *pos, int32_t n_atoms, double box, int32_t cells_per_side, int32_t *cell_of,
@@ -321,9 +335,12 @@ int md_adj_create(const md_adj_desc *desc, md_adj **out);
 /* Replace theta (eps and sigma positive); invalidates the last forward run. */
 int md_adj_set_theta(md_adj *adj, const double theta[5]);
 
-/* Forward run from pos, vel ([3N] x,y,z per atom, unwrapped positions, host
- * or device pointers, copied): stores the checkpoints and writes
- * obs = (J_U, J_R).  Synchronous. */
+/* Forward run from pos, vel ([3N] x,y,z per atom, host or device pointers,
+ * copied): stores the checkpoints and writes obs = (J_U, J_R).  Positions may
+ * be wrapped into the box or already continuous: the library first makes
+ * every chain continuous on the GPU (site k moved by whole box lengths so
+ * that each bond is its minimum image; a site that needs no move keeps its
+ * bits), since J_R needs unwrapped chains.  Synchronous. */
 int md_adj_forward(md_adj *adj, const double *pos, const double *vel, double obs[2]);
 
 /* d(w0 J_U + w1 J_R)/dtheta of the last forward run at the current theta.

@@ -491,8 +491,9 @@ class Adjoint:
     means (<U>, <R_ee^2>) with respect to theta = (eps_C32, eps_C33,
     sigma_C32, sigma_C33, k_phi) by the library's adjoint kernels.
 
-    `melt` is a chaingen-format dict; its positions are unwrapped chain by
-    chain (the end-to-end distance needs continuous chains)."""
+    `melt` is a chaingen-format dict; its positions may be wrapped into the
+    box: md_adj_forward makes each chain continuous on the GPU (the
+    end-to-end distance needs continuous chains)."""
 
     def __init__(self, melt: dict, n_steps: int = 500, checkpoint_every: int = 50, dt: float = 0.001,
                  rc: float = 1.0, params: dict | None = None, device: int | None = None, lj_form: int = 0,
@@ -502,14 +503,7 @@ class Adjoint:
             torch.cuda.set_device(device)
         self.params = dict(default_params() if params is None else params)
         n_chains, sites, L = int(melt["n_chains"]), int(melt["sites"]), float(melt["L"])
-        p = np.asarray(melt["pos"], np.float64).reshape(n_chains, sites, 3)
-        d = np.diff(p, axis=1)
-        if np.abs(d).max(initial=0.0) < 0.5 * L:      # chains already continuous: keep the bits
-            self.x0 = np.ascontiguousarray(p.reshape(-1, 3))
-        else:
-            d -= L * np.round(d / L)
-            self.x0 = np.ascontiguousarray(np.concatenate([p[:, :1], p[:, :1] + np.cumsum(d, axis=1)], axis=1)
-                                           .reshape(-1, 3))
+        self.x0 = np.ascontiguousarray(melt["pos"], np.float64).reshape(-1, 3)
         self.v0 = np.ascontiguousarray(melt["vel"], np.float64).reshape(-1, 3)
         self.n_atoms = n_chains * sites
         desc = md_adj_desc()

@@ -112,23 +112,27 @@ __global__ void __launch_bounds__(128) k_cell_sort(const T* __restrict__ x, int 
                                                    const uint16_t* __restrict__ site, const RepDev* __restrict__ reps,
                                                    int n_reps, int sites, int* __restrict__ perm,
                                                    int* __restrict__ inv_perm, float4* __restrict__ pos,
-                                                   int* __restrict__ tag, float4* __restrict__ ref) {
+                                                   int* __restrict__ tag, float4* __restrict__ ref,
+                                                   unsigned* __restrict__ flags) {
   __shared__ int ids[kSortCap];
   const int c = blockIdx.x;
   const int b = cell_start[c], n = cell_start[c + 1] - b;
   if (n == 0) return;
   const RepDev& R = reps[find_rep_by_cell(reps, n_reps, c)];
+  // A cell of more than kSortCap atoms (over 40 times a melt's ~46) cannot
+  // be staged by the force kernels either: it is reported as a capacity
+  // overflow, and its atoms keep their bucket order (bounded work).
   const bool in_smem = n <= kSortCap;
+  if (!in_smem && threadIdx.x == 0) atomicOr(flags, kFlagNbrOverflow);
   if (in_smem)
     for (int k = threadIdx.x; k < n; k += blockDim.x) ids[k] = tmp[b + k];
   __syncthreads();
   for (int k = threadIdx.x; k < n; k += blockDim.x) {
     const int id = in_smem ? ids[k] : tmp[b + k];
-    int rank = 0;
+    int rank = k;
     if (in_smem) {
+      rank = 0;
       for (int q = 0; q < n; ++q) rank += ids[q] < id;
-    } else {
-      for (int q = 0; q < n; ++q) rank += tmp[b + q] < id;
     }
     const int s = b + rank;
     perm[s] = id;
@@ -150,19 +154,19 @@ __global__ void __launch_bounds__(128) k_cell_sort(const T* __restrict__ x, int 
     p.w = (float)type;   // LJ type: the pipelined force kernel copies positions as they are
     pos[s] = p;
     ref[id] = p;
-    tag[s] = (chain << 9) | st | (type << kTagTypeBit);
+    tag[s] = (chain << kTagSiteBits) | st | (type << kTagTypeBit);
   }
 }
 
 void launch_cell_sort(bool mixed, const void* x, int N, const int* cell_start, const int* tmp, const int* cellc,
                       const uint16_t* site, const RepDev* reps, int n_reps, int C, int sites, int* perm,
-                      int* inv_perm, float4* pos, int* tag, float4* ref, cudaStream_t st) {
+                      int* inv_perm, float4* pos, int* tag, float4* ref, unsigned* flags, cudaStream_t st) {
   if (mixed)
     k_cell_sort<double><<<C, 128, 0, st>>>((const double*)x, N, cell_start, tmp, cellc, site, reps, n_reps, sites,
-                                           perm, inv_perm, pos, tag, ref);
+                                           perm, inv_perm, pos, tag, ref, flags);
   else
     k_cell_sort<float><<<C, 128, 0, st>>>((const float*)x, N, cell_start, tmp, cellc, site, reps, n_reps, sites,
-                                          perm, inv_perm, pos, tag, ref);
+                                          perm, inv_perm, pos, tag, ref, flags);
 }
 
 }  // namespace mdg

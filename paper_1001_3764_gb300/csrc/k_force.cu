@@ -1,26 +1,17 @@
-// k_force.cu -- Lennard-Jones (Eq. 2) and Dreiding II bonded forces
-// (Eqs. 4-6) on sm_103a.
+// k_force.cu -- Dreiding II bonded forces (Eqs. 4-6, Sec. 3.3) on sm_103a.
+// The Lennard-Jones force (Eq. 2) is in k_lj.cu.
 //
-// LJ: one thread per home atom in cell-sorted order walks its neighbour list
-// (Sec. 3.2).  Positions are FP32 coordinates in units of the cell side,
-// relative to each atom's cell centre; a pair's separation is
-// (u_i - u_j) - o_k, where o_k is the integer neighbour-cell offset stored in
-// the list entry, so there is no minimum-image arithmetic and no
-// large-magnitude FP32 subtraction in the pair loop.  The LJ constants are
-// pre-scaled to cell units per replica and the sum is scaled back by 1/h.  Truncation follows the Sec. 3.2
-// listing: r2inv = 0 when r^2 >= r_c^2.  The per-atom sum is formed in FP32
-// in list order and stored once (FP32, or int64 fixed point 2^-32 kJ/mol/nm
-// in the mixed form).  Energy and virial are reduced with warp shuffles in FP64.
-//
-// Bonded: each thread block owns a contiguous range of atoms (whole or partial
+// Each thread block owns a contiguous range of atoms (whole or partial
 // chains) plus a 3-atom halo.  Bond vectors are formed once per bond (FP64
 // differences of the master positions in the mixed form, exact FP32
 // differences in the plain form), every bond/angle/dihedral term is evaluated
 // once by the thread of its first atom, and each home atom then sums the
 // contributions of the (at most 2+3+4) terms that contain it in a fixed
 // order.  This removes the paper's 2x/3x/4x redundant per-home-atom flops
-// (Sec. 3.3) without atomics.  The kernel also adds the LJ force (gathered
-// from sorted order) so the integrator reads one force per atom.
+// (Sec. 3.3) without atomics.  The kernel also adds the LJ force of the atom
+// (read from cell-sorted order through inv_perm) so the integrator reads one
+// force per atom.  Energies and the virial are block sums: FP32 warp trees,
+// then FP64 across warps, in a fixed order.
 #include <type_traits>
 
 #include "md_kernels.cuh"

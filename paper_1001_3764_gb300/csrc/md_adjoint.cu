@@ -524,6 +524,27 @@ __global__ void __launch_bounds__(32) k_adj_reduce2(const double* __restrict__ p
 }
 
 // ------------------------------------------------------------------ integrator and adjoint updates
+// Make every chain continuous (one thread per chain, x,y,z per atom): site k
+// is moved by whole box lengths, L s_k, where s_k accumulates -rint(d / L)
+// over the bonds d = x_k - x_{k-1} of the positions as given, so each bond
+// becomes its minimum image.  A site with s_k = 0 keeps its bits.
+__global__ void __launch_bounds__(128) k_adj_unwrap(double* __restrict__ x, AdjDev P) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= P.n_chains) return;
+  double* xc = x + 3 * (size_t)c * P.sites;
+  double prev[3] = {xc[0], xc[1], xc[2]};
+  double s[3] = {0.0, 0.0, 0.0};
+  for (int k = 1; k < P.sites; ++k) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const double cur = xc[3 * k + a];
+      s[a] -= rint((cur - prev[a]) * P.inv_L);
+      prev[a] = cur;
+      if (s[a] != 0.0) xc[3 * k + a] = cur + P.L * s[a];
+    }
+  }
+}
+
 __global__ void __launch_bounds__(256) k_adj_kick_drift(double* __restrict__ x, double* __restrict__ v,
                                                         const double* __restrict__ gv, AdjDev P, double dt,
                                                         double* __restrict__ x_store) {
@@ -586,7 +607,7 @@ struct md_adj {
   void* mem;
   double *x, *v, *gv, *gt, *alpha, *beta, *rec, *part, *acc, *totals, *ckx, *ckv, *seg, *xk;
   float4* x32;
-  int *count, *cell_start, *cell_of, *slot, *tmp, *perm;
+  int *count, *cell_start, *cell_of, *slot, *tmp, *perm, *rbuf, *maxm;
   bool have_forward;
   double obs[2];
 };
@@ -620,7 +641,8 @@ int evaluate(md_adj* a, const double* xp, const double* beta, double cu, int mod
   k_adj_count<<<(N + 255) / 256, 256, 0, st>>>(xp, P, a->cell_of, a->count, a->slot, a->x32);
   launch_scan(a->count, a->cell_start, a->C_cells, st);
   launch_bin_scatter(a->cell_of, a->slot, a->cell_start, a->tmp, N, st);
-  launch_cell_rank(a->cell_start, a->tmp, a->perm, a->C_cells, st);
+  if (cudaMemsetAsync(a->maxm, 0, sizeof(int), st) != cudaSuccess) return MD_ECUDA;
+  launch_static_order(a->cell_start, a->C_cells, N, a->tmp, a->rbuf, a->slot, a->perm, a->maxm, st);
   const int lj_blocks = (N + kLjWarps - 1) / kLjWarps;
   if (beta && a->hvp32) {
     k_adj_lj<DualF><<<lj_blocks, 32 * kLjWarps, 0, st>>>(xp, beta, cu, a->cell_start, a->perm, P, a->x32, a->gv,
@@ -761,7 +783,8 @@ extern "C" int md_adj_create(const md_adj_desc* d, md_adj** out) {
                           sizeof(double) * kRec * kRedBlocks, sizeof(double) * kAccN, sizeof(double) * kRec,
                           n3 * a->S, n3 * a->S, n3 * (size_t)(a->C + 1), sizeof(int) * a->C_cells,
                           sizeof(int) * (a->C_cells + 1), sizeof(int) * (size_t)N, sizeof(int) * (size_t)N,
-                          sizeof(int) * (size_t)N, sizeof(int) * (size_t)N, n3, sizeof(float4) * (size_t)N};
+                          sizeof(int) * (size_t)N, sizeof(int) * (size_t)N, n3, sizeof(float4) * (size_t)N,
+                          sizeof(int) * (size_t)N, sizeof(int)};
   const int nbuf = sizeof(sizes) / sizeof(sizes[0]);
   size_t total = 0;
   for (int k = 0; k < nbuf; ++k) total += align256(sizes[k]);
@@ -781,6 +804,7 @@ extern "C" int md_adj_create(const md_adj_desc* d, md_adj** out) {
   a->cell_of = (int*)ptrs[15]; a->slot = (int*)ptrs[16]; a->tmp = (int*)ptrs[17]; a->perm = (int*)ptrs[18];
   a->xk = (double*)ptrs[19];
   a->x32 = (float4*)ptrs[20];
+  a->rbuf = (int*)ptrs[21]; a->maxm = (int*)ptrs[22];
   a->have_forward = false;
   *out = a;
   return MD_OK;
@@ -804,6 +828,7 @@ extern "C" int md_adj_forward(md_adj* a, const double* pos, const double* vel, d
       cudaMemcpyAsync(a->v, vel, n3, cudaMemcpyDefault, st) != cudaSuccess ||
       cudaMemsetAsync(a->acc, 0, sizeof(double) * kAccN, st) != cudaSuccess)
     return adj_fail(MD_ECUDA, "upload of the initial state failed");
+  k_adj_unwrap<<<(a->P.n_chains + 127) / 128, 128, 0, st>>>(a->x, a->P);
   const int nb = (a->P.N + 255) / 256;
   if (evaluate(a, a->x, nullptr, 0.0, 0, 0.0) != MD_OK) return adj_fail(MD_ECUDA, "force evaluation failed");
   // one velocity-Verlet step (kick-drift, forces and sums, kick) as a graph

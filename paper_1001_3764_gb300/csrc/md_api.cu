@@ -3,7 +3,10 @@
 // One md_system owns: a replica table, tile tables, every device buffer (one
 // allocation, or a caller workspace), a stream, and a CUDA graph holding one
 // rebin cycle (rebin + neighbour list + rebin_every steps).  Kernels are in
-// k_bin.cu, k_force.cu and k_integrate.cu.
+// k_bin.cu (binning), k_lj.cu (neighbour list and Lennard-Jones), k_force.cu
+// (bonded terms), k_integrate.cu (integration, kinetic energy, thermostats,
+// energy reductions, observables, state transfer) and md_adjoint.cu (the
+// adjoint); md_static.cu holds the allocation-free binning entry point.
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -199,7 +202,7 @@ static int configure(md_system* s, const md_desc* d) {
     atoms += q.n_atoms; cells += (int64_t)M * M * M; chains += nc;
     s->max_slices = std::max(s->max_slices, energy_slice_count(M * M * M));
     if (atoms >= (int64_t)kNbrIndexMask) return fail(s, MD_EINVAL, "too many atoms (limit 2^26)");
-    if (chains >= (1 << 21)) return fail(s, MD_EINVAL, "too many chains (limit 2^21)");
+    if (chains >= (1 << 20)) return fail(s, MD_EINVAL, "too many chains (limit 2^20)");
     if (cells >= (1 << 26)) return fail(s, MD_EINVAL, "too many cells");
   }
   s->N = atoms; s->C = (int)cells;
@@ -278,7 +281,7 @@ static void enqueue_rebin(md_system* s) {
   launch_scan(s->count, s->cell_start, s->C, s->st);
   launch_bin_scatter(s->cell_of, s->slot, s->cell_start, s->tmp, (int)s->N, s->st);
   launch_cell_sort(s->mixed, s->x, (int)s->N, s->cell_start, s->tmp, s->cellc, s->site, s->reps, s->n_reps, s->C,
-                   s->S, s->perm, s->inv_perm, s->pos, s->tag, s->ref, s->st);
+                   s->S, s->perm, s->inv_perm, s->pos, s->tag, s->ref, s->flags, s->st);
   prof_mark(s);
   launch_nbr_tile(s->pos, s->tag, s->cell_start, s->reps, s->n_reps, s->C, s->nbr, s->ncount, s->cap, s->Npad,
                   s->tile_cap, s->flags, s->st);

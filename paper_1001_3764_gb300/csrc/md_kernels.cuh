@@ -13,7 +13,8 @@
 //   sorted (cell-major) order, index s:
 //     pos        float4 [N] position in cell units relative to the centre of the
 //                atom's cell at the last rebin, u = (x - (c + 1/2) h) / h; w unused
-//     tag        int32 [N]  chain*512 + site | type << 30
+//     tag        int32 [N]  chain*1024 + site | type << 30 (sites < 1024, so the
+//                site fields of two chains never come within 2 of each other)
 //     perm       int32 [N]  original index of slot s
 //     Flj        AoS 32 B   LJ force on slot s
 //     nbr        uint16 entries in blocks of 8 ([cap/8][Npad] of 16 B):
@@ -28,6 +29,7 @@ namespace mdg {
 
 constexpr int kMaxReplicas = 4096;
 constexpr int kTagTypeBit = 30;
+constexpr int kTagSiteBits = 10;                      // site in bits 0..9, chain in bits 10..29
 constexpr uint32_t kTagMask = (1u << 30) - 1;
 constexpr int kNbrIndexBits = 26;                     // j in entry bits 0..25
 constexpr uint32_t kNbrIndexMask = (1u << kNbrIndexBits) - 1;
@@ -199,13 +201,17 @@ void launch_bin_count(bool mixed, const void* x, int N, const Tile* tiles, int n
                       const RepDev* reps, int* cell_of, int* cellc, int* count, int* slot,
                       cudaStream_t st);
 void launch_scan(const int* count, int* cell_start, int C, cudaStream_t st);
-// stable order by atom index inside each of C cells: perm[cell_start[c] + rank] = atom
-void launch_cell_rank(const int* cell_start, const int* tmp, int* perm, int C, cudaStream_t st);
+// stable order by atom index inside each of C cells (n atoms in all):
+// perm[cell_start[c] + rank] = atom, from the unsorted bucket contents in
+// `runs` (overwritten), in O(m log m) work for a cell of m atoms.  Scratch:
+// buf[n], pcell[n] and one int *maxm that the caller clears before the call.
+void launch_static_order(const int* cell_start, int C, int n, int* runs, int* buf, int* pcell, int* perm, int* maxm,
+                         cudaStream_t st);
 void launch_bin_scatter(const int* cell_of, const int* slot, const int* cell_start, int* tmp, int N,
                         cudaStream_t st);
 void launch_cell_sort(bool mixed, const void* x, int N, const int* cell_start, const int* tmp,
                       const int* cellc, const uint16_t* site, const RepDev* reps, int n_reps, int C,
-                      int sites, int* perm, int* inv_perm, float4* pos, int* tag, float4* ref,
+                      int sites, int* perm, int* inv_perm, float4* pos, int* tag, float4* ref, unsigned* flags,
                       cudaStream_t st);
 // ---------------------------------------------------------------- forces
 // neighbour list and LJ over 27-cell shared-memory tiles (k_lj.cu).  The list

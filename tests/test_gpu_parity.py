@@ -102,6 +102,52 @@ def test_binning_is_bit_exact(precision, n_chains, L):
     s.close()
 
 
+def _ingested(x, L, precision):
+    """What md_set_state / md_create store for caller positions x (the rule
+    stated in md.h): x - L floor(x / L), with a result that is not below L
+    (a tiny negative x) stored as 0; in the plain form then rounded to FP32,
+    with a value that rounds to L stored as 0."""
+    y = np.array(x, np.float64)
+    y = y - L * np.floor(y / L)
+    y[~((y < L) & (y >= 0.0))] = 0.0
+    if precision == md.MD_PLAIN_FP32:
+        y = y.astype(np.float32).astype(np.float64)
+        y[y >= np.float32(L)] = 0.0
+    return y
+
+
+@pytest.mark.parametrize("precision", [md.MD_MIXED, md.MD_PLAIN_FP32])
+def test_binning_at_cell_faces_is_bit_exact(precision):
+    """Coordinates placed exactly on cell faces, on the box faces, at -0.0,
+    at a tiny negative value and one ulp beyond L (the cases the oracle's
+    binning pins fix), uploaded through md_set_state.  r_c + skin = 1 nm and
+    L = 4 nm make M / L = 1 exact, so both sides decide every face alike."""
+    m = chaingen.melt(14, seed=23, L=4.0)
+    L = m["L"]
+    x = np.array(m["pos"], np.float64)
+    faces = [1.0, 2.0, 3.0, 0.0, -0.0, 4.0, np.nextafter(4.0, 5.0), -1e-300, np.nextafter(1.0, 0.0),
+             np.nextafter(4.0, 0.0), np.nextafter(2.0, 3.0)]
+    used = set()
+    for axis in range(3):
+        for v in faces:
+            d = np.abs(((x[:, axis] - v + 0.5 * L) % L) - 0.5 * L)
+            d[list(used)] = np.inf
+            i = int(np.argmin(d))
+            assert d[i] < 0.01
+            used.add(i)
+            x[i, axis] = v
+    s = md.System(m, precision=precision, rc=0.9, skin=0.1)
+    s.set_state(x, m["vel"])
+    M = s.info["cells_per_side"]
+    assert M == 4
+    co, cs, pm = s.bins()
+    oc, ocs, opm = oracle.bin_atoms(_ingested(x, L, precision), L, M)
+    assert np.array_equal(co, oc)
+    assert np.array_equal(cs, ocs)
+    assert np.array_equal(pm, opm)
+    s.close()
+
+
 @pytest.mark.parametrize("precision", [md.MD_MIXED, md.MD_PLAIN_FP32])
 def test_neighbour_pairs(precision):
     m = chaingen.melt(20, seed=5, L=4.6)
@@ -359,6 +405,45 @@ def test_short_chains_and_rebin_every_step(sites):
     s.close()
 
 
+def _two_chains_from_one_walk(sites, seed, L):
+    """Two chains whose ends nearly touch: one walk of 2 * sites + 2 sites
+    from the generator, with its two middle sites dropped, so that the last
+    site of chain 0 and the first site of chain 1 were 1-4 neighbours of the
+    walk (0.25 - 0.39 nm apart, inside r_c) but are not bonded here."""
+    w = chaingen.melt(1, sites=2 * sites + 2, seed=seed, L=L)
+    keep = np.r_[0:sites, sites + 2:2 * sites + 2]
+    return dict(pos=w["pos"][keep], vel=w["vel"][keep], L=w["L"], n_chains=2, sites=sites,
+                types=np.tile(chaingen.site_types(sites), 2), masses=np.tile(chaingen.site_masses(sites), 2),
+                T=w["T"], seed=seed)
+
+
+@pytest.mark.parametrize("precision", [md.MD_MIXED, md.MD_PLAIN_FP32])
+@pytest.mark.parametrize("sites", [150, 511])
+def test_last_site_and_next_chains_first_site_interact(sites, precision):
+    """The last site of chain c and the first site of chain c + 1 are not
+    bonded, so their LJ pair counts (Sec. 3.1 excludes only 1-2 and 1-3
+    pairs).  They are placed inside r_c, and the forces must match the
+    oracle's, including for 511-site chains, whose site fields sit closest
+    in the packed tags."""
+    m = _two_chains_from_one_walk(sites, seed=17, L=4.0 if sites == 150 else 5.0)
+    s = md.System(m, precision=precision)
+    x, _ = _uploaded(m, precision)
+    d = x[sites - 1] - x[sites]
+    d -= m["L"] * np.round(d / m["L"])
+    r = np.linalg.norm(d)
+    assert 0.2 < r < 0.45
+    ref = oracle.System(oracle.chain_topology(sites), 2, m["L"], use_cells=False)
+    f_orc = ref.forces(x)[0]
+    # the pair's own force is far above the per-atom bar, so a false
+    # exclusion could not pass the check below
+    p = oracle.default_params()
+    sig, eps = p["sigma"][1], p["eps"][1]
+    f_pair = abs(24 * eps / r * (2 * (sig / r) ** 12 - (sig / r) ** 6))
+    assert f_pair > 100 * ATOM_TOL * np.sqrt(np.mean(np.sum(f_orc ** 2, axis=1)))
+    check_forces(s.forces(), f_orc, x, m["L"])
+    s.close()
+
+
 def test_displacement_beyond_half_skin_is_reported():
     m = chaingen.melt(10, seed=1)
     s = md.System(m, precision=md.MD_MIXED, skin=0.002, rebin_every=10)
@@ -377,7 +462,6 @@ def test_workspace_and_library_allocation_agree():
     a.close(); b.close()
 
 
-@pytest.mark.parametrize("precision", [md.MD_MIXED, md.MD_PLAIN_FP32])
 def _check_sampled(f, x, sel, f_orc, L):
     """Sampled atoms against the oracle's all-atom sums, with the same bar as
     check_forces (an atom with a pair within 2e-6 nm of r_c gets |F(r_c)| per
@@ -661,6 +745,58 @@ def test_non_finite_state_is_reported():
     with pytest.raises(md.MDError) as e:
         s.step(10)
     assert e.value.code == md.MD_EUNSTABLE
+    s.close()
+
+
+@pytest.mark.parametrize("precision", [md.MD_MIXED, md.MD_PLAIN_FP32])
+def test_chain_observables_after_steps_and_rebins(precision):
+    """The observables of a stepped system (20 steps, a rebin every 5, atoms
+    wrapped across faces on the way) against the oracle's definitions on the
+    oracle's own 20-step trajectory from the same state (positions agree to
+    ~1e-5 nm after 20 steps)."""
+    from oracle import observables as ob
+    m = chaingen.melt(12, seed=43, L=3.6)
+    s = md.System(m, precision=md.MD_MIXED if precision == md.MD_MIXED else md.MD_PLAIN_FP32, rebin_every=5)
+    s.step(20)
+    got = s.observables()
+    x, v = _uploaded(m, precision)
+    ref = oracle.System(oracle.chain_topology(m["sites"]), m["n_chains"], m["L"], use_cells=False)
+    xo, _, _, _, _ = ref.run(chaingen.unwrapped(dict(m, pos=x)), v, 0.001, 20, sample_every=0)
+    ree = ob.end_to_end(xo, m["sites"])
+    rg2 = ob.radius_of_gyration_sq(xo, m["sites"], m["masses"])
+    tol = 1e-4 if precision == md.MD_MIXED else 1e-3
+    assert np.allclose(got["r_ee"], ree, rtol=tol, atol=tol)
+    assert np.allclose(got["rg2"], rg2, rtol=tol)
+    phi = ob.dihedral_angles(xo, m["sites"])
+    want = np.mean(np.abs(phi) > 120.0)
+    near = np.sum(np.abs(np.abs(phi) - 120.0) < 0.05)   # states the two trajectories may split
+    assert abs(got["trans_fraction"][0] - want) <= near / phi.size + 1e-15
+    s.close()
+
+
+def test_all_trans_chains_have_trans_fraction_one():
+    """Planar zigzag chains (every dihedral at 180 deg, bond 0.153 nm, angle
+    109.47 deg) in two replicas: the trans fraction is exactly 1, and R_ee is
+    the zigzag's closed form (sites - 1) b sin(theta / 2) along the chain."""
+    b, th = 0.153, np.arccos(-1.0 / 3.0)
+    sites, n_chains = 7, 3
+    melts = []
+    for r, L in enumerate((4.0, 4.4)):
+        pos = []
+        for c in range(n_chains):
+            base = np.array([0.5, 0.7 + 1.2 * c, 0.9 + 0.3 * r])
+            for k in range(sites):
+                pos.append(base + [k * b * np.sin(th / 2), (k % 2) * b * np.cos(th / 2), 0.0])
+        pos = np.array(pos)
+        rng = np.random.default_rng(r)
+        melts.append(dict(pos=pos, vel=0.1 * rng.normal(size=pos.shape), L=L, n_chains=n_chains, sites=sites,
+                          types=np.tile(chaingen.site_types(sites), n_chains),
+                          masses=np.tile(chaingen.site_masses(sites), n_chains), T=300.0))
+    s = md.System(melts, precision=md.MD_MIXED)
+    got = s.observables()
+    assert list(got["trans_fraction"]) == [1.0, 1.0]
+    want = (sites - 1) * b * np.sin(th / 2)
+    assert np.allclose(got["r_ee"][:, 0], want, rtol=1e-12)
     s.close()
 
 

@@ -157,6 +157,82 @@ def test_lj_brute_equals_cells(L):
     assert eb == pytest.approx(ec, rel=1e-11)
 
 
+@pytest.mark.parametrize("L", [3.05, 4.1])   # M = 3 and M = 4 cells of side >= r_c
+def test_lj_atoms_equals_brute_force_on_every_atom(L):
+    """orc_lj_atoms (the checker of the full-size GPU tests) against the
+    pinned all-pairs sum orc_lj_brute, element by element, for every atom of
+    a tiny box.  The boxes hold intra-chain pairs at |i - j| = 2 (excluded)
+    and 3 (counted, Sec. 3.1) inside r_c, and pairs across periodic faces,
+    so a dropped exclusion, a missing j == i test or a wrong image fails."""
+    m, s = _melt(2, L=L, seed=8)
+    x = m["pos"]
+    fb, _, _ = s.lj(x, method="brute")
+    fa = s.lj_atoms(x, np.arange(len(x)))
+    assert np.allclose(fa, fb, rtol=1e-12, atol=1e-12 * np.abs(fb).max())
+    # the geometry really holds the cases named above
+    n = len(x)
+    i, j = np.triu_indices(n, 1)
+    d = x[i] - x[j]
+    img = np.round(d / L)
+    r = np.linalg.norm(d - L * img, axis=1)
+    same = (i // 150) == (j // 150)
+    assert np.any(same & (np.abs(i - j) == 2) & (r < 1.0))
+    assert np.any(same & (np.abs(i - j) == 3) & (r < 1.0))
+    assert np.any((np.abs(img).sum(1) > 0) & (r < 1.0))
+
+
+def test_kinetic_energy_hand_computed():
+    """orc_kinetic = sum 1/2 m v^2 over atoms, masses by type (Table I:
+    14.027 amu for C_32, 15.035 for the C_33 chain ends).  One 4-site chain
+    with velocities chosen so the sum is done by hand:
+      1/2 15.035 (1)  + 1/2 14.027 (4) + 1/2 14.027 (9) + 1/2 15.035 (3)
+      = 7.5175 + 28.054 + 63.1215 + 22.5525 = 121.2455 kJ/mol."""
+    s = oracle.System(oracle.chain_topology(4), 1, 10.0)
+    v = np.array([[1.0, 0.0, 0.0], [0.0, 2.0, 0.0], [0.0, 0.0, 3.0], [1.0, 1.0, 1.0]])
+    assert s.kinetic(v) == pytest.approx(121.2455, rel=1e-14)
+    # two molecules: every atom counted once, with its own mass
+    s2 = oracle.System(oracle.chain_topology(4), 2, 10.0)
+    assert s2.kinetic(np.vstack([v, 2.0 * v])) == pytest.approx(5.0 * 121.2455, rel=1e-14)
+
+
+# Cell index of one coordinate by the binning reading (Sec. 3.1): wrap
+# s = x - L floor(x/L), then k = floor(s M / L) clamped to M - 1.  The boxes
+# are chosen so that M / L is exact in FP64 and every step below is exact,
+# so the expected cells follow from the reading by hand.
+_BIN_CASES = [
+    # (L, M, x, expected cell)
+    (3.0, 3, 1.0, 1),                 # exactly on the face k L / M: the upper cell
+    (3.0, 3, 2.0, 2),
+    (3.0, 3, np.nextafter(1.0, 0.0), 0),   # just below that face
+    (3.0, 3, 0.0, 0),
+    (3.0, 3, -0.0, 0),                # negative zero wraps to 0
+    (3.0, 3, 3.0, 0),                 # x = L wraps to 0
+    (3.0, 3, np.nextafter(3.0, 4.0), 0),   # L + ulp wraps to a tiny positive s
+    (3.0, 3, -1e-300, 2),             # tiny negative: s rounds to L, clamped to M - 1
+    (3.0, 3, -1.0, 2),                # one cell below the box: the top cell
+    (3.0, 3, 4.0, 1),                 # one box and one cell above
+    (2.5, 5, 0.5, 1),                 # M / L = 2 exactly; faces at multiples of 0.5
+    (2.5, 5, 2.0, 4),
+    (2.5, 5, np.nextafter(0.5, 0.0), 0),
+    (2.5, 5, 2.5, 0),
+    (4.0, 4, 3.0, 3),
+    (4.0, 4, np.nextafter(4.0, 0.0), 3),
+]
+
+
+@pytest.mark.parametrize("L,M,xv,want", _BIN_CASES)
+def test_binning_cell_index_convention(L, M, xv, want):
+    # the coordinate under test on each axis in turn, the others at a cell interior
+    for axis in range(3):
+        x = np.full((1, 3), 0.25 * L / M)
+        x[0, axis] = xv
+        cell_of, start, perm = oracle.bin_atoms(x, L, M)
+        k = [0, 0, 0]
+        k[axis] = want
+        assert cell_of[0] == (k[2] * M + k[1]) * M + k[0]
+        assert start[cell_of[0]] == 0 and start[cell_of[0] + 1] == 1 and perm[0] == 0
+
+
 def test_lj_exclusions_only_first_and_second_neighbours():
     # a straight 4-atom chain spaced 0.4 nm: pairs (0,3) at 1.2 nm are outside r_c,
     # pairs (0,1),(0,2),(1,3) ... are excluded; use spacing 0.3 so 1-4 = 0.9 nm is inside
