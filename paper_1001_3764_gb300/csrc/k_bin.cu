@@ -11,7 +11,7 @@
 // Sorted positions are stored in units of the cell side relative to the
 // centre of the atom's cell (|u| <= 1/2 at the rebin), so neighbour cells are
 // offset by exact integers and an FP32 coordinate carries about 2^-25 h.
-// The neighbour list itself is built in k_lj.cu.
+// The cluster lists are built in k_lj.cu.
 #include "md_kernels.cuh"
 
 namespace mdg {
@@ -89,6 +89,39 @@ __global__ void __launch_bounds__(1024) k_scan(const int* __restrict__ count, in
 
 void launch_scan(const int* count, int* cell_start, int C, cudaStream_t st) {
   k_scan<<<1, 1024, 0, st>>>(count, cell_start, C);
+}
+
+// the same scan for cell_start and, over ceil(count / 4), for cl_start
+__global__ void __launch_bounds__(1024) k_scan2(const int* __restrict__ count, int* __restrict__ start,
+                                                int* __restrict__ cl_start, int C) {
+  __shared__ int part[2][1024];
+  const int tid = threadIdx.x;
+  const int per = (C + 1023) / 1024;
+  const int b = tid * per, e = min(b + per, C);
+  int s = 0, sc = 0;
+  for (int k = b; k < e; ++k) { const int n = count[k]; s += n; sc += (n + 3) >> 2; }
+  part[0][tid] = s;
+  part[1][tid] = sc;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {     // Hillis-Steele inclusive scans
+    const int v = tid >= off ? part[0][tid - off] : 0;
+    const int vc = tid >= off ? part[1][tid - off] : 0;
+    __syncthreads();
+    part[0][tid] += v;
+    part[1][tid] += vc;
+    __syncthreads();
+  }
+  int run = part[0][tid] - s, runc = part[1][tid] - sc;
+  for (int k = b; k < e; ++k) {
+    const int n = count[k];
+    start[k] = run; run += n;
+    cl_start[k] = runc; runc += (n + 3) >> 2;
+  }
+  if (tid == 1023) { start[C] = part[0][1023]; cl_start[C] = part[1][1023]; }
+}
+
+void launch_scan2(const int* count, int* cell_start, int* cl_start, int C, cudaStream_t st) {
+  k_scan2<<<1, 1024, 0, st>>>(count, cell_start, cl_start, C);
 }
 
 // --------------------------------------------------------------- scatter

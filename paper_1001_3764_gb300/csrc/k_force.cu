@@ -113,10 +113,18 @@ __device__ __forceinline__ void add_vir(float (&W)[6], f3 r, f3 f) {
   W[3] += r.x * f.y; W[4] += r.x * f.z; W[5] += r.y * f.z;
 }
 
+// int64 fixed point (2^-32 kJ/mol/nm) -> FP32 on the 32-bit pipes: the high
+// word (|hi| < 2^24, exact) plus the low word scaled by 2^-32
+__device__ __forceinline__ float fix_to_float(long long q) {
+  const int hi = (int)(q >> 32);
+  const unsigned lo = (unsigned)q;
+  return fmaf((float)lo, 2.3283064365386963e-10f, (float)hi);
+}
+
 template <bool MIXED, bool ENERGY>
 __global__ void __launch_bounds__(kBondedBlock) k_bonded(const void* __restrict__ xv, const uint16_t* __restrict__ site,
-                                                         const int* __restrict__ inv_perm, const void* __restrict__ flj,
-                                                         int N, const Tile* __restrict__ tiles,
+                                                         const int* __restrict__ inv_perm, long long* __restrict__ flj,
+                                                         int Npad, int N, const Tile* __restrict__ tiles,
                                                          const RepDev* __restrict__ reps, const ForceParams fp,
                                                          void* __restrict__ Fout, double* __restrict__ epart,
                                                          unsigned* __restrict__ flags) {
@@ -225,18 +233,20 @@ __global__ void __launch_bounds__(kBondedBlock) k_bonded(const void* __restrict_
     f3 F = fbd[q] - fbd[q - 1];
     F = F + fan_a[q] - (fan_a[q - 1] + fan_c[q - 1]) + fan_c[q - 2];
     F = F + fdi1[q] + fdi2[q - 1] + fdi3[q - 2] - (fdi1[q - 3] + fdi2[q - 3] + fdi3[q - 3]);
+    // the LJ force of the atom (sorted slot s), then cleared for the next step
     const int s = inv_perm[i];
+    const long long lx = flj[s], ly = flj[Npad + s], lz = flj[2 * (size_t)Npad + s];
+    flj[s] = 0; flj[Npad + s] = 0; flj[2 * (size_t)Npad + s] = 0;
     if (MIXED) {
-      const F4i l = reinterpret_cast<const F4i*>(flj)[s];
       F4i o;
-      o.x = l.x + to_fix(F.x, flags);
-      o.y = l.y + to_fix(F.y, flags);
-      o.z = l.z + to_fix(F.z, flags);
+      o.x = lx + to_fix(F.x, flags);
+      o.y = ly + to_fix(F.y, flags);
+      o.z = lz + to_fix(F.z, flags);
       o.w = 0;
       reinterpret_cast<F4i*>(Fout)[i] = o;
     } else {
-      const float4 l = reinterpret_cast<const float4*>(flj)[s];
-      reinterpret_cast<float4*>(Fout)[i] = make_float4(l.x + F.x, l.y + F.y, l.z + F.z, 0.f);
+      reinterpret_cast<float4*>(Fout)[i] =
+          make_float4(fix_to_float(lx) + F.x, fix_to_float(ly) + F.y, fix_to_float(lz) + F.z, 0.f);
     }
   }
   if (ENERGY) {
@@ -246,15 +256,16 @@ __global__ void __launch_bounds__(kBondedBlock) k_bonded(const void* __restrict_
 }
 
 void launch_bonded(bool mixed, bool energy, const void* x, const uint16_t* site, const int* inv_perm,
-                   const void* flj, int N, const Tile* tiles, int n_tiles, const RepDev* reps,
+                   long long* flj, int Npad, int N, const Tile* tiles, int n_tiles, const RepDev* reps,
                    const ForceParams& fp, void* F, double* epart, unsigned* flags, cudaStream_t st) {
+#define MDG_BONDED(M, E) \
+  k_bonded<M, E><<<n_tiles, kBondedBlock, 0, st>>>(x, site, inv_perm, flj, Npad, N, tiles, reps, fp, F, epart, flags)
   if (mixed) {
-    if (energy) k_bonded<true, true><<<n_tiles, kBondedBlock, 0, st>>>(x, site, inv_perm, flj, N, tiles, reps, fp, F, epart, flags);
-    else k_bonded<true, false><<<n_tiles, kBondedBlock, 0, st>>>(x, site, inv_perm, flj, N, tiles, reps, fp, F, epart, flags);
+    if (energy) MDG_BONDED(true, true); else MDG_BONDED(true, false);
   } else {
-    if (energy) k_bonded<false, true><<<n_tiles, kBondedBlock, 0, st>>>(x, site, inv_perm, flj, N, tiles, reps, fp, F, epart, flags);
-    else k_bonded<false, false><<<n_tiles, kBondedBlock, 0, st>>>(x, site, inv_perm, flj, N, tiles, reps, fp, F, epart, flags);
+    if (energy) MDG_BONDED(false, true); else MDG_BONDED(false, false);
   }
+#undef MDG_BONDED
 }
 
 }  // namespace mdg

@@ -7,8 +7,11 @@
 // (bonded terms), k_integrate.cu (integration, kinetic energy, thermostats,
 // energy reductions, observables, state transfer) and md_adjoint.cu (the
 // adjoint); md_static.cu holds the allocation-free binning entry point.
+#include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
+#include <tuple>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -49,16 +52,25 @@ struct md_system {
   bool own_mem = false;
   RepDev* reps = nullptr;
   Tile* tiles_int = nullptr;
-  void *x = nullptr, *v = nullptr, *F = nullptr, *flj = nullptr;
+  void *x = nullptr, *v = nullptr, *F = nullptr;
+  long long* flj = nullptr;                  // LJ force, int64 SoA [3][Npad], sorted order
+  long long* flj_e = nullptr;                // the same for energy read-outs (kept apart from the dynamics)
   int* img = nullptr;
   uint16_t* site = nullptr;
   int *cellc = nullptr, *inv_perm = nullptr, *tag = nullptr, *perm = nullptr;
   float4 *ref = nullptr, *pos = nullptr;
-  uint4* nbr = nullptr;
+  unsigned* list = nullptr;                  // cluster lists [n_cl_max][cap]
+  int* ncl = nullptr;                        // entries per cluster
+  int* cl_start = nullptr;                   // first cluster of each cell [C + 1]
+  int64_t n_cl_max = 0;
+  std::vector<Region> regions_h;
+  std::vector<RegionShape> shapes_h;
+  Region* regions = nullptr;
+  RegionShape* shapes = nullptr;
   int tile_cap = 0;
   int lj_block = 256, persistent_grid = 0;   // persistent_grid > 0: fixed grid for the LJ kernel
   int* work = nullptr;                       // LJ work counters (persistent schedule)
-  int *ncount = nullptr, *count = nullptr, *cell_start = nullptr, *cell_of = nullptr;
+  int *count = nullptr, *cell_start = nullptr, *cell_of = nullptr;
   int *slot = nullptr, *tmp = nullptr;
   double *lj_part = nullptr, *b_part = nullptr, *kepart = nullptr, *ke_out = nullptr, *lam = nullptr;
   double* e_out = nullptr;
@@ -138,6 +150,44 @@ static void fill_force_params(md_system* s) {
   f.dt = s->dt;
 }
 
+// Region shapes: sx x sy x 1 home cells (sx, sy in {1, 2}; shape id
+// (sx - 1) + 2 (sy - 1)).  The tile lists the home cells first, then every
+// cell that a home cell's 13 forward offsets reach, in the order first met;
+// nb[h] gives home cell h's own tile cell and its 13 forward tile cells, in
+// the offset order (dz = +1 layer, then dz = 0, dy = +1, then (+1, 0, 0)).
+static RegionShape make_shape(int sx, int sy) {
+  RegionShape S{};
+  std::vector<std::array<int, 3>> tile;
+  for (int y = 0; y < sy; ++y)
+    for (int x = 0; x < sx; ++x) tile.push_back({x, y, 0});
+  S.n_home = sx * sy;
+  std::vector<std::array<int, 3>> fw;
+  for (int dz = -1; dz <= 1; ++dz)
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx)
+        if (dz > 0 || (dz == 0 && dy > 0) || (dz == 0 && dy == 0 && dx > 0)) fw.push_back({dx, dy, dz});
+  std::sort(fw.begin(), fw.end(), [](const std::array<int, 3>& a, const std::array<int, 3>& b) {
+    return std::make_tuple(-a[2], -a[1], a[0]) < std::make_tuple(-b[2], -b[1], b[0]);
+  });
+  for (int h = 0; h < S.n_home; ++h) {
+    S.nb[h][0] = (unsigned char)h;
+    for (int q = 0; q < 13; ++q) {
+      const std::array<int, 3> c = {tile[h][0] + fw[q][0], tile[h][1] + fw[q][1], tile[h][2] + fw[q][2]};
+      int k = 0;
+      while (k < (int)tile.size() && tile[k] != c) ++k;
+      if (k == (int)tile.size()) tile.push_back(c);
+      S.nb[h][q + 1] = (unsigned char)k;
+    }
+  }
+  S.n_tile = (int)tile.size();
+  for (int k = 0; k < S.n_tile; ++k)
+    for (int a = 0; a < 3; ++a) S.off[k][a] = (signed char)tile[k][a];
+  S.cx = 0.5f * (float)(sx - 1);
+  S.cy = 0.5f * (float)(sy - 1);
+  S.cz = 0.f;
+  return S;
+}
+
 // Validate the descriptor and fill geometry, tiles and sizes (no device work).
 static int configure(md_system* s, const md_desc* d) {
   if (!d) return fail(s, MD_EINVAL, "null descriptor");
@@ -206,12 +256,30 @@ static int configure(md_system* s, const md_desc* d) {
     if (cells >= (1 << 26)) return fail(s, MD_EINVAL, "too many cells");
   }
   s->N = atoms; s->C = (int)cells;
+  // regions of 2 x 2 x 1 cells (1 wide at the high faces of an odd M)
+  s->shapes_h.clear();
+  for (int sy = 1; sy <= 2; ++sy)
+    for (int sx = 1; sx <= 2; ++sx) s->shapes_h.push_back(make_shape(sx, sy));
+  s->regions_h.clear();
+  for (int r = 0; r < s->n_reps; ++r) {
+    const int M = s->reps_h[r].M;
+    for (int z = 0; z < M; ++z)
+      for (int y = 0; y < M; y += 2)
+        for (int x = 0; x < M; x += 2) {
+          Region g{};
+          g.rep = r; g.ox = x; g.oy = y; g.oz = z;
+          g.shape = (std::min(2, M - x) - 1) + 2 * (std::min(2, M - y) - 1);
+          s->regions_h.push_back(g);
+        }
+  }
+  s->n_cl_max = (atoms + 3 * cells) / 4 + 1;   // sum of ceil(n_c / 4) over the cells
   s->Npad = (int)((atoms + 31) / 32 * 32);
-  // default list capacity: twice the mean neighbour count at (at least) melt
-  // density plus 64 slots for sentinel padding of the per-thread sub-lists
-  s->cap = d->nbr_capacity > 0 ? d->nbr_capacity : (int)std::ceil(2.0 * max_expected + 64.0);
-  s->cap = (s->cap + 7) / 8 * 8;
-  if (s->cap > 1024) return fail(s, MD_EINVAL, "neighbour capacity above 1024");
+  // default list capacity (entries per 4-atom cluster): a cluster's list holds
+  // about 0.75 x the atoms within rc + skin of one atom at melt density
+  // (~135 in the benchmark melt, at most ~350); 2.5 x that plus 64
+  s->cap = d->nbr_capacity > 0 ? d->nbr_capacity : (int)std::ceil(2.5 * 0.75 * max_expected + 64.0);
+  s->cap = (s->cap + 31) / 32 * 32;
+  if (s->cap > 4096) return fail(s, MD_EINVAL, "neighbour capacity above 4096");
   // 27-cell tile capacity (shared memory per block): 1.4x the mean tile of
   // the densest replica (at least melt density, 33 sites/nm^3) plus 64, in
   // multiples of 128 atoms; a larger tile is reported as MD_EOVERFLOW
@@ -232,7 +300,8 @@ static size_t plan(md_system* s, char* base) {
   s->v = take(3 * N * fsz);
   s->img = (int*)take(3 * N * sizeof(int));
   s->F = take(N * (s->mixed ? sizeof(F4i) : sizeof(float4)));
-  s->flj = take(N * (s->mixed ? sizeof(F4i) : sizeof(float4)));
+  s->flj = (long long*)take(3 * (size_t)s->Npad * sizeof(long long));
+  s->flj_e = (long long*)take(3 * (size_t)s->Npad * sizeof(long long));
   s->site = (uint16_t*)take(N * sizeof(uint16_t));
   s->cellc = (int*)take(N * sizeof(int));
   s->ref = (float4*)take(N * sizeof(float4));
@@ -240,8 +309,11 @@ static size_t plan(md_system* s, char* base) {
   s->pos = (float4*)take(N * sizeof(float4));
   s->tag = (int*)take(N * sizeof(int));
   s->perm = (int*)take(N * sizeof(int));
-  s->nbr = (uint4*)take((size_t)(s->cap / 8) * s->Npad * sizeof(uint4));
-  s->ncount = (int*)take(N * sizeof(int));
+  s->regions = (Region*)take(sizeof(Region) * s->regions_h.size());
+  s->shapes = (RegionShape*)take(sizeof(RegionShape) * s->shapes_h.size());
+  s->list = (unsigned*)take((size_t)s->n_cl_max * s->cap * sizeof(unsigned));
+  s->ncl = (int*)take((size_t)s->n_cl_max * sizeof(int));
+  s->cl_start = (int*)take((C + 1) * sizeof(int));
   s->count = (int*)take(C * sizeof(int));
   s->cell_start = (int*)take((C + 1) * sizeof(int));
   s->cell_of = (int*)take(N * sizeof(int));
@@ -278,13 +350,13 @@ static void enqueue_rebin(md_system* s) {
   cudaMemsetAsync(s->count, 0, sizeof(int) * s->C, s->st);
   launch_bin_count(s->mixed, s->x, (int)s->N, s->tiles_int, (int)s->t_int.size(), s->reps, s->cell_of, s->cellc,
                    s->count, s->slot, s->st);
-  launch_scan(s->count, s->cell_start, s->C, s->st);
+  launch_scan2(s->count, s->cell_start, s->cl_start, s->C, s->st);
   launch_bin_scatter(s->cell_of, s->slot, s->cell_start, s->tmp, (int)s->N, s->st);
   launch_cell_sort(s->mixed, s->x, (int)s->N, s->cell_start, s->tmp, s->cellc, s->site, s->reps, s->n_reps, s->C,
                    s->S, s->perm, s->inv_perm, s->pos, s->tag, s->ref, s->flags, s->st);
   prof_mark(s);
-  launch_nbr_tile(s->pos, s->tag, s->cell_start, s->reps, s->n_reps, s->C, s->nbr, s->ncount, s->cap, s->Npad,
-                  s->tile_cap, s->flags, s->st);
+  launch_cl_build(s->pos, s->tag, s->cell_start, s->cl_start, s->regions, (int)s->regions_h.size(), s->shapes,
+                  s->reps, s->list, s->ncl, s->cap, s->tile_cap, s->flags, s->persistent_grid, s->work, s->st);
   prof_mark(s);
 }
 static const int kRebinLaunches = 6;   // memset counted as a launch
@@ -293,11 +365,14 @@ static const int kRebinLaunches = 6;   // memset counted as a launch
 // energy read-out, whose kernels need not reproduce the force bits of the
 // force-only kernels: the compiler may fuse their arithmetic differently)
 static void enqueue_forces(md_system* s, bool energy, void* F_out = nullptr) {
-  launch_lj_tile(s->mixed, energy, s->pos, s->tag, s->cell_start, s->nbr, s->ncount, s->Npad, s->tile_cap, s->reps,
-                 s->n_reps, s->C, s->fp, s->flj, s->lj_part, s->flags, s->lj_block, s->persistent_grid, s->work, s->st);
+  // an energy read-out accumulates its LJ forces apart from the dynamics'
+  long long* flj = F_out ? s->flj_e : s->flj;
+  launch_cl_force(energy, s->pos, s->cell_start, s->cl_start, s->regions, (int)s->regions_h.size(), s->shapes,
+                  s->reps, s->list, s->ncl, s->cap, s->tile_cap, s->fp, flj, s->Npad, s->lj_part, s->flags,
+                  s->lj_block, s->persistent_grid, s->work, s->st);
   prof_mark(s);
-  launch_bonded(s->mixed, energy, s->x, s->site, s->inv_perm, s->flj, (int)s->N, s->tiles_int, (int)s->t_int.size(),
-                s->reps, s->fp, F_out ? F_out : s->F, s->b_part, s->flags, s->st);
+  launch_bonded(s->mixed, energy, s->x, s->site, s->inv_perm, flj, s->Npad, (int)s->N, s->tiles_int,
+                (int)s->t_int.size(), s->reps, s->fp, F_out ? F_out : s->F, s->b_part, s->flags, s->st);
   prof_mark(s);
 }
 
@@ -461,7 +536,7 @@ int md_create(const md_desc* d, md_system** out) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int per_sm = lj_blocks_per_sm(s->lj_block, s->tile_cap);
-    s->persistent_grid = std::max(1, std::min(s->C, sms * std::max(per_sm, 1)));
+    s->persistent_grid = std::max(1, std::min((int)s->regions_h.size(), sms * std::max(per_sm, 1)));
   }
   // static tables
   std::vector<uint16_t> site(s->N);
@@ -483,6 +558,10 @@ int md_create(const md_desc* d, md_system** out) {
             up(s->tiles_int, s->t_int.data(), sizeof(Tile) * s->t_int.size()) &&
             up(s->site, site.data(), sizeof(uint16_t) * s->N) &&
             up(s->lam, ones.data(), sizeof(double) * 6 * s->n_reps) &&
+            up(s->regions, s->regions_h.data(), sizeof(Region) * s->regions_h.size()) &&
+            up(s->shapes, s->shapes_h.data(), sizeof(RegionShape) * s->shapes_h.size()) &&
+            cudaMemsetAsync(s->flj, 0, 3 * (size_t)s->Npad * sizeof(long long), s->st) == cudaSuccess &&
+            cudaMemsetAsync(s->flj_e, 0, 3 * (size_t)s->Npad * sizeof(long long), s->st) == cudaSuccess &&
             cudaMemsetAsync(s->done, 0, sizeof(unsigned), s->st) == cudaSuccess &&
             cudaMemsetAsync(s->work, 0, 2 * sizeof(int), s->st) == cudaSuccess &&
             cudaMemsetAsync(s->flags, 0, sizeof(unsigned), s->st) == cudaSuccess &&
@@ -692,41 +771,57 @@ int md_get_neighbors(md_system* s, int32_t* count, int32_t* entries) {
   if (!s) return fail(s, MD_EINVAL, "null system");
   CU(cudaStreamSynchronize(s->st));
   const size_t N = (size_t)s->N;
-  std::vector<int> cnt(N), pm(N), cs(s->C + 1);
-  std::vector<uint16_t> lst((size_t)s->cap * s->Npad);   // blocks of 8 entries
-  CU(cudaMemcpy(cnt.data(), s->ncount, N * sizeof(int), cudaMemcpyDeviceToHost));
+  std::vector<int> pm(N), cs(s->C + 1), cls(s->C + 1);
   CU(cudaMemcpy(pm.data(), s->perm, N * sizeof(int), cudaMemcpyDeviceToHost));
   CU(cudaMemcpy(cs.data(), s->cell_start, (s->C + 1) * sizeof(int), cudaMemcpyDeviceToHost));
-  CU(cudaMemcpy(lst.data(), s->nbr, lst.size() * sizeof(uint16_t), cudaMemcpyDeviceToHost));
-  for (int r = 0; r < s->n_reps; ++r) {
-    const RepDev& q = s->reps_h[r];
+  CU(cudaMemcpy(cls.data(), s->cl_start, (s->C + 1) * sizeof(int), cudaMemcpyDeviceToHost));
+  const size_t ncl_used = (size_t)cls[s->C];
+  std::vector<int> nc(ncl_used);
+  std::vector<unsigned> lst(ncl_used * s->cap);
+  if (ncl_used) {
+    CU(cudaMemcpy(nc.data(), s->ncl, ncl_used * sizeof(int), cudaMemcpyDeviceToHost));
+    CU(cudaMemcpy(lst.data(), s->list, lst.size() * sizeof(unsigned), cudaMemcpyDeviceToHost));
+  }
+  // every listed pair, both ways, by original atom index: the region tiles
+  // rebuilt here exactly as the kernels stage them
+  std::vector<std::vector<int>> nb(N);
+  for (const Region& g : s->regions_h) {
+    const RegionShape& S = s->shapes_h[g.shape];
+    const RepDev& q = s->reps_h[g.rep];
     const int M = q.M;
-    for (int lc = 0; lc < M * M * M; ++lc) {
-      const int c = q.cell_base + lc;
-      // the 27-cell tile of cell c, in the order the kernels stage it
-      int start[27], off[28];
-      off[0] = 0;
-      const int cx = lc % M, cy = (lc / M) % M, cz = lc / (M * M);
-      for (int k = 0; k < 27; ++k) {
-        const int ox = k % 3 - 1, oy = (k / 3) % 3 - 1, oz = k / 9 - 1;
-        const int nc = q.cell_base + (((cz + oz + M) % M) * M + ((cy + oy + M) % M)) * M + ((cx + ox + M) % M);
-        start[k] = cs[nc];
-        off[k + 1] = off[k] + cs[nc + 1] - cs[nc];
-      }
-      for (int sl = cs[c]; sl < cs[c + 1]; ++sl) {
-        const int i = pm[sl];
-        int m = 0;
-        for (int k2 = 0; k2 < 8 * cnt[sl]; ++k2) {      // cnt = blocks of 8; skip sentinel slots
-          const int t = lst[((size_t)(k2 >> 3) * s->Npad + sl) * 8 + (k2 & 7)];
-          if (t >= off[27]) continue;
-          int k = 0;
-          while (k < 26 && off[k + 1] <= t) ++k;
-          if (entries) entries[(size_t)i * s->cap + m] = pm[start[k] + (t - off[k])];
-          ++m;
+    int start[kMaxTileCells], off[kMaxTileCells + 1], cell[kMaxTileCells];
+    off[0] = 0;
+    for (int k = 0; k < S.n_tile; ++k) {
+      const int cx = (g.ox + S.off[k][0] + M) % M, cy = (g.oy + S.off[k][1] + M) % M, cz = (g.oz + S.off[k][2] + M) % M;
+      cell[k] = q.cell_base + (cz * M + cy) * M + cx;
+      start[k] = cs[cell[k]];
+      off[k + 1] = off[k] + cs[cell[k] + 1] - cs[cell[k]];
+    }
+    for (int h = 0; h < S.n_home; ++h) {
+      const int n_h = off[h + 1] - off[h];
+      for (int kq = 0; kq < (n_h + 3) / 4; ++kq) {
+        const int cl = cls[cell[h]] + kq;
+        for (int e = 0; e < nc[cl]; ++e) {
+          const unsigned E = lst[(size_t)cl * s->cap + e];
+          const int t = (int)(E & 0xffffu);
+          int kc = 0;
+          while (kc + 1 < S.n_tile && off[kc + 1] <= t) ++kc;
+          const int j = pm[start[kc] + (t - off[kc])];
+          for (int u = 0; u < 4; ++u)
+            if ((E >> (16 + u)) & 1u) {
+              const int i = pm[start[h] + 4 * kq + u];
+              nb[i].push_back(j);
+              nb[j].push_back(i);
+            }
         }
-        if (count) count[i] = m;
       }
     }
+  }
+  for (size_t i = 0; i < N; ++i) {
+    if ((int)nb[i].size() > s->cap) return fail(s, MD_EOVERFLOW, "an atom has more listed neighbours than the capacity");
+    if (count) count[i] = (int)nb[i].size();
+    if (entries)
+      for (size_t m = 0; m < nb[i].size(); ++m) entries[i * s->cap + m] = nb[i][m];
   }
   return MD_OK;
 }

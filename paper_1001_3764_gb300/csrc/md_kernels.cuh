@@ -16,11 +16,16 @@
 //     tag        int32 [N]  chain*1024 + site | type << 30 (sites < 1024, so the
 //                site fields of two chains never come within 2 of each other)
 //     perm       int32 [N]  original index of slot s
-//     Flj        AoS 32 B   LJ force on slot s
-//     nbr        uint16 entries in blocks of 8 ([cap/8][Npad] of 16 B):
-//                index into the 27-cell tile of the atom's cell
-//     ncount     int32 [N]
-//   cells: count int32 [C], cell_start int32 [C+1]
+//     Flj        int64 SoA [3][Npad]  LJ force on slot s (2^-32 kJ/mol/nm),
+//                added to by the force kernel, read and cleared by the
+//                bonded kernel
+//   clusters (4 consecutive slots of a cell; cluster k of cell c is
+//   cl_start[c] + k):
+//     list       uint32 [clusters][cap]: tile index (bits 0..15) and the mask
+//                of the cluster's atoms that pair with it (bits 16..19)
+//     ncl        int32 [clusters] entries per cluster
+//   cells: count int32 [C], cell_start int32 [C+1], cl_start int32 [C+1]
+//   regions: up to 2 x 2 x 1 cells each, the force and list-build work units
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -62,6 +67,19 @@ struct RepDev {
 };
 
 struct Tile { int start, len, rep, pad; };
+
+// Regions of up to 2 x 2 x 1 cells (the work unit of the list build and LJ
+// kernels) and their tiles: the region's home cells, then the cells their
+// 13 forward neighbours add, as offsets from the region's origin cell.
+constexpr int kMaxTileCells = 32;
+constexpr int kMaxHome = 4;
+struct RegionShape {
+  int n_home, n_tile;
+  signed char off[kMaxTileCells][3];      // tile cell offsets (x, y, z) from the origin cell
+  unsigned char nb[kMaxHome][14];         // home cell h: its own tile cell, then its 13 forward cells
+  float cx, cy, cz;                       // region centre relative to the origin cell's centre
+};
+struct Region { int rep, ox, oy, oz, shape, pad[3]; };
 
 // Position of atom x (one axis) in cell units relative to the centre of cell
 // c, shifted by w box lengths (w = +1/-1 for an atom that crossed a face
@@ -201,6 +219,8 @@ void launch_bin_count(bool mixed, const void* x, int N, const Tile* tiles, int n
                       const RepDev* reps, int* cell_of, int* cellc, int* count, int* slot,
                       cudaStream_t st);
 void launch_scan(const int* count, int* cell_start, int C, cudaStream_t st);
+// cell_start from count, and cl_start from ceil(count / 4) (clusters per cell)
+void launch_scan2(const int* count, int* cell_start, int* cl_start, int C, cudaStream_t st);
 // stable order by atom index inside each of C cells (n atoms in all):
 // perm[cell_start[c] + rank] = atom, from the unsorted bucket contents in
 // `runs` (overwritten), in O(m log m) work for a cell of m atoms.  Scratch:
@@ -214,25 +234,30 @@ void launch_cell_sort(bool mixed, const void* x, int N, const int* cell_start, c
                       int sites, int* perm, int* inv_perm, float4* pos, int* tag, float4* ref, unsigned* flags,
                       cudaStream_t st);
 // ---------------------------------------------------------------- forces
-// neighbour list and LJ over 27-cell shared-memory tiles (k_lj.cu).  The list
-// holds uint16 entries in blocks of 8: block q of slot s is nbr[q * Npad + s],
-// ncount[s] = number of blocks, unused slots hold the tile's sentinel index.
-// tile_cap = atoms a tile may hold (shared memory).
-void launch_nbr_tile(const float4* pos, const int* tag, const int* cell_start, const RepDev* reps, int n_reps, int C,
-                     uint4* nbr, int* ncount, int cap, int Npad, int tile_cap, unsigned* flags, cudaStream_t st);
-// block = 128 or 256 threads; persistent_grid > 0 runs that many blocks that
-// take cells from work[0..1] (two ints, zero before the first launch)
-void launch_lj_tile(bool mixed, bool energy, const float4* pos, const int* tag, const int* cell_start,
-                    const uint4* nbr, const int* ncount, int Npad, int tile_cap, const RepDev* reps, int n_reps, int C,
-                    const ForceParams& fp, void* flj, double* epart, unsigned* flags, int block, int persistent_grid,
-                    int* work, cudaStream_t st);
+// cluster lists and LJ forces by regions (k_lj.cu).  The build writes each
+// cluster's list (up to cap entries, ncl[cl] of them); the force kernel adds
+// the LJ force of every atom into flj (int64 SoA [3][Npad], cleared by the
+// bonded kernel) and, with energy, the per-region energy and virial sums into
+// epart (8 per cell).  persistent_grid > 0 runs that many blocks that take
+// regions from work[0..1] (two ints, zero before the first launch).
+void launch_cl_build(const float4* pos, const int* tag, const int* cell_start, const int* cl_start,
+                     const Region* regions, int n_regions, const RegionShape* shapes, const RepDev* reps,
+                     unsigned* list, int* ncl, int cap, int tile_cap, unsigned* flags, int persistent_grid, int* work,
+                     cudaStream_t st);
+void launch_cl_force(bool energy, const float4* pos, const int* cell_start, const int* cl_start,
+                     const Region* regions, int n_regions, const RegionShape* shapes, const RepDev* reps,
+                     const unsigned* list, const int* ncl, int cap, int tile_cap, const ForceParams& fp,
+                     long long* flj, int Npad, double* epart, unsigned* flags, int block, int persistent_grid,
+                     int* work, cudaStream_t st);
 int lj_blocks_per_sm(int block, int tile_cap);
 cudaError_t tile_kernels_init();
 int tile_capacity_max();
 // one block waits on an mbarrier nothing arrives on, `spins` rounds, then raises kFlagTimeout
 void launch_wait_selftest(unsigned spins, unsigned* flags, cudaStream_t st);
+// bonded forces plus the LJ force (read from flj[3][Npad] in sorted order,
+// then cleared) into F (original order)
 void launch_bonded(bool mixed, bool energy, const void* x, const uint16_t* site, const int* inv_perm,
-                   const void* flj, int N, const Tile* tiles, int n_tiles, const RepDev* reps,
+                   long long* flj, int Npad, int N, const Tile* tiles, int n_tiles, const RepDev* reps,
                    const ForceParams& fp, void* F, double* epart, unsigned* flags, cudaStream_t st);
 
 // ---------------------------------------------------------------- integration
