@@ -123,7 +123,7 @@ __device__ __forceinline__ float fix_to_float(long long q) {
 
 template <bool MIXED, bool ENERGY>
 __global__ void __launch_bounds__(kBondedBlock) k_bonded(const void* __restrict__ xv, const uint16_t* __restrict__ site,
-                                                         const int* __restrict__ inv_perm, long long* __restrict__ flj,
+                                                         const int* __restrict__ inv_perm, const long long* __restrict__ flj,
                                                          int Npad, int N, const Tile* __restrict__ tiles,
                                                          const RepDev* __restrict__ reps, const ForceParams fp,
                                                          void* __restrict__ Fout, double* __restrict__ epart,
@@ -233,10 +233,9 @@ __global__ void __launch_bounds__(kBondedBlock) k_bonded(const void* __restrict_
     f3 F = fbd[q] - fbd[q - 1];
     F = F + fan_a[q] - (fan_a[q - 1] + fan_c[q - 1]) + fan_c[q - 2];
     F = F + fdi1[q] + fdi2[q - 1] + fdi3[q - 2] - (fdi1[q - 3] + fdi2[q - 3] + fdi3[q - 3]);
-    // the LJ force of the atom (sorted slot s), then cleared for the next step
+    // the LJ force of the atom (sorted slot s)
     const int s = inv_perm[i];
-    const long long lx = flj[s], ly = flj[Npad + s], lz = flj[2 * (size_t)Npad + s];
-    flj[s] = 0; flj[Npad + s] = 0; flj[2 * (size_t)Npad + s] = 0;
+    const long long lx = __ldg(flj + s), ly = __ldg(flj + Npad + s), lz = __ldg(flj + 2 * (size_t)Npad + s);
     if (MIXED) {
       F4i o;
       o.x = lx + to_fix(F.x, flags);
@@ -256,7 +255,7 @@ __global__ void __launch_bounds__(kBondedBlock) k_bonded(const void* __restrict_
 }
 
 void launch_bonded(bool mixed, bool energy, const void* x, const uint16_t* site, const int* inv_perm,
-                   long long* flj, int Npad, int N, const Tile* tiles, int n_tiles, const RepDev* reps,
+                   const long long* flj, int Npad, int N, const Tile* tiles, int n_tiles, const RepDev* reps,
                    const ForceParams& fp, void* F, double* epart, unsigned* flags, cudaStream_t st) {
 #define MDG_BONDED(M, E) \
   k_bonded<M, E><<<n_tiles, kBondedBlock, 0, st>>>(x, site, inv_perm, flj, Npad, N, tiles, reps, fp, F, epart, flags)

@@ -240,6 +240,7 @@ __global__ void __launch_bounds__(NT) k_cl_build(const float4* __restrict__ pos,
 
 // ===================================================================== force
 constexpr int kEnergyVals = 8;   // lj, lj_shifted, vxx, vyy, vzz, vxy, vxz, vyz
+constexpr int kEnergyClusterCap = 512;   // clusters of one region the energy form can hold (2,048 home atoms)
 
 // FP32 force (cell units) -> fixed point 2^-13 kJ/mol/nm; F2I saturates
 // beyond +-2^31 (2^18 kJ/mol/nm), which the flush reports
@@ -259,8 +260,11 @@ __global__ void __launch_bounds__(NT, ENERGY ? 512 / NT : 768 / NT) k_cl_force(
   int* az = ay + tile_cap;
   __shared__ RegTile T;
   __shared__ int sh_r, sh_q;
-  __shared__ double red[kEnergyVals][NT / 32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // energy form: each cluster's 8 sums (FP32 lane tree), added over the
+  // region's clusters in cluster order, so the result does not depend on
+  // which warp took which cluster
+  __shared__ float ecl[ENERGY ? kEnergyClusterCap : 1][kEnergyVals];
+  const int lane = threadIdx.x & 31;
   for (int it = 0;; ++it) {
     const int r = next_region(persistent != 0, it, work, &sh_r);
     if (r < 0 || r >= n_regions) break;
@@ -270,8 +274,7 @@ __global__ void __launch_bounds__(NT, ENERGY ? 512 / NT : 768 / NT) k_cl_force(
     __syncthreads();
     region_setup(T, g, S, R, cell_start, cl_start);
     const int total = T.off[T.n_tile];
-    float ev[kEnergyVals] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    const bool fits = total <= tile_cap;
+    const bool fits = total <= tile_cap && (!ENERGY || T.ncl[T.n_home] <= kEnergyClusterCap);
     if (!fits) {
       if (threadIdx.x == 0) atomicOr(flags, kFlagNbrOverflow);
     } else {
@@ -309,6 +312,7 @@ __global__ void __launch_bounds__(NT, ENERGY ? 512 / NT : 768 / NT) k_cl_force(
         float fi[4][3];
 #pragma unroll
         for (int u = 0; u < 4; ++u) fi[u][0] = fi[u][1] = fi[u][2] = 0.f;
+        float ev[kEnergyVals] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         const int cl = T.cl0[h] + k;
         const int n = ncl[cl];
         const unsigned* L = list + (size_t)cl * cap;
@@ -362,6 +366,15 @@ __global__ void __launch_bounds__(NT, ENERGY ? 512 / NT : 768 / NT) k_cl_force(
             atomicAdd(ay + i0 + u, acc_fix(fi[u][1], scale));
             atomicAdd(az + i0 + u, acc_fix(fi[u][2], scale));
           }
+        if (ENERGY) {
+#pragma unroll
+          for (int a = 0; a < kEnergyVals; ++a) {
+            float v = ev[a];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (lane == 0) ecl[q][a] = v;
+          }
+        }
       }
       __syncthreads();
       // flush: one int64 atomic per component and tile atom with a non-zero sum
@@ -381,20 +394,14 @@ __global__ void __launch_bounds__(NT, ENERGY ? 512 / NT : 768 / NT) k_cl_force(
       }
     }
     if (ENERGY) {
-      // per region: FP32 warp trees, FP64 over the warps in order; the
-      // region's sums go to the slot of its first home cell, zeros to the
+      // per region: the clusters' FP32 sums added in FP64 in cluster order;
+      // the region's sums go to the slot of its first home cell, zeros to the
       // others (the reduction sums a replica's cell slots)
-#pragma unroll
-      for (int a = 0; a < kEnergyVals; ++a) {
-        float v = ev[a];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) red[a][warp] = (double)v;
-      }
       __syncthreads();
       if (threadIdx.x < kEnergyVals) {
         double v = 0.0;
-        for (int w = 0; w < NT / 32; ++w) v += red[threadIdx.x][w];
+        if (fits)
+          for (int q = 0; q < T.ncl[T.n_home]; ++q) v += (double)ecl[q][threadIdx.x];
         epart[(size_t)T.home_cell[0] * kEnergyVals + threadIdx.x] = v;
         for (int hh = 1; hh < T.n_home; ++hh) epart[(size_t)T.home_cell[hh] * kEnergyVals + threadIdx.x] = 0.0;
       }

@@ -367,6 +367,7 @@ static const int kRebinLaunches = 6;   // memset counted as a launch
 static void enqueue_forces(md_system* s, bool energy, void* F_out = nullptr) {
   // an energy read-out accumulates its LJ forces apart from the dynamics'
   long long* flj = F_out ? s->flj_e : s->flj;
+  cudaMemsetAsync(flj, 0, 3 * (size_t)s->Npad * sizeof(long long), s->st);
   launch_cl_force(energy, s->pos, s->cell_start, s->cl_start, s->regions, (int)s->regions_h.size(), s->shapes,
                   s->reps, s->list, s->ncl, s->cap, s->tile_cap, s->fp, flj, s->Npad, s->lj_part, s->flags,
                   s->lj_block, s->persistent_grid, s->work, s->st);
@@ -397,7 +398,7 @@ static void enqueue_block(md_system* s, int k, bool rebin = true) {
   }
   enqueue_integrate(s, kKickOnly, false);
 }
-static int64_t block_launches(int k) { return kRebinLaunches + 3LL * k + 1; }
+static int64_t block_launches(int k) { return kRebinLaunches + 4LL * k + 1; }   // memset counted as a launch
 
 // accumulate the event timings of the last block (requires a finished stream)
 static void prof_collect(md_system* s, int k) {

@@ -16,9 +16,9 @@
 //     tag        int32 [N]  chain*1024 + site | type << 30 (sites < 1024, so the
 //                site fields of two chains never come within 2 of each other)
 //     perm       int32 [N]  original index of slot s
-//     Flj        int64 SoA [3][Npad]  LJ force on slot s (2^-32 kJ/mol/nm),
-//                added to by the force kernel, read and cleared by the
-//                bonded kernel
+//     Flj        int64 SoA [3][Npad]  LJ force on slot s (2^-32 kJ/mol/nm):
+//                cleared, added to by the force kernel, read by the bonded
+//                kernel
 //   clusters (4 consecutive slots of a cell; cluster k of cell c is
 //   cl_start[c] + k):
 //     list       uint32 [clusters][cap]: tile index (bits 0..15) and the mask
@@ -237,7 +237,7 @@ void launch_cell_sort(bool mixed, const void* x, int N, const int* cell_start, c
 // cluster lists and LJ forces by regions (k_lj.cu).  The build writes each
 // cluster's list (up to cap entries, ncl[cl] of them); the force kernel adds
 // the LJ force of every atom into flj (int64 SoA [3][Npad], cleared by the
-// bonded kernel) and, with energy, the per-region energy and virial sums into
+// caller before) and, with energy, the per-region energy and virial sums into
 // epart (8 per cell).  persistent_grid > 0 runs that many blocks that take
 // regions from work[0..1] (two ints, zero before the first launch).
 void launch_cl_build(const float4* pos, const int* tag, const int* cell_start, const int* cl_start,
@@ -254,10 +254,10 @@ cudaError_t tile_kernels_init();
 int tile_capacity_max();
 // one block waits on an mbarrier nothing arrives on, `spins` rounds, then raises kFlagTimeout
 void launch_wait_selftest(unsigned spins, unsigned* flags, cudaStream_t st);
-// bonded forces plus the LJ force (read from flj[3][Npad] in sorted order,
-// then cleared) into F (original order)
+// bonded forces plus the LJ force (read from flj[3][Npad] in sorted order)
+// into F (original order)
 void launch_bonded(bool mixed, bool energy, const void* x, const uint16_t* site, const int* inv_perm,
-                   long long* flj, int Npad, int N, const Tile* tiles, int n_tiles, const RepDev* reps,
+                   const long long* flj, int Npad, int N, const Tile* tiles, int n_tiles, const RepDev* reps,
                    const ForceParams& fp, void* F, double* epart, unsigned* flags, cudaStream_t st);
 
 // ---------------------------------------------------------------- integration
