@@ -23,8 +23,9 @@
  * Errors: every int-returning function returns MD_OK (0) or a negative
  * MD_E* code; md_last_error() then holds a one-line message.  Device-side
  * conditions (neighbour-list overflow, fixed-point overflow, non-finite
- * state, displacement beyond skin/2) are raised on the GPU as flags and
- * reported by the next synchronising call (md_step, md_sync).  The library
+ * state) are raised on the GPU as flags and reported by the next
+ * synchronising call (md_step, md_sync).  A displacement beyond skin/2 is
+ * not an error: it triggers an extra rebuild (md_early_rebins).  The library
  * never traps or spins on the GPU.
  *
  * Threads: a system must not be used from two host threads at once.
@@ -45,7 +46,7 @@ enum {
   MD_ENOMEM = -2,      /* device allocation failed or workspace too small */
   MD_ECUDA = -3,       /* a CUDA call failed */
   MD_EOVERFLOW = -4,   /* neighbour-list capacity or fixed-point range exceeded */
-  MD_EUNSTABLE = -5,   /* non-finite state, or an atom moved more than skin/2 between rebins */
+  MD_EUNSTABLE = -5,   /* non-finite state */
   MD_ETIMEOUT = -6     /* a bounded device wait gave up */
 };
 
@@ -151,7 +152,12 @@ int md_create(const md_desc *desc, md_system **out);
 
 /* Advance n_steps time steps (velocity Verlet; Leap-Frog positions, Sec. 3.4).
  * The neighbour list is rebuilt at the start of every block of rebin_every
- * steps and of every call.  Synchronises and reports device flags. */
+ * steps and of every call (the paper rebuilds it every 10 steps, Sec. 5),
+ * and also before the force evaluation of any step in which an atom has
+ * moved more than skin/2 since the last rebuild (a device-side check that
+ * opens a conditional rebuild in the step graph; md_early_rebins counts
+ * them), so every force comes from a list that holds all pairs within rc.
+ * Synchronises and reports device flags. */
 int md_step(md_system *sys, int64_t n_steps);
 
 /* Same, without synchronising; flags are reported by the next md_sync. */
@@ -205,6 +211,41 @@ int md_set_temperature(md_system *sys, const double *T_target);
  * replicas; host or device pointers, any may be NULL.  Synchronous. */
 int md_observables(md_system *sys, double *r_ee, double *rg2, double *trans_fraction);
 
+/* Radial distribution function of non-bonded site pairs (Sec. 5, the RDF
+ * the paper compares with GROMACS): for every replica r, counts[r * n_bins +
+ * k] = the number of pairs i < j, other than 1-2 and 1-3 neighbours of a
+ * chain (Sec. 3.1), whose minimum-image distance lies in [edges[k],
+ * edges[k + 1]) (the last bin closed).  edges: [n_bins + 1] increasing, host
+ * pointer, edges[0] >= 0, edges[n_bins] = r_max at most the cell side (r_c +
+ * skin or more) of every replica; 1 <= n_bins <= 16384.  The distances are
+ * the FP64 definition (d = x_j - x_i, d -= L rint(d / L), r = sqrt(dx^2 +
+ * dy^2 + dz^2), each operation rounded once, left to right) on the state's
+ * positions, so the counts equal that definition's.  Re-bins the current
+ * positions first.  counts: host or device pointer, int64.  Allocates and
+ * frees two small device buffers.  Synchronous.  g(r) = counts / (n_pairs *
+ * shell volume / L^3) with n_pairs = N (N - 1) / 2 - n_chains (2 S - 3). */
+int md_rdf(md_system *sys, int32_t n_bins, const double *edges, int64_t *counts);
+
+/* End-to-end vector autocorrelation (Sec. 5, Fig. 8), accumulated on the GPU
+ * over samples: C_r(tau) = <R_c(t + tau) . R_c(t)> / <R_c(t) . R_c(t)>, the
+ * means over the chains c of replica r and every time origin t of the
+ * samples taken so far.  md_acf_reset(max_lag) starts over (0 <= max_lag <=
+ * 100000; allocates a ring of max_lag + 1 samples of 3 * n_chains doubles
+ * the first time, or when max_lag changes).  md_acf_sample adds the current
+ * state's end-to-end vectors (chains made continuous by minimum-image
+ * bonds, as md_observables) as the next sample (asynchronous); md_acf_push
+ * adds a given sample r_ee[3 * n_chains] (host or device pointer) instead
+ * (synchronous).  md_acf_read writes C[n_replicas * (max_lag + 1)] (NaN for
+ * lags with no pair of samples yet) and the number of samples. */
+int md_acf_reset(md_system *sys, int32_t max_lag);
+int md_acf_sample(md_system *sys);
+int md_acf_push(md_system *sys, const double *r_ee);
+int md_acf_read(md_system *sys, double *C, int64_t *n_samples);
+
+/* Number of rebuilds so far that the displacement check added (an atom
+ * moved more than skin/2 between scheduled rebuilds); synchronous. */
+int md_early_rebins(md_system *sys, int64_t *count);
+
 /* Nose-Hoover friction xi (1/ps) of each replica, [n_replicas]; zeros for
  * the other thermostats.  Synchronous. */
 int md_get_thermostat(md_system *sys, double *xi);
@@ -240,7 +281,8 @@ int md_profile_enable(md_system *sys, int32_t on);
 int md_profile_read(md_system *sys, double *ms_total, int64_t *launches);
 int md_profile_reset(md_system *sys);
 
-/* Kernel launches per call of md_step(n_steps) (all library kernels). */
+/* Kernel launches per call of md_step(n_steps) (all library kernels and
+ * memsets; an early rebuild adds six more). */
 int64_t md_launches_per_call(md_system *sys, int64_t n_steps);
 
 /* Cell binning of one periodic box into caller-provided DEVICE arrays, with

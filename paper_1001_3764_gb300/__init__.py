@@ -77,7 +77,8 @@ class md_energy_t(ctypes.Structure):
 
 
 EXPORTS = ["md_autotune", "md_workspace_size", "md_create", "md_step", "md_step_async", "md_sync", "md_forces", "md_energy",
-           "md_rebin", "md_get_state", "md_set_state", "md_set_params", "md_set_temperature", "md_get_thermostat", "md_observables", "md_stream",
+           "md_rebin", "md_get_state", "md_set_state", "md_set_params", "md_set_temperature", "md_get_thermostat", "md_observables", "md_rdf",
+           "md_acf_reset", "md_acf_sample", "md_acf_push", "md_acf_read", "md_early_rebins", "md_stream",
            "md_info", "md_get_bins", "md_get_neighbors", "md_get_cell_units", "md_profile_enable", "md_profile_read",
            "md_profile_reset", "md_launches_per_call", "md_bin_static", "md_destroy", "md_last_error",
            "md_adj_create", "md_adj_set_theta", "md_adj_forward", "md_adj_backward", "md_adj_tangent",
@@ -112,6 +113,12 @@ def load(path: str = LIB_PATH):
         "md_set_temperature": ([P, P], ctypes.c_int),
         "md_get_thermostat": ([P, P], ctypes.c_int),
         "md_observables": ([P, P, P, P], ctypes.c_int),
+        "md_rdf": ([P, i32, P, P], ctypes.c_int),
+        "md_acf_reset": ([P, i32], ctypes.c_int),
+        "md_acf_sample": ([P], ctypes.c_int),
+        "md_acf_push": ([P, P], ctypes.c_int),
+        "md_acf_read": ([P, P, P], ctypes.c_int),
+        "md_early_rebins": ([P, P], ctypes.c_int),
         "md_stream": ([P], P),
         "md_info": ([P, P, P, P, P], ctypes.c_int),
         "md_get_bins": ([P, P, P, P], ctypes.c_int),
@@ -457,6 +464,51 @@ class System:
         tf = np.zeros(self.n_replicas, np.float64)
         _check(load().md_observables(self.h, ree.ctypes.data, rg2.ctypes.data, tf.ctypes.data), self.h)
         return {"r_ee": ree, "rg2": rg2, "trans_fraction": tf}
+
+    def rdf(self, r_max: float, n_bins: int):
+        """Radial distribution function of non-bonded site pairs, computed on
+        the GPU (md_rdf): bin centres [n_bins], g(r) [n_replicas, n_bins] and
+        the integer pair counts [n_replicas, n_bins].  Bins are
+        numpy.linspace(0, r_max, n_bins + 1); g = counts / (n_pairs * shell /
+        L^3) with n_pairs = N (N - 1) / 2 - n_chains (2 S - 3) per replica."""
+        edges = np.linspace(0.0, float(r_max), int(n_bins) + 1)
+        counts = np.zeros((self.n_replicas, int(n_bins)), np.int64)
+        _check(load().md_rdf(self.h, int(n_bins), edges.ctypes.data, counts.ctypes.data), self.h)
+        shell = 4.0 / 3.0 * np.pi * (edges[1:] ** 3 - edges[:-1] ** 3)
+        g = np.zeros(counts.shape)
+        S = self.sites
+        for r in range(self.n_replicas):
+            n = int(self._n_chains[r]) * S
+            n_pairs = n * (n - 1) // 2 - int(self._n_chains[r]) * (2 * S - 3)
+            L = float(self._box[r])
+            g[r] = counts[r] / (n_pairs * shell / L ** 3)
+        return 0.5 * (edges[1:] + edges[:-1]), g, counts
+
+    def acf_reset(self, max_lag: int):
+        _check(load().md_acf_reset(self.h, int(max_lag)), self.h)
+        self._acf_lag = int(max_lag)
+
+    def acf_sample(self):
+        """Add the current end-to-end vectors as the next ACF sample (GPU)."""
+        _check(load().md_acf_sample(self.h), self.h)
+
+    def acf_push(self, r_ee):
+        """Add a given sample of end-to-end vectors [n_chains, 3]."""
+        r = np.ascontiguousarray(r_ee, np.float64).reshape(-1, 3)
+        _check(load().md_acf_push(self.h, r.ctypes.data), self.h)
+
+    def acf(self):
+        """(C [n_replicas, max_lag + 1], number of samples)."""
+        C = np.zeros((self.n_replicas, self._acf_lag + 1), np.float64)
+        n = ctypes.c_int64(0)
+        _check(load().md_acf_read(self.h, C.ctypes.data, ctypes.byref(n)), self.h)
+        return C, int(n.value)
+
+    def early_rebins(self) -> int:
+        """Rebuilds added by the displacement check so far."""
+        n = ctypes.c_int64(0)
+        _check(load().md_early_rebins(self.h, ctypes.byref(n)), self.h)
+        return int(n.value)
 
     def thermostat_xi(self) -> np.ndarray:
         """Nose-Hoover friction xi (1/ps) of each replica (zeros for the

@@ -286,6 +286,28 @@ void launch_integrate(bool mixed, IntegMode mode, bool ke, int thermostat, void*
                         n_reps, fp, kepart, done, ke_out, lam, tau, flags, st);
 }
 
+// ---------------------------------------------------------------- early rebin
+// After a drift: if an atom has moved more than skin/2 since the rebin (the
+// integrator raised kFlagDisplacement), open the conditional rebin that
+// follows in the step graph, clear the flag (the new bins reset the
+// reference) and count the event; else keep it closed.  One thread, so the
+// condition is set once.
+__global__ void __launch_bounds__(32) k_disp_check(cudaGraphConditionalHandle h, unsigned* __restrict__ flags,
+                                                   unsigned long long* __restrict__ events) {
+  if (threadIdx.x != 0) return;
+  const unsigned f = *(volatile unsigned*)flags;
+  const bool moved = (f & kFlagDisplacement) != 0u;
+  if (moved) {
+    atomicAnd(flags, ~kFlagDisplacement);
+    *events += 1ull;
+  }
+  cudaGraphSetConditional(h, moved ? 1u : 0u);
+}
+
+void launch_disp_check(cudaGraphConditionalHandle h, unsigned* flags, unsigned long long* events, cudaStream_t st) {
+  k_disp_check<<<1, 32, 0, st>>>(h, flags, events);
+}
+
 // ---------------------------------------------------------------- energy reduction
 // LJ partials are per cell (replica r owns cells [cell_base, cell_base + M^3)),
 // bonded partials per integrator tile.  Fixed summation order.

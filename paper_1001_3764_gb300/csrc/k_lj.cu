@@ -37,6 +37,7 @@ namespace mdg {
 
 constexpr int kStageCapMax = 6144;      // largest tile (atoms); list entries keep the tile index in 16 bits
 constexpr int kLjAccShift = 19;         // 2^-13 accumulators -> 2^-32 fixed point
+constexpr int kLanesPerCluster = 16;    // lanes that share one cluster's list in the force kernel
 constexpr float kLjAccScale = 8192.0f;  // 2^13
 
 __device__ __forceinline__ float rcp_approx(float x) {
@@ -239,20 +240,31 @@ __global__ void __launch_bounds__(NT) k_cl_build(const float4* __restrict__ pos,
 }
 
 // ===================================================================== force
-constexpr int kEnergyVals = 8;   // lj, lj_shifted, vxx, vyy, vzz, vxy, vxz, vyz
-constexpr int kEnergyClusterCap = 512;   // clusters of one region the energy form can hold (2,048 home atoms)
+constexpr int kEnergyVals = 8;           // lj, lj_shifted, vxx, vyy, vzz, vxy, vxz, vyz
+constexpr int kRegionClusterCap = 512;   // clusters of one region (2,048 home atoms); more is reported
 
 // FP32 force (cell units) -> fixed point 2^-13 kJ/mol/nm; F2I saturates
-// beyond +-2^31 (2^18 kJ/mol/nm), which the flush reports
-__device__ __forceinline__ int acc_fix(float f, float scale) { return __float2int_rn(f * scale); }
+// beyond +-2^31 (2^18 kJ/mol/nm)
+__device__ __forceinline__ int acc_fix(float f) { return __float2int_rn(f); }
 
-template <bool ENERGY, int NT>
+// a converted sum far from the int32 range (or not finite) is reported
+__device__ __forceinline__ void range_check(float sx, float sy, float sz, unsigned* flags) {
+  const float a = fabsf(sx) + fabsf(sy) + fabsf(sz);
+  if (!(a < 1.0e9f)) atomicOr(flags, (a == a && a <= 3.4e38f) ? kFlagFixOverflow : kFlagNaN);
+}
+
+// Lanes per cluster LP: a warp works on 32 / LP clusters at once (adjacent
+// clusters of the region, handed out to warps as they free up); lane l of a
+// cluster's group takes entries l, l + LP, ...  The warp's trip count is that
+// of its longest cluster; a lane past its own list idles.
+template <bool ENERGY, int NT, int LP>
 __global__ void __launch_bounds__(NT, ENERGY ? 512 / NT : 768 / NT) k_cl_force(
     const float4* __restrict__ pos, const int* __restrict__ cell_start, const int* __restrict__ cl_start,
     const Region* __restrict__ regions, int n_regions, const RegionShape* __restrict__ shapes,
     const RepDev* __restrict__ reps, const unsigned* __restrict__ list, const int* __restrict__ ncl, int cap,
     int tile_cap, const ForceParams fp, long long* __restrict__ flj, int Npad, double* __restrict__ epart,
     unsigned* __restrict__ flags, int persistent, int* __restrict__ work) {
+  constexpr int CPW = 32 / LP;
   extern __shared__ __align__(16) unsigned char smem[];
   float4* sp = reinterpret_cast<float4*>(smem);
   int* ax = reinterpret_cast<int*>(smem + (size_t)tile_cap * sizeof(float4));
@@ -260,11 +272,12 @@ __global__ void __launch_bounds__(NT, ENERGY ? 512 / NT : 768 / NT) k_cl_force(
   int* az = ay + tile_cap;
   __shared__ RegTile T;
   __shared__ int sh_r, sh_q;
+  __shared__ int s_ncl[kRegionClusterCap];     // list length of each of the region's clusters
   // energy form: each cluster's 8 sums (FP32 lane tree), added over the
   // region's clusters in cluster order, so the result does not depend on
   // which warp took which cluster
-  __shared__ float ecl[ENERGY ? kEnergyClusterCap : 1][kEnergyVals];
-  const int lane = threadIdx.x & 31;
+  __shared__ float ecl[ENERGY ? kRegionClusterCap : 1][kEnergyVals];
+  const int lane = threadIdx.x & 31, sub = lane / LP, sl = lane % LP;
   for (int it = 0;; ++it) {
     const int r = next_region(persistent != 0, it, work, &sh_r);
     if (r < 0 || r >= n_regions) break;
@@ -274,36 +287,51 @@ __global__ void __launch_bounds__(NT, ENERGY ? 512 / NT : 768 / NT) k_cl_force(
     __syncthreads();
     region_setup(T, g, S, R, cell_start, cl_start);
     const int total = T.off[T.n_tile];
-    const bool fits = total <= tile_cap && (!ENERGY || T.ncl[T.n_home] <= kEnergyClusterCap);
+    const int nq = T.ncl[T.n_home];
+    const bool fits = total <= tile_cap && nq <= kRegionClusterCap;
     if (!fits) {
       if (threadIdx.x == 0) atomicOr(flags, kFlagNbrOverflow);
     } else {
       tile_load<false>(T, pos, nullptr, sp, nullptr);
       for (int t = threadIdx.x; t < total; t += NT) { ax[t] = 0; ay[t] = 0; az[t] = 0; }
+      for (int q = threadIdx.x; q < nq; q += NT) {
+        int h, k;
+        cluster_of(T, q, h, k);
+        s_ncl[q] = __ldg(ncl + T.cl0[h] + k);
+      }
       if (threadIdx.x == 0) sh_q = 0;
       __syncthreads();
       const float rc2 = R.rc2u;
       const float scale = R.ih_hi * kLjAccScale;     // cell-unit force -> 2^-13 kJ/mol/nm
-      const int nq = T.ncl[T.n_home];
+      // pair coefficients by type sum (0: C32-C32, 1: C32-C33, 2: C33-C33)
+      const float A0 = 12.f * R.C12u[0], A1 = 12.f * R.C12u[1], A2 = 12.f * R.C12u[2];
+      const float B0 = 6.f * R.C6u[0], B1 = 6.f * R.C6u[1], B2 = 6.f * R.C6u[2];
       for (;;) {
-        int q = 0;
-        if (lane == 0) q = atomicAdd(&sh_q, 1);      // clusters handed out to warps as they free up
-        q = __shfl_sync(0xffffffffu, q, 0);
-        if (q >= nq) break;
+        int q0 = 0;
+        if (lane == 0) q0 = atomicAdd(&sh_q, CPW);
+        q0 = __shfl_sync(0xffffffffu, q0, 0);
+        if (q0 >= nq) break;
+        const int q = q0 + sub;
+        const bool valid = q < nq;
         int h, k;
-        cluster_of(T, q, h, k);
+        cluster_of(T, valid ? q : nq - 1, h, k);
         const int i0 = T.off[h] + 4 * k;
-        const int ni = min(4, T.off[h + 1] - i0);
+        const int ni = valid ? min(4, T.off[h + 1] - i0) : 0;
+        const int n = valid ? s_ncl[q] : 0;
+        int nmax = n;
+#pragma unroll
+        for (int o = LP; o < 32; o <<= 1) nmax = max(nmax, __shfl_xor_sync(0xffffffffu, nmax, o));
         float4 pi[4];
         float a0[4], da[4], b0[4], db[4];
         float ec[4][6];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          pi[u] = sp[i0 + min(u, ni - 1)];
-          const int ti = (int)pi[u].w;
-          a0[u] = 12.f * R.C12u[ti]; da[u] = 12.f * R.C12u[ti + 1] - a0[u];
-          b0[u] = 6.f * R.C6u[ti]; db[u] = 6.f * R.C6u[ti + 1] - b0[u];
+          pi[u] = sp[i0 + max(0, min(u, ni - 1))];
+          const bool t3 = pi[u].w != 0.f;           // the atom is a C_33 chain end
+          a0[u] = t3 ? A1 : A0; da[u] = t3 ? A2 - A1 : A1 - A0;
+          b0[u] = t3 ? B1 : B0; db[u] = t3 ? B2 - B1 : B1 - B0;
           if (ENERGY) {
+            const int ti = t3 ? 1 : 0;
             ec[u][0] = R.C12u[ti]; ec[u][1] = R.C12u[ti + 1] - ec[u][0];
             ec[u][2] = R.C6u[ti]; ec[u][3] = R.C6u[ti + 1] - ec[u][2];
             ec[u][4] = fp.erc[ti][0]; ec[u][5] = fp.erc[ti][1] - ec[u][4];
@@ -313,84 +341,91 @@ __global__ void __launch_bounds__(NT, ENERGY ? 512 / NT : 768 / NT) k_cl_force(
 #pragma unroll
         for (int u = 0; u < 4; ++u) fi[u][0] = fi[u][1] = fi[u][2] = 0.f;
         float ev[kEnergyVals] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        const int cl = T.cl0[h] + k;
-        const int n = ncl[cl];
-        const unsigned* L = list + (size_t)cl * cap;
-        unsigned E = lane < n ? __ldg(L + lane) : 0u;
-        for (int e = lane; e < n; e += 32) {
-          const unsigned En = e + 32 < n ? __ldg(L + e + 32) : 0u;    // next entry in flight
-          const int t = (int)(E & 0xffffu);
-          const unsigned m = E >> 16;
-          const float4 w = sp[t];
-          float gx = 0.f, gy = 0.f, gz = 0.f;
+        const unsigned* L = list + (size_t)(valid ? T.cl0[h] + k : 0) * cap;
+        // entries two iterations ahead in flight
+        unsigned E0 = sl < n ? __ldg(L + sl) : 0u;
+        unsigned E1 = sl + LP < n ? __ldg(L + sl + LP) : 0u;
+        for (int e = sl; e - sl < nmax; e += LP) {
+          const unsigned E2 = e + 2 * LP < n ? __ldg(L + e + 2 * LP) : 0u;
+          if (e < n) {
+            const int t = (int)(E0 & 0xffffu);
+            const unsigned m = E0 >> 16;
+            const float4 w = sp[t];
+            float gx = 0.f, gy = 0.f, gz = 0.f;
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const float dx = pi[u].x - w.x, dy = pi[u].y - w.y, dz = pi[u].z - w.z;
-            const float r2 = dx * dx + dy * dy + dz * dz;
-            const bool keep = ((m >> u) & 1u) && r2 < rc2;
-            const float ir2 = keep ? rcp_approx(r2) : 0.f;
-            const float ir6 = ir2 * ir2 * ir2;
-            const float A = fmaf(w.w, da[u], a0[u]), B = fmaf(w.w, db[u], b0[u]);
-            const float ff = ir2 * ir6 * (A * ir6 - B);
-            fi[u][0] = fmaf(ff, dx, fi[u][0]);
-            fi[u][1] = fmaf(ff, dy, fi[u][1]);
-            fi[u][2] = fmaf(ff, dz, fi[u][2]);
-            gx = fmaf(-ff, dx, gx);
-            gy = fmaf(-ff, dy, gy);
-            gz = fmaf(-ff, dz, gz);
-            if (ENERGY) {
-              const float c12 = fmaf(w.w, ec[u][1], ec[u][0]), c6 = fmaf(w.w, ec[u][3], ec[u][2]);
-              const float eij = ir6 * (c12 * ir6 - c6);
-              ev[0] += eij;
-              ev[1] += eij - (keep ? fmaf(w.w, ec[u][5], ec[u][4]) : 0.f);
-              ev[2] += dx * dx * ff; ev[3] += dy * dy * ff; ev[4] += dz * dz * ff;
-              ev[5] += dx * dy * ff; ev[6] += dx * dz * ff; ev[7] += dy * dz * ff;
+            for (int u = 0; u < 4; ++u) {
+              const float dx = pi[u].x - w.x, dy = pi[u].y - w.y, dz = pi[u].z - w.z;
+              const float r2 = dx * dx + dy * dy + dz * dz;
+              const bool keep = ((m >> u) & 1u) && r2 < rc2;
+              const float ir2 = keep ? rcp_approx(r2) : 0.f;
+              const float ir6 = ir2 * ir2 * ir2;
+              const float A = fmaf(w.w, da[u], a0[u]), B = fmaf(w.w, db[u], b0[u]);
+              const float ff = ir2 * ir6 * (A * ir6 - B);
+              fi[u][0] = fmaf(ff, dx, fi[u][0]);
+              fi[u][1] = fmaf(ff, dy, fi[u][1]);
+              fi[u][2] = fmaf(ff, dz, fi[u][2]);
+              gx = fmaf(-ff, dx, gx);
+              gy = fmaf(-ff, dy, gy);
+              gz = fmaf(-ff, dz, gz);
+              if (ENERGY) {
+                const float c12 = fmaf(w.w, ec[u][1], ec[u][0]), c6 = fmaf(w.w, ec[u][3], ec[u][2]);
+                const float eij = ir6 * (c12 * ir6 - c6);
+                ev[0] += eij;
+                ev[1] += eij - (keep ? fmaf(w.w, ec[u][5], ec[u][4]) : 0.f);
+                ev[2] += dx * dx * ff; ev[3] += dy * dy * ff; ev[4] += dz * dz * ff;
+                ev[5] += dx * dy * ff; ev[6] += dx * dz * ff; ev[7] += dy * dz * ff;
+              }
             }
+            gx *= scale; gy *= scale; gz *= scale;
+            range_check(gx, gy, gz, flags);
+            atomicAdd(ax + t, acc_fix(gx));
+            atomicAdd(ay + t, acc_fix(gy));
+            atomicAdd(az + t, acc_fix(gz));
           }
-          atomicAdd(ax + t, acc_fix(gx, scale));
-          atomicAdd(ay + t, acc_fix(gy, scale));
-          atomicAdd(az + t, acc_fix(gz, scale));
-          E = En;
+          E0 = E1;
+          E1 = E2;
         }
-        // forces on the cluster's atoms: fixed butterfly over the 32 lanes
+        // forces on the cluster's atoms: fixed butterfly over the LP lanes
 #pragma unroll
         for (int u = 0; u < 4; ++u)
 #pragma unroll
           for (int a = 0; a < 3; ++a)
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) fi[u][a] += __shfl_xor_sync(0xffffffffu, fi[u][a], o);
+            for (int o = LP / 2; o > 0; o >>= 1) fi[u][a] += __shfl_xor_sync(0xffffffffu, fi[u][a], o);
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-          if (lane == u && u < ni) {
-            atomicAdd(ax + i0 + u, acc_fix(fi[u][0], scale));
-            atomicAdd(ay + i0 + u, acc_fix(fi[u][1], scale));
-            atomicAdd(az + i0 + u, acc_fix(fi[u][2], scale));
+          if (sl == u && u < ni) {
+            const float sx = fi[u][0] * scale, sy = fi[u][1] * scale, sz = fi[u][2] * scale;
+            range_check(sx, sy, sz, flags);
+            atomicAdd(ax + i0 + u, acc_fix(sx));
+            atomicAdd(ay + i0 + u, acc_fix(sy));
+            atomicAdd(az + i0 + u, acc_fix(sz));
           }
         if (ENERGY) {
 #pragma unroll
           for (int a = 0; a < kEnergyVals; ++a) {
             float v = ev[a];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-            if (lane == 0) ecl[q][a] = v;
+            for (int o = LP / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (sl == 0 && valid) ecl[q][a] = v;
           }
         }
       }
       __syncthreads();
-      // flush: one int64 atomic per component and tile atom with a non-zero sum
-      for (int t = threadIdx.x; t < total; t += NT) {
-        const int qx = ax[t], qy = ay[t], qz = az[t];
-        if ((qx | qy | qz) == 0) continue;
-        int kc = 0;
-        while (kc + 1 < T.n_tile && T.off[kc + 1] <= t) ++kc;
-        const int s = T.start[kc] + (t - T.off[kc]);
-        if (qx >= (1 << 30) || qx <= -(1 << 30) || qy >= (1 << 30) || qy <= -(1 << 30) || qz >= (1 << 30) ||
-            qz <= -(1 << 30))
-          atomicOr(flags, kFlagFixOverflow);
-        atomicAdd(reinterpret_cast<unsigned long long*>(flj + s), (unsigned long long)((long long)qx << kLjAccShift));
-        atomicAdd(reinterpret_cast<unsigned long long*>(flj + Npad + s), (unsigned long long)((long long)qy << kLjAccShift));
-        atomicAdd(reinterpret_cast<unsigned long long*>(flj + 2 * (size_t)Npad + s),
-                  (unsigned long long)((long long)qz << kLjAccShift));
+      // flush, warp per tile cell: one int64 atomic per component and tile
+      // atom with a non-zero sum (consecutive atoms: coalesced)
+      for (int kc = threadIdx.x >> 5; kc < T.n_tile; kc += NT / 32) {
+        const int t0 = T.off[kc], nk = T.off[kc + 1] - t0, s0 = T.start[kc];
+        for (int q = lane; q < nk; q += 32) {
+          const int t = t0 + q, sidx = s0 + q;
+          const int qx = ax[t], qy = ay[t], qz = az[t];
+          if ((qx | qy | qz) == 0) continue;
+          atomicAdd(reinterpret_cast<unsigned long long*>(flj + sidx), (unsigned long long)((long long)qx << kLjAccShift));
+          atomicAdd(reinterpret_cast<unsigned long long*>(flj + Npad + sidx),
+                    (unsigned long long)((long long)qy << kLjAccShift));
+          atomicAdd(reinterpret_cast<unsigned long long*>(flj + 2 * (size_t)Npad + sidx),
+                    (unsigned long long)((long long)qz << kLjAccShift));
+        }
       }
     }
     if (ENERGY) {
@@ -401,7 +436,7 @@ __global__ void __launch_bounds__(NT, ENERGY ? 512 / NT : 768 / NT) k_cl_force(
       if (threadIdx.x < kEnergyVals) {
         double v = 0.0;
         if (fits)
-          for (int q = 0; q < T.ncl[T.n_home]; ++q) v += (double)ecl[q][threadIdx.x];
+          for (int q = 0; q < nq; ++q) v += (double)ecl[q][threadIdx.x];
         epart[(size_t)T.home_cell[0] * kEnergyVals + threadIdx.x] = v;
         for (int hh = 1; hh < T.n_home; ++hh) epart[(size_t)T.home_cell[hh] * kEnergyVals + threadIdx.x] = 0.0;
       }
@@ -435,7 +470,7 @@ void launch_cl_force(bool energy, const float4* pos, const int* cell_start, cons
   const size_t sm = cl_force_smem(tile_cap);
   const int pers = persistent_grid > 0;
 #define MDG_CLF(E, NT)                                                                                            \
-  k_cl_force<E, NT><<<grid, NT, sm, st>>>(pos, cell_start, cl_start, regions, n_regions, shapes, reps, list, ncl, \
+  k_cl_force<E, NT, kLanesPerCluster><<<grid, NT, sm, st>>>(pos, cell_start, cl_start, regions, n_regions, shapes, reps, list, ncl, \
                                           cap, tile_cap, fp, flj, Npad, epart, flags, pers, work)
   if (block == 128) {
     if (energy) MDG_CLF(true, 128); else MDG_CLF(false, 128);
@@ -450,9 +485,9 @@ int lj_blocks_per_sm(int block, int tile_cap) {
   int nb = 0;
   const size_t sm = cl_force_smem(tile_cap);
   if (block == 128)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cl_force<false, 128>, 128, sm);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cl_force<false, 128, kLanesPerCluster>, 128, sm);
   else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cl_force<false, 256>, 256, sm);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cl_force<false, 256, kLanesPerCluster>, 256, sm);
   return nb;
 }
 
@@ -461,10 +496,10 @@ int lj_blocks_per_sm(int block, int tile_cap) {
 cudaError_t tile_kernels_init() {
   const int mb = (int)cl_build_smem(kStageCapMax), mf = (int)cl_force_smem(kStageCapMax);
   cudaError_t e = cudaFuncSetAttribute(k_cl_build<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, mb);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cl_force<false, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, mf);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cl_force<true, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, mf);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cl_force<false, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, mf);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cl_force<true, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, mf);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cl_force<false, 128, kLanesPerCluster>, cudaFuncAttributeMaxDynamicSharedMemorySize, mf);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cl_force<true, 128, kLanesPerCluster>, cudaFuncAttributeMaxDynamicSharedMemorySize, mf);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cl_force<false, 256, kLanesPerCluster>, cudaFuncAttributeMaxDynamicSharedMemorySize, mf);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cl_force<true, 256, kLanesPerCluster>, cudaFuncAttributeMaxDynamicSharedMemorySize, mf);
   return e;
 }
 

@@ -76,8 +76,8 @@ __global__ void __launch_bounds__(kRdfThreads) k_rdf(const T* __restrict__ x, in
         d2 = ax == 0 ? __dmul_rn(d, d) : __dadd_rn(d2, __dmul_rn(d, d));
       }
       const double rr = __dsqrt_rn(d2);
-      if (!(rr <= r_max)) continue;
-      int k = (int)(rr * norm);
+      if (!(rr <= r_max) || rr < edges[0]) continue;
+      int k = (int)((rr - edges[0]) * norm);
       k = k < 0 ? 0 : (k > n_bins - 1 ? n_bins - 1 : k);
       if (rr < edges[k]) --k;
       else if (k < n_bins - 1 && rr >= edges[k + 1]) ++k;

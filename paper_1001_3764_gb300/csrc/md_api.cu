@@ -78,11 +78,18 @@ struct md_system {
   int max_slices = 1;
   double* stage = nullptr;                   // input staging (6N doubles)
   unsigned *done = nullptr, *flags = nullptr;
+  // end-to-end vector ACF (allocated by md_acf_reset)
+  double *acf_ring = nullptr, *acf_acc = nullptr;
+  int acf_lag = -1;
+  int64_t acf_n = 0;
   // execution
   cudaStream_t st = nullptr;
   bool own_stream = false;
   cudaGraphExec_t cycle = nullptr;
   cudaGraphExec_t cycle_fresh = nullptr;     // the same cycle without its leading rebin + list
+  std::vector<cudaGraphExec_t> rem_graphs;   // blocks of k < R steps (remainders), captured on first use
+  cudaStream_t side = nullptr;               // captures the bodies of the conditional rebins
+  unsigned long long* early = nullptr;       // early rebins (displacement beyond skin/2) so far
   bool fresh = false;                        // bins, list and forces are those of the current positions
   bool profile = false;
   std::vector<cudaEvent_t> ev;
@@ -329,6 +336,7 @@ static size_t plan(md_system* s, char* base) {
   s->done = (unsigned*)take(sizeof(unsigned));
   s->work = (int*)take(2 * sizeof(int));
   s->flags = (unsigned*)take(sizeof(unsigned));
+  s->early = (unsigned long long*)take(sizeof(unsigned long long));
   s->stage = (double*)take(6 * N * sizeof(double) + 3 * N * sizeof(int));   // staging: x, v (FP64), images
   return off;
 }
@@ -368,6 +376,7 @@ static void enqueue_forces(md_system* s, bool energy, void* F_out = nullptr) {
   // an energy read-out accumulates its LJ forces apart from the dynamics'
   long long* flj = F_out ? s->flj_e : s->flj;
   cudaMemsetAsync(flj, 0, 3 * (size_t)s->Npad * sizeof(long long), s->st);
+  prof_mark(s);   // closes the integrate group (integrator, displacement check, clear)
   launch_cl_force(energy, s->pos, s->cell_start, s->cl_start, s->regions, (int)s->regions_h.size(), s->shapes,
                   s->reps, s->list, s->ncl, s->cap, s->tile_cap, s->fp, flj, s->Npad, s->lj_part, s->flags,
                   s->lj_block, s->persistent_grid, s->work, s->st);
@@ -377,11 +386,53 @@ static void enqueue_forces(md_system* s, bool energy, void* F_out = nullptr) {
   prof_mark(s);
 }
 
-static void enqueue_integrate(md_system* s, IntegMode mode, bool ke) {
+// Inside a step-graph capture, after a drift: a one-thread check of the
+// displacement flag sets the condition of an IF node whose body re-bins and
+// rebuilds the list, so a step whose atoms moved more than skin/2 since the
+// last rebin computes its forces from fresh bins (and is counted), instead of
+// the run stopping.  No-op outside a capture.
+static void enqueue_cond_rebin(md_system* s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  const cudaGraphEdgeData* ed = nullptr;
+  size_t nd = 0;
+  if (cudaStreamGetCaptureInfo(s->st, &cs, nullptr, &g, &deps, &ed, &nd) != cudaSuccess ||
+      cs != cudaStreamCaptureStatusActive)
+    return;
+  cudaGraphConditionalHandle h;
+  if (cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault) != cudaSuccess) return;
+  launch_disp_check(h, s->flags, s->early, s->st);
+  if (cudaStreamGetCaptureInfo(s->st, &cs, nullptr, &g, &deps, &ed, &nd) != cudaSuccess) return;
+  cudaGraphNodeParams p{};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = h;
+  p.conditional.type = cudaGraphCondTypeIf;
+  p.conditional.size = 1;
+  cudaGraphNode_t node;
+  if (cudaGraphAddNode(&node, g, deps, ed, nd, &p) != cudaSuccess) return;
+  cudaGraph_t body = p.conditional.phGraph_out[0];
+  if (cudaStreamUpdateCaptureDependencies(s->st, &node, nullptr, 1, cudaStreamSetCaptureDependencies) != cudaSuccess)
+    return;
+  // the body: the rebin sequence, captured on the side stream
+  if (cudaStreamBeginCaptureToGraph(s->side, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    return;
+  cudaStream_t main = s->st;
+  const bool prof = s->profile;
+  s->st = s->side;
+  s->profile = false;
+  enqueue_rebin(s);
+  s->st = main;
+  s->profile = prof;
+  cudaGraph_t out = nullptr;
+  cudaStreamEndCapture(s->side, &out);
+}
+
+static void enqueue_integrate(md_system* s, IntegMode mode, bool ke, bool mark) {
   launch_integrate(s->mixed, mode, ke, s->thermo, s->x, s->v, s->img, s->F, s->site, s->cellc,
                    s->inv_perm, s->ref, s->pos, (int)s->N, s->tiles_int, (int)s->t_int.size(), s->reps, s->n_reps,
                    s->fp, s->kepart, s->done, s->ke_out, s->lam, s->tau, s->flags, s->st);
-  prof_mark(s);
+  if (mark) prof_mark(s);
 }
 
 // one block of k steps: rebin + list (unless the bins and list are already
@@ -390,15 +441,19 @@ static void enqueue_block(md_system* s, int k, bool rebin = true) {
   s->ev_used = 0;
   prof_mark(s);
   if (rebin) enqueue_rebin(s);
-  enqueue_integrate(s, kKickDrift, false);
+  enqueue_integrate(s, kKickDrift, false, false);
+  enqueue_cond_rebin(s);
   enqueue_forces(s, false);
   for (int j = 1; j < k; ++j) {
-    enqueue_integrate(s, kKickKickDrift, false);
+    enqueue_integrate(s, kKickKickDrift, false, false);
+    enqueue_cond_rebin(s);
     enqueue_forces(s, false);
   }
-  enqueue_integrate(s, kKickOnly, false);
+  enqueue_integrate(s, kKickOnly, false, true);
 }
-static int64_t block_launches(int k) { return kRebinLaunches + 4LL * k + 1; }   // memset counted as a launch
+// per step: integrate, displacement check, memset, LJ, bonded (a memset
+// counted as a launch; an early rebin adds kRebinLaunches)
+static int64_t block_launches(int k) { return kRebinLaunches + 5LL * k + 1; }
 
 // accumulate the event timings of the last block (requires a finished stream)
 static void prof_collect(md_system* s, int k) {
@@ -419,9 +474,29 @@ static void prof_collect(md_system* s, int k) {
 // the rebin cycle as a graph, and the same without its leading rebin + list
 // (used for the first cycle after md_set_state / md_rebin, which just did
 // them; never while profiling, so that the event layout stays fixed)
+static void drop_rem_graphs(md_system* s) {
+  for (cudaGraphExec_t& e : s->rem_graphs)
+    if (e) { cudaGraphExecDestroy(e); e = nullptr; }
+}
+
+// a block of k steps (leading rebin included) as a graph
+static int capture_block(md_system* s, int k, cudaGraphExec_t* out) {
+  cudaGraph_t g;
+  CU(cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal));
+  enqueue_block(s, k, true);
+  cudaError_t e = cudaStreamEndCapture(s->st, &g);
+  if (e != cudaSuccess) return fail(s, MD_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(s, MD_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  return MD_OK;
+}
+
 static int capture_cycle(md_system* s) {
   if (s->cycle) { cudaGraphExecDestroy(s->cycle); s->cycle = nullptr; }
   if (s->cycle_fresh) { cudaGraphExecDestroy(s->cycle_fresh); s->cycle_fresh = nullptr; }
+  drop_rem_graphs(s);
+  s->rem_graphs.assign(s->R, nullptr);
   for (int pass = 0; pass < 2; ++pass) {
     const bool prof = s->profile;
     if (pass == 1) s->profile = false;
@@ -527,6 +602,10 @@ int md_create(const md_desc* d, md_system** out) {
     }
     s->own_stream = true;
   }
+  if (cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking) != cudaSuccess) {
+    fail(s, MD_ECUDA, "stream creation failed");
+    return bail(MD_ECUDA);
+  }
   if (tile_kernels_init() != cudaSuccess) {
     cudaGetLastError();
     fail(s, MD_ECUDA, "cannot reserve shared memory for the neighbour-tile kernels");
@@ -566,6 +645,7 @@ int md_create(const md_desc* d, md_system** out) {
             cudaMemsetAsync(s->done, 0, sizeof(unsigned), s->st) == cudaSuccess &&
             cudaMemsetAsync(s->work, 0, 2 * sizeof(int), s->st) == cudaSuccess &&
             cudaMemsetAsync(s->flags, 0, sizeof(unsigned), s->st) == cudaSuccess &&
+            cudaMemsetAsync(s->early, 0, sizeof(unsigned long long), s->st) == cudaSuccess &&
             cudaStreamSynchronize(s->st) == cudaSuccess;
   if (!ok) { fail(s, MD_ECUDA, "initial upload failed"); return bail(MD_ECUDA); }
   rc = upload_state(s, d->pos, d->vel);
@@ -593,8 +673,13 @@ int md_step_async(md_system* s, int64_t n) {
   }
   if (rem) {
     s->fresh = false;
-    enqueue_block(s, (int)rem);
-    CU(cudaGetLastError());
+    cudaGraphExec_t& gr = s->rem_graphs[rem];
+    if (!gr) {
+      const int rc = capture_block(s, (int)rem, &gr);
+      if (rc) return rc;
+    }
+    if (s->profile) s->ev_used = (int)std::min<int64_t>(s->ev.size(), 3 + 3 * rem + 1);
+    CU(cudaGraphLaunch(gr, s->st));
     if (s->profile) { CU(cudaStreamSynchronize(s->st)); prof_collect(s, (int)rem); }
   }
   return MD_OK;
@@ -736,6 +821,135 @@ int md_observables(md_system* s, double* r_ee, double* rg2, double* trans_fracti
       const double nd = (double)s->reps_h[r].n_chains * (double)(s->S > 3 ? s->S - 3 : 0);
       trans_fraction[r] = nd > 0 ? (double)tr[r] / nd : 0.0;
     }
+  return MD_OK;
+}
+
+int md_rdf(md_system* s, int32_t n_bins, const double* edges, int64_t* counts) {
+  if (!s || !edges || !counts || n_bins < 1 || n_bins > 16384) return fail(s, MD_EINVAL, "bad arguments (1 <= n_bins <= 16384)");
+  if (!(edges[0] >= 0.0)) return fail(s, MD_EINVAL, "edges[0] must be >= 0");
+  for (int k = 0; k < n_bins; ++k)
+    if (!(edges[k + 1] > edges[k])) return fail(s, MD_EINVAL, "edges must increase");
+  for (const RepDev& q : s->reps_h)
+    if (edges[n_bins] > q.h) return fail(s, MD_EINVAL, "r_max beyond the cell side of a replica");
+  double* ed = nullptr;
+  unsigned long long* cnt = nullptr;
+  const size_t nc = (size_t)s->n_reps * n_bins;
+  if (cudaMalloc(&ed, sizeof(double) * (n_bins + 1)) != cudaSuccess ||
+      cudaMalloc(&cnt, sizeof(unsigned long long) * nc) != cudaSuccess) {
+    cudaGetLastError();
+    if (ed) cudaFree(ed);
+    return fail(s, MD_ENOMEM, "device memory for the histogram");
+  }
+  int rc = MD_OK;
+  // bins of the current positions (the last rebin's may be up to skin/2 old)
+  const bool p = s->profile;
+  s->profile = false;
+  enqueue_rebin(s);
+  s->profile = p;
+  if (cudaMemcpyAsync(ed, edges, sizeof(double) * (n_bins + 1), cudaMemcpyHostToDevice, s->st) != cudaSuccess ||
+      cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * nc, s->st) != cudaSuccess) {
+    rc = fail(s, MD_ECUDA, "histogram set-up failed");
+  } else {
+    const double norm = (double)n_bins / (edges[n_bins] - edges[0]);
+    launch_rdf(s->mixed, s->x, (int)s->N, s->cell_start, s->perm, s->reps, s->n_reps, s->C, s->S, ed, n_bins, norm,
+               cnt, s->st);
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(counts, cnt, sizeof(unsigned long long) * nc, cudaMemcpyDefault, s->st) != cudaSuccess)
+      rc = fail(s, MD_ECUDA, "histogram kernel failed");
+  }
+  if (rc == MD_OK) {
+    rc = check_flags(s);
+    s->fresh = rc == MD_OK;
+  } else {
+    cudaStreamSynchronize(s->st);
+  }
+  cudaFree(ed);
+  cudaFree(cnt);
+  return rc;
+}
+
+int md_acf_reset(md_system* s, int32_t max_lag) {
+  if (!s || max_lag < 0 || max_lag > 100000) return fail(s, MD_EINVAL, "max_lag must be 0 .. 100000");
+  CU(cudaStreamSynchronize(s->st));
+  int chains = 0;
+  for (const RepDev& q : s->reps_h) chains += q.n_chains;
+  if (max_lag != s->acf_lag) {
+    if (s->acf_ring) cudaFree(s->acf_ring);
+    if (s->acf_acc) cudaFree(s->acf_acc);
+    s->acf_ring = s->acf_acc = nullptr;
+    s->acf_lag = -1;
+    if (cudaMalloc(&s->acf_ring, sizeof(double) * 3 * (size_t)chains * (max_lag + 1)) != cudaSuccess ||
+        cudaMalloc(&s->acf_acc, sizeof(double) * (size_t)s->n_reps * (max_lag + 1)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(s, MD_ENOMEM, "device memory for the ACF ring");
+    }
+    s->acf_lag = max_lag;
+  }
+  CU(cudaMemset(s->acf_acc, 0, sizeof(double) * (size_t)s->n_reps * (max_lag + 1)));
+  s->acf_n = 0;
+  return MD_OK;
+}
+
+static int acf_add(md_system* s, int chains) {
+  launch_acf_add(s->acf_ring, chains, s->reps, s->n_reps, s->acf_n, s->acf_lag, s->acf_acc, s->st);
+  CU(cudaGetLastError());
+  ++s->acf_n;
+  return MD_OK;
+}
+
+int md_acf_push(md_system* s, const double* r_ee) {
+  if (!s || !r_ee) return fail(s, MD_EINVAL, "bad arguments");
+  if (s->acf_lag < 0) return fail(s, MD_EINVAL, "md_acf_reset first");
+  int chains = 0;
+  for (const RepDev& q : s->reps_h) chains += q.n_chains;
+  double* slot = s->acf_ring + (size_t)(s->acf_n % (s->acf_lag + 1)) * 3 * chains;
+  CU(cudaMemcpyAsync(slot, r_ee, sizeof(double) * 3 * chains, cudaMemcpyDefault, s->st));
+  int rc = acf_add(s, chains);
+  if (rc) return rc;
+  CU(cudaStreamSynchronize(s->st));
+  return MD_OK;
+}
+
+int md_acf_sample(md_system* s) {
+  if (!s) return fail(s, MD_EINVAL, "null system");
+  if (s->acf_lag < 0) return fail(s, MD_EINVAL, "md_acf_reset first");
+  int chains = 0;
+  for (const RepDev& q : s->reps_h) chains += q.n_chains;
+  double* slot = s->acf_ring + (size_t)(s->acf_n % (s->acf_lag + 1)) * 3 * chains;
+  // end-to-end vectors straight into the ring; R_g^2 and trans counts to scratch
+  double* rg_d = s->stage;
+  unsigned long long* tr_d = reinterpret_cast<unsigned long long*>(s->stage + chains);
+  CU(cudaMemsetAsync(tr_d, 0, sizeof(unsigned long long) * s->n_reps, s->st));
+  launch_chain_observables(s->mixed, s->x, (int)s->N, s->reps, s->n_reps, s->fp, chains, slot, rg_d, tr_d, s->st);
+  CU(cudaGetLastError());
+  return acf_add(s, chains);
+}
+
+int md_acf_read(md_system* s, double* C, int64_t* n_samples) {
+  if (!s) return fail(s, MD_EINVAL, "null system");
+  if (s->acf_lag < 0) return fail(s, MD_EINVAL, "md_acf_reset first");
+  const int slots = s->acf_lag + 1;
+  std::vector<double> acc((size_t)s->n_reps * slots);
+  CU(cudaMemcpyAsync(acc.data(), s->acf_acc, acc.size() * sizeof(double), cudaMemcpyDeviceToHost, s->st));
+  CU(cudaStreamSynchronize(s->st));
+  const int64_t n = s->acf_n;
+  if (n_samples) *n_samples = n;
+  if (C)
+    for (int r = 0; r < s->n_reps; ++r) {
+      const double nc = (double)s->reps_h[r].n_chains;
+      const double norm = n > 0 ? acc[(size_t)r * slots] / ((double)n * nc) : 0.0;
+      for (int t = 0; t < slots; ++t)
+        C[(size_t)r * slots + t] = t < n ? (acc[(size_t)r * slots + t] / ((double)(n - t) * nc)) / norm : NAN;
+    }
+  return MD_OK;
+}
+
+int md_early_rebins(md_system* s, int64_t* count) {
+  if (!s || !count) return fail(s, MD_EINVAL, "bad arguments");
+  unsigned long long v = 0;
+  CU(cudaStreamSynchronize(s->st));
+  CU(cudaMemcpy(&v, s->early, sizeof v, cudaMemcpyDeviceToHost));
+  *count = (int64_t)v;
   return MD_OK;
 }
 
@@ -993,8 +1207,12 @@ void md_destroy(md_system* s) {
   if (s->st) cudaStreamSynchronize(s->st);
   if (s->cycle) cudaGraphExecDestroy(s->cycle);
   if (s->cycle_fresh) cudaGraphExecDestroy(s->cycle_fresh);
+  drop_rem_graphs(s);
+  if (s->side) cudaStreamDestroy(s->side);
   for (cudaEvent_t e : s->ev) cudaEventDestroy(e);
   if (s->own_mem && s->base) cudaFree(s->base);
+  if (s->acf_ring) cudaFree(s->acf_ring);
+  if (s->acf_acc) cudaFree(s->acf_acc);
   if (s->own_stream && s->st) cudaStreamDestroy(s->st);
   delete s;
 }

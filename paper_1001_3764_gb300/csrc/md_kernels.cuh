@@ -283,6 +283,18 @@ void launch_integrate(bool mixed, IntegMode mode, bool ke, int thermostat, void*
                       const RepDev* reps, int n_reps, const ForceParams& fp, double* kepart,
                       unsigned* done, double* ke_out, double* lam, double tau, unsigned* flags,
                       cudaStream_t st);
+// RDF of non-bonded pairs (k_observe.cu): counts[r * n_bins + k] += pairs of
+// replica r with edges[k] <= r < edges[k + 1] (last bin closed); norm =
+// n_bins / (edges[n_bins] - edges[0]) gives the first guess of k
+void launch_rdf(bool mixed, const void* x, int N, const int* cell_start, const int* perm, const RepDev* reps,
+                int n_reps, int C, int sites, const double* edges, int n_bins, double norm,
+                unsigned long long* counts, cudaStream_t st);
+// ACF: add sample s (ring slot s % (max_lag + 1)) to acc[r][tau], tau <= min(s, max_lag)
+void launch_acf_add(const double* ring, int n_chains_total, const RepDev* reps, int n_reps, long long s, int max_lag,
+                    double* acc, cudaStream_t st);
+// opens the conditional rebin of a step graph when kFlagDisplacement is set
+// (then cleared and counted in *events)
+void launch_disp_check(cudaGraphConditionalHandle h, unsigned* flags, unsigned long long* events, cudaStream_t st);
 // cells per slice of the first energy-reduction pass
 constexpr int kEnergySliceCells = 1024;
 int energy_slice_count(int n_cells);

@@ -453,12 +453,24 @@ def test_last_site_and_next_chains_first_site_interact(sites, precision):
     s.close()
 
 
-def test_displacement_beyond_half_skin_is_reported():
-    m = chaingen.melt(10, seed=1)
+def test_displacement_beyond_half_skin_triggers_an_early_rebin():
+    """A skin of 0.002 nm with the list rebuilt only every 10 steps: atoms
+    move more than skin/2 within a few steps.  The displacement check then
+    rebuilds the bins and list before that step's forces (counted by
+    md_early_rebins), the run continues, and the forces after 10 and after
+    17 steps (a remainder block) match the oracle's own run from the same
+    state (mixed form: its trajectory follows the oracle's to ~1e-8 nm)."""
+    m = chaingen.melt(10, seed=1, L=3.6)
     s = md.System(m, precision=md.MD_MIXED, skin=0.002, rebin_every=10)
-    with pytest.raises(md.MDError) as e:
-        s.step(10)
-    assert e.value.code == md.MD_EUNSTABLE
+    x, v = _uploaded(m)
+    ref = oracle.System(oracle.chain_topology(150), 10, m["L"], use_cells=False)
+    s.step(10)
+    assert s.early_rebins() > 0
+    xo, vo, fo, _, _ = ref.run(x, v, 0.001, 10, sample_every=0)
+    check_forces(s.forces(), fo, xo, m["L"])
+    s.step(7)
+    xo, vo, fo, _, _ = ref.run(xo, vo, 0.001, 7, sample_every=0)
+    check_forces(s.forces(), fo, xo, m["L"])
     s.close()
 
 
@@ -833,3 +845,72 @@ def test_chain_observables_match_oracle(precision):
         assert abs(got["trans_fraction"][r] - want) <= near / phi.size + 1e-15
         off += n
     s.close()
+
+
+@pytest.mark.parametrize("precision", [md.MD_MIXED, md.MD_PLAIN_FP32])
+def test_rdf_counts_are_bit_exact(precision):
+    """RDF of non-bonded pairs on the GPU (md_rdf) against the FP64
+    definition of oracle/observables.rdf on the same positions, two
+    replicas: the integer pair counts per bin are equal."""
+    from oracle import observables as ob
+    melts = [chaingen.melt(12, seed=51), chaingen.melt(20, seed=52)]
+    s = md.System(melts, precision=precision)
+    r_max, n_bins = 1.0, 50
+    centres, g, counts = s.rdf(r_max, n_bins)
+    for r, m in enumerate(melts):
+        x, _ = _uploaded(m, precision)
+        c_o, g_o, n_o = ob.rdf(x, m["L"], m["sites"], r_max, n_bins)
+        assert np.array_equal(counts[r], n_o)
+        assert np.allclose(g[r], g_o, rtol=1e-12)
+        assert np.allclose(centres, c_o)
+    s.close()
+
+
+def test_end_to_end_acf_accumulator_matches_oracle():
+    """The on-GPU ACF accumulator fed a given series (md_acf_push): two
+    replicas, 60 samples of seeded end-to-end vectors (a slow rotation plus
+    noise), lags 0..20, against oracle/observables.end_to_end_acf of the same
+    series per replica."""
+    from oracle import observables as ob
+    melts = [chaingen.melt(6, seed=53), chaingen.melt(9, seed=54)]
+    s = md.System(melts, precision=md.MD_MIXED)
+    n_ch = [m["n_chains"] for m in melts]
+    rng = np.random.default_rng(7)
+    n_s, lag = 60, 20
+    phase = rng.uniform(0, 2 * np.pi, size=sum(n_ch))
+    series = []
+    for t in range(n_s):
+        a = phase + 0.05 * t
+        R = np.stack([3.0 * np.cos(a), 3.0 * np.sin(a), rng.normal(size=a.size)], axis=1)
+        series.append(R)
+    series = np.array(series)
+    s.acf_reset(lag)
+    for t in range(n_s):
+        s.acf_push(series[t])
+    C, n = s.acf()
+    assert n == n_s
+    off = 0
+    for r, k in enumerate(n_ch):
+        want = ob.end_to_end_acf(series[:, off:off + k], lag)
+        assert np.allclose(C[r], want, rtol=1e-12, atol=1e-14)
+        off += k
+    s.close()
+
+
+def test_end_to_end_acf_sampled_from_the_state():
+    """md_acf_sample takes the same end-to-end vectors as md_observables:
+    sampling a stepped system gives the same bits as pushing the vectors
+    that md_observables returns at each sample."""
+    m = chaingen.melt(8, seed=55)
+    a = md.System(m, precision=md.MD_MIXED, rebin_every=5)
+    b = md.System(m, precision=md.MD_MIXED, rebin_every=5)
+    a.acf_reset(6); b.acf_reset(6)
+    for _ in range(12):
+        a.step(5); b.step(5)
+        a.acf_sample()
+        b.acf_push(b.observables()["r_ee"])
+    ca, na = a.acf()
+    cb, nb = b.acf()
+    assert na == nb == 12
+    assert np.array_equal(ca, cb)
+    a.close(); b.close()
