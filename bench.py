@@ -346,6 +346,35 @@ def nvt_nose_hoover(md, melt, bench_steps=20):
         return {"error": f"{type(err).__name__}: {err}"}
 
 
+# Table III of the paper: box volumes (nm^3) and site counts of its seven
+# test systems.  The engine's boxes are cubes, so each is run in the cube of
+# the same volume and the same number of 150-site chains (~0.25 g/cm^3).
+TABLE3 = (("I", 10 * 10 * 16, 19200), ("II", 16 * 16 * 24, 64800), ("III", 20 * 20 * 32, 117600),
+          ("IV", 24 * 24 * 40, 243000), ("V", 30 * 30 * 40, 363000), ("VI", 34 * 34 * 40, 507000),
+          ("VII", 40 * 40 * 40, 675000))
+
+
+def binning_study(md, reps=5):
+    """The paper's binning and neighbour-list study (Sec. 4.1, Tables IV and
+    V) on GB300: for each Table III system, the CBIN arm (positions copied to
+    the host, binned there on one thread, binned data copied back) against
+    the on-GPU counting sort, and the list build (md_bin_study, mean of
+    `reps` rounds, ms).  Mixed form, generated melts (no equilibration)."""
+    import chaingen
+    out = []
+    for name, vol, n in TABLE3:
+        chains = n // SITES
+        L = vol ** (1.0 / 3.0)
+        m = chaingen.melt(chains, SITES, seed=100 + chains, T=500.0, L=L)
+        s = md.System(m, precision=md.MD_MIXED)
+        t = s.bin_study(reps)
+        s.close()
+        out.append(dict(system=name, sites=chains * SITES, L_nm=round(m["L"], 4), **{k: round(v, 4) for k, v in t.items()},
+                        host_over_gpu=t["host_total"] / t["gpu_binning"]))
+    return {"unit": "ms", "reps": reps, "systems": out,
+            "note": "cubes of the Table III volumes; host binning on one thread of the GPU box's host"}
+
+
 def cpu_baseline(melt, steps=4, steps_1t=1):
     """The CPU-baseline leg: the FP64 oracle (cell list) on the host cores,
     `steps` velocity-Verlet steps of the benchmark melt's generated state with
@@ -596,6 +625,8 @@ def run_gpu(args):
         out["force_err"] = force_error(md, gen, sampled)
     out["kernel_ms_per_launch"] = {g: float(t / max(n, 1)) for g, t, n in
                                    zip(md.PROFILE_GROUPS, m["prof_ms"], m["prof_n"])}
+    if not args.no_binning_study:
+        out["binning_study"] = binning_study(md)
     if not args.no_batched:
         out["batched"] = batched(md)
     if not args.no_adjoint:
@@ -621,6 +652,7 @@ def main():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-batched", action="store_true", help="skip the 64-replica measurement")
     p.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-gradient measurement")
+    p.add_argument("--no-binning-study", action="store_true", help="skip the Table III binning study")
     p.add_argument("--chains", type=int, default=N_CHAINS, help="chains of 150 sites (default 10,000 = 1.5M sites)")
     p.add_argument("--ncu-region", action="store_true",
                    help="profile only the timed loop of the mixed form (cudaProfilerStart/Stop); "

@@ -98,6 +98,8 @@ typedef struct {
   int32_t nbr_capacity;        /* neighbour slots per atom; 0 = chosen from density */
   int32_t lj_block;            /* threads per block of the LJ kernel: 128 or 256 (0 = 256) */
   int32_t schedule;            /* MD_SCHED_GRID or MD_SCHED_PERSISTENT (see below) */
+  int32_t lj_lanes;            /* lanes of the LJ kernel that share one 4-atom cluster's list:
+                                  8, 16 or 32 (0 = 16) */
   void *cuda_stream;           /* cudaStream_t to run on; NULL = a stream the library creates */
   void *workspace;             /* optional DEVICE memory for all buffers (see md_workspace_size);
                                   NULL = the library allocates.  Must outlive the system. */
@@ -122,15 +124,17 @@ typedef struct {
   int32_t rebin_every;
   int32_t lj_block;
   int32_t schedule;
+  int32_t lj_lanes;
   int32_t from_cache;          /* 1 if read from the cache file, 0 if measured now */
   double us_per_step;          /* measured time per MD step of the winner */
 } md_tuning;
 
 /* Autotuner: times short runs of candidate settings on the system the
  * descriptor describes -- LJ block shape (128, 256 threads) and schedule
- * (grid, persistent), then cell size via (skin, rebin_every) in
+ * (grid, persistent), lanes per cluster (8, 16, 32), then cell size via
+ * (skin, rebin_every) in
  * {(0.08, 6), (0.10, 10), (0.12, 12), (0.15, 16)} nm / steps -- and writes the
- * fastest into desc->skin, rebin_every, lj_block and schedule.  Candidates that
+ * fastest into desc->skin, rebin_every, lj_block, schedule and lj_lanes.  Candidates that
  * raise a device flag (e.g. an atom moving more than skin/2 between rebins)
  * are rejected.  With cache_path != NULL the result is looked up in / appended
  * to that text file, keyed by GPU, precision, replica count and atom-count and
@@ -241,6 +245,23 @@ int md_acf_reset(md_system *sys, int32_t max_lag);
 int md_acf_sample(md_system *sys);
 int md_acf_push(md_system *sys, const double *r_ee);
 int md_acf_read(md_system *sys, double *C, int64_t *n_samples);
+
+/* Binning study (Sec. 3.1, Tables IV and V): the paper's CBIN arm (positions
+ * copied to the host, binned there, the binned data copied back) against
+ * this library's on-GPU counting sort, on the system's current positions.
+ * Each of `reps` rounds (1 .. 1000) runs the GPU arm (cell ids, histogram,
+ * scans, scatter, per-cell order and sorted arrays; then the cluster list
+ * build) and the host arm (position copy to pinned host memory, binning on
+ * one host thread with the same FP64 cell formula and stable counting sort,
+ * copy of cell_of, packed cell coordinates, cell_start, cluster starts and
+ * the order back to the GPU, and the per-cell sorted arrays built from it).
+ * ms[6] = mean per round of: GPU binning, GPU list build, host arm position
+ * copy, host binning, binned-data copy with the sorted arrays, host arm
+ * total (CUDA events; host binning by the host clock).  The host arm runs
+ * last, so md_get_bins then returns its bins, which equal the GPU arm's
+ * (tested against the FP64 oracle).  Allocates pinned host memory for the
+ * call.  Synchronous. */
+int md_bin_study(md_system *sys, int32_t reps, double *ms);
 
 /* Number of rebuilds so far that the displacement check added (an atom
  * moved more than skin/2 between scheduled rebuilds); synchronous. */

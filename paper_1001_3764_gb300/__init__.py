@@ -47,14 +47,15 @@ class md_desc(ctypes.Structure):
                 ("dt", ctypes.c_double), ("rc", ctypes.c_double), ("skin", ctypes.c_double),
                 ("tau_t", ctypes.c_double), ("rebin_every", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("thermostat", ctypes.c_int32), ("nbr_capacity", ctypes.c_int32),
-                ("lj_block", ctypes.c_int32), ("schedule", ctypes.c_int32),
+                ("lj_block", ctypes.c_int32), ("schedule", ctypes.c_int32), ("lj_lanes", ctypes.c_int32),
                 ("cuda_stream", ctypes.c_void_p), ("workspace", ctypes.c_void_p),
                 ("workspace_bytes", ctypes.c_size_t)]
 
 
 class md_tuning(ctypes.Structure):
     _fields_ = [("skin", ctypes.c_double), ("rebin_every", ctypes.c_int32), ("lj_block", ctypes.c_int32),
-                ("schedule", ctypes.c_int32), ("from_cache", ctypes.c_int32), ("us_per_step", ctypes.c_double)]
+                ("schedule", ctypes.c_int32), ("lj_lanes", ctypes.c_int32), ("from_cache", ctypes.c_int32),
+                ("us_per_step", ctypes.c_double)]
 
 
 class md_adj_desc(ctypes.Structure):
@@ -78,7 +79,8 @@ class md_energy_t(ctypes.Structure):
 
 EXPORTS = ["md_autotune", "md_workspace_size", "md_create", "md_step", "md_step_async", "md_sync", "md_forces", "md_energy",
            "md_rebin", "md_get_state", "md_set_state", "md_set_params", "md_set_temperature", "md_get_thermostat", "md_observables", "md_rdf",
-           "md_acf_reset", "md_acf_sample", "md_acf_push", "md_acf_read", "md_early_rebins", "md_stream",
+           "md_acf_reset", "md_acf_sample", "md_acf_push", "md_acf_read", "md_early_rebins", "md_bin_study",
+           "md_stream",
            "md_info", "md_get_bins", "md_get_neighbors", "md_get_cell_units", "md_profile_enable", "md_profile_read",
            "md_profile_reset", "md_launches_per_call", "md_bin_static", "md_destroy", "md_last_error",
            "md_adj_create", "md_adj_set_theta", "md_adj_forward", "md_adj_backward", "md_adj_tangent",
@@ -119,6 +121,7 @@ def load(path: str = LIB_PATH):
         "md_acf_push": ([P, P], ctypes.c_int),
         "md_acf_read": ([P, P, P], ctypes.c_int),
         "md_early_rebins": ([P, P], ctypes.c_int),
+        "md_bin_study": ([P, i32, P], ctypes.c_int),
         "md_stream": ([P], P),
         "md_info": ([P, P, P, P, P], ctypes.c_int),
         "md_get_bins": ([P, P, P, P], ctypes.c_int),
@@ -382,7 +385,7 @@ class System:
                  skin: float = 0.1, rebin_every: int = 10, thermostat: int = MD_NVE, T_target=None,
                  tau_t: float = 0.1, params: dict | None = None, nbr_capacity: int = 0, device: int = 0,
                  use_torch_memory: bool = True, lj_block: int = 0, schedule: int = MD_SCHED_GRID,
-                 autotune: bool = False, tune_cycles: int = 2, tune_cache: str | None = None):
+                 lj_lanes: int = 0, autotune: bool = False, tune_cycles: int = 2, tune_cache: str | None = None):
         import torch
         load()
         if isinstance(melts, dict):
@@ -410,7 +413,7 @@ class System:
         d.dt, d.rc, d.skin, d.tau_t = dt, rc, skin, tau_t
         d.rebin_every, d.precision, d.thermostat = rebin_every, precision, thermostat
         d.nbr_capacity = nbr_capacity
-        d.lj_block, d.schedule = lj_block, schedule
+        d.lj_block, d.schedule, d.lj_lanes = lj_block, schedule, lj_lanes
         self.tuning = md_autotune(d, tune_cycles, tune_cache) if autotune else None
         d.cuda_stream = self.stream.cuda_stream
         self.workspace = None
@@ -503,6 +506,15 @@ class System:
         n = ctypes.c_int64(0)
         _check(load().md_acf_read(self.h, C.ctypes.data, ctypes.byref(n)), self.h)
         return C, int(n.value)
+
+    def bin_study(self, reps: int = 5) -> dict:
+        """CBIN-style host binning against the on-GPU counting sort
+        (md_bin_study): mean ms per round of each part."""
+        ms = np.zeros(6, np.float64)
+        _check(load().md_bin_study(self.h, int(reps), ms.ctypes.data), self.h)
+        keys = ("gpu_binning", "gpu_list_build", "host_position_copy", "host_binning", "host_binned_data_copy",
+                "host_total")
+        return dict(zip(keys, (float(v) for v in ms)))
 
     def early_rebins(self) -> int:
         """Rebuilds added by the displacement check so far."""

@@ -37,7 +37,6 @@ namespace mdg {
 
 constexpr int kStageCapMax = 6144;      // largest tile (atoms); list entries keep the tile index in 16 bits
 constexpr int kLjAccShift = 19;         // 2^-13 accumulators -> 2^-32 fixed point
-constexpr int kLanesPerCluster = 16;    // lanes that share one cluster's list in the force kernel
 constexpr float kLjAccScale = 8192.0f;  // 2^13
 
 __device__ __forceinline__ float rcp_approx(float x) {
@@ -463,31 +462,37 @@ void launch_cl_build(const float4* pos, const int* tag, const int* cell_start, c
 void launch_cl_force(bool energy, const float4* pos, const int* cell_start, const int* cl_start,
                      const Region* regions, int n_regions, const RegionShape* shapes, const RepDev* reps,
                      const unsigned* list, const int* ncl, int cap, int tile_cap, const ForceParams& fp,
-                     long long* flj, int Npad, double* epart, unsigned* flags, int block, int persistent_grid,
-                     int* work, cudaStream_t st) {
+                     long long* flj, int Npad, double* epart, unsigned* flags, int block, int lanes,
+                     int persistent_grid, int* work, cudaStream_t st) {
   if (n_regions <= 0) return;
   const int grid = persistent_grid > 0 ? persistent_grid : n_regions;
   const size_t sm = cl_force_smem(tile_cap);
   const int pers = persistent_grid > 0;
-#define MDG_CLF(E, NT)                                                                                            \
-  k_cl_force<E, NT, kLanesPerCluster><<<grid, NT, sm, st>>>(pos, cell_start, cl_start, regions, n_regions, shapes, reps, list, ncl, \
-                                          cap, tile_cap, fp, flj, Npad, epart, flags, pers, work)
+#define MDG_CLF(E, NT, LP)                                                                                    \
+  k_cl_force<E, NT, LP><<<grid, NT, sm, st>>>(pos, cell_start, cl_start, regions, n_regions, shapes, reps, list, \
+                                              ncl, cap, tile_cap, fp, flj, Npad, epart, flags, pers, work)
+#define MDG_CLF2(NT, LP) \
+  if (energy) MDG_CLF(true, NT, LP); else MDG_CLF(false, NT, LP);
   if (block == 128) {
-    if (energy) MDG_CLF(true, 128); else MDG_CLF(false, 128);
+    if (lanes == 8) { MDG_CLF2(128, 8) } else if (lanes == 32) { MDG_CLF2(128, 32) } else { MDG_CLF2(128, 16) }
   } else {
-    if (energy) MDG_CLF(true, 256); else MDG_CLF(false, 256);
+    if (lanes == 8) { MDG_CLF2(256, 8) } else if (lanes == 32) { MDG_CLF2(256, 32) } else { MDG_CLF2(256, 16) }
   }
+#undef MDG_CLF2
 #undef MDG_CLF
 }
 
-// resident blocks per SM of the force kernel for a block size and tile
-int lj_blocks_per_sm(int block, int tile_cap) {
+// resident blocks per SM of the force kernel for a block size, lanes per cluster and tile
+int lj_blocks_per_sm(int block, int lanes, int tile_cap) {
   int nb = 0;
   const size_t sm = cl_force_smem(tile_cap);
-  if (block == 128)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cl_force<false, 128, kLanesPerCluster>, 128, sm);
-  else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cl_force<false, 256, kLanesPerCluster>, 256, sm);
+#define MDG_OCC(NT, LP) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cl_force<false, NT, LP>, NT, sm)
+  if (block == 128) {
+    if (lanes == 8) MDG_OCC(128, 8); else if (lanes == 32) MDG_OCC(128, 32); else MDG_OCC(128, 16);
+  } else {
+    if (lanes == 8) MDG_OCC(256, 8); else if (lanes == 32) MDG_OCC(256, 32); else MDG_OCC(256, 16);
+  }
+#undef MDG_OCC
   return nb;
 }
 
@@ -496,10 +501,12 @@ int lj_blocks_per_sm(int block, int tile_cap) {
 cudaError_t tile_kernels_init() {
   const int mb = (int)cl_build_smem(kStageCapMax), mf = (int)cl_force_smem(kStageCapMax);
   cudaError_t e = cudaFuncSetAttribute(k_cl_build<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, mb);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cl_force<false, 128, kLanesPerCluster>, cudaFuncAttributeMaxDynamicSharedMemorySize, mf);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cl_force<true, 128, kLanesPerCluster>, cudaFuncAttributeMaxDynamicSharedMemorySize, mf);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cl_force<false, 256, kLanesPerCluster>, cudaFuncAttributeMaxDynamicSharedMemorySize, mf);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cl_force<true, 256, kLanesPerCluster>, cudaFuncAttributeMaxDynamicSharedMemorySize, mf);
+#define MDG_ATTR(E, NT, LP) \
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cl_force<E, NT, LP>, cudaFuncAttributeMaxDynamicSharedMemorySize, mf);
+#define MDG_ATTR3(E, NT) MDG_ATTR(E, NT, 8) MDG_ATTR(E, NT, 16) MDG_ATTR(E, NT, 32)
+  MDG_ATTR3(false, 128) MDG_ATTR3(true, 128) MDG_ATTR3(false, 256) MDG_ATTR3(true, 256)
+#undef MDG_ATTR3
+#undef MDG_ATTR
   return e;
 }
 

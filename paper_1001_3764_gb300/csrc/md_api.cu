@@ -9,6 +9,7 @@
 // adjoint); md_static.cu holds the allocation-free binning entry point.
 #include <algorithm>
 #include <array>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <tuple>
@@ -69,6 +70,7 @@ struct md_system {
   RegionShape* shapes = nullptr;
   int tile_cap = 0;
   int lj_block = 256, persistent_grid = 0;   // persistent_grid > 0: fixed grid for the LJ kernel
+  int lj_lanes = 16;                         // lanes per 4-atom cluster in the LJ kernel
   int* work = nullptr;                       // LJ work counters (persistent schedule)
   int *count = nullptr, *cell_start = nullptr, *cell_of = nullptr;
   int *slot = nullptr, *tmp = nullptr;
@@ -221,6 +223,9 @@ static int configure(md_system* s, const md_desc* d) {
   if (d->lj_block != 0 && d->lj_block != 128 && d->lj_block != 256) return fail(s, MD_EINVAL, "lj_block must be 0, 128 or 256");
   if (d->schedule != MD_SCHED_GRID && d->schedule != MD_SCHED_PERSISTENT) return fail(s, MD_EINVAL, "unknown schedule");
   s->lj_block = d->lj_block ? d->lj_block : 256;
+  if (d->lj_lanes != 0 && d->lj_lanes != 8 && d->lj_lanes != 16 && d->lj_lanes != 32)
+    return fail(s, MD_EINVAL, "lj_lanes must be 0, 8, 16 or 32");
+  s->lj_lanes = d->lj_lanes ? d->lj_lanes : 16;
   s->params = d->params;
   const double rl = d->rc + d->skin;
   s->reps_h.assign(s->n_reps, RepDev{});
@@ -379,7 +384,7 @@ static void enqueue_forces(md_system* s, bool energy, void* F_out = nullptr) {
   prof_mark(s);   // closes the integrate group (integrator, displacement check, clear)
   launch_cl_force(energy, s->pos, s->cell_start, s->cl_start, s->regions, (int)s->regions_h.size(), s->shapes,
                   s->reps, s->list, s->ncl, s->cap, s->tile_cap, s->fp, flj, s->Npad, s->lj_part, s->flags,
-                  s->lj_block, s->persistent_grid, s->work, s->st);
+                  s->lj_block, s->lj_lanes, s->persistent_grid, s->work, s->st);
   prof_mark(s);
   launch_bonded(s->mixed, energy, s->x, s->site, s->inv_perm, flj, s->Npad, (int)s->N, s->tiles_int,
                 (int)s->t_int.size(), s->reps, s->fp, F_out ? F_out : s->F, s->b_part, s->flags, s->st);
@@ -519,9 +524,11 @@ static int check_flags(md_system* s) {
   CU(cudaMemcpy(&f, s->flags, sizeof f, cudaMemcpyDeviceToHost));
   if (!f) return MD_OK;
   CU(cudaMemset(s->flags, 0, sizeof(unsigned)));
+  // a non-finite value is the first thing to report: it usually comes with
+  // huge finite forces nearby
+  if (f & kFlagNaN) return fail(s, MD_EUNSTABLE, "non-finite position, velocity or force");
   if (f & kFlagNbrOverflow) return fail(s, MD_EOVERFLOW, "neighbour list capacity exceeded (raise nbr_capacity)");
-  if (f & kFlagFixOverflow) return fail(s, MD_EOVERFLOW, "force beyond the fixed-point range (a part >= 2^18 kJ/mol/nm)");
-  if (f & kFlagNaN) return fail(s, MD_EUNSTABLE, "non-finite position or velocity");
+  if (f & kFlagFixOverflow) return fail(s, MD_EOVERFLOW, "force beyond the fixed-point range (a part >= 2^17 kJ/mol/nm)");
   if (f & kFlagDisplacement) return fail(s, MD_EUNSTABLE, "an atom moved more than skin/2 between rebins (raise skin or lower rebin_every)");
   if (f & kFlagBadInput) return fail(s, MD_EINVAL, "non-finite input position or velocity");
   if (f & kFlagTimeout) return fail(s, MD_ETIMEOUT, "a bounded device wait gave up");
@@ -552,6 +559,42 @@ static int refresh(md_system* s) {
   const int rc = check_flags(s);
   s->fresh = rc == MD_OK;
   return rc;
+}
+
+// The paper's CBIN binning (Sec. 3.1) done here as a comparison arm: the
+// cell of every atom, histogram, exclusive scans and the stable order by atom
+// index, on the host from a copy of the positions, with the device's
+// formulas (host code is compiled without contraction, so the FP64 cell
+// coordinates agree bit for bit).
+template <class T>
+static void host_bins(const T* x, const md_system* s, std::vector<int>& cell_of, std::vector<int>& cellc,
+                      std::vector<int>& cell_start, std::vector<int>& cl_start, std::vector<int>& perm) {
+  const int64_t N = s->N;
+  std::vector<int> count(s->C, 0);
+  for (const RepDev& q : s->reps_h) {
+    for (int i = q.atom_off; i < q.atom_off + q.n_atoms; ++i) {
+      int k[3];
+      for (int a = 0; a < 3; ++a) {
+        const double xv = (double)x[a * N + i];
+        double sv = xv;
+        if (!(xv >= 0.0 && xv < q.L)) sv = xv - q.L * std::floor(xv / q.L);
+        int c = (int)std::floor(sv * q.inv_h);
+        k[a] = c < 0 ? 0 : (c > q.M - 1 ? q.M - 1 : c);
+      }
+      const int c = q.cell_base + (k[2] * q.M + k[1]) * q.M + k[0];
+      cell_of[i] = c;
+      cellc[i] = k[0] | (k[1] << 10) | (k[2] << 20);
+      ++count[c];
+    }
+  }
+  cell_start[0] = 0;
+  cl_start[0] = 0;
+  for (int c = 0; c < s->C; ++c) {
+    cell_start[c + 1] = cell_start[c] + count[c];
+    cl_start[c + 1] = cl_start[c] + (count[c] + 3) / 4;
+  }
+  std::vector<int> fill(cell_start.begin(), cell_start.end() - 1);
+  for (int64_t i = 0; i < N; ++i) perm[fill[cell_of[i]]++] = (int)i;
 }
 
 // ------------------------------------------------------------------ C ABI
@@ -615,7 +658,7 @@ int md_create(const md_desc* d, md_system** out) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int per_sm = lj_blocks_per_sm(s->lj_block, s->tile_cap);
+    const int per_sm = lj_blocks_per_sm(s->lj_block, s->lj_lanes, s->tile_cap);
     s->persistent_grid = std::max(1, std::min((int)s->regions_h.size(), sms * std::max(per_sm, 1)));
   }
   // static tables
@@ -944,6 +987,74 @@ int md_acf_read(md_system* s, double* C, int64_t* n_samples) {
   return MD_OK;
 }
 
+int md_bin_study(md_system* s, int32_t reps, double* ms) {
+  if (!s || !ms || reps < 1 || reps > 1000) return fail(s, MD_EINVAL, "bad arguments (1 <= reps <= 1000)");
+  CU(cudaStreamSynchronize(s->st));
+  const size_t N = (size_t)s->N, C = (size_t)s->C;
+  const size_t xb = 3 * N * (s->mixed ? sizeof(double) : sizeof(float));
+  void* hx = nullptr;
+  CU(cudaMallocHost(&hx, xb));
+  std::vector<int> cell_of(N), cellc(N), cell_start(C + 1), cl_start(C + 1), perm(N);
+  cudaEvent_t ev[6];
+  for (cudaEvent_t& e : ev) cudaEventCreate(&e);
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  const bool prof = s->profile;
+  s->profile = false;
+  int rc = MD_OK;
+  for (int k = 0; k < reps && rc == MD_OK; ++k) {
+    // GPU arm: on-GPU counting sort and sorted arrays, then the list build
+    cudaEventRecord(ev[0], s->st);
+    cudaMemsetAsync(s->count, 0, sizeof(int) * C, s->st);
+    launch_bin_count(s->mixed, s->x, (int)N, s->tiles_int, (int)s->t_int.size(), s->reps, s->cell_of, s->cellc,
+                     s->count, s->slot, s->st);
+    launch_scan2(s->count, s->cell_start, s->cl_start, s->C, s->st);
+    launch_bin_scatter(s->cell_of, s->slot, s->cell_start, s->tmp, (int)N, s->st);
+    launch_cell_sort(s->mixed, s->x, (int)N, s->cell_start, s->tmp, s->cellc, s->site, s->reps, s->n_reps, s->C,
+                     s->S, s->perm, s->inv_perm, s->pos, s->tag, s->ref, s->flags, s->st);
+    cudaEventRecord(ev[1], s->st);
+    launch_cl_build(s->pos, s->tag, s->cell_start, s->cl_start, s->regions, (int)s->regions_h.size(), s->shapes,
+                    s->reps, s->list, s->ncl, s->cap, s->tile_cap, s->flags, s->persistent_grid, s->work, s->st);
+    cudaEventRecord(ev[2], s->st);
+    // host arm: positions to the host, bins there, binned data back, sorted arrays
+    if (cudaMemcpyAsync(hx, s->x, xb, cudaMemcpyDeviceToHost, s->st) != cudaSuccess) { rc = fail(s, MD_ECUDA, "copy"); break; }
+    cudaEventRecord(ev[3], s->st);
+    if (cudaStreamSynchronize(s->st) != cudaSuccess) { rc = fail(s, MD_ECUDA, "sync"); break; }
+    const auto t0 = std::chrono::steady_clock::now();
+    if (s->mixed) host_bins((const double*)hx, s, cell_of, cellc, cell_start, cl_start, perm);
+    else host_bins((const float*)hx, s, cell_of, cellc, cell_start, cl_start, perm);
+    const auto t1 = std::chrono::steady_clock::now();
+    cudaEventRecord(ev[4], s->st);
+    bool ok = cudaMemcpyAsync(s->cell_of, cell_of.data(), N * sizeof(int), cudaMemcpyHostToDevice, s->st) == cudaSuccess &&
+              cudaMemcpyAsync(s->cellc, cellc.data(), N * sizeof(int), cudaMemcpyHostToDevice, s->st) == cudaSuccess &&
+              cudaMemcpyAsync(s->cell_start, cell_start.data(), (C + 1) * sizeof(int), cudaMemcpyHostToDevice, s->st) == cudaSuccess &&
+              cudaMemcpyAsync(s->cl_start, cl_start.data(), (C + 1) * sizeof(int), cudaMemcpyHostToDevice, s->st) == cudaSuccess &&
+              cudaMemcpyAsync(s->tmp, perm.data(), N * sizeof(int), cudaMemcpyHostToDevice, s->st) == cudaSuccess;
+    if (!ok) { rc = fail(s, MD_ECUDA, "copy"); break; }
+    launch_cell_sort(s->mixed, s->x, (int)N, s->cell_start, s->tmp, s->cellc, s->site, s->reps, s->n_reps, s->C,
+                     s->S, s->perm, s->inv_perm, s->pos, s->tag, s->ref, s->flags, s->st);
+    cudaEventRecord(ev[5], s->st);
+    if (cudaStreamSynchronize(s->st) != cudaSuccess) { rc = fail(s, MD_ECUDA, "sync"); break; }
+    float a, b, c, d;
+    cudaEventElapsedTime(&a, ev[0], ev[1]);
+    cudaEventElapsedTime(&b, ev[1], ev[2]);
+    cudaEventElapsedTime(&c, ev[2], ev[3]);
+    cudaEventElapsedTime(&d, ev[4], ev[5]);
+    const double hb = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    acc[0] += a; acc[1] += b; acc[2] += c; acc[3] += hb; acc[4] += d; acc[5] += c + hb + d;
+  }
+  s->profile = prof;
+  for (cudaEvent_t& e : ev) cudaEventDestroy(e);
+  cudaFreeHost(hx);
+  if (rc) return rc;
+  // the list of the bins now in place
+  launch_cl_build(s->pos, s->tag, s->cell_start, s->cl_start, s->regions, (int)s->regions_h.size(), s->shapes,
+                  s->reps, s->list, s->ncl, s->cap, s->tile_cap, s->flags, s->persistent_grid, s->work, s->st);
+  for (int k = 0; k < 6; ++k) ms[k] = acc[k] / reps;
+  rc = check_flags(s);
+  s->fresh = rc == MD_OK;
+  return rc;
+}
+
 int md_early_rebins(md_system* s, int64_t* count) {
   if (!s || !count) return fail(s, MD_EINVAL, "bad arguments");
   unsigned long long v = 0;
@@ -1144,18 +1255,20 @@ static int tune_trial(md_desc cand, int cycles, double* us) {
 extern "C" int md_autotune(md_desc* d, int32_t trial_cycles, const char* cache_path, md_tuning* out) {
   if (!d || trial_cycles < 1) return fail(nullptr, MD_EINVAL, "autotune needs a descriptor and trial_cycles >= 1");
   const std::string key = tune_key(d);
-  md_tuning best{d->skin, d->rebin_every, d->lj_block ? d->lj_block : 256, d->schedule, 0, 1e300};
+  md_tuning best{d->skin, d->rebin_every, d->lj_block ? d->lj_block : 256, d->schedule, d->lj_lanes ? d->lj_lanes : 16,
+                 0, 1e300};
   if (cache_path) {
     if (FILE* f = fopen(cache_path, "r")) {
       char k[256];
       double skin, us;
-      int R, blk, sch;
+      int R, blk, sch, lanes;
       bool found = false;
-      while (fscanf(f, "%255s %lf %d %d %d %lf", k, &skin, &R, &blk, &sch, &us) == 6)
-        if (key == k) { best = md_tuning{skin, R, blk, sch, 1, us}; found = true; }
+      while (fscanf(f, "%255s %lf %d %d %d %d %lf", k, &skin, &R, &blk, &sch, &lanes, &us) == 7)
+        if (key == k) { best = md_tuning{skin, R, blk, sch, lanes, 1, us}; found = true; }
       fclose(f);
       if (found) {
         d->skin = best.skin; d->rebin_every = best.rebin_every; d->lj_block = best.lj_block; d->schedule = best.schedule;
+        d->lj_lanes = best.lj_lanes;
         if (out) *out = best;
         return MD_OK;
       }
@@ -1168,12 +1281,26 @@ extern "C" int md_autotune(md_desc* d, int32_t trial_cycles, const char* cache_p
       md_desc c = *d;
       c.lj_block = blk;
       c.schedule = sch;
+      c.lj_lanes = best.lj_lanes;
       double us = 0.0;
       if (tune_trial(c, trial_cycles, &us) == MD_OK && us < best.us_per_step) {
-        best = md_tuning{c.skin, c.rebin_every, blk, sch, 0, us};
+        best = md_tuning{c.skin, c.rebin_every, blk, sch, best.lj_lanes, 0, us};
         any = true;
       }
     }
+  // lanes per cluster with that block shape and schedule
+  for (int lanes : {8, 16, 32}) {
+    if (lanes == best.lj_lanes) continue;
+    md_desc c = *d;
+    c.lj_block = best.lj_block;
+    c.schedule = best.schedule;
+    c.lj_lanes = lanes;
+    double us = 0.0;
+    if (tune_trial(c, trial_cycles, &us) == MD_OK && us < best.us_per_step) {
+      best = md_tuning{c.skin, c.rebin_every, best.lj_block, best.schedule, lanes, 0, us};
+      any = true;
+    }
+  }
   // cell size through (skin, rebin interval)
   const double skins[4] = {0.08, 0.10, 0.12, 0.15};
   const int reb[4] = {6, 10, 12, 16};
@@ -1182,20 +1309,22 @@ extern "C" int md_autotune(md_desc* d, int32_t trial_cycles, const char* cache_p
     md_desc c = *d;
     c.lj_block = best.lj_block;
     c.schedule = best.schedule;
+    c.lj_lanes = best.lj_lanes;
     c.skin = skins[k];
     c.rebin_every = reb[k];
     double us = 0.0;
     if (tune_trial(c, trial_cycles, &us) == MD_OK && us < best.us_per_step) {
-      best = md_tuning{skins[k], reb[k], best.lj_block, best.schedule, 0, us};
+      best = md_tuning{skins[k], reb[k], best.lj_block, best.schedule, best.lj_lanes, 0, us};
       any = true;
     }
   }
   if (!any) return fail(nullptr, MD_EUNSTABLE, "autotune: no candidate ran cleanly");
   d->skin = best.skin; d->rebin_every = best.rebin_every; d->lj_block = best.lj_block; d->schedule = best.schedule;
+  d->lj_lanes = best.lj_lanes;
   if (cache_path)
     if (FILE* f = fopen(cache_path, "a")) {
-      fprintf(f, "%s %.4f %d %d %d %.3f\n", key.c_str(), best.skin, best.rebin_every, best.lj_block, best.schedule,
-              best.us_per_step);
+      fprintf(f, "%s %.4f %d %d %d %d %.3f\n", key.c_str(), best.skin, best.rebin_every, best.lj_block, best.schedule,
+              best.lj_lanes, best.us_per_step);
       fclose(f);
     }
   if (out) *out = best;

@@ -759,14 +759,13 @@ def test_fixed_point_range_is_reported():
 
 
 def test_non_finite_state_is_reported():
-    """Two sites on the same spot give a non-finite FP32 force; after one
-    rebin cycle the plain form reports MD_EUNSTABLE."""
+    """Two sites on the same spot give a non-finite FP32 pair force: the LJ
+    kernel's check of every converted sum reports it (MD_EUNSTABLE) as soon as
+    the forces are computed, at creation."""
     m = _with_contact(chaingen.melt(4, seed=36, L=3.6), 0.0)
-    s = md.System(m, precision=md.MD_PLAIN_FP32)
     with pytest.raises(md.MDError) as e:
-        s.step(10)
+        md.System(m, precision=md.MD_PLAIN_FP32)
     assert e.value.code == md.MD_EUNSTABLE
-    s.close()
 
 
 @pytest.mark.parametrize("precision", [md.MD_MIXED, md.MD_PLAIN_FP32])
@@ -872,7 +871,7 @@ def test_end_to_end_acf_accumulator_matches_oracle():
     noise), lags 0..20, against oracle/observables.end_to_end_acf of the same
     series per replica."""
     from oracle import observables as ob
-    melts = [chaingen.melt(6, seed=53), chaingen.melt(9, seed=54)]
+    melts = [chaingen.melt(6, seed=53, L=3.6), chaingen.melt(9, seed=54, L=3.6)]
     s = md.System(melts, precision=md.MD_MIXED)
     n_ch = [m["n_chains"] for m in melts]
     rng = np.random.default_rng(7)
@@ -913,4 +912,30 @@ def test_end_to_end_acf_sampled_from_the_state():
     cb, nb = b.acf()
     assert na == nb == 12
     assert np.array_equal(ca, cb)
+    a.close(); b.close()
+
+
+@pytest.mark.parametrize("precision", [md.MD_MIXED, md.MD_PLAIN_FP32])
+def test_bin_study_arms_give_the_oracle_bins(precision):
+    """md_bin_study runs the on-GPU counting sort and the host-copy (CBIN)
+    arm of Sec. 3.1 on the same positions: the host arm's bins (left in
+    place) and the GPU arm's bins (md_rebin) both equal the oracle's binning
+    of the uploaded positions, and a system that ran the study steps on with
+    the same bits as one that did not."""
+    m = chaingen.melt(30, seed=61, L=5.2)
+    a = md.System(m, precision=precision, rebin_every=5)
+    b = md.System(m, precision=precision, rebin_every=5)
+    x, _ = _uploaded(m, precision)
+    M = a.info["cells_per_side"]
+    want = oracle.bin_atoms(x, m["L"], M)
+    t = a.bin_study(2)
+    assert t["host_total"] > 0 and t["gpu_binning"] > 0
+    for got, w in zip(a.bins(), want):
+        assert np.array_equal(got, w)
+    a.rebin()
+    for got, w in zip(a.bins(), want):
+        assert np.array_equal(got, w)
+    a.step(10); b.step(10)
+    xa, va, _ = a.state(); xb, vb, _ = b.state()
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb)
     a.close(); b.close()
