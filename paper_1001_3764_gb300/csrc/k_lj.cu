@@ -37,6 +37,7 @@ namespace mdg {
 
 constexpr int kStageCapMax = 6144;      // largest tile (atoms); list entries keep the tile index in 16 bits
 constexpr int kLjAccShift = 19;         // 2^-13 accumulators -> 2^-32 fixed point
+constexpr bool kPackedPairs = true;     // force-only kernel: two pairs per FFMA2 (this GPU's packed FP32)
 constexpr float kLjAccScale = 8192.0f;  // 2^13
 
 __device__ __forceinline__ float rcp_approx(float x) {
@@ -149,10 +150,33 @@ __device__ __forceinline__ void persistent_done(int* work) {
 }
 
 // ===================================================================== build
-// One warp per home cluster: its lanes take 32 candidates j at a time from the
-// cluster's own cell (from the cluster on) and its 13 forward cells, test
-// them against the four atoms i, and append the j with a non-empty mask in
-// candidate order (ballot + prefix count: the list is the same on every run).
+// One warp per home cluster.  Candidates j are the later atoms of the
+// cluster's own cell and the atoms of its 13 forward cells.  Each j is tested
+// against the cluster's four atoms i (within r_c + skin, not a 1-2 or 1-3
+// neighbour, and for the own cell i before j); a j with a non-empty mask is
+// appended to the cluster's list in candidate order (ballot + prefix count,
+// so the list is the same on every run).  The forward cells' candidates
+// first pass a cheap test against a sphere around the cluster (centre c,
+// radius rad: |j - c| < r_list + rad holds for every j that can pair); those
+// that pass are queued per warp in shared memory and tested 32 at a time,
+// so the lanes of a warp run the four-atom test on candidates that may pair
+// rather than on every 32nd atom of the tile.
+constexpr int kBuildQueue = 64;
+
+// the four-atom test of candidate t: bit u set if atom u of the cluster pairs with t
+__device__ __forceinline__ unsigned pair_mask(const float4 (&pi)[4], const int (&ti)[4], const float4& w, int tg,
+                                              float rl2) {
+  unsigned m = 0u;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const float dx = pi[u].x - w.x, dy = pi[u].y - w.y, dz = pi[u].z - w.z;
+    // |i - j| <= 2 within one chain: 1-2 and 1-3 neighbours (and i itself)
+    const bool keep = (dx * dx + dy * dy + dz * dz < rl2) & ((unsigned)(ti[u] - tg + 2) > 4u);
+    m |= keep ? (1u << u) : 0u;
+  }
+  return m;
+}
+
 template <int NT>
 __global__ void __launch_bounds__(NT) k_cl_build(const float4* __restrict__ pos, const int* __restrict__ tag,
                                                  const int* __restrict__ cell_start, const int* __restrict__ cl_start,
@@ -166,7 +190,9 @@ __global__ void __launch_bounds__(NT) k_cl_build(const float4* __restrict__ pos,
   int* st = reinterpret_cast<int*>(smem + (size_t)tile_cap * sizeof(float4));
   __shared__ RegTile T;
   __shared__ int sh_r;
+  __shared__ int queue[NT / 32][kBuildQueue];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int* qw = queue[warp];
   for (int it = 0;; ++it) {
     const int r = next_region(persistent != 0, it, work, &sh_r);
     if (r < 0 || r >= n_regions) break;
@@ -188,6 +214,7 @@ __global__ void __launch_bounds__(NT) k_cl_build(const float4* __restrict__ pos,
     tile_load<true>(T, pos, tag, sp, st);
     __syncthreads();
     const float rl2 = R.rlist2u;
+    const float rl = sqrtf(rl2);
     const unsigned lt = (1u << lane) - 1u;
     for (int q = warp; q < T.ncl[T.n_home]; q += NT / 32) {
       int h, k;
@@ -196,32 +223,40 @@ __global__ void __launch_bounds__(NT) k_cl_build(const float4* __restrict__ pos,
       const int ni = min(4, T.off[h + 1] - i0);
       float4 pi[4];
       int ti[4];
+      float cx = 0.f, cy = 0.f, cz = 0.f;
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int t = i0 + min(u, ni - 1);
         pi[u] = sp[t];
         ti[u] = st[t];
+        cx += pi[u].x; cy += pi[u].y; cz += pi[u].z;
       }
+      cx *= 0.25f; cy *= 0.25f; cz *= 0.25f;
+      float rad2 = 0.f;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float dx = pi[u].x - cx, dy = pi[u].y - cy, dz = pi[u].z - cz;
+        rad2 = fmaxf(rad2, dx * dx + dy * dy + dz * dz);
+        // a slot past the cell's last atom gets a far position: it pairs with nothing
+        if (u >= ni) pi[u] = make_float4(1e9f, 1e9f, 1e9f, 0.f);
+      }
+      // the sphere test is taken with a margin of 1e-5 cell units over the
+      // FP32 roundings of c and rad, so it never rejects a pair the exact
+      // test keeps
+      const float reach = rl + sqrtf(rad2) + 1e-5f;
+      const float reach2 = reach * reach;
       const int cl = T.cl0[h] + k;
       unsigned* out = list + (size_t)cl * cap;
       int cnt = 0;
-      for (int c14 = 0; c14 < 14; ++c14) {
-        const int tc = S.nb[h][c14];
-        const int t_end = T.off[tc + 1];
-        for (int t0 = c14 == 0 ? i0 : T.off[tc]; t0 < t_end; t0 += 32) {
+      // own cell, from the cluster on: each pair once, i before j
+      {
+        const int t_end = T.off[h + 1];
+        for (int t0 = i0; t0 < t_end; t0 += 32) {
           const int t = t0 + lane;
           unsigned m = 0u;
           if (t < t_end) {
-            const float4 w = sp[t];
-            const int tg = st[t];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              const float dx = pi[u].x - w.x, dy = pi[u].y - w.y, dz = pi[u].z - w.z;
-              // |i - j| <= 2 within one chain: 1-2 and 1-3 neighbours (and i itself)
-              bool keep = (u < ni) & (dx * dx + dy * dy + dz * dz < rl2) & ((unsigned)(ti[u] - tg + 2) > 4u);
-              if (c14 == 0) keep &= t > i0 + u;     // own cell: each pair once, i before j
-              m |= keep ? (1u << u) : 0u;
-            }
+            m = pair_mask(pi, ti, sp[t], st[t], rl2);
+            m &= ((t > i0) ? 1u : 0u) | ((t > i0 + 1) ? 2u : 0u) | ((t > i0 + 2) ? 4u : 0u) | ((t > i0 + 3) ? 8u : 0u);
           }
           const unsigned b = __ballot_sync(0xffffffffu, m != 0u);
           const int p = cnt + __popc(b & lt);
@@ -229,6 +264,52 @@ __global__ void __launch_bounds__(NT) k_cl_build(const float4* __restrict__ pos,
           cnt += __popc(b);
         }
       }
+      // the 13 forward cells: sphere test, queue, four-atom test 32 at a time
+      int qn = 0;
+      for (int c14 = 1; c14 < 14; ++c14) {
+        const int tc = S.nb[h][c14];
+        const int t_end = T.off[tc + 1];
+        for (int t0 = T.off[tc]; t0 < t_end; t0 += 32) {
+          const int t = t0 + lane;
+          bool pass = false;
+          if (t < t_end) {
+            const float4 w = sp[t];
+            const float dx = w.x - cx, dy = w.y - cy, dz = w.z - cz;
+            pass = dx * dx + dy * dy + dz * dz < reach2;
+          }
+          const unsigned b = __ballot_sync(0xffffffffu, pass);
+          if (pass) qw[qn + __popc(b & lt)] = t;
+          qn += __popc(b);
+          __syncwarp();
+          if (qn >= 32) {
+            const int tq = qw[lane];
+            const unsigned m = pair_mask(pi, ti, sp[tq], st[tq], rl2);
+            const unsigned bm = __ballot_sync(0xffffffffu, m != 0u);
+            const int p = cnt + __popc(bm & lt);
+            if (m != 0u && p < cap) out[p] = (unsigned)tq | (m << 16);
+            cnt += __popc(bm);
+            const int rest = qn - 32;
+            const int moved = lane < rest ? qw[32 + lane] : 0;
+            __syncwarp();
+            if (lane < rest) qw[lane] = moved;
+            __syncwarp();
+            qn = rest;
+          }
+        }
+      }
+      if (qn > 0) {
+        unsigned m = 0u;
+        int tq = 0;
+        if (lane < qn) {
+          tq = qw[lane];
+          m = pair_mask(pi, ti, sp[tq], st[tq], rl2);
+        }
+        const unsigned bm = __ballot_sync(0xffffffffu, m != 0u);
+        const int p = cnt + __popc(bm & lt);
+        if (m != 0u && p < cap) out[p] = (unsigned)tq | (m << 16);
+        cnt += __popc(bm);
+      }
+      __syncwarp();
       if (lane == 0) {
         ncl[cl] = min(cnt, cap);
         if (cnt > cap) atomicOr(flags, kFlagNbrOverflow);
@@ -250,6 +331,43 @@ __device__ __forceinline__ int acc_fix(float f) { return __float2int_rn(f); }
 __device__ __forceinline__ void range_check(float sx, float sy, float sz, unsigned* flags) {
   const float a = fabsf(sx) + fabsf(sy) + fabsf(sz);
   if (!(a < 1.0e9f)) atomicOr(flags, (a == a && a <= 3.4e38f) ? kFlagFixOverflow : kFlagNaN);
+}
+
+// One list entry against the cluster's four atoms with packed FP32 pairs
+// (two atoms per float2 lane: 0,1 and 2,3; one FFMA2 does both): the force
+// on the four atoms is added to f*[2] and minus the force on j, summed over
+// the four atoms, is returned in g*.  Same arithmetic per pair as the scalar
+// form (rcp of r^2, r2inv = 0 beyond r_c or outside the mask).
+__device__ __forceinline__ void entry_packed(const float2 (&px)[2], const float2 (&py)[2], const float2 (&pz)[2],
+                                             const float2 (&a0)[2], const float2 (&da)[2], const float2 (&nb0)[2],
+                                             const float2 (&ndb)[2], float rc2, const float4& w, unsigned m,
+                                             float2 (&fx)[2], float2 (&fy)[2], float2 (&fz)[2], float& gx, float& gy,
+                                             float& gz) {
+  const float2 wx = make_float2(-w.x, -w.x), wy = make_float2(-w.y, -w.y), wz = make_float2(-w.z, -w.z);
+  const float2 wt = make_float2(w.w, w.w);
+  float2 sx = make_float2(0.f, 0.f), sy = make_float2(0.f, 0.f), sz = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int p = 0; p < 2; ++p) {
+    const float2 dx = __fadd2_rn(px[p], wx), dy = __fadd2_rn(py[p], wy), dz = __fadd2_rn(pz[p], wz);
+    float2 r2 = __fmul2_rn(dx, dx);
+    r2 = __ffma2_rn(dy, dy, r2);
+    r2 = __ffma2_rn(dz, dz, r2);
+    const float q0 = rcp_approx(r2.x), q1 = rcp_approx(r2.y);
+    const bool k0 = ((m >> (2 * p)) & 1u) && r2.x < rc2, k1 = ((m >> (2 * p + 1)) & 1u) && r2.y < rc2;
+    const float2 ir2 = make_float2(k0 ? q0 : 0.f, k1 ? q1 : 0.f);
+    const float2 ir4 = __fmul2_rn(ir2, ir2), ir6 = __fmul2_rn(ir4, ir2), ir8 = __fmul2_rn(ir4, ir4);
+    const float2 A = __ffma2_rn(wt, da[p], a0[p]), nB = __ffma2_rn(wt, ndb[p], nb0[p]);
+    const float2 ff = __fmul2_rn(ir8, __ffma2_rn(A, ir6, nB));
+    fx[p] = __ffma2_rn(ff, dx, fx[p]);
+    fy[p] = __ffma2_rn(ff, dy, fy[p]);
+    fz[p] = __ffma2_rn(ff, dz, fz[p]);
+    sx = __ffma2_rn(ff, dx, sx);
+    sy = __ffma2_rn(ff, dy, sy);
+    sz = __ffma2_rn(ff, dz, sz);
+  }
+  gx = -(sx.x + sx.y);
+  gy = -(sy.x + sy.y);
+  gz = -(sz.x + sz.y);
 }
 
 // Lanes per cluster LP: a warp works on 32 / LP clusters at once (adjacent
@@ -340,6 +458,20 @@ __global__ void __launch_bounds__(NT, ENERGY ? 512 / NT : 768 / NT) k_cl_force(
 #pragma unroll
         for (int u = 0; u < 4; ++u) fi[u][0] = fi[u][1] = fi[u][2] = 0.f;
         float ev[kEnergyVals] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        // packed copies for the force-only form (atoms 0,1 and 2,3)
+        float2 px[2], py[2], pz[2], pa0[2], pda[2], pnb0[2], pndb[2];
+        float2 qx[2], qy[2], qz[2];
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+          px[p] = make_float2(pi[2 * p].x, pi[2 * p + 1].x);
+          py[p] = make_float2(pi[2 * p].y, pi[2 * p + 1].y);
+          pz[p] = make_float2(pi[2 * p].z, pi[2 * p + 1].z);
+          pa0[p] = make_float2(a0[2 * p], a0[2 * p + 1]);
+          pda[p] = make_float2(da[2 * p], da[2 * p + 1]);
+          pnb0[p] = make_float2(-b0[2 * p], -b0[2 * p + 1]);
+          pndb[p] = make_float2(-db[2 * p], -db[2 * p + 1]);
+          qx[p] = qy[p] = qz[p] = make_float2(0.f, 0.f);
+        }
         const unsigned* L = list + (size_t)(valid ? T.cl0[h] + k : 0) * cap;
         // entries two iterations ahead in flight
         unsigned E0 = sl < n ? __ldg(L + sl) : 0u;
@@ -351,12 +483,18 @@ __global__ void __launch_bounds__(NT, ENERGY ? 512 / NT : 768 / NT) k_cl_force(
             const unsigned m = E0 >> 16;
             const float4 w = sp[t];
             float gx = 0.f, gy = 0.f, gz = 0.f;
+            if (kPackedPairs && !ENERGY)
+              entry_packed(px, py, pz, pa0, pda, pnb0, pndb, rc2, w, m, qx, qy, qz, gx, gy, gz);
+            else
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
               const float dx = pi[u].x - w.x, dy = pi[u].y - w.y, dz = pi[u].z - w.z;
               const float r2 = dx * dx + dy * dy + dz * dz;
               const bool keep = ((m >> u) & 1u) && r2 < rc2;
-              const float ir2 = keep ? rcp_approx(r2) : 0.f;
+              // the reciprocal for every pair, then a select: no branch
+              // around the inline instruction
+              const float rr = rcp_approx(r2);
+              const float ir2 = keep ? rr : 0.f;
               const float ir6 = ir2 * ir2 * ir2;
               const float A = fmaf(w.w, da[u], a0[u]), B = fmaf(w.w, db[u], b0[u]);
               const float ff = ir2 * ir6 * (A * ir6 - B);
@@ -383,6 +521,14 @@ __global__ void __launch_bounds__(NT, ENERGY ? 512 / NT : 768 / NT) k_cl_force(
           }
           E0 = E1;
           E1 = E2;
+        }
+        if (kPackedPairs && !ENERGY) {
+#pragma unroll
+          for (int p = 0; p < 2; ++p) {
+            fi[2 * p][0] = qx[p].x; fi[2 * p + 1][0] = qx[p].y;
+            fi[2 * p][1] = qy[p].x; fi[2 * p + 1][1] = qy[p].y;
+            fi[2 * p][2] = qz[p].x; fi[2 * p + 1][2] = qz[p].y;
+          }
         }
         // forces on the cluster's atoms: fixed butterfly over the LP lanes
 #pragma unroll
