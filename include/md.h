@@ -71,9 +71,27 @@ typedef struct {
   int32_t pad;
 } md_params;
 
+/* Molecule topology (Sec. 3.3): the one molecule type of a system, naom
+ * atoms with a bond graph and a type per atom.  From it the library builds
+ * the per-type lists the paper describes: t_exclusions (every atom's 1-2
+ * and 1-3 neighbours, left out of the LJ sum, Sec. 3.1), t_bonds, t_angles
+ * (every path a-b-c, vertex b) and the dihedral analogue (every path
+ * a-b-c-d around each bond b-c), and evaluates every term once per molecule.
+ * Copied during md_create.  md_desc.topology = NULL means linear chains of
+ * sites_per_chain atoms with C_33 ends (the paper's polyethylene), which
+ * take the faster chain kernels; a topology needs the mixed precision form,
+ * and md_observables, md_acf_sample and md_rdf (defined for linear chains)
+ * then return MD_EINVAL. */
+typedef struct {
+  int32_t naom;                /* atoms per molecule (NAOM, Table II), 4 .. 1023 */
+  int32_t n_bonds;             /* bonds per molecule, 1 .. 4 naom */
+  const int32_t *bonds;        /* [2 * n_bonds] atom pairs, 0-based index in the molecule (MAIDX - 1) */
+  const int32_t *types;        /* [naom] 0 = C_32, 1 = C_33 (LJ parameters and mass) */
+} md_topology;
+
 typedef struct {
   int32_t n_replicas;          /* independent systems stepped together (>= 1) */
-  int32_t sites_per_chain;     /* NAOM (Table II), 4 .. 511; at most 2^20 - 1 chains in all */
+  int32_t sites_per_chain;     /* NAOM (Table II), 4 .. 1022 (.. 1023 with a topology); < 2^20 chains in all */
   const int32_t *n_chains;     /* [n_replicas] */
   const double *box;           /* [n_replicas] cube side L, nm; L >= 3 (rc + skin) */
   const double *pos;           /* [3 * N] x,y,z per atom, original order (any image) */
@@ -100,6 +118,8 @@ typedef struct {
   int32_t schedule;            /* MD_SCHED_GRID or MD_SCHED_PERSISTENT (see below) */
   int32_t lj_lanes;            /* lanes of the LJ kernel that share one 4-atom cluster's list:
                                   8, 16 or 32 (0 = 16) */
+  const md_topology *topology; /* NULL: linear chains; else the molecule type (sites_per_chain must
+                                  equal topology->naom) */
   void *cuda_stream;           /* cudaStream_t to run on; NULL = a stream the library creates */
   void *workspace;             /* optional DEVICE memory for all buffers (see md_workspace_size);
                                   NULL = the library allocates.  Must outlive the system. */

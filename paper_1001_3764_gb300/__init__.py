@@ -40,6 +40,11 @@ class md_params(ctypes.Structure):
                 ("n_mult", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
+class md_topology(ctypes.Structure):
+    _fields_ = [("naom", ctypes.c_int32), ("n_bonds", ctypes.c_int32), ("bonds", ctypes.c_void_p),
+                ("types", ctypes.c_void_p)]
+
+
 class md_desc(ctypes.Structure):
     _fields_ = [("n_replicas", ctypes.c_int32), ("sites_per_chain", ctypes.c_int32),
                 ("n_chains", ctypes.c_void_p), ("box", ctypes.c_void_p), ("pos", ctypes.c_void_p),
@@ -48,6 +53,7 @@ class md_desc(ctypes.Structure):
                 ("tau_t", ctypes.c_double), ("rebin_every", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("thermostat", ctypes.c_int32), ("nbr_capacity", ctypes.c_int32),
                 ("lj_block", ctypes.c_int32), ("schedule", ctypes.c_int32), ("lj_lanes", ctypes.c_int32),
+                ("topology", ctypes.c_void_p),
                 ("cuda_stream", ctypes.c_void_p), ("workspace", ctypes.c_void_p),
                 ("workspace_bytes", ctypes.c_size_t)]
 
@@ -385,7 +391,8 @@ class System:
                  skin: float = 0.1, rebin_every: int = 10, thermostat: int = MD_NVE, T_target=None,
                  tau_t: float = 0.1, params: dict | None = None, nbr_capacity: int = 0, device: int = 0,
                  use_torch_memory: bool = True, lj_block: int = 0, schedule: int = MD_SCHED_GRID,
-                 lj_lanes: int = 0, autotune: bool = False, tune_cycles: int = 2, tune_cache: str | None = None):
+                 lj_lanes: int = 0, autotune: bool = False, tune_cycles: int = 2, tune_cache: str | None = None,
+                 topology=None):
         import torch
         load()
         if isinstance(melts, dict):
@@ -414,6 +421,12 @@ class System:
         d.rebin_every, d.precision, d.thermostat = rebin_every, precision, thermostat
         d.nbr_capacity = nbr_capacity
         d.lj_block, d.schedule, d.lj_lanes = lj_block, schedule, lj_lanes
+        if topology is not None:
+            # (bonds [n_bonds, 2], types [naom]) of the molecule type (Sec. 3.3)
+            self._tb = np.ascontiguousarray(np.asarray(topology[0], np.int32).reshape(-1, 2))
+            self._tt = np.ascontiguousarray(np.asarray(topology[1], np.int32))
+            self._topo = md_topology(len(self._tt), len(self._tb), _p(self._tb), _p(self._tt))
+            d.topology = ctypes.cast(ctypes.pointer(self._topo), ctypes.c_void_p)
         self.tuning = md_autotune(d, tune_cycles, tune_cache) if autotune else None
         d.cuda_stream = self.stream.cuda_stream
         self.workspace = None

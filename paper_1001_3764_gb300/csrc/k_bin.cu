@@ -141,7 +141,8 @@ constexpr int kSortCap = 2048;
 
 template <typename T>
 __global__ void __launch_bounds__(128) k_cell_sort(const T* __restrict__ x, int N, const int* __restrict__ cell_start,
-                                                   const int* __restrict__ tmp, const int* __restrict__ cellc,
+                                                   const int* __restrict__ tmp, const unsigned char* __restrict__ mtype,
+                                                   const int* __restrict__ cellc,
                                                    const uint16_t* __restrict__ site, const RepDev* __restrict__ reps,
                                                    int n_reps, int sites, int* __restrict__ perm,
                                                    int* __restrict__ inv_perm, float4* __restrict__ pos,
@@ -183,7 +184,7 @@ __global__ void __launch_bounds__(128) k_cell_sort(const T* __restrict__ x, int 
     }
     const int st = site[id];
     const int chain = R.chain_off + (id - R.atom_off) / sites;
-    const int type = (st == 0 || st == sites - 1) ? 1 : 0;
+    const int type = mtype ? (int)mtype[st] : ((st == 0 || st == sites - 1) ? 1 : 0);
     p.w = (float)type;   // LJ type: the pipelined force kernel copies positions as they are
     pos[s] = p;
     ref[id] = p;
@@ -191,14 +192,15 @@ __global__ void __launch_bounds__(128) k_cell_sort(const T* __restrict__ x, int 
   }
 }
 
-void launch_cell_sort(bool mixed, const void* x, int N, const int* cell_start, const int* tmp, const int* cellc,
+void launch_cell_sort(bool mixed, const void* x, int N, const int* cell_start, const int* tmp,
+                      const unsigned char* mtype, const int* cellc,
                       const uint16_t* site, const RepDev* reps, int n_reps, int C, int sites, int* perm,
                       int* inv_perm, float4* pos, int* tag, float4* ref, unsigned* flags, cudaStream_t st) {
   if (mixed)
-    k_cell_sort<double><<<C, 128, 0, st>>>((const double*)x, N, cell_start, tmp, cellc, site, reps, n_reps, sites,
+    k_cell_sort<double><<<C, 128, 0, st>>>((const double*)x, N, cell_start, tmp, mtype, cellc, site, reps, n_reps, sites,
                                            perm, inv_perm, pos, tag, ref, flags);
   else
-    k_cell_sort<float><<<C, 128, 0, st>>>((const float*)x, N, cell_start, tmp, cellc, site, reps, n_reps, sites,
+    k_cell_sort<float><<<C, 128, 0, st>>>((const float*)x, N, cell_start, tmp, mtype, cellc, site, reps, n_reps, sites,
                                           perm, inv_perm, pos, tag, ref, flags);
 }
 

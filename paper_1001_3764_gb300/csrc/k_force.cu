@@ -254,6 +254,137 @@ __global__ void __launch_bounds__(kBondedBlock) k_bonded(const void* __restrict_
   }
 }
 
+// ======================================================================= bonded, general molecules
+// A general molecule type (Sec. 3.3, t_bonds / t_angles / dihedral lists):
+// one thread per atom of an integrator tile evaluates the terms listed under
+// that atom (each term once, under its first atom) and adds their forces to
+// every atom of the term with int64 atomics (integer sums: order-free, so
+// deterministic).  The separations are FP64 minimum-image differences of the
+// master positions rounded to FP32, as in the chain kernel, and the term
+// formulas are those of the chain kernel.  k_bonded_init first writes the
+// LJ force of every atom into F.
+
+// FP32 separation x_b - x_a and, for a bond, |x_b - x_a|^2 - b0^2 in FP64
+__device__ __forceinline__ f3 sep_ab(const double* x, int N, int a, int b, const RepDev& R) {
+  const double dx = bond_diff(x[a], x[b], R.L, R.half_L);
+  const double dy = bond_diff(x[N + a], x[N + b], R.L, R.half_L);
+  const double dz = bond_diff(x[2 * N + a], x[2 * N + b], R.L, R.half_L);
+  return mk(d2f_rn_int(dx), d2f_rn_int(dy), d2f_rn_int(dz));
+}
+
+__device__ __forceinline__ void fix_add(F4i* F, int i, f3 f, unsigned* flags) {
+  atomicAdd(reinterpret_cast<unsigned long long*>(&F[i].x), (unsigned long long)to_fix(f.x, flags));
+  atomicAdd(reinterpret_cast<unsigned long long*>(&F[i].y), (unsigned long long)to_fix(f.y, flags));
+  atomicAdd(reinterpret_cast<unsigned long long*>(&F[i].z), (unsigned long long)to_fix(f.z, flags));
+}
+
+__global__ void __launch_bounds__(256) k_bonded_init(const int* __restrict__ inv_perm, const long long* __restrict__ flj,
+                                                     int Npad, int N, F4i* __restrict__ F) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int s = inv_perm[i];
+  F4i o;
+  o.x = __ldg(flj + s); o.y = __ldg(flj + Npad + s); o.z = __ldg(flj + 2 * (size_t)Npad + s); o.w = 0;
+  F[i] = o;
+}
+
+template <bool ENERGY>
+__global__ void __launch_bounds__(kBondedBlock) k_bonded_generic(const double* __restrict__ x, int N,
+                                                                 const Tile* __restrict__ tiles,
+                                                                 const RepDev* __restrict__ reps, const ForceParams fp,
+                                                                 const TopoDev tp, F4i* __restrict__ F,
+                                                                 double* __restrict__ epart,
+                                                                 unsigned* __restrict__ flags) {
+  const Tile t = tiles[blockIdx.x];
+  const RepDev& R = reps[t.rep];
+  float Eb = 0.f, Ea = 0.f, Ed = 0.f;
+  float W[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  if ((int)threadIdx.x < t.len) {
+    const int i = t.start + threadIdx.x;
+    const int a = (i - R.atom_off) % tp.naom, m0 = i - a;
+    // bonds (a, b), Eq. (4)
+    for (int q = tp.b_off[a]; q < tp.b_off[a + 1]; ++q) {
+      const int j = m0 + tp.b_at[q];
+      const f3 b = sep_ab(x, N, i, j, R);
+      const double dx = bond_diff(x[i], x[j], R.L, R.half_L), dy = bond_diff(x[N + i], x[N + j], R.L, R.half_L);
+      const double dz = bond_diff(x[2 * N + i], x[2 * N + j], R.L, R.half_L);
+      const float D = d2f_rn_int(fma(dx, dx, fma(dy, dy, fma(dz, dz, -fp.b0sq))));
+      const float r = sqrtf(dot(b, b));
+      const float dr = D / (r + fp.b0);   // r - b0 without cancellation
+      const f3 fb = (fp.kb * dr / r) * b; // force on a
+      fix_add(F, i, fb, flags);
+      fix_add(F, j, -fb, flags);
+      if (ENERGY) { Eb += 0.5f * fp.kb * dr * dr; add_vir(W, b, -fb); }
+    }
+    // angles (a, b, c), vertex b, Eq. (5)
+    for (int q = tp.a_off[a]; q < tp.a_off[a + 1]; ++q) {
+      const int jb = m0 + tp.a_at[2 * q], jc = m0 + tp.a_at[2 * q + 1];
+      const f3 u = sep_ab(x, N, jb, i, R), w = sep_ab(x, N, jb, jc, R);
+      const float lu = sqrtf(dot(u, u)), lw = sqrtf(dot(w, w));
+      const f3 cr = cross(u, w);
+      const float sn = sqrtf(dot(cr, cr)), cs = dot(u, w);
+      const float th = atan2f(sn, cs);
+      const float dth = th - fp.theta0;
+      const float inv = 1.0f / (lu * lw);
+      const float sin_t = sn * inv, cos_t = cs * inv;
+      f3 fa = mk(0.f, 0.f, 0.f), fc = fa;
+      if (sin_t > 1e-6f) {
+        const float g = fp.ka * dth / sin_t;
+        const f3 uh = (1.0f / lu) * u, wh = (1.0f / lw) * w;
+        fa = (g / lu) * (wh - cos_t * uh);
+        fc = (g / lw) * (uh - cos_t * wh);
+      }
+      fix_add(F, i, fa, flags);
+      fix_add(F, jc, fc, flags);
+      fix_add(F, jb, -(fa + fc), flags);
+      if (ENERGY) { Ea += 0.5f * fp.ka * dth * dth; add_vir(W, u, fa); add_vir(W, w, fc); }
+    }
+    // dihedrals (a, b, c, d), Eq. (6), IUPAC phi
+    for (int q = tp.d_off[a]; q < tp.d_off[a + 1]; ++q) {
+      const int jb = m0 + tp.d_at[3 * q], jc = m0 + tp.d_at[3 * q + 1], jd = m0 + tp.d_at[3 * q + 2];
+      const f3 b1 = sep_ab(x, N, i, jb, R), b2 = sep_ab(x, N, jb, jc, R), b3 = sep_ab(x, N, jc, jd, R);
+      const f3 mm = cross(b1, b2), nn = cross(b2, b3);
+      const float lb2 = sqrtf(dot(b2, b2)), m2 = dot(mm, mm), n2 = dot(nn, nn);
+      const float phi = atan2f(lb2 * dot(b1, nn), dot(mm, nn));
+      const float arg = (float)fp.n_mult * phi - fp.phis;
+      float sa, ca;
+      sincosf(arg, &sa, &ca);
+      if (m2 > 1e-24f && n2 > 1e-24f) {
+        const float dEdphi = -fp.kphi * (float)fp.n_mult * sa;
+        const float cam = -lb2 / m2, cdn = lb2 / n2;
+        const float cbm = lb2 / m2 + dot(b1, b2) / (lb2 * m2), cbn = dot(b2, b3) / (lb2 * n2);
+        const f3 ga = cam * mm, gd = cdn * nn, gb = cbm * mm + cbn * nn;
+        const f3 gc = -(ga + gb + gd);
+        const f3 f1 = -dEdphi * ga, f2 = -dEdphi * gb, f3v = -dEdphi * gc;
+        const f3 f4 = -(f1 + f2 + f3v);
+        fix_add(F, i, f1, flags);
+        fix_add(F, jb, f2, flags);
+        fix_add(F, jc, f3v, flags);
+        fix_add(F, jd, f4, flags);
+        if (ENERGY) { add_vir(W, b1, f2); add_vir(W, b1 + b2, f3v); add_vir(W, b1 + b2 + b3, f4); }
+      }
+      if (ENERGY) Ed += fp.kphi * (1.0f + ca);
+    }
+  }
+  if (ENERGY) {
+    const float v[kBondedVals] = {Eb, Ea, Ed, W[0], W[1], W[2], W[3], W[4], W[5]};
+    block_sum<kBondedVals, kBondedBlock>(v, epart + (size_t)blockIdx.x * kBondedVals);
+  }
+}
+
+void launch_bonded_generic(bool energy, const double* x, const int* inv_perm, const long long* flj, int Npad, int N,
+                           const Tile* tiles, int n_tiles, const RepDev* reps, const ForceParams& fp,
+                           const TopoDev& topo, void* F, double* epart, unsigned* flags, cudaStream_t st) {
+  if (N <= 0) return;
+  k_bonded_init<<<(N + 255) / 256, 256, 0, st>>>(inv_perm, flj, Npad, N, reinterpret_cast<F4i*>(F));
+  if (energy)
+    k_bonded_generic<true><<<n_tiles, kBondedBlock, 0, st>>>(x, N, tiles, reps, fp, topo, reinterpret_cast<F4i*>(F),
+                                                             epart, flags);
+  else
+    k_bonded_generic<false><<<n_tiles, kBondedBlock, 0, st>>>(x, N, tiles, reps, fp, topo, reinterpret_cast<F4i*>(F),
+                                                              epart, flags);
+}
+
 void launch_bonded(bool mixed, bool energy, const void* x, const uint16_t* site, const int* inv_perm,
                    const long long* flj, int Npad, int N, const Tile* tiles, int n_tiles, const RepDev* reps,
                    const ForceParams& fp, void* F, double* epart, unsigned* flags, cudaStream_t st) {

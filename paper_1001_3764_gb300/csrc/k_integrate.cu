@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(kIntBlock) k_integrate(void* __restrict__ xv, 
   double mom[3] = {0.0, 0.0, 0.0};   // Nose-Hoover: momentum of v_{k+1/2}
   if ((int)threadIdx.x < t.len) {
     const int sm = site[i];
-    const int type = (sm == 0 || sm == fp.sites - 1) ? 1 : 0;
+    const int type = atom_type(sm, fp);
     // mixed form: F stays in fixed-point units (int64 -> FP64 is a fast
     // conversion) and 2^-32 is folded into dt / 2m
     T hdt_m;
@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(kIntBlock) k_integrate(void* __restrict__ xv, 
             double* nh = lam + 6 * r;
             const double xi = nh[0] + fp.dt * (T_half - Q.T0) / Qm;
             const double c = 0.5 * fp.dt * xi;
-            const double M = (double)Q.n_chains * ((double)(fp.sites - 2) * fp.mass[0] + 2.0 * fp.mass[1]);
+            const double M = (double)Q.n_chains * fp.mol_mass;
             nh[0] = xi; nh[1] = 1.0 - c; nh[2] = 1.0 / (1.0 + c);
             nh[3] = P[0] / M; nh[4] = P[1] / M; nh[5] = P[2] / M;
           }

@@ -163,28 +163,43 @@ __device__ __forceinline__ void persistent_done(int* work) {
 // rather than on every 32nd atom of the tile.
 constexpr int kBuildQueue = 64;
 
+// is atom b of a molecule a 1-2 or 1-3 neighbour of atom a (general type)?
+__device__ __forceinline__ bool topo_excluded(int a, int b, const TopoDev& tp) {
+  for (int q = tp.x_off[a]; q < tp.x_off[a + 1]; ++q)
+    if (tp.x_at[q] == b) return true;
+  return a == b;
+}
+
 // the four-atom test of candidate t: bit u set if atom u of the cluster pairs with t
+template <bool GEN>
 __device__ __forceinline__ unsigned pair_mask(const float4 (&pi)[4], const int (&ti)[4], const float4& w, int tg,
-                                              float rl2) {
+                                              float rl2, const TopoDev& tp) {
   unsigned m = 0u;
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
     const float dx = pi[u].x - w.x, dy = pi[u].y - w.y, dz = pi[u].z - w.z;
-    // |i - j| <= 2 within one chain: 1-2 and 1-3 neighbours (and i itself)
-    const bool keep = (dx * dx + dy * dy + dz * dz < rl2) & ((unsigned)(ti[u] - tg + 2) > 4u);
+    bool keep = dx * dx + dy * dy + dz * dz < rl2;
+    if (GEN) {
+      // same molecule: its exclusion list (Sec. 3.1, t_exclusions)
+      if (keep && ((ti[u] ^ tg) >> kTagSiteBits) == 0)
+        keep = !topo_excluded(ti[u] & ((1 << kTagSiteBits) - 1), tg & ((1 << kTagSiteBits) - 1), tp);
+    } else {
+      // |i - j| <= 2 within one chain: 1-2 and 1-3 neighbours (and i itself)
+      keep &= (unsigned)(ti[u] - tg + 2) > 4u;
+    }
     m |= keep ? (1u << u) : 0u;
   }
   return m;
 }
 
-template <int NT>
+template <int NT, bool GEN>
 __global__ void __launch_bounds__(NT) k_cl_build(const float4* __restrict__ pos, const int* __restrict__ tag,
                                                  const int* __restrict__ cell_start, const int* __restrict__ cl_start,
                                                  const Region* __restrict__ regions, int n_regions,
                                                  const RegionShape* __restrict__ shapes, const RepDev* __restrict__ reps,
                                                  unsigned* __restrict__ list, int* __restrict__ ncl, int cap,
                                                  int tile_cap, unsigned* __restrict__ flags, int persistent,
-                                                 int* __restrict__ work) {
+                                                 int* __restrict__ work, const TopoDev tp) {
   extern __shared__ __align__(16) unsigned char smem[];
   float4* sp = reinterpret_cast<float4*>(smem);
   int* st = reinterpret_cast<int*>(smem + (size_t)tile_cap * sizeof(float4));
@@ -255,7 +270,7 @@ __global__ void __launch_bounds__(NT) k_cl_build(const float4* __restrict__ pos,
           const int t = t0 + lane;
           unsigned m = 0u;
           if (t < t_end) {
-            m = pair_mask(pi, ti, sp[t], st[t], rl2);
+            m = pair_mask<GEN>(pi, ti, sp[t], st[t], rl2, tp);
             m &= ((t > i0) ? 1u : 0u) | ((t > i0 + 1) ? 2u : 0u) | ((t > i0 + 2) ? 4u : 0u) | ((t > i0 + 3) ? 8u : 0u);
           }
           const unsigned b = __ballot_sync(0xffffffffu, m != 0u);
@@ -283,7 +298,7 @@ __global__ void __launch_bounds__(NT) k_cl_build(const float4* __restrict__ pos,
           __syncwarp();
           if (qn >= 32) {
             const int tq = qw[lane];
-            const unsigned m = pair_mask(pi, ti, sp[tq], st[tq], rl2);
+            const unsigned m = pair_mask<GEN>(pi, ti, sp[tq], st[tq], rl2, tp);
             const unsigned bm = __ballot_sync(0xffffffffu, m != 0u);
             const int p = cnt + __popc(bm & lt);
             if (m != 0u && p < cap) out[p] = (unsigned)tq | (m << 16);
@@ -302,7 +317,7 @@ __global__ void __launch_bounds__(NT) k_cl_build(const float4* __restrict__ pos,
         int tq = 0;
         if (lane < qn) {
           tq = qw[lane];
-          m = pair_mask(pi, ti, sp[tq], st[tq], rl2);
+          m = pair_mask<GEN>(pi, ti, sp[tq], st[tq], rl2, tp);
         }
         const unsigned bm = __ballot_sync(0xffffffffu, m != 0u);
         const int p = cnt + __popc(bm & lt);
@@ -597,12 +612,16 @@ size_t cl_force_smem(int tile_cap) { return (size_t)tile_cap * (sizeof(float4) +
 void launch_cl_build(const float4* pos, const int* tag, const int* cell_start, const int* cl_start,
                      const Region* regions, int n_regions, const RegionShape* shapes, const RepDev* reps,
                      unsigned* list, int* ncl, int cap, int tile_cap, unsigned* flags, int persistent_grid, int* work,
-                     cudaStream_t st) {
+                     const TopoDev* topo, cudaStream_t st) {
   if (n_regions <= 0) return;
   const int grid = persistent_grid > 0 ? persistent_grid : n_regions;
-  k_cl_build<256><<<grid, 256, cl_build_smem(tile_cap), st>>>(pos, tag, cell_start, cl_start, regions, n_regions,
-                                                              shapes, reps, list, ncl, cap, tile_cap, flags,
-                                                              persistent_grid > 0, work);
+  const size_t sm = cl_build_smem(tile_cap);
+  if (topo)
+    k_cl_build<256, true><<<grid, 256, sm, st>>>(pos, tag, cell_start, cl_start, regions, n_regions, shapes, reps, list,
+                                                 ncl, cap, tile_cap, flags, persistent_grid > 0, work, *topo);
+  else
+    k_cl_build<256, false><<<grid, 256, sm, st>>>(pos, tag, cell_start, cl_start, regions, n_regions, shapes, reps,
+                                                  list, ncl, cap, tile_cap, flags, persistent_grid > 0, work, TopoDev{});
 }
 
 void launch_cl_force(bool energy, const float4* pos, const int* cell_start, const int* cl_start,
@@ -646,7 +665,8 @@ int lj_blocks_per_sm(int block, int lanes, int tile_cap) {
 // attribute is an upper bound, set for the largest tile accepted.
 cudaError_t tile_kernels_init() {
   const int mb = (int)cl_build_smem(kStageCapMax), mf = (int)cl_force_smem(kStageCapMax);
-  cudaError_t e = cudaFuncSetAttribute(k_cl_build<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, mb);
+  cudaError_t e = cudaFuncSetAttribute(k_cl_build<256, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mb);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cl_build<256, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mb);
 #define MDG_ATTR(E, NT, LP) \
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cl_force<E, NT, LP>, cudaFuncAttributeMaxDynamicSharedMemorySize, mf);
 #define MDG_ATTR3(E, NT) MDG_ATTR(E, NT, 8) MDG_ATTR(E, NT, 16) MDG_ATTR(E, NT, 32)

@@ -92,6 +92,12 @@ struct md_system {
   std::vector<cudaGraphExec_t> rem_graphs;   // blocks of k < R steps (remainders), captured on first use
   cudaStream_t side = nullptr;               // captures the bodies of the conditional rebins
   unsigned long long* early = nullptr;       // early rebins (displacement beyond skin/2) so far
+  // a general molecule type (md_desc.topology), or linear chains
+  bool generic = false;
+  std::vector<unsigned char> mtype_h;        // type of each atom of the molecule
+  std::vector<int> t_boff, t_bat, t_aoff, t_aat, t_doff, t_dat, t_xoff, t_xat;   // term and exclusion lists
+  unsigned char* mtype = nullptr;            // device copies
+  TopoDev topo{};
   bool fresh = false;                        // bins, list and forces are those of the current positions
   bool profile = false;
   std::vector<cudaEvent_t> ev;
@@ -157,6 +163,14 @@ static void fill_force_params(md_system* s) {
   }
   f.dt_f = (float)s->dt;
   f.dt = s->dt;
+  if (s->generic) {
+    double mm = 0.0;
+    for (unsigned char t : s->mtype_h) mm += p.mass[t];
+    f.mol_mass = mm;
+  } else {
+    f.mol_mass = (double)(s->S - 2) * p.mass[0] + 2.0 * p.mass[1];
+  }
+  f.mtype = s->generic ? s->mtype : nullptr;
 }
 
 // Region shapes: sx x sy x 1 home cells (sx, sy in {1, 2}; shape id
@@ -197,11 +211,94 @@ static RegionShape make_shape(int sx, int sy) {
   return S;
 }
 
+// The per-type lists of Sec. 3.3 from a molecule's bond graph: each atom's
+// neighbours (ascending); exclusions = 1-2 and 1-3 neighbours; angles = every
+// path a-b-c (vertex b, a < c), listed under a; dihedrals = every path
+// a-b-c-d around each bond b-c (in bond order, b < c), listed under a; bonds
+// listed under their first atom as given.
+static int build_topology(md_system* s, const md_topology* t) {
+  const int n = t->naom;
+  if (n < 4 || n > 1023) return fail(s, MD_EINVAL, "topology: naom must be 4 .. 1023");
+  if (t->n_bonds < 1 || t->n_bonds > 4 * n || !t->bonds || !t->types)
+    return fail(s, MD_EINVAL, "topology: 1 .. 4 naom bonds, bonds and types required");
+  std::vector<std::vector<int>> nb(n);
+  std::vector<std::pair<int, int>> bl;
+  for (int k = 0; k < t->n_bonds; ++k) {
+    const int a = t->bonds[2 * k], b = t->bonds[2 * k + 1];
+    if (a < 0 || b < 0 || a >= n || b >= n || a == b) return fail(s, MD_EINVAL, "topology: bond atom out of range");
+    for (int c : nb[a])
+      if (c == b) return fail(s, MD_EINVAL, "topology: repeated bond");
+    nb[a].push_back(b);
+    nb[b].push_back(a);
+    bl.push_back({a, b});
+  }
+  for (auto& v : nb) std::sort(v.begin(), v.end());
+  s->mtype_h.assign(n, 0);
+  for (int a = 0; a < n; ++a) {
+    if (t->types[a] != 0 && t->types[a] != 1) return fail(s, MD_EINVAL, "topology: types must be 0 or 1");
+    s->mtype_h[a] = (unsigned char)t->types[a];
+  }
+  std::vector<std::vector<int>> ob(n), oa(n), od(n), ex(n);
+  for (auto& e : bl) ob[e.first].push_back(e.second);
+  for (int b = 0; b < n; ++b)
+    for (size_t p = 0; p < nb[b].size(); ++p)
+      for (size_t q = p + 1; q < nb[b].size(); ++q) {
+        oa[nb[b][p]].push_back(b);
+        oa[nb[b][p]].push_back(nb[b][q]);
+      }
+  for (auto& e : bl) {
+    const int b = std::min(e.first, e.second), c = std::max(e.first, e.second);
+    for (int a : nb[b]) {
+      if (a == c) continue;
+      for (int d : nb[c]) {
+        if (d == b || d == a) continue;
+        od[a].push_back(b); od[a].push_back(c); od[a].push_back(d);
+      }
+    }
+  }
+  for (int a = 0; a < n; ++a) {
+    for (int b : nb[a]) {
+      ex[a].push_back(b);
+      for (int c : nb[b])
+        if (c != a) ex[a].push_back(c);
+    }
+    std::sort(ex[a].begin(), ex[a].end());
+    ex[a].erase(std::unique(ex[a].begin(), ex[a].end()), ex[a].end());
+  }
+  auto csr = [n](const std::vector<std::vector<int>>& v, std::vector<int>& off, std::vector<int>& at) {
+    off.assign(n + 1, 0);
+    at.clear();
+    for (int a = 0; a < n; ++a) { at.insert(at.end(), v[a].begin(), v[a].end()); off[a + 1] = (int)at.size(); }
+    if (at.empty()) at.push_back(0);
+  };
+  csr(ob, s->t_boff, s->t_bat);
+  csr(oa, s->t_aoff, s->t_aat);
+  csr(od, s->t_doff, s->t_dat);
+  csr(ex, s->t_xoff, s->t_xat);
+  // the CSR offsets of angles and dihedrals count ints; the kernels index terms
+  for (int& o : s->t_aoff) o /= 2;
+  for (int& o : s->t_doff) o /= 3;
+  return MD_OK;
+}
+
 // Validate the descriptor and fill geometry, tiles and sizes (no device work).
 static int configure(md_system* s, const md_desc* d) {
   if (!d) return fail(s, MD_EINVAL, "null descriptor");
   if (d->n_replicas < 1 || d->n_replicas > kMaxReplicas) return fail(s, MD_EINVAL, "n_replicas out of range");
-  if (d->sites_per_chain < 4 || d->sites_per_chain > 511) return fail(s, MD_EINVAL, "sites_per_chain must be 4..511");
+  // chains: the packed tags keep the site in 10 bits, and the last site of one
+  // chain must stay more than 2 away from the next chain's first (1024 - S + 1 > 2)
+  if (d->sites_per_chain < 4 || d->sites_per_chain > (d->topology ? 1023 : 1022))
+    return fail(s, MD_EINVAL, "sites_per_chain must be 4..1022 (4..1023 with a topology)");
+  s->generic = d->topology != nullptr;
+  if (s->generic) {
+    if (d->topology->naom != d->sites_per_chain) return fail(s, MD_EINVAL, "sites_per_chain must equal topology->naom");
+    if (d->precision != MD_MIXED) return fail(s, MD_EINVAL, "a molecule topology needs the mixed precision form");
+    const int rc = build_topology(s, d->topology);
+    if (rc) return rc;
+  } else {
+    s->mtype_h.assign(d->sites_per_chain, 0);
+    s->mtype_h[0] = s->mtype_h[d->sites_per_chain - 1] = 1;
+  }
   if (!d->n_chains || !d->box) return fail(s, MD_EINVAL, "n_chains and box are required");
   if (!(d->dt > 0) || !(d->rc > 0) || !(d->skin >= 0) || d->rebin_every < 1)
     return fail(s, MD_EINVAL, "dt, rc must be > 0, skin >= 0, rebin_every >= 1");
@@ -343,6 +440,15 @@ static size_t plan(md_system* s, char* base) {
   s->flags = (unsigned*)take(sizeof(unsigned));
   s->early = (unsigned long long*)take(sizeof(unsigned long long));
   s->stage = (double*)take(6 * N * sizeof(double) + 3 * N * sizeof(int));   // staging: x, v (FP64), images
+  if (s->generic) {
+    s->mtype = (unsigned char*)take(s->mtype_h.size());
+    auto ti = [&](const std::vector<int>& v) { return (const int*)take(v.size() * sizeof(int)); };
+    s->topo.b_off = ti(s->t_boff); s->topo.b_at = ti(s->t_bat);
+    s->topo.a_off = ti(s->t_aoff); s->topo.a_at = ti(s->t_aat);
+    s->topo.d_off = ti(s->t_doff); s->topo.d_at = ti(s->t_dat);
+    s->topo.x_off = ti(s->t_xoff); s->topo.x_at = ti(s->t_xat);
+    s->topo.naom = s->S;
+  }
   return off;
 }
 
@@ -365,11 +471,12 @@ static void enqueue_rebin(md_system* s) {
                    s->count, s->slot, s->st);
   launch_scan2(s->count, s->cell_start, s->cl_start, s->C, s->st);
   launch_bin_scatter(s->cell_of, s->slot, s->cell_start, s->tmp, (int)s->N, s->st);
-  launch_cell_sort(s->mixed, s->x, (int)s->N, s->cell_start, s->tmp, s->cellc, s->site, s->reps, s->n_reps, s->C,
+  launch_cell_sort(s->mixed, s->x, (int)s->N, s->cell_start, s->tmp, s->fp.mtype, s->cellc, s->site, s->reps, s->n_reps, s->C,
                    s->S, s->perm, s->inv_perm, s->pos, s->tag, s->ref, s->flags, s->st);
   prof_mark(s);
   launch_cl_build(s->pos, s->tag, s->cell_start, s->cl_start, s->regions, (int)s->regions_h.size(), s->shapes,
-                  s->reps, s->list, s->ncl, s->cap, s->tile_cap, s->flags, s->persistent_grid, s->work, s->st);
+                  s->reps, s->list, s->ncl, s->cap, s->tile_cap, s->flags, s->persistent_grid, s->work,
+                  s->generic ? &s->topo : nullptr, s->st);
   prof_mark(s);
 }
 static const int kRebinLaunches = 6;   // memset counted as a launch
@@ -386,8 +493,13 @@ static void enqueue_forces(md_system* s, bool energy, void* F_out = nullptr) {
                   s->reps, s->list, s->ncl, s->cap, s->tile_cap, s->fp, flj, s->Npad, s->lj_part, s->flags,
                   s->lj_block, s->lj_lanes, s->persistent_grid, s->work, s->st);
   prof_mark(s);
-  launch_bonded(s->mixed, energy, s->x, s->site, s->inv_perm, flj, s->Npad, (int)s->N, s->tiles_int,
-                (int)s->t_int.size(), s->reps, s->fp, F_out ? F_out : s->F, s->b_part, s->flags, s->st);
+  if (s->generic)
+    launch_bonded_generic(energy, (const double*)s->x, s->inv_perm, flj, s->Npad, (int)s->N, s->tiles_int,
+                          (int)s->t_int.size(), s->reps, s->fp, s->topo, F_out ? F_out : s->F, s->b_part, s->flags,
+                          s->st);
+  else
+    launch_bonded(s->mixed, energy, s->x, s->site, s->inv_perm, flj, s->Npad, (int)s->N, s->tiles_int,
+                  (int)s->t_int.size(), s->reps, s->fp, F_out ? F_out : s->F, s->b_part, s->flags, s->st);
   prof_mark(s);
 }
 
@@ -636,6 +748,7 @@ int md_create(const md_desc* d, md_system** out) {
     s->own_mem = true;
   }
   plan(s, s->base);
+  s->fp.mtype = s->generic ? s->mtype : nullptr;
   if (d->cuda_stream) {
     s->st = (cudaStream_t)d->cuda_stream;
   } else {
@@ -682,6 +795,15 @@ int md_create(const md_desc* d, md_system** out) {
             up(s->site, site.data(), sizeof(uint16_t) * s->N) &&
             up(s->lam, ones.data(), sizeof(double) * 6 * s->n_reps) &&
             up(s->regions, s->regions_h.data(), sizeof(Region) * s->regions_h.size()) &&
+            (!s->generic || (up(s->mtype, s->mtype_h.data(), s->mtype_h.size()) &&
+                             up((void*)s->topo.b_off, s->t_boff.data(), s->t_boff.size() * sizeof(int)) &&
+                             up((void*)s->topo.b_at, s->t_bat.data(), s->t_bat.size() * sizeof(int)) &&
+                             up((void*)s->topo.a_off, s->t_aoff.data(), s->t_aoff.size() * sizeof(int)) &&
+                             up((void*)s->topo.a_at, s->t_aat.data(), s->t_aat.size() * sizeof(int)) &&
+                             up((void*)s->topo.d_off, s->t_doff.data(), s->t_doff.size() * sizeof(int)) &&
+                             up((void*)s->topo.d_at, s->t_dat.data(), s->t_dat.size() * sizeof(int)) &&
+                             up((void*)s->topo.x_off, s->t_xoff.data(), s->t_xoff.size() * sizeof(int)) &&
+                             up((void*)s->topo.x_at, s->t_xat.data(), s->t_xat.size() * sizeof(int)))) &&
             up(s->shapes, s->shapes_h.data(), sizeof(RegionShape) * s->shapes_h.size()) &&
             cudaMemsetAsync(s->flj, 0, 3 * (size_t)s->Npad * sizeof(long long), s->st) == cudaSuccess &&
             cudaMemsetAsync(s->flj_e, 0, 3 * (size_t)s->Npad * sizeof(long long), s->st) == cudaSuccess &&
@@ -845,6 +967,7 @@ int md_set_temperature(md_system* s, const double* T) {
 
 int md_observables(md_system* s, double* r_ee, double* rg2, double* trans_fraction) {
   if (!s) return fail(s, MD_EINVAL, "null system");
+  if (s->generic) return fail(s, MD_EINVAL, "chain observables need linear chains");
   int chains = 0;
   for (int r = 0; r < s->n_reps; ++r) chains += s->reps_h[r].n_chains;
   // scratch in the staging buffer (6N doubles + 3N ints >= 4 doubles per chain + counts)
@@ -869,6 +992,7 @@ int md_observables(md_system* s, double* r_ee, double* rg2, double* trans_fracti
 
 int md_rdf(md_system* s, int32_t n_bins, const double* edges, int64_t* counts) {
   if (!s || !edges || !counts || n_bins < 1 || n_bins > 16384) return fail(s, MD_EINVAL, "bad arguments (1 <= n_bins <= 16384)");
+  if (s->generic) return fail(s, MD_EINVAL, "the RDF's exclusions are those of linear chains");
   if (!(edges[0] >= 0.0)) return fail(s, MD_EINVAL, "edges[0] must be >= 0");
   for (int k = 0; k < n_bins; ++k)
     if (!(edges[k + 1] > edges[k])) return fail(s, MD_EINVAL, "edges must increase");
@@ -955,6 +1079,7 @@ int md_acf_push(md_system* s, const double* r_ee) {
 
 int md_acf_sample(md_system* s) {
   if (!s) return fail(s, MD_EINVAL, "null system");
+  if (s->generic) return fail(s, MD_EINVAL, "end-to-end vectors need linear chains");
   if (s->acf_lag < 0) return fail(s, MD_EINVAL, "md_acf_reset first");
   int chains = 0;
   for (const RepDev& q : s->reps_h) chains += q.n_chains;
@@ -1009,11 +1134,12 @@ int md_bin_study(md_system* s, int32_t reps, double* ms) {
                      s->count, s->slot, s->st);
     launch_scan2(s->count, s->cell_start, s->cl_start, s->C, s->st);
     launch_bin_scatter(s->cell_of, s->slot, s->cell_start, s->tmp, (int)N, s->st);
-    launch_cell_sort(s->mixed, s->x, (int)N, s->cell_start, s->tmp, s->cellc, s->site, s->reps, s->n_reps, s->C,
+    launch_cell_sort(s->mixed, s->x, (int)N, s->cell_start, s->tmp, s->fp.mtype, s->cellc, s->site, s->reps, s->n_reps, s->C,
                      s->S, s->perm, s->inv_perm, s->pos, s->tag, s->ref, s->flags, s->st);
     cudaEventRecord(ev[1], s->st);
     launch_cl_build(s->pos, s->tag, s->cell_start, s->cl_start, s->regions, (int)s->regions_h.size(), s->shapes,
-                    s->reps, s->list, s->ncl, s->cap, s->tile_cap, s->flags, s->persistent_grid, s->work, s->st);
+                    s->reps, s->list, s->ncl, s->cap, s->tile_cap, s->flags, s->persistent_grid, s->work,
+                  s->generic ? &s->topo : nullptr, s->st);
     cudaEventRecord(ev[2], s->st);
     // host arm: positions to the host, bins there, binned data back, sorted arrays
     if (cudaMemcpyAsync(hx, s->x, xb, cudaMemcpyDeviceToHost, s->st) != cudaSuccess) { rc = fail(s, MD_ECUDA, "copy"); break; }
@@ -1030,7 +1156,7 @@ int md_bin_study(md_system* s, int32_t reps, double* ms) {
               cudaMemcpyAsync(s->cl_start, cl_start.data(), (C + 1) * sizeof(int), cudaMemcpyHostToDevice, s->st) == cudaSuccess &&
               cudaMemcpyAsync(s->tmp, perm.data(), N * sizeof(int), cudaMemcpyHostToDevice, s->st) == cudaSuccess;
     if (!ok) { rc = fail(s, MD_ECUDA, "copy"); break; }
-    launch_cell_sort(s->mixed, s->x, (int)N, s->cell_start, s->tmp, s->cellc, s->site, s->reps, s->n_reps, s->C,
+    launch_cell_sort(s->mixed, s->x, (int)N, s->cell_start, s->tmp, s->fp.mtype, s->cellc, s->site, s->reps, s->n_reps, s->C,
                      s->S, s->perm, s->inv_perm, s->pos, s->tag, s->ref, s->flags, s->st);
     cudaEventRecord(ev[5], s->st);
     if (cudaStreamSynchronize(s->st) != cudaSuccess) { rc = fail(s, MD_ECUDA, "sync"); break; }
@@ -1048,7 +1174,8 @@ int md_bin_study(md_system* s, int32_t reps, double* ms) {
   if (rc) return rc;
   // the list of the bins now in place
   launch_cl_build(s->pos, s->tag, s->cell_start, s->cl_start, s->regions, (int)s->regions_h.size(), s->shapes,
-                  s->reps, s->list, s->ncl, s->cap, s->tile_cap, s->flags, s->persistent_grid, s->work, s->st);
+                  s->reps, s->list, s->ncl, s->cap, s->tile_cap, s->flags, s->persistent_grid, s->work,
+                  s->generic ? &s->topo : nullptr, s->st);
   for (int k = 0; k < 6; ++k) ms[k] = acc[k] / reps;
   rc = check_flags(s);
   s->fresh = rc == MD_OK;

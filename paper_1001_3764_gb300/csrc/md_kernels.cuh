@@ -210,6 +210,26 @@ struct ForceParams {
   float pad_f;
   double hdt_m[2];                // dt / (2 m) per type
   double hdt_m_fix[2];            // dt / (2 m) * 2^-32 (applied to int64 fixed-point forces)
+  double mol_mass;                // mass of one molecule
+  const unsigned char* mtype;     // type of each atom of the molecule (device), or null: linear
+                                  // chains, whose ends (sites 0 and sites - 1) are C_33
+};
+
+// LJ / mass type of the atom at position st of its molecule
+__device__ __forceinline__ int atom_type(int st, const ForceParams& fp) {
+  return fp.mtype ? (int)fp.mtype[st] : ((st == 0 || st == fp.sites - 1) ? 1 : 0);
+}
+
+// The terms of a general molecule type (Sec. 3.3), in device memory, each
+// term listed under its first atom (0-based index in the molecule):
+// bonds (a, b), angles (a, b, c) with vertex b, dihedrals (a, b, c, d).
+// Exclusions: each atom's 1-2 and 1-3 neighbours, ascending.
+struct TopoDev {
+  const int *b_off, *b_at;        // b_at[q] = b of bond q owned by a, q in [b_off[a], b_off[a+1])
+  const int *a_off, *a_at;        // a_at[2q..2q+1] = (b, c)
+  const int *d_off, *d_at;        // d_at[3q..3q+2] = (b, c, d)
+  const int *x_off, *x_at;        // exclusions of a: x_at[x_off[a] .. x_off[a+1])
+  int naom, pad;
 };
 
 struct F4i { long long x, y, z, w; };   // fixed-point force, 32 B
@@ -229,7 +249,7 @@ void launch_static_order(const int* cell_start, int C, int n, int* runs, int* bu
                          cudaStream_t st);
 void launch_bin_scatter(const int* cell_of, const int* slot, const int* cell_start, int* tmp, int N,
                         cudaStream_t st);
-void launch_cell_sort(bool mixed, const void* x, int N, const int* cell_start, const int* tmp,
+void launch_cell_sort(bool mixed, const void* x, int N, const int* cell_start, const int* tmp, const unsigned char* mtype,
                       const int* cellc, const uint16_t* site, const RepDev* reps, int n_reps, int C,
                       int sites, int* perm, int* inv_perm, float4* pos, int* tag, float4* ref, unsigned* flags,
                       cudaStream_t st);
@@ -240,10 +260,12 @@ void launch_cell_sort(bool mixed, const void* x, int N, const int* cell_start, c
 // caller before) and, with energy, the per-region energy and virial sums into
 // epart (8 per cell).  persistent_grid > 0 runs that many blocks that take
 // regions from work[0..1] (two ints, zero before the first launch).
+// topo != null: exclusions of a general molecule type from its lists; else
+// linear chains (1-2 and 1-3 neighbours by site index)
 void launch_cl_build(const float4* pos, const int* tag, const int* cell_start, const int* cl_start,
                      const Region* regions, int n_regions, const RegionShape* shapes, const RepDev* reps,
                      unsigned* list, int* ncl, int cap, int tile_cap, unsigned* flags, int persistent_grid, int* work,
-                     cudaStream_t st);
+                     const TopoDev* topo, cudaStream_t st);
 void launch_cl_force(bool energy, const float4* pos, const int* cell_start, const int* cl_start,
                      const Region* regions, int n_regions, const RegionShape* shapes, const RepDev* reps,
                      const unsigned* list, const int* ncl, int cap, int tile_cap, const ForceParams& fp,
@@ -255,7 +277,12 @@ int tile_capacity_max();
 // one block waits on an mbarrier nothing arrives on, `spins` rounds, then raises kFlagTimeout
 void launch_wait_selftest(unsigned spins, unsigned* flags, cudaStream_t st);
 // bonded forces plus the LJ force (read from flj[3][Npad] in sorted order)
-// into F (original order)
+// into F (original order); launch_bonded_generic does the same for a general
+// molecule type (mixed form only): F = LJ, then every term adds its forces
+// with integer atomics, energies per integrator tile
+void launch_bonded_generic(bool energy, const double* x, const int* inv_perm, const long long* flj, int Npad, int N,
+                           const Tile* tiles, int n_tiles, const RepDev* reps, const ForceParams& fp,
+                           const TopoDev& topo, void* F, double* epart, unsigned* flags, cudaStream_t st);
 void launch_bonded(bool mixed, bool energy, const void* x, const uint16_t* site, const int* inv_perm,
                    const long long* flj, int Npad, int N, const Tile* tiles, int n_tiles, const RepDev* reps,
                    const ForceParams& fp, void* F, double* epart, unsigned* flags, cudaStream_t st);

@@ -106,3 +106,29 @@ def test_bad_adjoint_descriptors_are_rejected(lib, field, value):
     with pytest.raises(md.MDError) as e:
         md.md_adj_create(_adj_desc(**{field: value}))
     assert e.value.code == md.MD_EINVAL
+
+
+def test_topology_descriptor_validation(lib):
+    """md_desc.topology is checked before any GPU work: atom indices in
+    range, no self or repeated bonds, types 0/1, naom equal to
+    sites_per_chain, and the mixed precision form."""
+    m = chaingen.melt(2, sites=6, seed=1, L=3.4)
+
+    def size_with(bonds, types, naom=6, precision=md.MD_MIXED):
+        b = np.ascontiguousarray(np.asarray(bonds, np.int32))
+        t = np.ascontiguousarray(np.asarray(types, np.int32))
+        topo = md.md_topology(naom, len(b) // 2, b.ctypes.data, t.ctypes.data)
+        d, keep = _desc(m, precision=precision)
+        d.topology = ctypes.cast(ctypes.pointer(topo), ctypes.c_void_p)
+        sz = ctypes.c_size_t()
+        return lib.md_workspace_size(ctypes.byref(d), ctypes.byref(sz)), keep, b, t, topo
+
+    chain = [0, 1, 1, 2, 2, 3, 3, 4, 4, 5]
+    ends = [1, 0, 0, 0, 0, 1]
+    assert size_with(chain, ends)[0] == md.MD_OK
+    assert size_with([0, 1, 1, 6], ends)[0] == md.MD_EINVAL          # atom out of range
+    assert size_with([0, 0, 1, 2], ends)[0] == md.MD_EINVAL          # self bond
+    assert size_with([0, 1, 1, 0], ends)[0] == md.MD_EINVAL          # repeated bond
+    assert size_with(chain, [2, 0, 0, 0, 0, 1])[0] == md.MD_EINVAL   # unknown type
+    assert size_with(chain, ends, naom=7)[0] == md.MD_EINVAL         # naom != sites_per_chain
+    assert size_with(chain, ends, precision=md.MD_PLAIN_FP32)[0] == md.MD_EINVAL

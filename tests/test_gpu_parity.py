@@ -939,3 +939,85 @@ def test_bin_study_arms_give_the_oracle_bins(precision):
     xa, va, _ = a.state(); xb, vb, _ = b.state()
     assert np.array_equal(xa, xb) and np.array_equal(va, vb)
     a.close(); b.close()
+
+
+# ---------------------------------------------------------------- general molecules (Sec. 3.3)
+
+def _branched_topology(mixed_types=False):
+    """A 12-atom branched molecule: backbone 0-1-...-7, side atoms 8 on 2, 9 on
+    4, and a two-atom branch 10-11 on 6.  Atoms with one bond are C_33, the
+    others C_32 (the polyethylene convention); with mixed_types the interior
+    atom 3 is C_33 as well."""
+    bonds = [(k, k + 1) for k in range(7)] + [(2, 8), (4, 9), (6, 10), (10, 11)]
+    deg = np.zeros(12, int)
+    for a, b in bonds:
+        deg[a] += 1; deg[b] += 1
+    types = (deg == 1).astype(np.int32)
+    if mixed_types:
+        types[3] = 1
+    return np.array(bonds, np.int32), types
+
+
+def _branched_melt(n_mol, L, seed):
+    """Molecules placed one by one at random positions and orientations,
+    rejected while any site comes within 0.32 nm of a site of another
+    molecule (periodic cube of side L).  Backbone: a planar zigzag (bond
+    0.153 nm, angle 109.47 deg); side atoms 0.153 nm from their parent,
+    normal to the backbone plane (alternating sides), and atom 11 off the
+    10 - 6 axis (no straight angle)."""
+    b, th = 0.153, np.arccos(-1.0 / 3.0)
+    base = [np.array([k * b * np.sin(th / 2), (k % 2) * b * np.cos(th / 2), 0.0]) for k in range(8)]
+    base.append(base[2] + [0.0, 0.0, b])
+    base.append(base[4] + [0.0, 0.0, -b])
+    base.append(base[6] + [0.0, 0.0, b])
+    base.append(base[10] + b * np.array([0.5, 0.3, 0.8124]) / np.linalg.norm([0.5, 0.3, 0.8124]))
+    base = np.array(base)
+    base -= base.mean(0)
+    rng = np.random.default_rng(seed)
+    placed = []
+    while len(placed) < n_mol:
+        q = rng.normal(size=4)
+        q /= np.linalg.norm(q)
+        w, x, y, z = q
+        Rm = np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                       [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                       [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+        mol = base @ Rm.T + rng.uniform(0, L, size=3)
+        ok = True
+        for other in placed:
+            d = mol[:, None, :] - other[None, :, :]
+            d -= L * np.round(d / L)
+            if np.min(np.sum(d * d, axis=2)) < 0.32 ** 2:
+                ok = False
+                break
+        if ok:
+            placed.append(mol)
+    pos = np.mod(np.concatenate(placed), L)
+    vel = 0.3 * rng.normal(size=pos.shape)
+    return dict(pos=pos, vel=vel, L=L, n_chains=n_mol, sites=12, T=300.0)
+
+
+@pytest.mark.parametrize("mixed_types", [False, True])
+def test_branched_molecules_match_oracle(mixed_types):
+    """A branched, and a mixed-type, molecule given by its bond graph
+    (md_desc.topology): exclusions, bonds, angles and dihedrals come from the
+    per-type lists of Sec. 3.3 built by the library.  Forces and energies at
+    the start, and forces after 20 steps, against the oracle's topology built
+    from the same bond graph."""
+    bonds, types = _branched_topology(mixed_types)
+    m = _branched_melt(70, 4.4, seed=91 + int(mixed_types))
+    s = md.System(m, precision=md.MD_MIXED, topology=(bonds, types), rebin_every=5)
+    topo = oracle.Topology(12, bonds, types)
+    ref = oracle.System(topo, m["n_chains"], m["L"], use_cells=False)
+    x = np.array(m["pos"], np.float64)
+    f_orc, en, _ = ref.forces(x)
+    check_forces(s.forces(), f_orc, x, m["L"])
+    e = s.energy()[0]
+    for k, idx in (("lj", 0), ("lj_shifted", 1), ("bond", 2), ("angle", 3), ("dihedral", 4)):
+        assert abs(e[k] - en[idx]) <= 1e-5 * max(1.0, abs(en[idx])), (k, e[k], en[idx])
+    s.step(20)
+    xo, _, fo, _, _ = ref.run(x, m["vel"], 0.001, 20, sample_every=0)
+    check_forces(s.forces(), fo, xo, m["L"])
+    with pytest.raises(md.MDError):
+        s.observables()
+    s.close()
