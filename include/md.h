@@ -25,7 +25,8 @@
  * conditions (neighbour-list overflow, fixed-point overflow, non-finite
  * state) are raised on the GPU as flags and reported by the next
  * synchronising call (md_step, md_sync).  A displacement beyond skin/2 is
- * not an error: it triggers an extra rebuild (md_early_rebins).  The library
+ * not an error unless md_desc.displacement = MD_DISP_ERROR: it triggers an
+ * extra rebuild (md_early_rebins).  The library
  * never traps or spins on the GPU.
  *
  * Threads: a system must not be used from two host threads at once.
@@ -46,7 +47,7 @@ enum {
   MD_ENOMEM = -2,      /* device allocation failed or workspace too small */
   MD_ECUDA = -3,       /* a CUDA call failed */
   MD_EOVERFLOW = -4,   /* neighbour-list capacity or fixed-point range exceeded */
-  MD_EUNSTABLE = -5,   /* non-finite state */
+  MD_EUNSTABLE = -5,   /* non-finite state, or (MD_DISP_ERROR) an atom moved more than skin/2 */
   MD_ETIMEOUT = -6     /* a bounded device wait gave up */
 };
 
@@ -55,6 +56,11 @@ enum { MD_NVE = 0, MD_VRESCALE = 1, MD_NOSE_HOOVER = 2 };   /* thermostat */
 /* LJ work schedule: one thread block per cell, or a fixed grid (resident
  * blocks x SMs) whose blocks take cells from a device counter */
 enum { MD_SCHED_GRID = 0, MD_SCHED_PERSISTENT = 1 };
+/* What a step does when an atom has moved more than skin/2 since the last
+ * list build: rebuild the bins and list before its forces (a conditional
+ * node in the step graph), or report MD_EUNSTABLE at the next synchronising
+ * call (graphs without conditional nodes, which profilers can take apart). */
+enum { MD_DISP_REBUILD = 0, MD_DISP_ERROR = 1 };
 
 typedef struct md_system md_system;         /* opaque, owned by the library */
 
@@ -120,6 +126,7 @@ typedef struct {
                                   8, 16 or 32 (0 = 16) */
   const md_topology *topology; /* NULL: linear chains; else the molecule type (sites_per_chain must
                                   equal topology->naom) */
+  int32_t displacement;        /* MD_DISP_REBUILD (default) or MD_DISP_ERROR */
   void *cuda_stream;           /* cudaStream_t to run on; NULL = a stream the library creates */
   void *workspace;             /* optional DEVICE memory for all buffers (see md_workspace_size);
                                   NULL = the library allocates.  Must outlive the system. */
@@ -180,7 +187,8 @@ int md_create(const md_desc *desc, md_system **out);
  * and also before the force evaluation of any step in which an atom has
  * moved more than skin/2 since the last rebuild (a device-side check that
  * opens a conditional rebuild in the step graph; md_early_rebins counts
- * them), so every force comes from a list that holds all pairs within rc.
+ * them), so every force comes from a list that holds all pairs within rc;
+ * with MD_DISP_ERROR such a step is reported as MD_EUNSTABLE instead.
  * Synchronises and reports device flags. */
 int md_step(md_system *sys, int64_t n_steps);
 

@@ -21,6 +21,7 @@ MD_OK, MD_EINVAL, MD_ENOMEM, MD_ECUDA, MD_EOVERFLOW, MD_EUNSTABLE, MD_ETIMEOUT =
 MD_PLAIN_FP32, MD_MIXED = 0, 1
 MD_NVE, MD_VRESCALE, MD_NOSE_HOOVER = 0, 1, 2
 MD_SCHED_GRID, MD_SCHED_PERSISTENT = 0, 1
+MD_DISP_REBUILD, MD_DISP_ERROR = 0, 1
 KB = 0.0083144626  # kJ/mol/K
 
 _ERRNAMES = {MD_EINVAL: "MD_EINVAL", MD_ENOMEM: "MD_ENOMEM", MD_ECUDA: "MD_ECUDA",
@@ -53,7 +54,7 @@ class md_desc(ctypes.Structure):
                 ("tau_t", ctypes.c_double), ("rebin_every", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("thermostat", ctypes.c_int32), ("nbr_capacity", ctypes.c_int32),
                 ("lj_block", ctypes.c_int32), ("schedule", ctypes.c_int32), ("lj_lanes", ctypes.c_int32),
-                ("topology", ctypes.c_void_p),
+                ("topology", ctypes.c_void_p), ("displacement", ctypes.c_int32),
                 ("cuda_stream", ctypes.c_void_p), ("workspace", ctypes.c_void_p),
                 ("workspace_bytes", ctypes.c_size_t)]
 
@@ -392,7 +393,7 @@ class System:
                  tau_t: float = 0.1, params: dict | None = None, nbr_capacity: int = 0, device: int = 0,
                  use_torch_memory: bool = True, lj_block: int = 0, schedule: int = MD_SCHED_GRID,
                  lj_lanes: int = 0, autotune: bool = False, tune_cycles: int = 2, tune_cache: str | None = None,
-                 topology=None):
+                 topology=None, displacement: int = 0):
         import torch
         load()
         if isinstance(melts, dict):
@@ -421,6 +422,7 @@ class System:
         d.rebin_every, d.precision, d.thermostat = rebin_every, precision, thermostat
         d.nbr_capacity = nbr_capacity
         d.lj_block, d.schedule, d.lj_lanes = lj_block, schedule, lj_lanes
+        d.displacement = displacement
         if topology is not None:
             # (bonds [n_bonds, 2], types [naom]) of the molecule type (Sec. 3.3)
             self._tb = np.ascontiguousarray(np.asarray(topology[0], np.int32).reshape(-1, 2))

@@ -94,6 +94,7 @@ struct md_system {
   unsigned long long* early = nullptr;       // early rebins (displacement beyond skin/2) so far
   // a general molecule type (md_desc.topology), or linear chains
   bool generic = false;
+  int disp = MD_DISP_REBUILD;                // what a displacement beyond skin/2 does
   std::vector<unsigned char> mtype_h;        // type of each atom of the molecule
   std::vector<int> t_boff, t_bat, t_aoff, t_aat, t_doff, t_dat, t_xoff, t_xat;   // term and exclusion lists
   unsigned char* mtype = nullptr;            // device copies
@@ -323,6 +324,9 @@ static int configure(md_system* s, const md_desc* d) {
   if (d->lj_lanes != 0 && d->lj_lanes != 8 && d->lj_lanes != 16 && d->lj_lanes != 32)
     return fail(s, MD_EINVAL, "lj_lanes must be 0, 8, 16 or 32");
   s->lj_lanes = d->lj_lanes ? d->lj_lanes : 16;
+  if (d->displacement != MD_DISP_REBUILD && d->displacement != MD_DISP_ERROR)
+    return fail(s, MD_EINVAL, "displacement must be MD_DISP_REBUILD or MD_DISP_ERROR");
+  s->disp = d->displacement;
   s->params = d->params;
   const double rl = d->rc + d->skin;
   s->reps_h.assign(s->n_reps, RepDev{});
@@ -509,6 +513,7 @@ static void enqueue_forces(md_system* s, bool energy, void* F_out = nullptr) {
 // last rebin computes its forces from fresh bins (and is counted), instead of
 // the run stopping.  No-op outside a capture.
 static void enqueue_cond_rebin(md_system* s) {
+  if (s->disp != MD_DISP_REBUILD) return;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   cudaGraph_t g = nullptr;
   const cudaGraphNode_t* deps = nullptr;
@@ -570,7 +575,7 @@ static void enqueue_block(md_system* s, int k, bool rebin = true) {
 }
 // per step: integrate, displacement check, memset, LJ, bonded (a memset
 // counted as a launch; an early rebin adds kRebinLaunches)
-static int64_t block_launches(int k) { return kRebinLaunches + 5LL * k + 1; }
+static int64_t block_launches(int k, bool check) { return kRebinLaunches + (check ? 5LL : 4LL) * k + 1; }
 
 // accumulate the event timings of the last block (requires a finished stream)
 static void prof_collect(md_system* s, int k) {
@@ -1325,7 +1330,8 @@ int md_profile_reset(md_system* s) {
 int64_t md_launches_per_call(md_system* s, int64_t n) {
   if (!s || n <= 0) return 0;
   const int64_t full = n / s->R, rem = n % s->R;
-  return full * block_launches(s->R) + (rem ? block_launches((int)rem) : 0);
+  const bool check = s->disp == MD_DISP_REBUILD;
+  return full * block_launches(s->R, check) + (rem ? block_launches((int)rem, check) : 0);
 }
 
 // ------------------------------------------------------------------ autotuner

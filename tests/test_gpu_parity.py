@@ -474,6 +474,18 @@ def test_displacement_beyond_half_skin_triggers_an_early_rebin():
     s.close()
 
 
+def test_displacement_error_policy_reports_instead():
+    """With MD_DISP_ERROR the same run stops with MD_EUNSTABLE (round-trip of
+    the policy, and the graphs then hold no conditional node)."""
+    m = chaingen.melt(10, seed=1, L=3.6)
+    s = md.System(m, precision=md.MD_MIXED, skin=0.002, rebin_every=10, displacement=md.MD_DISP_ERROR)
+    with pytest.raises(md.MDError) as e:
+        s.step(10)
+    assert e.value.code == md.MD_EUNSTABLE
+    assert s.early_rebins() == 0
+    s.close()
+
+
 def test_workspace_and_library_allocation_agree():
     m = chaingen.melt(10, seed=13)
     a = md.System(m, use_torch_memory=True, rebin_every=3)
