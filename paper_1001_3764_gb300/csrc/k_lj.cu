@@ -385,6 +385,43 @@ __device__ __forceinline__ void entry_packed(const float2 (&px)[2], const float2
   gz = -(sz.x + sz.y);
 }
 
+// One list entry against the cluster's four atoms, one pair at a time (and,
+// with ENERGY, the pair energies and virial): adds the forces on the four
+// atoms to fi, returns minus their sum (the force on j) in g*.
+template <bool ENERGY>
+__device__ __forceinline__ void entry_scalar(const float4 (&pi)[4], const float (&a0)[4], const float (&da)[4],
+                                             const float (&b0)[4], const float (&db)[4], const float (&ec)[4][6],
+                                             float rc2, const float4& w, unsigned m, float (&fi)[4][3],
+                                             float (&ev)[kEnergyVals], float& gx, float& gy, float& gz) {
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const float dx = pi[u].x - w.x, dy = pi[u].y - w.y, dz = pi[u].z - w.z;
+    const float r2 = dx * dx + dy * dy + dz * dz;
+    const bool keep = ((m >> u) & 1u) && r2 < rc2;
+    // the reciprocal for every pair, then a select: no branch around the
+    // inline instruction
+    const float rr = rcp_approx(r2);
+    const float ir2 = keep ? rr : 0.f;
+    const float ir6 = ir2 * ir2 * ir2;
+    const float A = fmaf(w.w, da[u], a0[u]), B = fmaf(w.w, db[u], b0[u]);
+    const float ff = ir2 * ir6 * (A * ir6 - B);
+    fi[u][0] = fmaf(ff, dx, fi[u][0]);
+    fi[u][1] = fmaf(ff, dy, fi[u][1]);
+    fi[u][2] = fmaf(ff, dz, fi[u][2]);
+    gx = fmaf(-ff, dx, gx);
+    gy = fmaf(-ff, dy, gy);
+    gz = fmaf(-ff, dz, gz);
+    if (ENERGY) {
+      const float c12 = fmaf(w.w, ec[u][1], ec[u][0]), c6 = fmaf(w.w, ec[u][3], ec[u][2]);
+      const float eij = ir6 * (c12 * ir6 - c6);
+      ev[0] += eij;
+      ev[1] += eij - (keep ? fmaf(w.w, ec[u][5], ec[u][4]) : 0.f);
+      ev[2] += dx * dx * ff; ev[3] += dy * dy * ff; ev[4] += dz * dz * ff;
+      ev[5] += dx * dy * ff; ev[6] += dx * dz * ff; ev[7] += dy * dz * ff;
+    }
+  }
+}
+
 // Lanes per cluster LP: a warp works on 32 / LP clusters at once (adjacent
 // clusters of the region, handed out to warps as they free up); lane l of a
 // cluster's group takes entries l, l + LP, ...  The warp's trip count is that
@@ -405,6 +442,7 @@ __global__ void __launch_bounds__(NT, ENERGY ? 512 / NT : 768 / NT) k_cl_force(
   __shared__ RegTile T;
   __shared__ int sh_r, sh_q;
   __shared__ int s_ncl[kRegionClusterCap];     // list length of each of the region's clusters
+  __shared__ short s_ord[kRegionClusterCap];   // the clusters, longest list first (ties: lower index)
   // energy form: each cluster's 8 sums (FP32 lane tree), added over the
   // region's clusters in cluster order, so the result does not depend on
   // which warp took which cluster
@@ -433,6 +471,18 @@ __global__ void __launch_bounds__(NT, ENERGY ? 512 / NT : 768 / NT) k_cl_force(
       }
       if (threadIdx.x == 0) sh_q = 0;
       __syncthreads();
+      // longest list first: warps that take the last clusters finish soon,
+      // and the clusters that share a warp have similar lengths
+      for (int q = threadIdx.x; q < nq; q += NT) {
+        const int nqv = s_ncl[q];
+        int rank = 0;
+        for (int o = 0; o < nq; ++o) {
+          const int no = s_ncl[o];
+          rank += (no > nqv) || (no == nqv && o < q);
+        }
+        s_ord[rank] = (short)q;
+      }
+      __syncthreads();
       const float rc2 = R.rc2u;
       const float scale = R.ih_hi * kLjAccScale;     // cell-unit force -> 2^-13 kJ/mol/nm
       // pair coefficients by type sum (0: C32-C32, 1: C32-C33, 2: C33-C33)
@@ -443,8 +493,8 @@ __global__ void __launch_bounds__(NT, ENERGY ? 512 / NT : 768 / NT) k_cl_force(
         if (lane == 0) q0 = atomicAdd(&sh_q, CPW);
         q0 = __shfl_sync(0xffffffffu, q0, 0);
         if (q0 >= nq) break;
-        const int q = q0 + sub;
-        const bool valid = q < nq;
+        const bool valid = q0 + sub < nq;
+        const int q = valid ? (int)s_ord[q0 + sub] : nq;
         int h, k;
         cluster_of(T, valid ? q : nq - 1, h, k);
         const int i0 = T.off[h] + 4 * k;
@@ -488,54 +538,40 @@ __global__ void __launch_bounds__(NT, ENERGY ? 512 / NT : 768 / NT) k_cl_force(
           qx[p] = qy[p] = qz[p] = make_float2(0.f, 0.f);
         }
         const unsigned* L = list + (size_t)(valid ? T.cl0[h] + k : 0) * cap;
-        // entries two iterations ahead in flight
+        // two entries per lane per iteration (independent work for the
+        // scheduler), the next two in flight; an entry past the list is 0:
+        // tile atom 0 with an empty mask, which adds nothing
         unsigned E0 = sl < n ? __ldg(L + sl) : 0u;
         unsigned E1 = sl + LP < n ? __ldg(L + sl + LP) : 0u;
-        for (int e = sl; e - sl < nmax; e += LP) {
+        for (int e = sl; e - sl < nmax; e += 2 * LP) {
           const unsigned E2 = e + 2 * LP < n ? __ldg(L + e + 2 * LP) : 0u;
-          if (e < n) {
-            const int t = (int)(E0 & 0xffffu);
-            const unsigned m = E0 >> 16;
-            const float4 w = sp[t];
-            float gx = 0.f, gy = 0.f, gz = 0.f;
-            if (kPackedPairs && !ENERGY)
-              entry_packed(px, py, pz, pa0, pda, pnb0, pndb, rc2, w, m, qx, qy, qz, gx, gy, gz);
-            else
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              const float dx = pi[u].x - w.x, dy = pi[u].y - w.y, dz = pi[u].z - w.z;
-              const float r2 = dx * dx + dy * dy + dz * dz;
-              const bool keep = ((m >> u) & 1u) && r2 < rc2;
-              // the reciprocal for every pair, then a select: no branch
-              // around the inline instruction
-              const float rr = rcp_approx(r2);
-              const float ir2 = keep ? rr : 0.f;
-              const float ir6 = ir2 * ir2 * ir2;
-              const float A = fmaf(w.w, da[u], a0[u]), B = fmaf(w.w, db[u], b0[u]);
-              const float ff = ir2 * ir6 * (A * ir6 - B);
-              fi[u][0] = fmaf(ff, dx, fi[u][0]);
-              fi[u][1] = fmaf(ff, dy, fi[u][1]);
-              fi[u][2] = fmaf(ff, dz, fi[u][2]);
-              gx = fmaf(-ff, dx, gx);
-              gy = fmaf(-ff, dy, gy);
-              gz = fmaf(-ff, dz, gz);
-              if (ENERGY) {
-                const float c12 = fmaf(w.w, ec[u][1], ec[u][0]), c6 = fmaf(w.w, ec[u][3], ec[u][2]);
-                const float eij = ir6 * (c12 * ir6 - c6);
-                ev[0] += eij;
-                ev[1] += eij - (keep ? fmaf(w.w, ec[u][5], ec[u][4]) : 0.f);
-                ev[2] += dx * dx * ff; ev[3] += dy * dy * ff; ev[4] += dz * dz * ff;
-                ev[5] += dx * dy * ff; ev[6] += dx * dz * ff; ev[7] += dy * dz * ff;
-              }
-            }
-            gx *= scale; gy *= scale; gz *= scale;
-            range_check(gx, gy, gz, flags);
-            atomicAdd(ax + t, acc_fix(gx));
-            atomicAdd(ay + t, acc_fix(gy));
-            atomicAdd(az + t, acc_fix(gz));
+          const unsigned E3 = e + 3 * LP < n ? __ldg(L + e + 3 * LP) : 0u;
+          const int t0 = (int)(E0 & 0xffffu), t1 = (int)(E1 & 0xffffu);
+          const float4 w0 = sp[t0], w1 = sp[t1];
+          float g0x = 0.f, g0y = 0.f, g0z = 0.f, g1x = 0.f, g1y = 0.f, g1z = 0.f;
+          if (kPackedPairs && !ENERGY) {
+            entry_packed(px, py, pz, pa0, pda, pnb0, pndb, rc2, w0, E0 >> 16, qx, qy, qz, g0x, g0y, g0z);
+            entry_packed(px, py, pz, pa0, pda, pnb0, pndb, rc2, w1, E1 >> 16, qx, qy, qz, g1x, g1y, g1z);
+          } else {
+            entry_scalar<ENERGY>(pi, a0, da, b0, db, ec, rc2, w0, E0 >> 16, fi, ev, g0x, g0y, g0z);
+            entry_scalar<ENERGY>(pi, a0, da, b0, db, ec, rc2, w1, E1 >> 16, fi, ev, g1x, g1y, g1z);
           }
-          E0 = E1;
-          E1 = E2;
+          if (e < n) {
+            g0x *= scale; g0y *= scale; g0z *= scale;
+            range_check(g0x, g0y, g0z, flags);
+            atomicAdd(ax + t0, acc_fix(g0x));
+            atomicAdd(ay + t0, acc_fix(g0y));
+            atomicAdd(az + t0, acc_fix(g0z));
+          }
+          if (e + LP < n) {
+            g1x *= scale; g1y *= scale; g1z *= scale;
+            range_check(g1x, g1y, g1z, flags);
+            atomicAdd(ax + t1, acc_fix(g1x));
+            atomicAdd(ay + t1, acc_fix(g1y));
+            atomicAdd(az + t1, acc_fix(g1z));
+          }
+          E0 = E2;
+          E1 = E3;
         }
         if (kPackedPairs && !ENERGY) {
 #pragma unroll
