@@ -123,7 +123,7 @@ typedef struct {
   int32_t lj_block;            /* threads per block of the LJ kernel: 128 or 256 (0 = 256) */
   int32_t schedule;            /* MD_SCHED_GRID or MD_SCHED_PERSISTENT (see below) */
   int32_t lj_lanes;            /* lanes of the LJ kernel that share one 4-atom cluster's list:
-                                  8, 16 or 32 (0 = 16) */
+                                  8, 16 or 32 (0 = 8) */
   const md_topology *topology; /* NULL: linear chains; else the molecule type (sites_per_chain must
                                   equal topology->naom) */
   int32_t displacement;        /* MD_DISP_REBUILD (default) or MD_DISP_ERROR */

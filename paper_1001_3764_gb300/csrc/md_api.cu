@@ -70,7 +70,7 @@ struct md_system {
   RegionShape* shapes = nullptr;
   int tile_cap = 0;
   int lj_block = 256, persistent_grid = 0;   // persistent_grid > 0: fixed grid for the LJ kernel
-  int lj_lanes = 16;                         // lanes per 4-atom cluster in the LJ kernel
+  int lj_lanes = 8;                          // lanes per 4-atom cluster in the LJ kernel
   int* work = nullptr;                       // LJ work counters (persistent schedule)
   int *count = nullptr, *cell_start = nullptr, *cell_of = nullptr;
   int *slot = nullptr, *tmp = nullptr;
@@ -323,7 +323,7 @@ static int configure(md_system* s, const md_desc* d) {
   s->lj_block = d->lj_block ? d->lj_block : 256;
   if (d->lj_lanes != 0 && d->lj_lanes != 8 && d->lj_lanes != 16 && d->lj_lanes != 32)
     return fail(s, MD_EINVAL, "lj_lanes must be 0, 8, 16 or 32");
-  s->lj_lanes = d->lj_lanes ? d->lj_lanes : 16;
+  s->lj_lanes = d->lj_lanes ? d->lj_lanes : 8;
   if (d->displacement != MD_DISP_REBUILD && d->displacement != MD_DISP_ERROR)
     return fail(s, MD_EINVAL, "displacement must be MD_DISP_REBUILD or MD_DISP_ERROR");
   s->disp = d->displacement;
@@ -1388,7 +1388,7 @@ static int tune_trial(md_desc cand, int cycles, double* us) {
 extern "C" int md_autotune(md_desc* d, int32_t trial_cycles, const char* cache_path, md_tuning* out) {
   if (!d || trial_cycles < 1) return fail(nullptr, MD_EINVAL, "autotune needs a descriptor and trial_cycles >= 1");
   const std::string key = tune_key(d);
-  md_tuning best{d->skin, d->rebin_every, d->lj_block ? d->lj_block : 256, d->schedule, d->lj_lanes ? d->lj_lanes : 16,
+  md_tuning best{d->skin, d->rebin_every, d->lj_block ? d->lj_block : 256, d->schedule, d->lj_lanes ? d->lj_lanes : 8,
                  0, 1e300};
   if (cache_path) {
     if (FILE* f = fopen(cache_path, "r")) {
