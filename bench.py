@@ -262,13 +262,14 @@ def batched(md, cycles=5):
         for m, T in zip(ms, T0):
             q = md.System(m, precision=prec, thermostat=md.MD_VRESCALE, T_target=T, tau_t=0.1,
                           skin=tuning["skin"], rebin_every=R, lj_block=tuning["lj_block"],
-                          schedule=tuning["schedule"])
+                          schedule=tuning["schedule"], lj_lanes=tuning["lj_lanes"], lj_region=tuning["lj_region"])
             t_seq[prec] += timed(q)
             q.close()
     # one plain FP32 melt with the same total number of chains
     big = equilibrate(md, chaingen.melt(sum(m["n_chains"] for m in ms), SITES, seed=4, T=400.0), rounds=2)
     q = md.System(big, precision=md.MD_PLAIN_FP32, skin=tuning["skin"], rebin_every=R,
-                  lj_block=tuning["lj_block"], schedule=tuning["schedule"])
+                  lj_block=tuning["lj_block"], schedule=tuning["schedule"], lj_lanes=tuning["lj_lanes"],
+                  lj_region=tuning["lj_region"])
     t_big = timed(q)
     n_big = len(big["pos"])
     q.close()

@@ -53,8 +53,10 @@ enum {
 
 enum { MD_PLAIN_FP32 = 0, MD_MIXED = 1 };   /* precision forms */
 enum { MD_NVE = 0, MD_VRESCALE = 1, MD_NOSE_HOOVER = 2 };   /* thermostat */
-/* LJ work schedule: one thread block per cell, or a fixed grid (resident
- * blocks x SMs) whose blocks take cells from a device counter */
+/* LJ work schedule: one thread block per region of cells, or a fixed grid
+ * (resident blocks x SMs) whose blocks take regions from a device counter.
+ * Both give the same forces bit for bit.  The list build always runs one
+ * block per region. */
 enum { MD_SCHED_GRID = 0, MD_SCHED_PERSISTENT = 1 };
 /* What a step does when an atom has moved more than skin/2 since the last
  * list build: rebuild the bins and list before its forces (a conditional
@@ -120,10 +122,13 @@ typedef struct {
                                   velocity of v_{k+1/2} removed before the next step.  xi starts
                                   at 0 and persists across md_step and md_set_state calls. */
   int32_t nbr_capacity;        /* neighbour slots per atom; 0 = chosen from density */
-  int32_t lj_block;            /* threads per block of the LJ kernel: 128 or 256 (0 = 256) */
+  int32_t lj_block;            /* threads per block of the LJ kernel: 128, 256 or 384 (0 = 384 with
+                                  3 x 3 regions, 256 with 2 x 2) */
   int32_t schedule;            /* MD_SCHED_GRID or MD_SCHED_PERSISTENT (see below) */
   int32_t lj_lanes;            /* lanes of the LJ kernel that share one 4-atom cluster's list:
                                   8, 16 or 32 (0 = 8) */
+  int32_t lj_region;           /* cells per side (x and y) of the work unit of the list build and
+                                  LJ kernels, 1 cell deep: 2 or 3 (0 = 3) */
   const md_topology *topology; /* NULL: linear chains; else the molecule type (sites_per_chain must
                                   equal topology->naom) */
   int32_t displacement;        /* MD_DISP_REBUILD (default) or MD_DISP_ERROR */
@@ -152,16 +157,18 @@ typedef struct {
   int32_t lj_block;
   int32_t schedule;
   int32_t lj_lanes;
+  int32_t lj_region;
   int32_t from_cache;          /* 1 if read from the cache file, 0 if measured now */
   double us_per_step;          /* measured time per MD step of the winner */
 } md_tuning;
 
 /* Autotuner: times short runs of candidate settings on the system the
- * descriptor describes -- LJ block shape (128, 256 threads) and schedule
- * (grid, persistent), lanes per cluster (8, 16, 32), then cell size via
- * (skin, rebin_every) in
+ * descriptor describes -- region side and LJ block shape ((2, 128), (2, 256),
+ * (3, 256), (3, 384) cells / threads) with schedule (grid, persistent),
+ * lanes per cluster (8, 16, 32), then cell size via (skin, rebin_every) in
  * {(0.08, 6), (0.10, 10), (0.12, 12), (0.15, 16)} nm / steps -- and writes the
- * fastest into desc->skin, rebin_every, lj_block, schedule and lj_lanes.  Candidates that
+ * fastest into desc->skin, rebin_every, lj_block, schedule, lj_lanes and
+ * lj_region.  Candidates that
  * raise a device flag (e.g. an atom moving more than skin/2 between rebins)
  * are rejected.  With cache_path != NULL the result is looked up in / appended
  * to that text file, keyed by GPU, precision, replica count and atom-count and

@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(128) k_cell_sort(const T* __restrict__ x, int 
     const int st = site[id];
     const int chain = R.chain_off + (id - R.atom_off) / sites;
     const int type = mtype ? (int)mtype[st] : ((st == 0 || st == sites - 1) ? 1 : 0);
-    p.w = (float)type;   // LJ type: the pipelined force kernel copies positions as they are
+    p.w = (float)type;   // LJ type: the tile kernels copy positions as they are
     pos[s] = p;
     ref[id] = p;
     tag[s] = (chain << kTagSiteBits) | st | (type << kTagTypeBit);

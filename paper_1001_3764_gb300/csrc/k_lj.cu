@@ -31,6 +31,8 @@
 // accumulator is added to the int64 force (2^-32 kJ/mol/nm) with one
 // integer atomic per component.  Integer sums do not depend on the order in
 // which they are made, so the forces are deterministic.
+#include <type_traits>
+
 #include "md_kernels.cuh"
 
 namespace mdg {
@@ -55,14 +57,16 @@ struct RegTile {
   int ncl[kMaxHome + 1];          // clusters of home cells before h (ncl[n_home] = all)
   int cl0[kMaxHome];              // global id of home cell h's first cluster
   int home_cell[kMaxHome];        // global id of home cell h
+  int cnt[kMaxTileCells];         // atoms of tile cell k (set-up scratch)
   int n_tile, n_home;
 };
 
-// Threads 0..31 fill the table (one warp scan over the <= 32 tile cells).
+// Threads 0..63 read the tile cells' bounds, then one warp scans the counts
+// (two cells per lane: up to 64 tile cells); needs NT >= 64.
 __device__ __forceinline__ void region_setup(RegTile& T, const Region& g, const RegionShape& S, const RepDev& R,
                                              const int* __restrict__ cell_start, const int* __restrict__ cl_start) {
-  if (threadIdx.x < 32) {
-    const int k = threadIdx.x;
+  const int k = threadIdx.x;
+  if (k < kMaxTileCells) {
     int n = 0;
     if (k < S.n_tile) {
       const int M = R.M;
@@ -78,47 +82,83 @@ __device__ __forceinline__ void region_setup(RegTile& T, const Region& g, const 
         T.cl0[k] = cl_start[c];
       }
     }
-    int incl = n;
+    T.cnt[k] = n;
+  }
+  __syncthreads();
+  if (k < 32) {
+    const int a = T.cnt[2 * k], b = T.cnt[2 * k + 1];
+    int incl = a + b;
+    // clusters of the home cells (ceil(n / 4) each); home cells come first
+    const int ca = 2 * k < S.n_home ? (a + 3) >> 2 : 0, cb = 2 * k + 1 < S.n_home ? (b + 3) >> 2 : 0;
+    int ci = ca + cb;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const int v = __shfl_up_sync(0xffffffffu, incl, o);
-      if (k >= o) incl += v;
+      const int v = __shfl_up_sync(0xffffffffu, incl, o), w = __shfl_up_sync(0xffffffffu, ci, o);
+      if (k >= o) { incl += v; ci += w; }
     }
-    if (k < S.n_tile) T.off[k] = incl - n;
-    if (k == S.n_tile - 1) T.off[S.n_tile] = incl;
-    // clusters of the home cells (ceil(n / 4) each), prefix over h
-    int nc = k < S.n_home ? (n + 3) >> 2 : 0;
-    int ci = nc;
-#pragma unroll
-    for (int o = 1; o < kMaxHome; o <<= 1) {
-      const int v = __shfl_up_sync(0xffffffffu, ci, o);
-      if (k >= o) ci += v;
+    const int ex = incl - a - b, cx = ci - ca - cb;
+    if (2 * k < S.n_tile) T.off[2 * k] = ex;
+    if (2 * k + 1 < S.n_tile) T.off[2 * k + 1] = ex + a;
+    if (2 * k < S.n_home) T.ncl[2 * k] = cx;
+    if (2 * k + 1 < S.n_home) T.ncl[2 * k + 1] = cx + ca;
+    if (k == 31) {
+      T.off[S.n_tile] = incl;
+      T.ncl[S.n_home] = ci;
+      T.n_tile = S.n_tile;
+      T.n_home = S.n_home;
     }
-    if (k < S.n_home) T.ncl[k] = ci - nc;
-    if (k == S.n_home - 1) T.ncl[S.n_home] = ci;
-    if (k == 0) { T.n_tile = S.n_tile; T.n_home = S.n_home; }
   }
   __syncthreads();
 }
 
-// Copy the tile into shared memory in the region frame: warp w copies tile
-// cells k = w, w + nwarps, ...  WITH_TAG: also the chain/site tag of each
-// atom (list build); the w component keeps the LJ type (0.0 / 1.0) that
-// binning and integration store.
-template <bool WITH_TAG>
-__device__ __forceinline__ void tile_load(const RegTile& T, const float4* __restrict__ pos, const int* __restrict__ tag,
+// Copy the tile into shared memory in the region frame.  Tile atom t lies
+// in tile cell k with off[k] <= t < off[k + 1] (binary search over the
+// table); every thread starts asynchronous copies (cp.async, global to
+// shared without registers) for atoms t = threadIdx.x + i NT, so the whole
+// tile is in flight at once; after the wait and a barrier, a warp per tile
+// cell adds the cell's frame shift.  WITH_TAG: also the chain/site tag of
+// each atom (list build); the w component keeps the LJ type (0.0 / 1.0)
+// that binning and integration store.  tile_issue starts the copies,
+// tile_finish waits for them, shifts, and ends with a barrier.
+template <bool WITH_TAG, int NT>
+__device__ __forceinline__ void tile_issue(const RegTile& T, const float4* __restrict__ pos, const int* __restrict__ tag,
                                           float4* __restrict__ sp, int* __restrict__ st) {
-  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int k = threadIdx.x >> 5; k < T.n_tile; k += nw) {
-    const int n = T.off[k + 1] - T.off[k], j0 = T.start[k], t0 = T.off[k];
+  const int total = T.off[T.n_tile], nt = T.n_tile;
+  for (int t = threadIdx.x; t < total; t += NT) {
+    int lo = 0, hi = nt - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (T.off[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    const int j = T.start[lo] + (t - T.off[lo]);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(sp + t)),
+                 "l"(pos + j)
+                 : "memory");
+    if (WITH_TAG)
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(st + t)),
+                   "l"(tag + j)
+                   : "memory");
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+template <bool WITH_TAG, int NT>
+__device__ __forceinline__ void tile_finish(const RegTile& T, float4* __restrict__ sp, int* __restrict__ st) {
+  const int nt = T.n_tile;
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  for (int k = threadIdx.x >> 5; k < nt; k += NT / 32) {
+    const int t0 = T.off[k], n = T.off[k + 1] - t0;
     const float ox = T.sx[k], oy = T.sy[k], oz = T.sz[k];
     for (int q = lane; q < n; q += 32) {
-      float4 p = __ldg(pos + j0 + q);
+      float4 p = sp[t0 + q];
       p.x += ox; p.y += oy; p.z += oz;
       sp[t0 + q] = p;
-      if (WITH_TAG) st[t0 + q] = __ldg(tag + j0 + q) & (int)kTagMask;
+      if (WITH_TAG) st[t0 + q] &= (int)kTagMask;
     }
   }
+  __syncthreads();
 }
 
 // home cluster q of the region -> (home cell h, cluster k within the cell)
@@ -226,8 +266,8 @@ __global__ void __launch_bounds__(NT) k_cl_build(const float4* __restrict__ pos,
       }
       continue;
     }
-    tile_load<true>(T, pos, tag, sp, st);
-    __syncthreads();
+    tile_issue<true, NT>(T, pos, tag, sp, st);
+    tile_finish<true, NT>(T, sp, st);
     const float rl2 = R.rlist2u;
     const float rl = sqrtf(rl2);
     const unsigned lt = (1u << lane) - 1u;
@@ -348,18 +388,42 @@ __device__ __forceinline__ void range_check(float sx, float sy, float sz, unsign
   if (!(a < 1.0e9f)) atomicOr(flags, (a == a && a <= 3.4e38f) ? kFlagFixOverflow : kFlagNaN);
 }
 
+// Add the force g (cell units) on tile atom t to the 2^-13 accumulators.
+// While |g| scale < 2^22 (|g| < 512 kJ/mol/nm, the usual case) the
+// conversion is one FFMA: g scale + 1.5 2^23 lies in [2^23, 2^24), where
+// the FP32 spacing is 1, so the sum rounds g scale to the nearest integer
+// (ties to even) and its low mantissa bits are that integer plus 2^22; the
+// integer subtraction removes the offset.  Larger (or non-finite) values
+// take the FMUL + F2I path with the range check.  lim = 2^22 / scale.
+__device__ __forceinline__ void acc_add(int* __restrict__ ax, int* __restrict__ ay, int* __restrict__ az, int t,
+                                        float gx, float gy, float gz, float scale, float lim,
+                                        unsigned* __restrict__ flags) {
+  constexpr float kMagic = 12582912.0f;   // 1.5 2^23
+  constexpr int kMagicBits = 0x4B400000;
+  if (fabsf(gx) + fabsf(gy) + fabsf(gz) < lim) {
+    atomicAdd(ax + t, __float_as_int(fmaf(gx, scale, kMagic)) - kMagicBits);
+    atomicAdd(ay + t, __float_as_int(fmaf(gy, scale, kMagic)) - kMagicBits);
+    atomicAdd(az + t, __float_as_int(fmaf(gz, scale, kMagic)) - kMagicBits);
+  } else {
+    gx *= scale; gy *= scale; gz *= scale;
+    range_check(gx, gy, gz, flags);
+    atomicAdd(ax + t, acc_fix(gx));
+    atomicAdd(ay + t, acc_fix(gy));
+    atomicAdd(az + t, acc_fix(gz));
+  }
+}
+
 // One list entry against the cluster's four atoms with packed FP32 pairs
 // (two atoms per float2 lane: 0,1 and 2,3; one FFMA2 does both): the force
 // on the four atoms is added to f*[2] and minus the force on j, summed over
 // the four atoms, is returned in g*.  Same arithmetic per pair as the scalar
-// form (rcp of r^2, r2inv = 0 beyond r_c or outside the mask).
+// form (rcp of r^2, r2inv = 0 beyond r_c or outside the mask).  A[p], nB[p]:
+// the pair coefficients 12 C12 and -6 C6 of atoms 2p, 2p+1 with j.
 __device__ __forceinline__ void entry_packed(const float2 (&px)[2], const float2 (&py)[2], const float2 (&pz)[2],
-                                             const float2 (&a0)[2], const float2 (&da)[2], const float2 (&nb0)[2],
-                                             const float2 (&ndb)[2], float rc2, const float4& w, unsigned m,
-                                             float2 (&fx)[2], float2 (&fy)[2], float2 (&fz)[2], float& gx, float& gy,
-                                             float& gz) {
+                                             const float2 (&A)[2], const float2 (&nB)[2], float rc2, const float4& w,
+                                             unsigned m, float2 (&fx)[2], float2 (&fy)[2], float2 (&fz)[2], float& gx,
+                                             float& gy, float& gz) {
   const float2 wx = make_float2(-w.x, -w.x), wy = make_float2(-w.y, -w.y), wz = make_float2(-w.z, -w.z);
-  const float2 wt = make_float2(w.w, w.w);
   float2 sx = make_float2(0.f, 0.f), sy = make_float2(0.f, 0.f), sz = make_float2(0.f, 0.f);
 #pragma unroll
   for (int p = 0; p < 2; ++p) {
@@ -371,8 +435,7 @@ __device__ __forceinline__ void entry_packed(const float2 (&px)[2], const float2
     const bool k0 = ((m >> (2 * p)) & 1u) && r2.x < rc2, k1 = ((m >> (2 * p + 1)) & 1u) && r2.y < rc2;
     const float2 ir2 = make_float2(k0 ? q0 : 0.f, k1 ? q1 : 0.f);
     const float2 ir4 = __fmul2_rn(ir2, ir2), ir6 = __fmul2_rn(ir4, ir2), ir8 = __fmul2_rn(ir4, ir4);
-    const float2 A = __ffma2_rn(wt, da[p], a0[p]), nB = __ffma2_rn(wt, ndb[p], nb0[p]);
-    const float2 ff = __fmul2_rn(ir8, __ffma2_rn(A, ir6, nB));
+    const float2 ff = __fmul2_rn(ir8, __ffma2_rn(A[p], ir6, nB[p]));
     fx[p] = __ffma2_rn(ff, dx, fx[p]);
     fy[p] = __ffma2_rn(ff, dy, fy[p]);
     fz[p] = __ffma2_rn(ff, dz, fz[p]);
@@ -422,10 +485,218 @@ __device__ __forceinline__ void entry_scalar(const float4 (&pi)[4], const float 
   }
 }
 
-// Lanes per cluster LP: a warp works on 32 / LP clusters at once (adjacent
-// clusters of the region, handed out to warps as they free up); lane l of a
-// cluster's group takes entries l, l + LP, ...  The warp's trip count is that
-// of its longest cluster; a lane past its own list idles.
+// Per-replica constants of the force evaluation (cell units).
+struct LjConst {
+  float rc2, scale, lim;
+  float A0, A1, A2, B0, B1, B2;   // 12 C12 and 6 C6 by type sum (C32-C32, C32-C33, C33-C33)
+};
+__device__ __forceinline__ LjConst lj_const(const RepDev& R) {
+  LjConst c;
+  c.rc2 = R.rc2u;
+  c.scale = R.ih_hi * kLjAccScale;     // cell-unit force -> 2^-13 kJ/mol/nm
+  c.lim = 4194304.0f / c.scale;        // 2^22 accumulator units
+  c.A0 = 12.f * R.C12u[0]; c.A1 = 12.f * R.C12u[1]; c.A2 = 12.f * R.C12u[2];
+  c.B0 = 6.f * R.C6u[0]; c.B1 = 6.f * R.C6u[1]; c.B2 = 6.f * R.C6u[2];
+  return c;
+}
+
+// One warp task: clusters s_ord[q0 .. q0 + 32/LP) of the region, LP lanes
+// each; lane l of a cluster's group takes entries l, l + LP, ...  The warp's
+// trip count is that of its longest cluster; a lane past its own list idles.
+template <bool ENERGY, int LP>
+__device__ __forceinline__ void cluster_task(int q0, int nq, const RegTile& T, const float4* __restrict__ sp,
+                                             int* __restrict__ ax, int* __restrict__ ay, int* __restrict__ az,
+                                             const int* __restrict__ s_ncl, const short* __restrict__ s_ord,
+                                             float (*__restrict__ ecl)[kEnergyVals], const unsigned* __restrict__ list,
+                                             int cap, const RepDev& R, const ForceParams& fp, const LjConst& c,
+                                             unsigned* __restrict__ flags) {
+  const int lane = threadIdx.x & 31, sub = lane / LP, sl = lane % LP;
+  const float rc2 = c.rc2, scale = c.scale, lim = c.lim;
+  const float A0 = c.A0, A1 = c.A1, A2 = c.A2, B0 = c.B0, B1 = c.B1, B2 = c.B2;
+  const bool valid = q0 + sub < nq;
+  const int q = valid ? (int)s_ord[q0 + sub] : nq;
+  int h, k;
+  cluster_of(T, valid ? q : nq - 1, h, k);
+  const int i0 = T.off[h] + 4 * k;
+  const int ni = valid ? min(4, T.off[h + 1] - i0) : 0;
+  const int n = valid ? s_ncl[q] : 0;
+  int nmax = n;
+#pragma unroll
+  for (int o = LP; o < 32; o <<= 1) nmax = max(nmax, __shfl_xor_sync(0xffffffffu, nmax, o));
+  float4 pi[4];
+  float a0[4], da[4], b0[4], db[4];
+  float ec[4][6];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    pi[u] = sp[i0 + max(0, min(u, ni - 1))];
+    const bool t3 = pi[u].w != 0.f;           // the atom is a C_33 chain end
+    a0[u] = t3 ? A1 : A0; da[u] = t3 ? A2 - A1 : A1 - A0;
+    b0[u] = t3 ? B1 : B0; db[u] = t3 ? B2 - B1 : B1 - B0;
+    if (ENERGY) {
+      const int ti = t3 ? 1 : 0;
+      ec[u][0] = R.C12u[ti]; ec[u][1] = R.C12u[ti + 1] - ec[u][0];
+      ec[u][2] = R.C6u[ti]; ec[u][3] = R.C6u[ti + 1] - ec[u][2];
+      ec[u][4] = fp.erc[ti][0]; ec[u][5] = fp.erc[ti][1] - ec[u][4];
+    }
+  }
+  float fi[4][3];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) fi[u][0] = fi[u][1] = fi[u][2] = 0.f;
+  float ev[kEnergyVals] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  // packed copies for the force-only form (atoms 0,1 and 2,3)
+  float2 px[2], py[2], pz[2], pa0[2], pda[2], pnb0[2], pndb[2];
+  float2 qx[2], qy[2], qz[2];
+#pragma unroll
+  for (int p = 0; p < 2; ++p) {
+    px[p] = make_float2(pi[2 * p].x, pi[2 * p + 1].x);
+    py[p] = make_float2(pi[2 * p].y, pi[2 * p + 1].y);
+    pz[p] = make_float2(pi[2 * p].z, pi[2 * p + 1].z);
+    pa0[p] = make_float2(a0[2 * p], a0[2 * p + 1]);
+    pda[p] = make_float2(da[2 * p], da[2 * p + 1]);
+    pnb0[p] = make_float2(-b0[2 * p], -b0[2 * p + 1]);
+    pndb[p] = make_float2(-db[2 * p], -db[2 * p + 1]);
+    qx[p] = qy[p] = qz[p] = make_float2(0.f, 0.f);
+  }
+  const unsigned* L = list + (size_t)(valid ? T.cl0[h] + k : 0) * cap;
+  // clusters without a chain end (the common case) share one pair
+  // coefficient per j type: two scalar FMAs per entry instead of four
+  // FFMA2 (same values: each coefficient is the same single-rounded FMA)
+  bool uni_c = true;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) uni_c &= pi[u].w == 0.f;
+  const bool uni = __all_sync(0xffffffffu, uni_c);
+  // two entries per lane per iteration (independent work for the
+  // scheduler), the next two in flight; an entry past the list is 0:
+  // tile atom 0 with an empty mask, which adds nothing
+  auto run = [&](auto uni_tag) {
+    constexpr bool UNI = decltype(uni_tag)::value;
+    unsigned E0 = sl < n ? __ldg(L + sl) : 0u;
+    unsigned E1 = sl + LP < n ? __ldg(L + sl + LP) : 0u;
+    for (int e = sl; e - sl < nmax; e += 2 * LP) {
+      const unsigned E2 = e + 2 * LP < n ? __ldg(L + e + 2 * LP) : 0u;
+      const unsigned E3 = e + 3 * LP < n ? __ldg(L + e + 3 * LP) : 0u;
+      const int t0 = (int)(E0 & 0xffffu), t1 = (int)(E1 & 0xffffu);
+      const float4 w0 = sp[t0], w1 = sp[t1];
+      float g0x = 0.f, g0y = 0.f, g0z = 0.f, g1x = 0.f, g1y = 0.f, g1z = 0.f;
+      if (kPackedPairs && !ENERGY) {
+        float2 cA0[2], cB0[2], cA1[2], cB1[2];
+        if (UNI) {
+          const float a_0 = fmaf(w0.w, A1 - A0, A0), b_0 = fmaf(w0.w, -(B1 - B0), -B0);
+          const float a_1 = fmaf(w1.w, A1 - A0, A0), b_1 = fmaf(w1.w, -(B1 - B0), -B0);
+          cA0[0] = cA0[1] = make_float2(a_0, a_0); cB0[0] = cB0[1] = make_float2(b_0, b_0);
+          cA1[0] = cA1[1] = make_float2(a_1, a_1); cB1[0] = cB1[1] = make_float2(b_1, b_1);
+        } else {
+          const float2 wt0 = make_float2(w0.w, w0.w), wt1 = make_float2(w1.w, w1.w);
+#pragma unroll
+          for (int p = 0; p < 2; ++p) {
+            cA0[p] = __ffma2_rn(wt0, pda[p], pa0[p]); cB0[p] = __ffma2_rn(wt0, pndb[p], pnb0[p]);
+            cA1[p] = __ffma2_rn(wt1, pda[p], pa0[p]); cB1[p] = __ffma2_rn(wt1, pndb[p], pnb0[p]);
+          }
+        }
+        entry_packed(px, py, pz, cA0, cB0, rc2, w0, E0 >> 16, qx, qy, qz, g0x, g0y, g0z);
+        entry_packed(px, py, pz, cA1, cB1, rc2, w1, E1 >> 16, qx, qy, qz, g1x, g1y, g1z);
+      } else {
+        entry_scalar<ENERGY>(pi, a0, da, b0, db, ec, rc2, w0, E0 >> 16, fi, ev, g0x, g0y, g0z);
+        entry_scalar<ENERGY>(pi, a0, da, b0, db, ec, rc2, w1, E1 >> 16, fi, ev, g1x, g1y, g1z);
+      }
+      if (e < n) acc_add(ax, ay, az, t0, g0x, g0y, g0z, scale, lim, flags);
+      if (e + LP < n) acc_add(ax, ay, az, t1, g1x, g1y, g1z, scale, lim, flags);
+      E0 = E2;
+      E1 = E3;
+    }
+  };
+  if (!ENERGY && uni) run(std::true_type{});
+  else run(std::false_type{});
+  if (kPackedPairs && !ENERGY) {
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+      fi[2 * p][0] = qx[p].x; fi[2 * p + 1][0] = qx[p].y;
+      fi[2 * p][1] = qy[p].x; fi[2 * p + 1][1] = qy[p].y;
+      fi[2 * p][2] = qz[p].x; fi[2 * p + 1][2] = qz[p].y;
+    }
+  }
+  // forces on the cluster's atoms: fixed butterfly over the LP lanes
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int o = LP / 2; o > 0; o >>= 1) fi[u][a] += __shfl_xor_sync(0xffffffffu, fi[u][a], o);
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+    if (sl == u && u < ni) {
+      const float sx = fi[u][0] * scale, sy = fi[u][1] * scale, sz = fi[u][2] * scale;
+      range_check(sx, sy, sz, flags);
+      atomicAdd(ax + i0 + u, acc_fix(sx));
+      atomicAdd(ay + i0 + u, acc_fix(sy));
+      atomicAdd(az + i0 + u, acc_fix(sz));
+    }
+  if (ENERGY) {
+#pragma unroll
+    for (int a = 0; a < kEnergyVals; ++a) {
+      float v = ev[a];
+#pragma unroll
+      for (int o = LP / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (sl == 0 && valid) ecl[q][a] = v;
+    }
+  }
+}
+
+// Add the tile's accumulators to the int64 forces (2^-32 kJ/mol/nm): warps
+// w0, w0 + nw, ... take tile cells; one integer atomic per component and
+// tile atom with a non-zero sum (consecutive atoms: coalesced).
+__device__ __forceinline__ void flush_tile(const RegTile& T, const int* __restrict__ ax, const int* __restrict__ ay,
+                                           const int* __restrict__ az, long long* __restrict__ flj, int Npad, int w0,
+                                           int nw) {
+  const int lane = threadIdx.x & 31;
+  for (int kc = w0; kc < T.n_tile; kc += nw) {
+    const int t0 = T.off[kc], nk = T.off[kc + 1] - t0, s0 = T.start[kc];
+    for (int q = lane; q < nk; q += 32) {
+      const int t = t0 + q, sidx = s0 + q;
+      const int qx = ax[t], qy = ay[t], qz = az[t];
+      if ((qx | qy | qz) == 0) continue;
+      atomicAdd(reinterpret_cast<unsigned long long*>(flj + sidx), (unsigned long long)((long long)qx << kLjAccShift));
+      atomicAdd(reinterpret_cast<unsigned long long*>(flj + Npad + sidx),
+                (unsigned long long)((long long)qy << kLjAccShift));
+      atomicAdd(reinterpret_cast<unsigned long long*>(flj + 2 * (size_t)Npad + sidx),
+                (unsigned long long)((long long)qz << kLjAccShift));
+    }
+  }
+}
+
+// Per region: the clusters' FP32 sums added in FP64 in cluster order; the
+// region's sums go to the slot of its first home cell, zeros to the others
+// (the reduction sums a replica's cell slots).  Lanes 0..7 of the caller.
+__device__ __forceinline__ void region_energy(const RegTile& T, int nq, bool fits,
+                                              const float (*__restrict__ ecl)[kEnergyVals], double* __restrict__ epart,
+                                              int a) {
+  double v = 0.0;
+  if (fits)
+    for (int q = 0; q < nq; ++q) v += (double)ecl[q][a];
+  epart[(size_t)T.home_cell[0] * kEnergyVals + a] = v;
+  for (int hh = 1; hh < T.n_home; ++hh) epart[(size_t)T.home_cell[hh] * kEnergyVals + a] = 0.0;
+}
+
+// longest list first: warps that take the last clusters finish soon, and
+// the clusters that share a warp have similar lengths (threads t0, t0 + nt, ...)
+__device__ __forceinline__ void rank_clusters(const int* __restrict__ s_ncl, short* __restrict__ s_ord, int nq,
+                                              int t0, int nt) {
+  for (int q = t0; q < nq; q += nt) {
+    const int nqv = s_ncl[q];
+    int rank = 0;
+    for (int o = 0; o < nq; ++o) {
+      const int no = s_ncl[o];
+      rank += (no > nqv) || (no == nqv && o < q);
+    }
+    s_ord[rank] = (short)q;
+  }
+}
+
+// One block per region (grid schedule), or a fixed grid whose blocks take
+// regions from a device counter (persistent schedule).  The block stages
+// the tile, its warps take tasks of 32/LP clusters from a shared counter
+// (longest lists first), and after a barrier the block flushes the tile's
+// accumulators.
 template <bool ENERGY, int NT, int LP>
 __global__ void __launch_bounds__(NT, ENERGY ? 512 / NT : 768 / NT) k_cl_force(
     const float4* __restrict__ pos, const int* __restrict__ cell_start, const int* __restrict__ cl_start,
@@ -447,14 +718,14 @@ __global__ void __launch_bounds__(NT, ENERGY ? 512 / NT : 768 / NT) k_cl_force(
   // region's clusters in cluster order, so the result does not depend on
   // which warp took which cluster
   __shared__ float ecl[ENERGY ? kRegionClusterCap : 1][kEnergyVals];
-  const int lane = threadIdx.x & 31, sub = lane / LP, sl = lane % LP;
+  const int lane = threadIdx.x & 31;
   for (int it = 0;; ++it) {
     const int r = next_region(persistent != 0, it, work, &sh_r);
     if (r < 0 || r >= n_regions) break;
     const Region g = regions[r];
     const RegionShape& S = shapes[g.shape];
     const RepDev& R = reps[g.rep];
-    __syncthreads();
+    __syncthreads();   // the previous region's tables are no longer read
     region_setup(T, g, S, R, cell_start, cl_start);
     const int total = T.off[T.n_tile];
     const int nq = T.ncl[T.n_home];
@@ -462,7 +733,8 @@ __global__ void __launch_bounds__(NT, ENERGY ? 512 / NT : 768 / NT) k_cl_force(
     if (!fits) {
       if (threadIdx.x == 0) atomicOr(flags, kFlagNbrOverflow);
     } else {
-      tile_load<false>(T, pos, nullptr, sp, nullptr);
+      // list lengths and zeroed accumulators while the tile copies fly
+      tile_issue<false, NT>(T, pos, nullptr, sp, nullptr);
       for (int t = threadIdx.x; t < total; t += NT) { ax[t] = 0; ay[t] = 0; az[t] = 0; }
       for (int q = threadIdx.x; q < nq; q += NT) {
         int h, k;
@@ -470,172 +742,23 @@ __global__ void __launch_bounds__(NT, ENERGY ? 512 / NT : 768 / NT) k_cl_force(
         s_ncl[q] = __ldg(ncl + T.cl0[h] + k);
       }
       if (threadIdx.x == 0) sh_q = 0;
+      tile_finish<false, NT>(T, sp, nullptr);   // ends with a barrier
+      rank_clusters(s_ncl, s_ord, nq, threadIdx.x, NT);
       __syncthreads();
-      // longest list first: warps that take the last clusters finish soon,
-      // and the clusters that share a warp have similar lengths
-      for (int q = threadIdx.x; q < nq; q += NT) {
-        const int nqv = s_ncl[q];
-        int rank = 0;
-        for (int o = 0; o < nq; ++o) {
-          const int no = s_ncl[o];
-          rank += (no > nqv) || (no == nqv && o < q);
-        }
-        s_ord[rank] = (short)q;
-      }
-      __syncthreads();
-      const float rc2 = R.rc2u;
-      const float scale = R.ih_hi * kLjAccScale;     // cell-unit force -> 2^-13 kJ/mol/nm
-      // pair coefficients by type sum (0: C32-C32, 1: C32-C33, 2: C33-C33)
-      const float A0 = 12.f * R.C12u[0], A1 = 12.f * R.C12u[1], A2 = 12.f * R.C12u[2];
-      const float B0 = 6.f * R.C6u[0], B1 = 6.f * R.C6u[1], B2 = 6.f * R.C6u[2];
+      const LjConst c = lj_const(R);
       for (;;) {
         int q0 = 0;
         if (lane == 0) q0 = atomicAdd(&sh_q, CPW);
         q0 = __shfl_sync(0xffffffffu, q0, 0);
         if (q0 >= nq) break;
-        const bool valid = q0 + sub < nq;
-        const int q = valid ? (int)s_ord[q0 + sub] : nq;
-        int h, k;
-        cluster_of(T, valid ? q : nq - 1, h, k);
-        const int i0 = T.off[h] + 4 * k;
-        const int ni = valid ? min(4, T.off[h + 1] - i0) : 0;
-        const int n = valid ? s_ncl[q] : 0;
-        int nmax = n;
-#pragma unroll
-        for (int o = LP; o < 32; o <<= 1) nmax = max(nmax, __shfl_xor_sync(0xffffffffu, nmax, o));
-        float4 pi[4];
-        float a0[4], da[4], b0[4], db[4];
-        float ec[4][6];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          pi[u] = sp[i0 + max(0, min(u, ni - 1))];
-          const bool t3 = pi[u].w != 0.f;           // the atom is a C_33 chain end
-          a0[u] = t3 ? A1 : A0; da[u] = t3 ? A2 - A1 : A1 - A0;
-          b0[u] = t3 ? B1 : B0; db[u] = t3 ? B2 - B1 : B1 - B0;
-          if (ENERGY) {
-            const int ti = t3 ? 1 : 0;
-            ec[u][0] = R.C12u[ti]; ec[u][1] = R.C12u[ti + 1] - ec[u][0];
-            ec[u][2] = R.C6u[ti]; ec[u][3] = R.C6u[ti + 1] - ec[u][2];
-            ec[u][4] = fp.erc[ti][0]; ec[u][5] = fp.erc[ti][1] - ec[u][4];
-          }
-        }
-        float fi[4][3];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) fi[u][0] = fi[u][1] = fi[u][2] = 0.f;
-        float ev[kEnergyVals] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        // packed copies for the force-only form (atoms 0,1 and 2,3)
-        float2 px[2], py[2], pz[2], pa0[2], pda[2], pnb0[2], pndb[2];
-        float2 qx[2], qy[2], qz[2];
-#pragma unroll
-        for (int p = 0; p < 2; ++p) {
-          px[p] = make_float2(pi[2 * p].x, pi[2 * p + 1].x);
-          py[p] = make_float2(pi[2 * p].y, pi[2 * p + 1].y);
-          pz[p] = make_float2(pi[2 * p].z, pi[2 * p + 1].z);
-          pa0[p] = make_float2(a0[2 * p], a0[2 * p + 1]);
-          pda[p] = make_float2(da[2 * p], da[2 * p + 1]);
-          pnb0[p] = make_float2(-b0[2 * p], -b0[2 * p + 1]);
-          pndb[p] = make_float2(-db[2 * p], -db[2 * p + 1]);
-          qx[p] = qy[p] = qz[p] = make_float2(0.f, 0.f);
-        }
-        const unsigned* L = list + (size_t)(valid ? T.cl0[h] + k : 0) * cap;
-        // two entries per lane per iteration (independent work for the
-        // scheduler), the next two in flight; an entry past the list is 0:
-        // tile atom 0 with an empty mask, which adds nothing
-        unsigned E0 = sl < n ? __ldg(L + sl) : 0u;
-        unsigned E1 = sl + LP < n ? __ldg(L + sl + LP) : 0u;
-        for (int e = sl; e - sl < nmax; e += 2 * LP) {
-          const unsigned E2 = e + 2 * LP < n ? __ldg(L + e + 2 * LP) : 0u;
-          const unsigned E3 = e + 3 * LP < n ? __ldg(L + e + 3 * LP) : 0u;
-          const int t0 = (int)(E0 & 0xffffu), t1 = (int)(E1 & 0xffffu);
-          const float4 w0 = sp[t0], w1 = sp[t1];
-          float g0x = 0.f, g0y = 0.f, g0z = 0.f, g1x = 0.f, g1y = 0.f, g1z = 0.f;
-          if (kPackedPairs && !ENERGY) {
-            entry_packed(px, py, pz, pa0, pda, pnb0, pndb, rc2, w0, E0 >> 16, qx, qy, qz, g0x, g0y, g0z);
-            entry_packed(px, py, pz, pa0, pda, pnb0, pndb, rc2, w1, E1 >> 16, qx, qy, qz, g1x, g1y, g1z);
-          } else {
-            entry_scalar<ENERGY>(pi, a0, da, b0, db, ec, rc2, w0, E0 >> 16, fi, ev, g0x, g0y, g0z);
-            entry_scalar<ENERGY>(pi, a0, da, b0, db, ec, rc2, w1, E1 >> 16, fi, ev, g1x, g1y, g1z);
-          }
-          if (e < n) {
-            g0x *= scale; g0y *= scale; g0z *= scale;
-            range_check(g0x, g0y, g0z, flags);
-            atomicAdd(ax + t0, acc_fix(g0x));
-            atomicAdd(ay + t0, acc_fix(g0y));
-            atomicAdd(az + t0, acc_fix(g0z));
-          }
-          if (e + LP < n) {
-            g1x *= scale; g1y *= scale; g1z *= scale;
-            range_check(g1x, g1y, g1z, flags);
-            atomicAdd(ax + t1, acc_fix(g1x));
-            atomicAdd(ay + t1, acc_fix(g1y));
-            atomicAdd(az + t1, acc_fix(g1z));
-          }
-          E0 = E2;
-          E1 = E3;
-        }
-        if (kPackedPairs && !ENERGY) {
-#pragma unroll
-          for (int p = 0; p < 2; ++p) {
-            fi[2 * p][0] = qx[p].x; fi[2 * p + 1][0] = qx[p].y;
-            fi[2 * p][1] = qy[p].x; fi[2 * p + 1][1] = qy[p].y;
-            fi[2 * p][2] = qz[p].x; fi[2 * p + 1][2] = qz[p].y;
-          }
-        }
-        // forces on the cluster's atoms: fixed butterfly over the LP lanes
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-          for (int a = 0; a < 3; ++a)
-#pragma unroll
-            for (int o = LP / 2; o > 0; o >>= 1) fi[u][a] += __shfl_xor_sync(0xffffffffu, fi[u][a], o);
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-          if (sl == u && u < ni) {
-            const float sx = fi[u][0] * scale, sy = fi[u][1] * scale, sz = fi[u][2] * scale;
-            range_check(sx, sy, sz, flags);
-            atomicAdd(ax + i0 + u, acc_fix(sx));
-            atomicAdd(ay + i0 + u, acc_fix(sy));
-            atomicAdd(az + i0 + u, acc_fix(sz));
-          }
-        if (ENERGY) {
-#pragma unroll
-          for (int a = 0; a < kEnergyVals; ++a) {
-            float v = ev[a];
-#pragma unroll
-            for (int o = LP / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (sl == 0 && valid) ecl[q][a] = v;
-          }
-        }
+        cluster_task<ENERGY, LP>(q0, nq, T, sp, ax, ay, az, s_ncl, s_ord, ecl, list, cap, R, fp, c, flags);
       }
       __syncthreads();
-      // flush, warp per tile cell: one int64 atomic per component and tile
-      // atom with a non-zero sum (consecutive atoms: coalesced)
-      for (int kc = threadIdx.x >> 5; kc < T.n_tile; kc += NT / 32) {
-        const int t0 = T.off[kc], nk = T.off[kc + 1] - t0, s0 = T.start[kc];
-        for (int q = lane; q < nk; q += 32) {
-          const int t = t0 + q, sidx = s0 + q;
-          const int qx = ax[t], qy = ay[t], qz = az[t];
-          if ((qx | qy | qz) == 0) continue;
-          atomicAdd(reinterpret_cast<unsigned long long*>(flj + sidx), (unsigned long long)((long long)qx << kLjAccShift));
-          atomicAdd(reinterpret_cast<unsigned long long*>(flj + Npad + sidx),
-                    (unsigned long long)((long long)qy << kLjAccShift));
-          atomicAdd(reinterpret_cast<unsigned long long*>(flj + 2 * (size_t)Npad + sidx),
-                    (unsigned long long)((long long)qz << kLjAccShift));
-        }
-      }
+      flush_tile(T, ax, ay, az, flj, Npad, threadIdx.x >> 5, NT / 32);
     }
     if (ENERGY) {
-      // per region: the clusters' FP32 sums added in FP64 in cluster order;
-      // the region's sums go to the slot of its first home cell, zeros to the
-      // others (the reduction sums a replica's cell slots)
       __syncthreads();
-      if (threadIdx.x < kEnergyVals) {
-        double v = 0.0;
-        if (fits)
-          for (int q = 0; q < nq; ++q) v += (double)ecl[q][threadIdx.x];
-        epart[(size_t)T.home_cell[0] * kEnergyVals + threadIdx.x] = v;
-        for (int hh = 1; hh < T.n_home; ++hh) epart[(size_t)T.home_cell[hh] * kEnergyVals + threadIdx.x] = 0.0;
-      }
+      if (threadIdx.x < kEnergyVals) region_energy(T, nq, fits, ecl, epart, threadIdx.x);
     }
   }
   if (persistent) persistent_done(work);
@@ -667,8 +790,8 @@ void launch_cl_force(bool energy, const float4* pos, const int* cell_start, cons
                      int persistent_grid, int* work, cudaStream_t st) {
   if (n_regions <= 0) return;
   const int grid = persistent_grid > 0 ? persistent_grid : n_regions;
-  const size_t sm = cl_force_smem(tile_cap);
   const int pers = persistent_grid > 0;
+  const size_t sm = cl_force_smem(tile_cap);
 #define MDG_CLF(E, NT, LP)                                                                                    \
   k_cl_force<E, NT, LP><<<grid, NT, sm, st>>>(pos, cell_start, cl_start, regions, n_regions, shapes, reps, list, \
                                               ncl, cap, tile_cap, fp, flj, Npad, epart, flags, pers, work)
@@ -676,6 +799,8 @@ void launch_cl_force(bool energy, const float4* pos, const int* cell_start, cons
   if (energy) MDG_CLF(true, NT, LP); else MDG_CLF(false, NT, LP);
   if (block == 128) {
     if (lanes == 8) { MDG_CLF2(128, 8) } else if (lanes == 32) { MDG_CLF2(128, 32) } else { MDG_CLF2(128, 16) }
+  } else if (block == 384) {
+    if (lanes == 8) { MDG_CLF2(384, 8) } else if (lanes == 32) { MDG_CLF2(384, 32) } else { MDG_CLF2(384, 16) }
   } else {
     if (lanes == 8) { MDG_CLF2(256, 8) } else if (lanes == 32) { MDG_CLF2(256, 32) } else { MDG_CLF2(256, 16) }
   }
@@ -690,6 +815,8 @@ int lj_blocks_per_sm(int block, int lanes, int tile_cap) {
 #define MDG_OCC(NT, LP) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cl_force<false, NT, LP>, NT, sm)
   if (block == 128) {
     if (lanes == 8) MDG_OCC(128, 8); else if (lanes == 32) MDG_OCC(128, 32); else MDG_OCC(128, 16);
+  } else if (block == 384) {
+    if (lanes == 8) MDG_OCC(384, 8); else if (lanes == 32) MDG_OCC(384, 32); else MDG_OCC(384, 16);
   } else {
     if (lanes == 8) MDG_OCC(256, 8); else if (lanes == 32) MDG_OCC(256, 32); else MDG_OCC(256, 16);
   }
@@ -707,6 +834,7 @@ cudaError_t tile_kernels_init() {
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cl_force<E, NT, LP>, cudaFuncAttributeMaxDynamicSharedMemorySize, mf);
 #define MDG_ATTR3(E, NT) MDG_ATTR(E, NT, 8) MDG_ATTR(E, NT, 16) MDG_ATTR(E, NT, 32)
   MDG_ATTR3(false, 128) MDG_ATTR3(true, 128) MDG_ATTR3(false, 256) MDG_ATTR3(true, 256)
+  MDG_ATTR3(false, 384) MDG_ATTR3(true, 384)
 #undef MDG_ATTR3
 #undef MDG_ATTR
   return e;

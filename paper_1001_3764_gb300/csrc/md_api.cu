@@ -71,6 +71,7 @@ struct md_system {
   int tile_cap = 0;
   int lj_block = 256, persistent_grid = 0;   // persistent_grid > 0: fixed grid for the LJ kernel
   int lj_lanes = 8;                          // lanes per 4-atom cluster in the LJ kernel
+  int lj_region = 3;                         // cells per side (x, y) of an LJ / list region
   int* work = nullptr;                       // LJ work counters (persistent schedule)
   int *count = nullptr, *cell_start = nullptr, *cell_of = nullptr;
   int *slot = nullptr, *tmp = nullptr;
@@ -318,12 +319,18 @@ static int configure(md_system* s, const md_desc* d) {
   s->mixed = d->precision == MD_MIXED;
   s->thermo = d->thermostat;
   s->dt = d->dt; s->rc = d->rc; s->skin = d->skin; s->tau = d->thermostat ? d->tau_t : 0.1;
-  if (d->lj_block != 0 && d->lj_block != 128 && d->lj_block != 256) return fail(s, MD_EINVAL, "lj_block must be 0, 128 or 256");
+  if (d->lj_block != 0 && d->lj_block != 128 && d->lj_block != 256 && d->lj_block != 384)
+    return fail(s, MD_EINVAL, "lj_block must be 0, 128, 256 or 384");
   if (d->schedule != MD_SCHED_GRID && d->schedule != MD_SCHED_PERSISTENT) return fail(s, MD_EINVAL, "unknown schedule");
-  s->lj_block = d->lj_block ? d->lj_block : 256;
   if (d->lj_lanes != 0 && d->lj_lanes != 8 && d->lj_lanes != 16 && d->lj_lanes != 32)
     return fail(s, MD_EINVAL, "lj_lanes must be 0, 8, 16 or 32");
   s->lj_lanes = d->lj_lanes ? d->lj_lanes : 8;
+  if (d->lj_region != 0 && d->lj_region != 2 && d->lj_region != 3)
+    return fail(s, MD_EINVAL, "lj_region must be 0, 2 or 3");
+  s->lj_region = d->lj_region ? d->lj_region : 3;
+  // default block: two resident blocks of 12 warps for the 3 x 3 regions'
+  // larger tiles, three of 8 warps for 2 x 2
+  s->lj_block = d->lj_block ? d->lj_block : (s->lj_region == 3 ? 384 : 256);
   if (d->displacement != MD_DISP_REBUILD && d->displacement != MD_DISP_ERROR)
     return fail(s, MD_EINVAL, "displacement must be MD_DISP_REBUILD or MD_DISP_ERROR");
   s->disp = d->displacement;
@@ -333,6 +340,12 @@ static int configure(md_system* s, const md_desc* d) {
   s->T0.assign(s->n_reps, 0.0);
   int64_t atoms = 0, cells = 0, chains = 0;
   double max_expected = 0.0, max_tile = 0.0;
+  // regions of G x G x 1 cells (narrower at the high faces when G does not divide M)
+  const int G = s->lj_region;
+  s->shapes_h.clear();
+  for (int sy = 1; sy <= G; ++sy)
+    for (int sx = 1; sx <= G; ++sx) s->shapes_h.push_back(make_shape(sx, sy));
+  const double tile_cells = (double)s->shapes_h.back().n_tile;
   s->t_int.clear();
   for (int r = 0; r < s->n_reps; ++r) {
     const int nc = d->n_chains[r];
@@ -361,7 +374,7 @@ static int configure(md_system* s, const md_desc* d) {
     // density used for the capacity is at least that of a dense melt
     const double rho = std::max(q.n_atoms / (L * L * L), 40.0);
     max_expected = std::max(max_expected, 4.0 / 3.0 * M_PI * rl * rl * rl * rho);
-    max_tile = std::max(max_tile, 27.0 * std::max(q.n_atoms / (L * L * L), 33.0) * q.h * q.h * q.h);
+    max_tile = std::max(max_tile, tile_cells * std::max(q.n_atoms / (L * L * L), 33.0) * q.h * q.h * q.h);
     atoms += q.n_atoms; cells += (int64_t)M * M * M; chains += nc;
     s->max_slices = std::max(s->max_slices, energy_slice_count(M * M * M));
     if (atoms >= (int64_t)kNbrIndexMask) return fail(s, MD_EINVAL, "too many atoms (limit 2^26)");
@@ -369,19 +382,15 @@ static int configure(md_system* s, const md_desc* d) {
     if (cells >= (1 << 26)) return fail(s, MD_EINVAL, "too many cells");
   }
   s->N = atoms; s->C = (int)cells;
-  // regions of 2 x 2 x 1 cells (1 wide at the high faces of an odd M)
-  s->shapes_h.clear();
-  for (int sy = 1; sy <= 2; ++sy)
-    for (int sx = 1; sx <= 2; ++sx) s->shapes_h.push_back(make_shape(sx, sy));
   s->regions_h.clear();
   for (int r = 0; r < s->n_reps; ++r) {
     const int M = s->reps_h[r].M;
     for (int z = 0; z < M; ++z)
-      for (int y = 0; y < M; y += 2)
-        for (int x = 0; x < M; x += 2) {
+      for (int y = 0; y < M; y += G)
+        for (int x = 0; x < M; x += G) {
           Region g{};
           g.rep = r; g.ox = x; g.oy = y; g.oz = z;
-          g.shape = (std::min(2, M - x) - 1) + 2 * (std::min(2, M - y) - 1);
+          g.shape = (std::min(G, M - x) - 1) + G * (std::min(G, M - y) - 1);
           s->regions_h.push_back(g);
         }
   }
@@ -393,7 +402,7 @@ static int configure(md_system* s, const md_desc* d) {
   s->cap = d->nbr_capacity > 0 ? d->nbr_capacity : (int)std::ceil(2.5 * 0.75 * max_expected + 64.0);
   s->cap = (s->cap + 31) / 32 * 32;
   if (s->cap > 4096) return fail(s, MD_EINVAL, "neighbour capacity above 4096");
-  // 27-cell tile capacity (shared memory per block): 1.4x the mean tile of
+  // tile capacity (shared memory per block): 1.4x the mean tile of
   // the densest replica (at least melt density, 33 sites/nm^3) plus 64, in
   // multiples of 128 atoms; a larger tile is reported as MD_EOVERFLOW
   s->tile_cap = std::min(tile_capacity_max(), ((int)std::ceil(1.4 * max_tile + 64.0) + 127) / 128 * 128);
@@ -479,7 +488,7 @@ static void enqueue_rebin(md_system* s) {
                    s->S, s->perm, s->inv_perm, s->pos, s->tag, s->ref, s->flags, s->st);
   prof_mark(s);
   launch_cl_build(s->pos, s->tag, s->cell_start, s->cl_start, s->regions, (int)s->regions_h.size(), s->shapes,
-                  s->reps, s->list, s->ncl, s->cap, s->tile_cap, s->flags, s->persistent_grid, s->work,
+                  s->reps, s->list, s->ncl, s->cap, s->tile_cap, s->flags, 0, s->work,
                   s->generic ? &s->topo : nullptr, s->st);
   prof_mark(s);
 }
@@ -1143,7 +1152,7 @@ int md_bin_study(md_system* s, int32_t reps, double* ms) {
                      s->S, s->perm, s->inv_perm, s->pos, s->tag, s->ref, s->flags, s->st);
     cudaEventRecord(ev[1], s->st);
     launch_cl_build(s->pos, s->tag, s->cell_start, s->cl_start, s->regions, (int)s->regions_h.size(), s->shapes,
-                    s->reps, s->list, s->ncl, s->cap, s->tile_cap, s->flags, s->persistent_grid, s->work,
+                    s->reps, s->list, s->ncl, s->cap, s->tile_cap, s->flags, 0, s->work,
                   s->generic ? &s->topo : nullptr, s->st);
     cudaEventRecord(ev[2], s->st);
     // host arm: positions to the host, bins there, binned data back, sorted arrays
@@ -1179,7 +1188,7 @@ int md_bin_study(md_system* s, int32_t reps, double* ms) {
   if (rc) return rc;
   // the list of the bins now in place
   launch_cl_build(s->pos, s->tag, s->cell_start, s->cl_start, s->regions, (int)s->regions_h.size(), s->shapes,
-                  s->reps, s->list, s->ncl, s->cap, s->tile_cap, s->flags, s->persistent_grid, s->work,
+                  s->reps, s->list, s->ncl, s->cap, s->tile_cap, s->flags, 0, s->work,
                   s->generic ? &s->topo : nullptr, s->st);
   for (int k = 0; k < 6; ++k) ms[k] = acc[k] / reps;
   rc = check_flags(s);
@@ -1388,49 +1397,60 @@ static int tune_trial(md_desc cand, int cycles, double* us) {
 extern "C" int md_autotune(md_desc* d, int32_t trial_cycles, const char* cache_path, md_tuning* out) {
   if (!d || trial_cycles < 1) return fail(nullptr, MD_EINVAL, "autotune needs a descriptor and trial_cycles >= 1");
   const std::string key = tune_key(d);
-  md_tuning best{d->skin, d->rebin_every, d->lj_block ? d->lj_block : 256, d->schedule, d->lj_lanes ? d->lj_lanes : 8,
-                 0, 1e300};
+  const int region0 = d->lj_region ? d->lj_region : 3;
+  md_tuning best{d->skin, d->rebin_every, d->lj_block ? d->lj_block : (region0 == 3 ? 384 : 256), d->schedule,
+                 d->lj_lanes ? d->lj_lanes : 8, region0, 0, 1e300};
+  auto apply = [&](const md_tuning& t) {
+    d->skin = t.skin; d->rebin_every = t.rebin_every; d->lj_block = t.lj_block; d->schedule = t.schedule;
+    d->lj_lanes = t.lj_lanes; d->lj_region = t.lj_region;
+  };
   if (cache_path) {
     if (FILE* f = fopen(cache_path, "r")) {
-      char k[256];
+      char line[512], k[256];
       double skin, us;
-      int R, blk, sch, lanes;
+      int R, blk, sch, lanes, reg;
       bool found = false;
-      while (fscanf(f, "%255s %lf %d %d %d %d %lf", k, &skin, &R, &blk, &sch, &lanes, &us) == 7)
-        if (key == k) { best = md_tuning{skin, R, blk, sch, lanes, 1, us}; found = true; }
+      // one setting per line; lines of another layout are skipped
+      while (fgets(line, sizeof line, f))
+        if (sscanf(line, "%255s %lf %d %d %d %d %d %lf", k, &skin, &R, &blk, &sch, &lanes, &reg, &us) == 8 && key == k) {
+          best = md_tuning{skin, R, blk, sch, lanes, reg, 1, us};
+          found = true;
+        }
       fclose(f);
       if (found) {
-        d->skin = best.skin; d->rebin_every = best.rebin_every; d->lj_block = best.lj_block; d->schedule = best.schedule;
-        d->lj_lanes = best.lj_lanes;
+        apply(best);
         if (out) *out = best;
         return MD_OK;
       }
     }
   }
   bool any = false;
-  // block shape x schedule at the descriptor's cell size
-  for (int blk : {128, 256})
+  // region side x block shape x schedule at the descriptor's cell size
+  const int shapes[4][2] = {{2, 128}, {2, 256}, {3, 256}, {3, 384}};
+  for (const auto& rb : shapes)
     for (int sch : {(int)MD_SCHED_GRID, (int)MD_SCHED_PERSISTENT}) {
       md_desc c = *d;
-      c.lj_block = blk;
+      c.lj_region = rb[0];
+      c.lj_block = rb[1];
       c.schedule = sch;
       c.lj_lanes = best.lj_lanes;
       double us = 0.0;
       if (tune_trial(c, trial_cycles, &us) == MD_OK && us < best.us_per_step) {
-        best = md_tuning{c.skin, c.rebin_every, blk, sch, best.lj_lanes, 0, us};
+        best = md_tuning{c.skin, c.rebin_every, rb[1], sch, best.lj_lanes, rb[0], 0, us};
         any = true;
       }
     }
-  // lanes per cluster with that block shape and schedule
+  // lanes per cluster with that region, block shape and schedule
   for (int lanes : {8, 16, 32}) {
     if (lanes == best.lj_lanes) continue;
     md_desc c = *d;
+    c.lj_region = best.lj_region;
     c.lj_block = best.lj_block;
     c.schedule = best.schedule;
     c.lj_lanes = lanes;
     double us = 0.0;
     if (tune_trial(c, trial_cycles, &us) == MD_OK && us < best.us_per_step) {
-      best = md_tuning{c.skin, c.rebin_every, best.lj_block, best.schedule, lanes, 0, us};
+      best = md_tuning{c.skin, c.rebin_every, best.lj_block, best.schedule, lanes, best.lj_region, 0, us};
       any = true;
     }
   }
@@ -1440,6 +1460,7 @@ extern "C" int md_autotune(md_desc* d, int32_t trial_cycles, const char* cache_p
   for (int k = 0; k < 4; ++k) {
     if (skins[k] == best.skin && reb[k] == best.rebin_every) continue;
     md_desc c = *d;
+    c.lj_region = best.lj_region;
     c.lj_block = best.lj_block;
     c.schedule = best.schedule;
     c.lj_lanes = best.lj_lanes;
@@ -1447,17 +1468,16 @@ extern "C" int md_autotune(md_desc* d, int32_t trial_cycles, const char* cache_p
     c.rebin_every = reb[k];
     double us = 0.0;
     if (tune_trial(c, trial_cycles, &us) == MD_OK && us < best.us_per_step) {
-      best = md_tuning{skins[k], reb[k], best.lj_block, best.schedule, best.lj_lanes, 0, us};
+      best = md_tuning{skins[k], reb[k], best.lj_block, best.schedule, best.lj_lanes, best.lj_region, 0, us};
       any = true;
     }
   }
   if (!any) return fail(nullptr, MD_EUNSTABLE, "autotune: no candidate ran cleanly");
-  d->skin = best.skin; d->rebin_every = best.rebin_every; d->lj_block = best.lj_block; d->schedule = best.schedule;
-  d->lj_lanes = best.lj_lanes;
+  apply(best);
   if (cache_path)
     if (FILE* f = fopen(cache_path, "a")) {
-      fprintf(f, "%s %.4f %d %d %d %d %.3f\n", key.c_str(), best.skin, best.rebin_every, best.lj_block, best.schedule,
-              best.lj_lanes, best.us_per_step);
+      fprintf(f, "%s %.4f %d %d %d %d %d %.3f\n", key.c_str(), best.skin, best.rebin_every, best.lj_block, best.schedule,
+              best.lj_lanes, best.lj_region, best.us_per_step);
       fclose(f);
     }
   if (out) *out = best;

@@ -71,8 +71,8 @@ struct Tile { int start, len, rep, pad; };
 // Regions of up to 2 x 2 x 1 cells (the work unit of the list build and LJ
 // kernels) and their tiles: the region's home cells, then the cells their
 // 13 forward neighbours add, as offsets from the region's origin cell.
-constexpr int kMaxTileCells = 32;
-constexpr int kMaxHome = 4;
+constexpr int kMaxTileCells = 64;   // 44 cells for a 3 x 3 x 1 region
+constexpr int kMaxHome = 9;
 struct RegionShape {
   int n_home, n_tile;
   signed char off[kMaxTileCells][3];      // tile cell offsets (x, y, z) from the origin cell

@@ -626,26 +626,32 @@ def test_first_cycle_after_set_state_skips_the_rebin_with_the_same_bits():
 
 
 def test_schedules_and_block_shapes_agree():
-    """The persistent schedule gives the same bits as one block per cell (each
-    cell's forces do not depend on which block computes them); 128-thread
-    blocks split an atom's list differently, so they agree to FP32 rounding."""
+    """The persistent schedule gives the same bits as one block per region,
+    and so does any block size (a cluster's forces do not depend on which warp
+    of which block computes them).  Regions of 2 x 2 and 3 x 3 cells stage
+    positions in different frames, so those two agree to FP32 rounding."""
     m = chaingen.melt(30, seed=23)
     runs = {}
-    for blk, sch in ((256, md.MD_SCHED_GRID), (256, md.MD_SCHED_PERSISTENT), (128, md.MD_SCHED_GRID),
-                     (128, md.MD_SCHED_PERSISTENT)):
-        s = md.System(m, precision=md.MD_MIXED, rebin_every=4, lj_block=blk, schedule=sch)
+    cases = ((3, 384, md.MD_SCHED_GRID), (3, 384, md.MD_SCHED_PERSISTENT), (3, 256, md.MD_SCHED_GRID),
+             (3, 128, md.MD_SCHED_PERSISTENT), (2, 256, md.MD_SCHED_GRID), (2, 256, md.MD_SCHED_PERSISTENT),
+             (2, 128, md.MD_SCHED_GRID))
+    f0 = {}
+    for reg, blk, sch in cases:
+        s = md.System(m, precision=md.MD_MIXED, rebin_every=4, lj_block=blk, schedule=sch, lj_region=reg)
+        f0[reg] = s.forces()
         s.step(12)
-        runs[(blk, sch)] = (s.forces(), s.state()[0], s.energy()[0])
+        runs[(reg, blk, sch)] = (s.forces(), s.state()[0], s.energy()[0])
         s.close()
-    for blk in (128, 256):
-        fa, xa, ea = runs[(blk, md.MD_SCHED_GRID)]
-        fb, xb, eb = runs[(blk, md.MD_SCHED_PERSISTENT)]
-        assert np.array_equal(fa, fb) and np.array_equal(xa, xb) and ea == eb
-    f1, x1, _ = runs[(128, md.MD_SCHED_GRID)]
-    f2, x2, _ = runs[(256, md.MD_SCHED_GRID)]
-    scale = np.sqrt(np.mean(np.sum(f2 ** 2, axis=1)))
-    assert np.abs(f1 - f2).max() < 1e-5 * scale
-    assert np.abs(x1 - x2).max() < 1e-7
+    for key in cases[1:]:
+        ref = runs[(key[0],) + ((384, md.MD_SCHED_GRID) if key[0] == 3 else (256, md.MD_SCHED_GRID))]
+        f, x, e = runs[key]
+        assert np.array_equal(f, ref[0]) and np.array_equal(x, ref[1]) and e == ref[2], key
+    # same state: forces to FP32 rounding (the relative RMS bound of the
+    # parity tests); after 12 steps the positions
+    rel = np.sqrt(np.sum((f0[3] - f0[2]) ** 2) / np.sum(f0[2] ** 2))
+    assert rel <= FORCE_TOL, rel
+    x3, x2 = runs[(3, 384, md.MD_SCHED_GRID)][1], runs[(2, 256, md.MD_SCHED_GRID)][1]
+    assert np.abs(x3 - x2).max() < 1e-6
 
 
 def test_autotune_picks_a_working_setting_and_caches_it(tmp_path):
@@ -653,12 +659,14 @@ def test_autotune_picks_a_working_setting_and_caches_it(tmp_path):
     cache = str(tmp_path / "tune.txt")
     s = md.System(m, precision=md.MD_MIXED, autotune=True, tune_cycles=1, tune_cache=cache)
     t = s.tuning
-    assert t["from_cache"] == 0 and t["lj_block"] in (128, 256) and t["schedule"] in (0, 1)
+    assert t["from_cache"] == 0 and t["lj_block"] in (128, 256, 384) and t["schedule"] in (0, 1)
+    assert t["lj_region"] in (2, 3) and t["lj_lanes"] in (8, 16, 32)
     assert t["skin"] > 0 and t["rebin_every"] >= 1 and t["us_per_step"] > 0
     s.step(2 * s.rebin_every)
     s.close()
     s2 = md.System(m, precision=md.MD_MIXED, autotune=True, tune_cycles=1, tune_cache=cache)
     assert s2.tuning["from_cache"] == 1 and s2.tuning["skin"] == t["skin"]
+    assert s2.tuning["lj_region"] == t["lj_region"] and s2.tuning["lj_block"] == t["lj_block"]
     s2.close()
 
 
