@@ -382,10 +382,13 @@ constexpr int kRegionClusterCap = 512;   // clusters of one region (2,048 home a
 // beyond +-2^31 (2^18 kJ/mol/nm)
 __device__ __forceinline__ int acc_fix(float f) { return __float2int_rn(f); }
 
-// a converted sum far from the int32 range (or not finite) is reported
+// a converted component at or beyond 2^30 (2^17 kJ/mol/nm, half the int32
+// range of the tile accumulators) or not finite is reported
 __device__ __forceinline__ void range_check(float sx, float sy, float sz, unsigned* flags) {
-  const float a = fabsf(sx) + fabsf(sy) + fabsf(sz);
-  if (!(a < 1.0e9f)) atomicOr(flags, (a == a && a <= 3.4e38f) ? kFlagFixOverflow : kFlagNaN);
+  const float a = fmaxf(fabsf(sx), fmaxf(fabsf(sy), fabsf(sz)));
+  const bool finite = (sx - sx) == 0.f && (sy - sy) == 0.f && (sz - sz) == 0.f;
+  if (!finite) atomicOr(flags, kFlagNaN);
+  else if (!(a < 1073741824.0f)) atomicOr(flags, kFlagFixOverflow);
 }
 
 // Add the force g (cell units) on tile atom t to the 2^-13 accumulators.
