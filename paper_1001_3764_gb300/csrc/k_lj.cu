@@ -116,13 +116,13 @@ __device__ __forceinline__ void region_setup(RegTile& T, const Region& g, const 
 // table); every thread starts asynchronous copies (cp.async, global to
 // shared without registers) for atoms t = threadIdx.x + i NT, so the whole
 // tile is in flight at once; after the wait and a barrier, a warp per tile
-// cell adds the cell's frame shift.  WITH_TAG: also the chain/site tag of
-// each atom (list build); the w component keeps the LJ type (0.0 / 1.0)
-// that binning and integration store.  tile_issue starts the copies,
-// tile_finish waits for them, shifts, and ends with a barrier.
-template <bool WITH_TAG, int NT>
-__device__ __forceinline__ void tile_issue(const RegTile& T, const float4* __restrict__ pos, const int* __restrict__ tag,
-                                          float4* __restrict__ sp, int* __restrict__ st) {
+// cell adds the cell's frame shift.  The w component keeps the LJ type
+// (0.0 / 1.0) that binning and integration store; WITH_TAG (list build)
+// replaces it by the bits of the atom's chain/site tag, which the build
+// needs instead.  tile_issue starts the copies, tile_finish waits for them,
+// shifts, and ends with a barrier.
+template <int NT>
+__device__ __forceinline__ void tile_issue(const RegTile& T, const float4* __restrict__ pos, float4* __restrict__ sp) {
   const int total = T.off[T.n_tile], nt = T.n_tile;
   for (int t = threadIdx.x; t < total; t += NT) {
     int lo = 0, hi = nt - 1;
@@ -134,28 +134,24 @@ __device__ __forceinline__ void tile_issue(const RegTile& T, const float4* __res
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(sp + t)),
                  "l"(pos + j)
                  : "memory");
-    if (WITH_TAG)
-      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(st + t)),
-                   "l"(tag + j)
-                   : "memory");
   }
   asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
 template <bool WITH_TAG, int NT>
-__device__ __forceinline__ void tile_finish(const RegTile& T, float4* __restrict__ sp, int* __restrict__ st) {
+__device__ __forceinline__ void tile_finish(const RegTile& T, float4* __restrict__ sp, const int* __restrict__ tag) {
   const int nt = T.n_tile;
   asm volatile("cp.async.wait_group 0;" ::: "memory");
   __syncthreads();
   const int lane = threadIdx.x & 31;
   for (int k = threadIdx.x >> 5; k < nt; k += NT / 32) {
-    const int t0 = T.off[k], n = T.off[k + 1] - t0;
+    const int t0 = T.off[k], n = T.off[k + 1] - t0, j0 = T.start[k];
     const float ox = T.sx[k], oy = T.sy[k], oz = T.sz[k];
     for (int q = lane; q < n; q += 32) {
       float4 p = sp[t0 + q];
       p.x += ox; p.y += oy; p.z += oz;
+      if (WITH_TAG) p.w = __int_as_float(__ldg(tag + j0 + q) & (int)kTagMask);
       sp[t0 + q] = p;
-      if (WITH_TAG) st[t0 + q] &= (int)kTagMask;
     }
   }
   __syncthreads();
@@ -212,8 +208,9 @@ __device__ __forceinline__ bool topo_excluded(int a, int b, const TopoDev& tp) {
 
 // the four-atom test of candidate t: bit u set if atom u of the cluster pairs with t
 template <bool GEN>
-__device__ __forceinline__ unsigned pair_mask(const float4 (&pi)[4], const int (&ti)[4], const float4& w, int tg,
-                                              float rl2, const TopoDev& tp) {
+__device__ __forceinline__ unsigned pair_mask(const float4 (&pi)[4], const int (&ti)[4], const float4& w, float rl2,
+                                              const TopoDev& tp) {
+  const int tg = __float_as_int(w.w);   // the candidate's tag (list-build tile)
   unsigned m = 0u;
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
@@ -233,7 +230,7 @@ __device__ __forceinline__ unsigned pair_mask(const float4 (&pi)[4], const int (
 }
 
 template <int NT, bool GEN>
-__global__ void __launch_bounds__(NT) k_cl_build(const float4* __restrict__ pos, const int* __restrict__ tag,
+__global__ void __launch_bounds__(NT, 1024 / NT) k_cl_build(const float4* __restrict__ pos, const int* __restrict__ tag,
                                                  const int* __restrict__ cell_start, const int* __restrict__ cl_start,
                                                  const Region* __restrict__ regions, int n_regions,
                                                  const RegionShape* __restrict__ shapes, const RepDev* __restrict__ reps,
@@ -241,8 +238,7 @@ __global__ void __launch_bounds__(NT) k_cl_build(const float4* __restrict__ pos,
                                                  int tile_cap, unsigned* __restrict__ flags, int persistent,
                                                  int* __restrict__ work, const TopoDev tp) {
   extern __shared__ __align__(16) unsigned char smem[];
-  float4* sp = reinterpret_cast<float4*>(smem);
-  int* st = reinterpret_cast<int*>(smem + (size_t)tile_cap * sizeof(float4));
+  float4* sp = reinterpret_cast<float4*>(smem);   // w: the atom's chain/site tag bits
   __shared__ RegTile T;
   __shared__ int sh_r;
   __shared__ int queue[NT / 32][kBuildQueue];
@@ -266,8 +262,8 @@ __global__ void __launch_bounds__(NT) k_cl_build(const float4* __restrict__ pos,
       }
       continue;
     }
-    tile_issue<true, NT>(T, pos, tag, sp, st);
-    tile_finish<true, NT>(T, sp, st);
+    tile_issue<NT>(T, pos, sp);
+    tile_finish<true, NT>(T, sp, tag);
     const float rl2 = R.rlist2u;
     const float rl = sqrtf(rl2);
     const unsigned lt = (1u << lane) - 1u;
@@ -283,7 +279,7 @@ __global__ void __launch_bounds__(NT) k_cl_build(const float4* __restrict__ pos,
       for (int u = 0; u < 4; ++u) {
         const int t = i0 + min(u, ni - 1);
         pi[u] = sp[t];
-        ti[u] = st[t];
+        ti[u] = __float_as_int(pi[u].w);
         cx += pi[u].x; cy += pi[u].y; cz += pi[u].z;
       }
       cx *= 0.25f; cy *= 0.25f; cz *= 0.25f;
@@ -310,7 +306,7 @@ __global__ void __launch_bounds__(NT) k_cl_build(const float4* __restrict__ pos,
           const int t = t0 + lane;
           unsigned m = 0u;
           if (t < t_end) {
-            m = pair_mask<GEN>(pi, ti, sp[t], st[t], rl2, tp);
+            m = pair_mask<GEN>(pi, ti, sp[t], rl2, tp);
             m &= ((t > i0) ? 1u : 0u) | ((t > i0 + 1) ? 2u : 0u) | ((t > i0 + 2) ? 4u : 0u) | ((t > i0 + 3) ? 8u : 0u);
           }
           const unsigned b = __ballot_sync(0xffffffffu, m != 0u);
@@ -338,7 +334,7 @@ __global__ void __launch_bounds__(NT) k_cl_build(const float4* __restrict__ pos,
           __syncwarp();
           if (qn >= 32) {
             const int tq = qw[lane];
-            const unsigned m = pair_mask<GEN>(pi, ti, sp[tq], st[tq], rl2, tp);
+            const unsigned m = pair_mask<GEN>(pi, ti, sp[tq], rl2, tp);
             const unsigned bm = __ballot_sync(0xffffffffu, m != 0u);
             const int p = cnt + __popc(bm & lt);
             if (m != 0u && p < cap) out[p] = (unsigned)tq | (m << 16);
@@ -357,7 +353,7 @@ __global__ void __launch_bounds__(NT) k_cl_build(const float4* __restrict__ pos,
         int tq = 0;
         if (lane < qn) {
           tq = qw[lane];
-          m = pair_mask<GEN>(pi, ti, sp[tq], st[tq], rl2, tp);
+          m = pair_mask<GEN>(pi, ti, sp[tq], rl2, tp);
         }
         const unsigned bm = __ballot_sync(0xffffffffu, m != 0u);
         const int p = cnt + __popc(bm & lt);
@@ -737,7 +733,7 @@ __global__ void __launch_bounds__(NT, ENERGY ? 512 / NT : 768 / NT) k_cl_force(
       if (threadIdx.x == 0) atomicOr(flags, kFlagNbrOverflow);
     } else {
       // list lengths and zeroed accumulators while the tile copies fly
-      tile_issue<false, NT>(T, pos, nullptr, sp, nullptr);
+      tile_issue<NT>(T, pos, sp);
       for (int t = threadIdx.x; t < total; t += NT) { ax[t] = 0; ay[t] = 0; az[t] = 0; }
       for (int q = threadIdx.x; q < nq; q += NT) {
         int h, k;
@@ -768,7 +764,7 @@ __global__ void __launch_bounds__(NT, ENERGY ? 512 / NT : 768 / NT) k_cl_force(
 }
 
 // ===================================================================== launch
-size_t cl_build_smem(int tile_cap) { return (size_t)tile_cap * (sizeof(float4) + sizeof(int)); }
+size_t cl_build_smem(int tile_cap) { return (size_t)tile_cap * sizeof(float4); }
 size_t cl_force_smem(int tile_cap) { return (size_t)tile_cap * (sizeof(float4) + 3 * sizeof(int)); }
 
 void launch_cl_build(const float4* pos, const int* tag, const int* cell_start, const int* cl_start,
