@@ -374,10 +374,11 @@ int64_t md_launches_per_call(md_system *sys, int64_t n_steps);
 int md_bin_static(const double *pos, int32_t n_atoms, double box, int32_t cells_per_side, int32_t *cell_of,
                   int32_t *cell_start, int32_t *perm, void *cuda_stream);
 
-/* Self-test of the bounded device waits (the pipelined LJ kernel's mbarrier
- * waits use the same code): one block waits on an mbarrier that nothing
- * arrives on, gives up after `spins` try_wait rounds (1 .. 100000), raises
- * its timeout flag and returns.  Returns MD_ETIMEOUT when the wait gave up
+/* Self-test of the bounded device wait, the pattern any device wait of this
+ * library follows (no hot-path kernel waits on another block or launch
+ * today): one block waits on an mbarrier that nothing arrives on, gives up
+ * after `spins` try_wait rounds (1 .. 100000), raises its timeout flag and
+ * returns.  Returns MD_ETIMEOUT when the wait gave up
  * (the expected result), MD_OK if it did not, another MD_E* code on a
  * failure.  Allocates and frees a 4-byte device flag; synchronous. */
 int md_wait_selftest(int32_t spins);

@@ -559,11 +559,10 @@ def test_batched_replicas_full_size_sampled_forces():
     s.close()
 
 
-def test_full_size_pipelined_schedule_gives_the_same_bits():
-    """1.5M sites as benchmarked: the pipelined persistent LJ kernel (tile and
-    list rows staged by bulk copies; a cell whose rows exceed a stage reads
-    them from global memory) gives the same forces and energies, bit for bit,
-    as one block per cell."""
+def test_full_size_persistent_schedule_gives_the_same_bits():
+    """1.5M sites as benchmarked: the persistent schedule (a fixed grid whose
+    blocks take regions from a device counter) gives the same forces and
+    energies, bit for bit, as one block per region."""
     m = chaingen.melt(10000, seed=3)
     out = []
     for sch in (md.MD_SCHED_GRID, md.MD_SCHED_PERSISTENT):
