@@ -447,6 +447,42 @@ __device__ __forceinline__ void entry_packed(const float2 (&px)[2], const float2
   gz = -(sz.x + sz.y);
 }
 
+// Energy form: one list entry against the cluster's four atoms, packed as
+// in entry_packed, adding the pair energies, the cutoff shifts of the kept
+// pairs and the virial terms r (x) f to ev2[8] (two FP32 halves each); no
+// force is accumulated (the energy read-out needs none).  cA[p] etc.: the
+// pair coefficients C12, C6 and E(r_c) of atoms 2p, 2p+1 with j.
+__device__ __forceinline__ void entry_packed_energy(const float2 (&px)[2], const float2 (&py)[2],
+                                                    const float2 (&pz)[2], const float2 (&c12)[2],
+                                                    const float2 (&c6)[2], const float2 (&sh)[2], float rc2,
+                                                    const float4& w, unsigned m, float2 (&ev2)[kEnergyVals]) {
+  const float2 wx = make_float2(-w.x, -w.x), wy = make_float2(-w.y, -w.y), wz = make_float2(-w.z, -w.z);
+  const float2 k12 = make_float2(12.f, 12.f), km6 = make_float2(-6.f, -6.f);
+#pragma unroll
+  for (int p = 0; p < 2; ++p) {
+    const float2 dx = __fadd2_rn(px[p], wx), dy = __fadd2_rn(py[p], wy), dz = __fadd2_rn(pz[p], wz);
+    float2 r2 = __fmul2_rn(dx, dx);
+    r2 = __ffma2_rn(dy, dy, r2);
+    r2 = __ffma2_rn(dz, dz, r2);
+    const float q0 = rcp_approx(r2.x), q1 = rcp_approx(r2.y);
+    const bool k0 = ((m >> (2 * p)) & 1u) && r2.x < rc2, k1 = ((m >> (2 * p + 1)) & 1u) && r2.y < rc2;
+    const float2 ir2 = make_float2(k0 ? q0 : 0.f, k1 ? q1 : 0.f);
+    const float2 ir4 = __fmul2_rn(ir2, ir2), ir6 = __fmul2_rn(ir4, ir2), ir8 = __fmul2_rn(ir4, ir4);
+    // F/r = r^-8 (12 C12 r^-6 - 6 C6), E = r^-6 (C12 r^-6 - C6)
+    const float2 ff = __fmul2_rn(ir8, __ffma2_rn(__fmul2_rn(k12, c12[p]), ir6, __fmul2_rn(km6, c6[p])));
+    const float2 e = __fmul2_rn(ir6, __ffma2_rn(c12[p], ir6, make_float2(-c6[p].x, -c6[p].y)));
+    ev2[0] = __fadd2_rn(ev2[0], e);
+    ev2[1] = __fadd2_rn(ev2[1], make_float2(k0 ? sh[p].x : 0.f, k1 ? sh[p].y : 0.f));
+    const float2 fx = __fmul2_rn(ff, dx), fy = __fmul2_rn(ff, dy);
+    ev2[2] = __ffma2_rn(fx, dx, ev2[2]);
+    ev2[3] = __ffma2_rn(fy, dy, ev2[3]);
+    ev2[4] = __ffma2_rn(__fmul2_rn(ff, dz), dz, ev2[4]);
+    ev2[5] = __ffma2_rn(fx, dy, ev2[5]);
+    ev2[6] = __ffma2_rn(fx, dz, ev2[6]);
+    ev2[7] = __ffma2_rn(fy, dz, ev2[7]);
+  }
+}
+
 // One list entry against the cluster's four atoms, one pair at a time (and,
 // with ENERGY, the pair energies and virial): adds the forces on the four
 // atoms to fi, returns minus their sum (the force on j) in g*.
@@ -556,6 +592,18 @@ __device__ __forceinline__ void cluster_task(int q0, int nq, const RegTile& T, c
     pndb[p] = make_float2(-db[2 * p], -db[2 * p + 1]);
     qx[p] = qy[p] = qz[p] = make_float2(0.f, 0.f);
   }
+  // energy form: C12, C6 and E(r_c) coefficients (base, difference for a
+  // C_33 j) of atoms 2p, 2p+1, and the eight sums in two FP32 halves
+  float2 pec[6][2];
+  float2 ev2[kEnergyVals];
+  if (ENERGY) {
+#pragma unroll
+    for (int a = 0; a < 6; ++a)
+#pragma unroll
+      for (int p = 0; p < 2; ++p) pec[a][p] = make_float2(ec[2 * p][a], ec[2 * p + 1][a]);
+#pragma unroll
+    for (int a = 0; a < kEnergyVals; ++a) ev2[a] = make_float2(0.f, 0.f);
+  }
   const unsigned* L = list + (size_t)(valid ? T.cl0[h] + k : 0) * cap;
   // clusters without a chain end (the common case) share one pair
   // coefficient per j type: two scalar FMAs per entry instead of four
@@ -594,18 +642,36 @@ __device__ __forceinline__ void cluster_task(int q0, int nq, const RegTile& T, c
         }
         entry_packed(px, py, pz, cA0, cB0, rc2, w0, E0 >> 16, qx, qy, qz, g0x, g0y, g0z);
         entry_packed(px, py, pz, cA1, cB1, rc2, w1, E1 >> 16, qx, qy, qz, g1x, g1y, g1z);
+      } else if (ENERGY) {
+        const float2 wt0 = make_float2(w0.w, w0.w), wt1 = make_float2(w1.w, w1.w);
+        float2 c12a[2], c6a[2], sha[2], c12b[2], c6b[2], shb[2];
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+          c12a[p] = __ffma2_rn(wt0, pec[1][p], pec[0][p]); c12b[p] = __ffma2_rn(wt1, pec[1][p], pec[0][p]);
+          c6a[p] = __ffma2_rn(wt0, pec[3][p], pec[2][p]); c6b[p] = __ffma2_rn(wt1, pec[3][p], pec[2][p]);
+          sha[p] = __ffma2_rn(wt0, pec[5][p], pec[4][p]); shb[p] = __ffma2_rn(wt1, pec[5][p], pec[4][p]);
+        }
+        entry_packed_energy(px, py, pz, c12a, c6a, sha, rc2, w0, E0 >> 16, ev2);
+        entry_packed_energy(px, py, pz, c12b, c6b, shb, rc2, w1, E1 >> 16, ev2);
       } else {
         entry_scalar<ENERGY>(pi, a0, da, b0, db, ec, rc2, w0, E0 >> 16, fi, ev, g0x, g0y, g0z);
         entry_scalar<ENERGY>(pi, a0, da, b0, db, ec, rc2, w1, E1 >> 16, fi, ev, g1x, g1y, g1z);
       }
-      if (e < n) acc_add(ax, ay, az, t0, g0x, g0y, g0z, scale, lim, flags);
-      if (e + LP < n) acc_add(ax, ay, az, t1, g1x, g1y, g1z, scale, lim, flags);
+      if (!ENERGY) {
+        if (e < n) acc_add(ax, ay, az, t0, g0x, g0y, g0z, scale, lim, flags);
+        if (e + LP < n) acc_add(ax, ay, az, t1, g1x, g1y, g1z, scale, lim, flags);
+      }
       E0 = E2;
       E1 = E3;
     }
   };
   if (!ENERGY && uni) run(std::true_type{});
   else run(std::false_type{});
+  if (ENERGY) {
+#pragma unroll
+    for (int a = 0; a < kEnergyVals; ++a) ev[a] = ev2[a].x + ev2[a].y;
+    ev[1] = ev[0] - ev[1];   // lj_shifted: the pair energies less the kept pairs' E(r_c)
+  }
   if (kPackedPairs && !ENERGY) {
 #pragma unroll
     for (int p = 0; p < 2; ++p) {
@@ -615,21 +681,23 @@ __device__ __forceinline__ void cluster_task(int q0, int nq, const RegTile& T, c
     }
   }
   // forces on the cluster's atoms: fixed butterfly over the LP lanes
+  if (!ENERGY) {
 #pragma unroll
-  for (int u = 0; u < 4; ++u)
+    for (int u = 0; u < 4; ++u)
 #pragma unroll
-    for (int a = 0; a < 3; ++a)
+      for (int a = 0; a < 3; ++a)
 #pragma unroll
-      for (int o = LP / 2; o > 0; o >>= 1) fi[u][a] += __shfl_xor_sync(0xffffffffu, fi[u][a], o);
+        for (int o = LP / 2; o > 0; o >>= 1) fi[u][a] += __shfl_xor_sync(0xffffffffu, fi[u][a], o);
 #pragma unroll
-  for (int u = 0; u < 4; ++u)
-    if (sl == u && u < ni) {
-      const float sx = fi[u][0] * scale, sy = fi[u][1] * scale, sz = fi[u][2] * scale;
-      range_check(sx, sy, sz, flags);
-      atomicAdd(ax + i0 + u, acc_fix(sx));
-      atomicAdd(ay + i0 + u, acc_fix(sy));
-      atomicAdd(az + i0 + u, acc_fix(sz));
-    }
+    for (int u = 0; u < 4; ++u)
+      if (sl == u && u < ni) {
+        const float sx = fi[u][0] * scale, sy = fi[u][1] * scale, sz = fi[u][2] * scale;
+        range_check(sx, sy, sz, flags);
+        atomicAdd(ax + i0 + u, acc_fix(sx));
+        atomicAdd(ay + i0 + u, acc_fix(sy));
+        atomicAdd(az + i0 + u, acc_fix(sz));
+      }
+  }
   if (ENERGY) {
 #pragma unroll
     for (int a = 0; a < kEnergyVals; ++a) {
@@ -734,7 +802,8 @@ __global__ void __launch_bounds__(NT, ENERGY ? 512 / NT : 768 / NT) k_cl_force(
     } else {
       // list lengths and zeroed accumulators while the tile copies fly
       tile_issue<NT>(T, pos, sp);
-      for (int t = threadIdx.x; t < total; t += NT) { ax[t] = 0; ay[t] = 0; az[t] = 0; }
+      if (!ENERGY)
+        for (int t = threadIdx.x; t < total; t += NT) { ax[t] = 0; ay[t] = 0; az[t] = 0; }
       for (int q = threadIdx.x; q < nq; q += NT) {
         int h, k;
         cluster_of(T, q, h, k);
@@ -753,7 +822,7 @@ __global__ void __launch_bounds__(NT, ENERGY ? 512 / NT : 768 / NT) k_cl_force(
         cluster_task<ENERGY, LP>(q0, nq, T, sp, ax, ay, az, s_ncl, s_ord, ecl, list, cap, R, fp, c, flags);
       }
       __syncthreads();
-      flush_tile(T, ax, ay, az, flj, Npad, threadIdx.x >> 5, NT / 32);
+      if (!ENERGY) flush_tile(T, ax, ay, az, flj, Npad, threadIdx.x >> 5, NT / 32);
     }
     if (ENERGY) {
       __syncthreads();
