@@ -1,12 +1,13 @@
 // k_lj.cu -- neighbour list (Sec. 3.1) and Lennard-Jones force (Eq. 2,
 // Sec. 3.2) with every pair evaluated once (Newton's third law).
 //
-// Work unit: a region of up to 2 x 2 x 1 cells (cells of side >= r_c + skin,
-// Sec. 3.1), one thread block per region.  The block stages in shared memory
-// the "tile": the region's cells and every cell that one of them reaches by
-// one of the 13 forward offsets of a half shell (27 cells for a full region),
-// each cell a contiguous run of sorted atoms, moved into the region's frame:
-// w = u + (cell offset - region centre) in cell units, |w| <= 2.  The paper's
+// Work unit: a region of up to G x G x 1 cells (G = 2 or 3; cells of side
+// >= r_c + skin, Sec. 3.1), one thread block per region.  The block stages in
+// shared memory the "tile": the region's cells and every cell that one of
+// them reaches by one of the 13 forward offsets of a half shell (27 cells
+// for G = 2, 44 for G = 3), each cell a contiguous run of sorted atoms, moved
+// into the region's frame: w = u + (cell offset - region centre) in cell
+// units, |w| < 3.  The paper's
 // neighbour-search kernel also assigns a block to grid cells and stages the
 // neighbour cells (Sec. 3.1, last paragraph); here the same staging serves
 // the force kernel, and the list holds indices into the staged tile.
@@ -21,9 +22,9 @@
 // 4-bit mask of the atoms i that pair with j: within r_c + skin, not a 1-2 or
 // 1-3 neighbour (Sec. 3.1) and, inside the cluster, i before j.
 //
-// Force: a warp takes one cluster; its 32 lanes take 32 list entries at a
-// time, and each lane evaluates the entry's j against the cluster's four i
-// (r2inv = 0 beyond r_c, as in the Sec. 3.2 listing).  The force on i is
+// Force: a warp takes 32/LP clusters at a time (LP lanes each); each lane
+// evaluates list entries against its cluster's four atoms i (r2inv = 0
+// beyond r_c, as in the Sec. 3.2 listing).  The force on i is
 // summed in FP32 registers in list order and reduced over the lanes by a
 // fixed butterfly; the force on j of one entry (at most four pairs, summed in
 // FP32) is converted once to 2^-13 kJ/mol/nm fixed point and added to the
