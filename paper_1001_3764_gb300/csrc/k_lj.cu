@@ -766,7 +766,7 @@ __device__ __forceinline__ void rank_clusters(const int* __restrict__ s_ncl, sho
 // (longest lists first), and after a barrier the block flushes the tile's
 // accumulators.
 template <bool ENERGY, int NT, int LP>
-__global__ void __launch_bounds__(NT, ENERGY ? 512 / NT : 768 / NT) k_cl_force(
+__global__ void __launch_bounds__(NT, 768 / NT) k_cl_force(
     const float4* __restrict__ pos, const int* __restrict__ cell_start, const int* __restrict__ cl_start,
     const Region* __restrict__ regions, int n_regions, const RegionShape* __restrict__ shapes,
     const RepDev* __restrict__ reps, const unsigned* __restrict__ list, const int* __restrict__ ncl, int cap,
