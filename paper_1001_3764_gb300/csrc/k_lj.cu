@@ -580,28 +580,26 @@ __device__ __forceinline__ void cluster_task(int q0, int nq, const RegTile& T, c
   for (int u = 0; u < 4; ++u) fi[u][0] = fi[u][1] = fi[u][2] = 0.f;
   float ev[kEnergyVals] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   // packed copies for the force-only form (atoms 0,1 and 2,3)
-  float2 px[2], py[2], pz[2], pa0[2], pda[2], pnb0[2], pndb[2];
+  float2 px[2], py[2], pz[2];
   float2 qx[2], qy[2], qz[2];
 #pragma unroll
   for (int p = 0; p < 2; ++p) {
     px[p] = make_float2(pi[2 * p].x, pi[2 * p + 1].x);
     py[p] = make_float2(pi[2 * p].y, pi[2 * p + 1].y);
     pz[p] = make_float2(pi[2 * p].z, pi[2 * p + 1].z);
-    pa0[p] = make_float2(a0[2 * p], a0[2 * p + 1]);
-    pda[p] = make_float2(da[2 * p], da[2 * p + 1]);
-    pnb0[p] = make_float2(-b0[2 * p], -b0[2 * p + 1]);
-    pndb[p] = make_float2(-db[2 * p], -db[2 * p + 1]);
     qx[p] = qy[p] = qz[p] = make_float2(0.f, 0.f);
   }
   // energy form: C12, C6 and E(r_c) coefficients (base, difference for a
   // C_33 j) of atoms 2p, 2p+1, and the eight sums in two FP32 halves
-  float2 pec[6][2];
+  float ecd[2][6];   // ec of a C_32 (0) and a C_33 (1) atom i
   float2 ev2[kEnergyVals];
   if (ENERGY) {
 #pragma unroll
-    for (int a = 0; a < 6; ++a)
-#pragma unroll
-      for (int p = 0; p < 2; ++p) pec[a][p] = make_float2(ec[2 * p][a], ec[2 * p + 1][a]);
+    for (int ty = 0; ty < 2; ++ty) {
+      ecd[ty][0] = R.C12u[ty]; ecd[ty][1] = R.C12u[ty + 1] - ecd[ty][0];
+      ecd[ty][2] = R.C6u[ty]; ecd[ty][3] = R.C6u[ty + 1] - ecd[ty][2];
+      ecd[ty][4] = fp.erc[ty][0]; ecd[ty][5] = fp.erc[ty][1] - ecd[ty][4];
+    }
 #pragma unroll
     for (int a = 0; a < kEnergyVals; ++a) ev2[a] = make_float2(0.f, 0.f);
   }
@@ -610,8 +608,12 @@ __device__ __forceinline__ void cluster_task(int q0, int nq, const RegTile& T, c
   // coefficient per j type: two scalar FMAs per entry instead of four
   // FFMA2 (same values: each coefficient is the same single-rounded FMA)
   bool uni_c = true;
+  unsigned tb = 0u;   // bit u: atom u is a C_33 chain end
 #pragma unroll
-  for (int u = 0; u < 4; ++u) uni_c &= pi[u].w == 0.f;
+  for (int u = 0; u < 4; ++u) {
+    uni_c &= pi[u].w == 0.f;
+    tb |= pi[u].w != 0.f ? (1u << u) : 0u;
+  }
   const bool uni = __all_sync(0xffffffffu, uni_c);
   // two entries per lane per iteration (independent work for the
   // scheduler), the next two in flight; an entry past the list is 0:
@@ -634,23 +636,44 @@ __device__ __forceinline__ void cluster_task(int q0, int nq, const RegTile& T, c
           cA0[0] = cA0[1] = make_float2(a_0, a_0); cB0[0] = cB0[1] = make_float2(b_0, b_0);
           cA1[0] = cA1[1] = make_float2(a_1, a_1); cB1[0] = cB1[1] = make_float2(b_1, b_1);
         } else {
-          const float2 wt0 = make_float2(w0.w, w0.w), wt1 = make_float2(w1.w, w1.w);
+          // the coefficients of j with a C_32 and with a C_33 atom, then
+          // per atom of the cluster the one of its type (bit u of tb)
+          const float a2_0 = fmaf(w0.w, A1 - A0, A0), a3_0 = fmaf(w0.w, A2 - A1, A1);
+          const float b2_0 = fmaf(w0.w, -(B1 - B0), -B0), b3_0 = fmaf(w0.w, -(B2 - B1), -B1);
+          const float a2_1 = fmaf(w1.w, A1 - A0, A0), a3_1 = fmaf(w1.w, A2 - A1, A1);
+          const float b2_1 = fmaf(w1.w, -(B1 - B0), -B0), b3_1 = fmaf(w1.w, -(B2 - B1), -B1);
 #pragma unroll
           for (int p = 0; p < 2; ++p) {
-            cA0[p] = __ffma2_rn(wt0, pda[p], pa0[p]); cB0[p] = __ffma2_rn(wt0, pndb[p], pnb0[p]);
-            cA1[p] = __ffma2_rn(wt1, pda[p], pa0[p]); cB1[p] = __ffma2_rn(wt1, pndb[p], pnb0[p]);
+            const bool ta = (tb >> (2 * p)) & 1u, tc = (tb >> (2 * p + 1)) & 1u;
+            cA0[p] = make_float2(ta ? a3_0 : a2_0, tc ? a3_0 : a2_0);
+            cB0[p] = make_float2(ta ? b3_0 : b2_0, tc ? b3_0 : b2_0);
+            cA1[p] = make_float2(ta ? a3_1 : a2_1, tc ? a3_1 : a2_1);
+            cB1[p] = make_float2(ta ? b3_1 : b2_1, tc ? b3_1 : b2_1);
           }
         }
         entry_packed(px, py, pz, cA0, cB0, rc2, w0, E0 >> 16, qx, qy, qz, g0x, g0y, g0z);
         entry_packed(px, py, pz, cA1, cB1, rc2, w1, E1 >> 16, qx, qy, qz, g1x, g1y, g1z);
       } else if (ENERGY) {
-        const float2 wt0 = make_float2(w0.w, w0.w), wt1 = make_float2(w1.w, w1.w);
+        // C12, C6 and E(r_c) of j with a C_32 and with a C_33 atom, then per
+        // atom of the cluster the one of its type (bit u of tb)
+        float k0[2][3], k1[2][3];
+#pragma unroll
+        for (int ty = 0; ty < 2; ++ty)
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            k0[ty][a] = fmaf(w0.w, ecd[ty][2 * a + 1], ecd[ty][2 * a]);
+            k1[ty][a] = fmaf(w1.w, ecd[ty][2 * a + 1], ecd[ty][2 * a]);
+          }
         float2 c12a[2], c6a[2], sha[2], c12b[2], c6b[2], shb[2];
 #pragma unroll
         for (int p = 0; p < 2; ++p) {
-          c12a[p] = __ffma2_rn(wt0, pec[1][p], pec[0][p]); c12b[p] = __ffma2_rn(wt1, pec[1][p], pec[0][p]);
-          c6a[p] = __ffma2_rn(wt0, pec[3][p], pec[2][p]); c6b[p] = __ffma2_rn(wt1, pec[3][p], pec[2][p]);
-          sha[p] = __ffma2_rn(wt0, pec[5][p], pec[4][p]); shb[p] = __ffma2_rn(wt1, pec[5][p], pec[4][p]);
+          const bool ta = (tb >> (2 * p)) & 1u, tc = (tb >> (2 * p + 1)) & 1u;
+          c12a[p] = make_float2(ta ? k0[1][0] : k0[0][0], tc ? k0[1][0] : k0[0][0]);
+          c12b[p] = make_float2(ta ? k1[1][0] : k1[0][0], tc ? k1[1][0] : k1[0][0]);
+          c6a[p] = make_float2(ta ? k0[1][1] : k0[0][1], tc ? k0[1][1] : k0[0][1]);
+          c6b[p] = make_float2(ta ? k1[1][1] : k1[0][1], tc ? k1[1][1] : k1[0][1]);
+          sha[p] = make_float2(ta ? k0[1][2] : k0[0][2], tc ? k0[1][2] : k0[0][2]);
+          shb[p] = make_float2(ta ? k1[1][2] : k1[0][2], tc ? k1[1][2] : k1[0][2]);
         }
         entry_packed_energy(px, py, pz, c12a, c6a, sha, rc2, w0, E0 >> 16, ev2);
         entry_packed_energy(px, py, pz, c12b, c6b, shb, rc2, w1, E1 >> 16, ev2);
