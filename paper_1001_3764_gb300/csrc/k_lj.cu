@@ -401,15 +401,15 @@ __device__ __forceinline__ void acc_add(int* __restrict__ ax, int* __restrict__ 
   constexpr float kMagic = 12582912.0f;   // 1.5 2^23
   constexpr int kMagicBits = 0x4B400000;
   if (fabsf(gx) + fabsf(gy) + fabsf(gz) < lim) {
-    atomicAdd(ax + t, __float_as_int(fmaf(gx, scale, kMagic)) - kMagicBits);
-    atomicAdd(ay + t, __float_as_int(fmaf(gy, scale, kMagic)) - kMagicBits);
-    atomicAdd(az + t, __float_as_int(fmaf(gz, scale, kMagic)) - kMagicBits);
+    atomicAdd(ax + 3 * t, __float_as_int(fmaf(gx, scale, kMagic)) - kMagicBits);
+    atomicAdd(ay + 3 * t, __float_as_int(fmaf(gy, scale, kMagic)) - kMagicBits);
+    atomicAdd(az + 3 * t, __float_as_int(fmaf(gz, scale, kMagic)) - kMagicBits);
   } else {
     gx *= scale; gy *= scale; gz *= scale;
     range_check(gx, gy, gz, flags);
-    atomicAdd(ax + t, acc_fix(gx));
-    atomicAdd(ay + t, acc_fix(gy));
-    atomicAdd(az + t, acc_fix(gz));
+    atomicAdd(ax + 3 * t, acc_fix(gx));
+    atomicAdd(ay + 3 * t, acc_fix(gy));
+    atomicAdd(az + 3 * t, acc_fix(gz));
   }
 }
 
@@ -717,9 +717,9 @@ __device__ __forceinline__ void cluster_task(int q0, int nq, const RegTile& T, c
       if (sl == u && u < ni) {
         const float sx = fi[u][0] * scale, sy = fi[u][1] * scale, sz = fi[u][2] * scale;
         range_check(sx, sy, sz, flags);
-        atomicAdd(ax + i0 + u, acc_fix(sx));
-        atomicAdd(ay + i0 + u, acc_fix(sy));
-        atomicAdd(az + i0 + u, acc_fix(sz));
+        atomicAdd(ax + 3 * (i0 + u), acc_fix(sx));
+        atomicAdd(ay + 3 * (i0 + u), acc_fix(sy));
+        atomicAdd(az + 3 * (i0 + u), acc_fix(sz));
       }
   }
   if (ENERGY) {
@@ -744,7 +744,7 @@ __device__ __forceinline__ void flush_tile(const RegTile& T, const int* __restri
     const int t0 = T.off[kc], nk = T.off[kc + 1] - t0, s0 = T.start[kc];
     for (int q = lane; q < nk; q += 32) {
       const int t = t0 + q, sidx = s0 + q;
-      const int qx = ax[t], qy = ay[t], qz = az[t];
+      const int qx = ax[3 * t], qy = ay[3 * t], qz = az[3 * t];
       if ((qx | qy | qz) == 0) continue;
       atomicAdd(reinterpret_cast<unsigned long long*>(flj + sidx), (unsigned long long)((long long)qx << kLjAccShift));
       atomicAdd(reinterpret_cast<unsigned long long*>(flj + Npad + sidx),
@@ -798,9 +798,11 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_cl_force(
   constexpr int CPW = 32 / LP;
   extern __shared__ __align__(16) unsigned char smem[];
   float4* sp = reinterpret_cast<float4*>(smem);
+  // accumulators of tile atom t at ax[3t], ay[3t] = ax[3t + 1], az[3t] = ax[3t + 2]
+  // (one base register in the pair loop; lanes on consecutive t hit distinct banks)
   int* ax = reinterpret_cast<int*>(smem + (size_t)tile_cap * sizeof(float4));
-  int* ay = ax + tile_cap;
-  int* az = ay + tile_cap;
+  int* ay = ax + 1;
+  int* az = ax + 2;
   __shared__ RegTile T;
   __shared__ int sh_r, sh_q;
   __shared__ int s_ncl[kRegionClusterCap];     // list length of each of the region's clusters
@@ -827,7 +829,7 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_cl_force(
       // list lengths and zeroed accumulators while the tile copies fly
       tile_issue<NT>(T, pos, sp);
       if (!ENERGY)
-        for (int t = threadIdx.x; t < total; t += NT) { ax[t] = 0; ay[t] = 0; az[t] = 0; }
+        for (int t = threadIdx.x; t < 3 * total; t += NT) ax[t] = 0;
       for (int q = threadIdx.x; q < nq; q += NT) {
         int h, k;
         cluster_of(T, q, h, k);
