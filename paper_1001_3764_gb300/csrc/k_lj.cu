@@ -40,7 +40,6 @@ namespace mdg {
 
 constexpr int kStageCapMax = 6144;      // largest tile (atoms); list entries keep the tile index in 16 bits
 constexpr int kLjAccShift = 19;         // 2^-13 accumulators -> 2^-32 fixed point
-constexpr bool kPackedPairs = true;     // force-only kernel: two pairs per FFMA2 (this GPU's packed FP32)
 constexpr float kLjAccScale = 8192.0f;  // 2^13
 
 __device__ __forceinline__ float rcp_approx(float x) {
@@ -416,8 +415,8 @@ __device__ __forceinline__ void acc_add(int* __restrict__ ax, int* __restrict__ 
 // One list entry against the cluster's four atoms with packed FP32 pairs
 // (two atoms per float2 lane: 0,1 and 2,3; one FFMA2 does both): the force
 // on the four atoms is added to f*[2] and minus the force on j, summed over
-// the four atoms, is returned in g*.  Same arithmetic per pair as the scalar
-// form (rcp of r^2, r2inv = 0 beyond r_c or outside the mask).  A[p], nB[p]:
+// the four atoms, is returned in g* (rcp of r^2; r2inv = 0 beyond r_c or
+// outside the mask).  A[p], nB[p]:
 // the pair coefficients 12 C12 and -6 C6 of atoms 2p, 2p+1 with j.
 __device__ __forceinline__ void entry_packed(const float2 (&px)[2], const float2 (&py)[2], const float2 (&pz)[2],
                                              const float2 (&A)[2], const float2 (&nB)[2], float rc2, const float4& w,
@@ -484,43 +483,6 @@ __device__ __forceinline__ void entry_packed_energy(const float2 (&px)[2], const
   }
 }
 
-// One list entry against the cluster's four atoms, one pair at a time (and,
-// with ENERGY, the pair energies and virial): adds the forces on the four
-// atoms to fi, returns minus their sum (the force on j) in g*.
-template <bool ENERGY>
-__device__ __forceinline__ void entry_scalar(const float4 (&pi)[4], const float (&a0)[4], const float (&da)[4],
-                                             const float (&b0)[4], const float (&db)[4], const float (&ec)[4][6],
-                                             float rc2, const float4& w, unsigned m, float (&fi)[4][3],
-                                             float (&ev)[kEnergyVals], float& gx, float& gy, float& gz) {
-#pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    const float dx = pi[u].x - w.x, dy = pi[u].y - w.y, dz = pi[u].z - w.z;
-    const float r2 = dx * dx + dy * dy + dz * dz;
-    const bool keep = ((m >> u) & 1u) && r2 < rc2;
-    // the reciprocal for every pair, then a select: no branch around the
-    // inline instruction
-    const float rr = rcp_approx(r2);
-    const float ir2 = keep ? rr : 0.f;
-    const float ir6 = ir2 * ir2 * ir2;
-    const float A = fmaf(w.w, da[u], a0[u]), B = fmaf(w.w, db[u], b0[u]);
-    const float ff = ir2 * ir6 * (A * ir6 - B);
-    fi[u][0] = fmaf(ff, dx, fi[u][0]);
-    fi[u][1] = fmaf(ff, dy, fi[u][1]);
-    fi[u][2] = fmaf(ff, dz, fi[u][2]);
-    gx = fmaf(-ff, dx, gx);
-    gy = fmaf(-ff, dy, gy);
-    gz = fmaf(-ff, dz, gz);
-    if (ENERGY) {
-      const float c12 = fmaf(w.w, ec[u][1], ec[u][0]), c6 = fmaf(w.w, ec[u][3], ec[u][2]);
-      const float eij = ir6 * (c12 * ir6 - c6);
-      ev[0] += eij;
-      ev[1] += eij - (keep ? fmaf(w.w, ec[u][5], ec[u][4]) : 0.f);
-      ev[2] += dx * dx * ff; ev[3] += dy * dy * ff; ev[4] += dz * dz * ff;
-      ev[5] += dx * dy * ff; ev[6] += dx * dz * ff; ev[7] += dy * dz * ff;
-    }
-  }
-}
-
 // Per-replica constants of the force evaluation (cell units).
 struct LjConst {
   float rc2, scale, lim;
@@ -559,22 +521,9 @@ __device__ __forceinline__ void cluster_task(int q0, int nq, const RegTile& T, c
   int nmax = n;
 #pragma unroll
   for (int o = LP; o < 32; o <<= 1) nmax = max(nmax, __shfl_xor_sync(0xffffffffu, nmax, o));
-  float4 pi[4];
-  float a0[4], da[4], b0[4], db[4];
-  float ec[4][6];
+  float4 pi[4];   // w: LJ type (1.0 for a C_33 chain end)
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    pi[u] = sp[i0 + max(0, min(u, ni - 1))];
-    const bool t3 = pi[u].w != 0.f;           // the atom is a C_33 chain end
-    a0[u] = t3 ? A1 : A0; da[u] = t3 ? A2 - A1 : A1 - A0;
-    b0[u] = t3 ? B1 : B0; db[u] = t3 ? B2 - B1 : B1 - B0;
-    if (ENERGY) {
-      const int ti = t3 ? 1 : 0;
-      ec[u][0] = R.C12u[ti]; ec[u][1] = R.C12u[ti + 1] - ec[u][0];
-      ec[u][2] = R.C6u[ti]; ec[u][3] = R.C6u[ti + 1] - ec[u][2];
-      ec[u][4] = fp.erc[ti][0]; ec[u][5] = fp.erc[ti][1] - ec[u][4];
-    }
-  }
+  for (int u = 0; u < 4; ++u) pi[u] = sp[i0 + max(0, min(u, ni - 1))];
   float fi[4][3];
 #pragma unroll
   for (int u = 0; u < 4; ++u) fi[u][0] = fi[u][1] = fi[u][2] = 0.f;
@@ -628,7 +577,7 @@ __device__ __forceinline__ void cluster_task(int q0, int nq, const RegTile& T, c
       const int t0 = (int)(E0 & 0xffffu), t1 = (int)(E1 & 0xffffu);
       const float4 w0 = sp[t0], w1 = sp[t1];
       float g0x = 0.f, g0y = 0.f, g0z = 0.f, g1x = 0.f, g1y = 0.f, g1z = 0.f;
-      if (kPackedPairs && !ENERGY) {
+      if (!ENERGY) {
         float2 cA0[2], cB0[2], cA1[2], cB1[2];
         if (UNI) {
           const float a_0 = fmaf(w0.w, A1 - A0, A0), b_0 = fmaf(w0.w, -(B1 - B0), -B0);
@@ -653,7 +602,7 @@ __device__ __forceinline__ void cluster_task(int q0, int nq, const RegTile& T, c
         }
         entry_packed(px, py, pz, cA0, cB0, rc2, w0, E0 >> 16, qx, qy, qz, g0x, g0y, g0z);
         entry_packed(px, py, pz, cA1, cB1, rc2, w1, E1 >> 16, qx, qy, qz, g1x, g1y, g1z);
-      } else if (ENERGY) {
+      } else {
         // C12, C6 and E(r_c) of j with a C_32 and with a C_33 atom, then per
         // atom of the cluster the one of its type (bit u of tb)
         float k0[2][3], k1[2][3];
@@ -677,9 +626,6 @@ __device__ __forceinline__ void cluster_task(int q0, int nq, const RegTile& T, c
         }
         entry_packed_energy(px, py, pz, c12a, c6a, sha, rc2, w0, E0 >> 16, ev2);
         entry_packed_energy(px, py, pz, c12b, c6b, shb, rc2, w1, E1 >> 16, ev2);
-      } else {
-        entry_scalar<ENERGY>(pi, a0, da, b0, db, ec, rc2, w0, E0 >> 16, fi, ev, g0x, g0y, g0z);
-        entry_scalar<ENERGY>(pi, a0, da, b0, db, ec, rc2, w1, E1 >> 16, fi, ev, g1x, g1y, g1z);
       }
       if (!ENERGY) {
         if (e < n) acc_add(ax, ay, az, t0, g0x, g0y, g0z, scale, lim, flags);
@@ -696,7 +642,7 @@ __device__ __forceinline__ void cluster_task(int q0, int nq, const RegTile& T, c
     for (int a = 0; a < kEnergyVals; ++a) ev[a] = ev2[a].x + ev2[a].y;
     ev[1] = ev[0] - ev[1];   // lj_shifted: the pair energies less the kept pairs' E(r_c)
   }
-  if (kPackedPairs && !ENERGY) {
+  if (!ENERGY) {
 #pragma unroll
     for (int p = 0; p < 2; ++p) {
       fi[2 * p][0] = qx[p].x; fi[2 * p + 1][0] = qx[p].y;
