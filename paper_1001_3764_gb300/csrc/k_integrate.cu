@@ -12,8 +12,8 @@
 // which it sums through a per-atom array and a tree reduction (Sec. 3.4).
 // Here each block writes one FP64 partial; the last block to finish (ticket
 // counter, no waiting) sums the partials of each replica in a fixed order
-// (one warp per replica, see below) and computes that replica's rescaling
-// factor.
+// (one warp per replica and summed value, see below) and computes that
+// replica's rescaling factor.
 // The factor computed at step k is applied at step k+1 (one-step lag).
 //
 // Nose-Hoover (TH = 2; the paper's NVT ensemble with Leap-Frog, Sec. 2 and
@@ -159,27 +159,37 @@ __global__ void __launch_bounds__(kIntBlock) k_integrate(void* __restrict__ xv, 
     }
   }
   if (KE) {
-    __shared__ double red[4][kIntBlock / 32];
+    // block sums in FP64 through shared memory: thread q < 8 NV adds the 32
+    // values of warp q % 8 in order, thread 0 the 8 warp sums in order (a
+    // fixed order; 255 FP64 adds per value and block, where a shuffle tree
+    // per warp would issue five on every lane: this GPU's FP64 pipe is narrow)
+    constexpr int NV = TH == 2 ? 4 : 1;
+    constexpr int NW = kIntBlock / 32;
+    __shared__ double vals[NV][kIntBlock];
+    __shared__ double wsum[NV][NW];
     __shared__ bool last;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    double s = warp_sum_i(ke);
-    if (lane == 0) red[0][w] = s;
+    vals[0][threadIdx.x] = ke;
     if constexpr (TH == 2) {
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        const double sm = warp_sum_i(mom[a]);
-        if (lane == 0) red[1 + a][w] = sm;
-      }
+      for (int a = 0; a < 3; ++a) vals[1 + a][threadIdx.x] = mom[a];
+    }
+    __syncthreads();
+    if (threadIdx.x < NV * NW) {
+      const int a = threadIdx.x / NW, w = threadIdx.x % NW;
+      double b = 0.0;
+#pragma unroll 8
+      for (int k = 0; k < 32; ++k) b += vals[a][32 * w + k];
+      wsum[a][w] = b;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
       double b = 0.0;
-      for (int q = 0; q < kIntBlock / 32; ++q) b += red[0][q];
+      for (int q = 0; q < NW; ++q) b += wsum[0][q];
       kepart[blockIdx.x] = b;
       if constexpr (TH == 2) {
         for (int a = 0; a < 3; ++a) {
           double bm = 0.0;
-          for (int q = 0; q < kIntBlock / 32; ++q) bm += red[1 + a][q];
+          for (int q = 0; q < NW; ++q) bm += wsum[1 + a][q];
           kepart[gridDim.x + 3 * blockIdx.x + a] = bm;   // momentum partials follow the energy partials
         }
       }
@@ -187,9 +197,10 @@ __global__ void __launch_bounds__(kIntBlock) k_integrate(void* __restrict__ xv, 
       last = atomicAdd(done, 1u) == gridDim.x - 1;
     }
     __syncthreads();
+    const int lane = threadIdx.x & 31;
     if (last) {
       __threadfence();
-      // one warp per replica: lane l keeps eight chains P_m (m = 0..7), P_m
+      // a warp per (replica, value): lane l keeps eight chains P_m (m = 0..7), P_m
       // adding the replica's partials l + 32 m, l + 32 m + 256, ... in order
       // (eight loads in flight); then each P_m is summed over the lanes by a
       // fixed tree and the eight results in m order.  The order depends only
@@ -208,29 +219,42 @@ __global__ void __launch_bounds__(kIntBlock) k_integrate(void* __restrict__ xv, 
         for (int m = 0; m < 8; ++m) sum += warp_sum_i(P[m]);
         return sum;
       };
-      for (int r = threadIdx.x >> 5; r < n_reps; r += kIntBlock / 32) {
-        const RepDev& Q = reps[r];
-        const double sum = replica_sum(kepart + Q.tile_off, 1, Q.n_tiles);
-        double P[3] = {0.0, 0.0, 0.0};
-        if constexpr (TH == 2)
-          for (int a = 0; a < 3; ++a) P[a] = replica_sum(kepart + gridDim.x + 3 * Q.tile_off + a, 3, Q.n_tiles);
-        if (lane == 0) {
-          ke_out[r] = sum;
+      // (replica, value) jobs over the warps: 8 replicas per round for the
+      // kinetic energy alone, 2 for energy and momentum; then one thread per
+      // replica forms its thermostat factors
+      constexpr int RPR = NW / NV;
+      __shared__ double res[RPR][NV];
+      const int w = threadIdx.x >> 5;
+      for (int r0 = 0; r0 < n_reps; r0 += RPR) {
+        const int r = r0 + w / NV, a = w % NV;
+        if (r < n_reps) {
+          const RepDev& Q = reps[r];
+          const double sum = a == 0 ? replica_sum(kepart + Q.tile_off, 1, Q.n_tiles)
+                                    : replica_sum(kepart + gridDim.x + 3 * Q.tile_off + (a - 1), 3, Q.n_tiles);
+          if (lane == 0) res[w / NV][a] = sum;
+        }
+        __syncthreads();
+        if ((int)threadIdx.x < RPR && r0 + (int)threadIdx.x < n_reps) {
+          const int rr = r0 + threadIdx.x;
+          const RepDev& Q = reps[rr];
+          const double sum = res[threadIdx.x][0];
+          ke_out[rr] = sum;
           if (TH == 1) {
             const double T_inst = 2.0 * sum / (Q.dof * 0.0083144626);
-            lam[r] = sqrt(1.0 + fp.dt / tau * (Q.T0 / T_inst - 1.0));
+            lam[rr] = sqrt(1.0 + fp.dt / tau * (Q.T0 / T_inst - 1.0));
           }
           if constexpr (TH == 2) {
             const double T_half = 2.0 * sum / (Q.dof * 0.0083144626);
             const double Qm = tau * tau * Q.T0 / (4.0 * 3.14159265358979323846 * 3.14159265358979323846);
-            double* nh = lam + 6 * r;
+            double* nh = lam + 6 * rr;
             const double xi = nh[0] + fp.dt * (T_half - Q.T0) / Qm;
             const double c = 0.5 * fp.dt * xi;
             const double M = (double)Q.n_chains * fp.mol_mass;
             nh[0] = xi; nh[1] = 1.0 - c; nh[2] = 1.0 / (1.0 + c);
-            nh[3] = P[0] / M; nh[4] = P[1] / M; nh[5] = P[2] / M;
+            nh[3] = res[threadIdx.x][1] / M; nh[4] = res[threadIdx.x][2] / M; nh[5] = res[threadIdx.x][3] / M;
           }
         }
+        __syncthreads();
       }
       if (threadIdx.x == 0) *done = 0u;
     }
