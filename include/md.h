@@ -129,6 +129,14 @@ typedef struct {
                                   8, 16 or 32 (0 = 8) */
   int32_t lj_region;           /* cells per side (x and y) of the work unit of the list build and
                                   LJ kernels, 1 cell deep: 2 or 3 (0 = 3) */
+  int32_t lj_pair_exact;       /* 1: every LJ pair force (Eq. 2) is converted once to fixed point
+                                  and added to i and subtracted from j as the same integer, so the
+                                  LJ forces obey Newton's third law bit for bit (their sum over
+                                  all atoms is exactly zero); the pair loop does more work (about
+                                  1.2x the LJ time of the default on a 1.5M-atom melt).  A pair
+                                  force component of 2^17 kJ/mol/nm or more, or a non-finite one,
+                                  is reported as MD_EOVERFLOW.
+                                  0 (default): per-cluster FP32 sums converted once. */
   const md_topology *topology; /* NULL: linear chains; else the molecule type (sites_per_chain must
                                   equal topology->naom) */
   int32_t displacement;        /* MD_DISP_REBUILD (default) or MD_DISP_ERROR */

@@ -54,7 +54,7 @@ class md_desc(ctypes.Structure):
                 ("tau_t", ctypes.c_double), ("rebin_every", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("thermostat", ctypes.c_int32), ("nbr_capacity", ctypes.c_int32),
                 ("lj_block", ctypes.c_int32), ("schedule", ctypes.c_int32), ("lj_lanes", ctypes.c_int32),
-                ("lj_region", ctypes.c_int32), ("topology", ctypes.c_void_p), ("displacement", ctypes.c_int32),
+                ("lj_region", ctypes.c_int32), ("lj_pair_exact", ctypes.c_int32), ("topology", ctypes.c_void_p), ("displacement", ctypes.c_int32),
                 ("cuda_stream", ctypes.c_void_p), ("workspace", ctypes.c_void_p),
                 ("workspace_bytes", ctypes.c_size_t)]
 
@@ -394,7 +394,7 @@ class System:
                  tau_t: float = 0.1, params: dict | None = None, nbr_capacity: int = 0, device: int = 0,
                  use_torch_memory: bool = True, lj_block: int = 0, schedule: int = MD_SCHED_GRID,
                  lj_lanes: int = 0, autotune: bool = False, tune_cycles: int = 2, tune_cache: str | None = None,
-                 topology=None, displacement: int = 0, lj_region: int = 0):
+                 topology=None, displacement: int = 0, lj_region: int = 0, lj_pair_exact: bool = False):
         import torch
         load()
         if isinstance(melts, dict):
@@ -424,6 +424,7 @@ class System:
         d.nbr_capacity = nbr_capacity
         d.lj_block, d.schedule, d.lj_lanes = lj_block, schedule, lj_lanes
         d.lj_region = lj_region
+        d.lj_pair_exact = 1 if lj_pair_exact else 0
         d.displacement = displacement
         if topology is not None:
             # (bonds [n_bonds, 2], types [naom]) of the molecule type (Sec. 3.3)

@@ -397,12 +397,12 @@ __device__ __forceinline__ void range_check(float sx, float sy, float sz, unsign
 __device__ __forceinline__ void acc_add(int* __restrict__ ax, int* __restrict__ ay, int* __restrict__ az, int t,
                                         float gx, float gy, float gz, float scale, float lim,
                                         unsigned* __restrict__ flags) {
-  constexpr float kMagic = 12582912.0f;   // 1.5 2^23
-  constexpr int kMagicBits = 0x4B400000;
+  constexpr float kMagicF = 12582912.0f;   // 1.5 2^23
+  constexpr int kMagicI = 0x4B400000;
   if (fabsf(gx) + fabsf(gy) + fabsf(gz) < lim) {
-    atomicAdd(ax + 3 * t, __float_as_int(fmaf(gx, scale, kMagic)) - kMagicBits);
-    atomicAdd(ay + 3 * t, __float_as_int(fmaf(gy, scale, kMagic)) - kMagicBits);
-    atomicAdd(az + 3 * t, __float_as_int(fmaf(gz, scale, kMagic)) - kMagicBits);
+    atomicAdd(ax + 3 * t, __float_as_int(fmaf(gx, scale, kMagicF)) - kMagicI);
+    atomicAdd(ay + 3 * t, __float_as_int(fmaf(gy, scale, kMagicF)) - kMagicI);
+    atomicAdd(az + 3 * t, __float_as_int(fmaf(gz, scale, kMagicF)) - kMagicI);
   } else {
     gx *= scale; gy *= scale; gz *= scale;
     range_check(gx, gy, gz, flags);
@@ -445,6 +445,66 @@ __device__ __forceinline__ void entry_packed(const float2 (&px)[2], const float2
   gx = -(sx.x + sx.y);
   gy = -(sy.x + sy.y);
   gz = -(sz.x + sz.y);
+}
+
+// Pairwise fixed-point form of entry_packed: each pair's force component v
+// (the coefficients A, nB carry the 2^13 accumulator scale, so v is in
+// 2^-13 kJ/mol/nm) is rounded once to the nearest integer and that integer
+// is added to atom i's sum qi and subtracted from j's (returned in j*), so
+// the two atoms receive exactly opposite integers.  The rounding is exact
+// in FP32 for |v| < 2^30: hi = rint(v / 2^8) by one FFMA with the 1.5 2^23
+// offset (t = hi + offset, in [2^23, 2^24) where the spacing is 1); the
+// remainder v - 2^8 hi (|.| <= 2^7, a multiple of v's spacing) is exact in
+// one FFMA and rounded by the same offset; rint(v) = 2^8 hi + rint(rem)
+// (2^8 hi is an even integer, so ties go the same way).  The integer is
+// taken as (bits(t) << 8) + bits(rem + offset), which is rint(v) plus the
+// constant kExactOff; qi and the j sums carry one kExactOff per addition,
+// which the caller removes by counting.  |v| >= 2^30 (2^17 kJ/mol/nm, the
+// range checked by the default path) or a non-finite v leaves t outside
+// [2^23, 2^24) and sets bit 23 or above of `chk`.
+constexpr float kMagic = 12582912.0f;   // 1.5 2^23
+constexpr unsigned kMagicBits = 0x4B400000u;
+constexpr unsigned kExactOff = (kMagicBits << 8) + kMagicBits;
+__device__ __forceinline__ void exact_round(float2 v, unsigned& b0, unsigned& b1, unsigned& chk) {
+  const float2 mg = make_float2(kMagic, kMagic), nmg = make_float2(-kMagic, -kMagic);
+  const float2 t = __ffma2_rn(v, make_float2(0.00390625f, 0.00390625f), mg);   // hi + offset
+  const float2 hi = __fadd2_rn(t, nmg);
+  const float2 lo = __fadd2_rn(__ffma2_rn(hi, make_float2(-256.f, -256.f), v), mg);
+  const unsigned t0 = __float_as_uint(t.x), t1 = __float_as_uint(t.y);
+  chk |= (t0 ^ kMagicBits) | (t1 ^ kMagicBits);
+  b0 = (t0 << 8) + __float_as_uint(lo.x);
+  b1 = (t1 << 8) + __float_as_uint(lo.y);
+}
+__device__ __forceinline__ void entry_packed_exact(const float2 (&px)[2], const float2 (&py)[2],
+                                                   const float2 (&pz)[2], const float2 (&A)[2], const float2 (&nB)[2],
+                                                   float rc2, const float4& w, unsigned m, unsigned (&qi)[4][3],
+                                                   unsigned& jx, unsigned& jy, unsigned& jz, unsigned& chk) {
+  const float2 wx = make_float2(-w.x, -w.x), wy = make_float2(-w.y, -w.y), wz = make_float2(-w.z, -w.z);
+  unsigned sx = 0u, sy = 0u, sz = 0u;
+#pragma unroll
+  for (int p = 0; p < 2; ++p) {
+    const float2 dx = __fadd2_rn(px[p], wx), dy = __fadd2_rn(py[p], wy), dz = __fadd2_rn(pz[p], wz);
+    float2 r2 = __fmul2_rn(dx, dx);
+    r2 = __ffma2_rn(dy, dy, r2);
+    r2 = __ffma2_rn(dz, dz, r2);
+    const float q0 = rcp_approx(r2.x), q1 = rcp_approx(r2.y);
+    const bool k0 = ((m >> (2 * p)) & 1u) && r2.x < rc2, k1 = ((m >> (2 * p + 1)) & 1u) && r2.y < rc2;
+    const float2 ir2 = make_float2(k0 ? q0 : 0.f, k1 ? q1 : 0.f);
+    const float2 ir4 = __fmul2_rn(ir2, ir2), ir6 = __fmul2_rn(ir4, ir2), ir8 = __fmul2_rn(ir4, ir4);
+    const float2 ff = __fmul2_rn(ir8, __ffma2_rn(A[p], ir6, nB[p]));
+    unsigned bx0, bx1, by0, by1, bz0, bz1;
+    exact_round(__fmul2_rn(ff, dx), bx0, bx1, chk);
+    exact_round(__fmul2_rn(ff, dy), by0, by1, chk);
+    exact_round(__fmul2_rn(ff, dz), bz0, bz1, chk);
+    qi[2 * p][0] += bx0; qi[2 * p + 1][0] += bx1;
+    qi[2 * p][1] += by0; qi[2 * p + 1][1] += by1;
+    qi[2 * p][2] += bz0; qi[2 * p + 1][2] += bz1;
+    sx += bx0 + bx1; sy += by0 + by1; sz += bz0 + bz1;
+  }
+  // j: minus the four pairs' integers (four offsets removed)
+  jx = 4u * kExactOff - sx;
+  jy = 4u * kExactOff - sy;
+  jz = 4u * kExactOff - sz;
 }
 
 // Energy form: one list entry against the cluster's four atoms, packed as
@@ -501,7 +561,7 @@ __device__ __forceinline__ LjConst lj_const(const RepDev& R) {
 // One warp task: clusters s_ord[q0 .. q0 + 32/LP) of the region, LP lanes
 // each; lane l of a cluster's group takes entries l, l + LP, ...  The warp's
 // trip count is that of its longest cluster; a lane past its own list idles.
-template <bool ENERGY, int LP>
+template <bool ENERGY, int LP, bool EXACT = false>
 __device__ __forceinline__ void cluster_task(int q0, int nq, const RegTile& T, const float4* __restrict__ sp,
                                              int* __restrict__ ax, int* __restrict__ ay, int* __restrict__ az,
                                              const int* __restrict__ s_ncl, const short* __restrict__ s_ord,
@@ -510,7 +570,10 @@ __device__ __forceinline__ void cluster_task(int q0, int nq, const RegTile& T, c
                                              unsigned* __restrict__ flags) {
   const int lane = threadIdx.x & 31, sub = lane / LP, sl = lane % LP;
   const float rc2 = c.rc2, scale = c.scale, lim = c.lim;
-  const float A0 = c.A0, A1 = c.A1, A2 = c.A2, B0 = c.B0, B1 = c.B1, B2 = c.B2;
+  // EXACT: the coefficients carry the accumulator scale (pair forces in
+  // accumulator units, rounded per pair)
+  const float cs = EXACT ? scale : 1.f;
+  const float A0 = c.A0 * cs, A1 = c.A1 * cs, A2 = c.A2 * cs, B0 = c.B0 * cs, B1 = c.B1 * cs, B2 = c.B2 * cs;
   const bool valid = q0 + sub < nq;
   const int q = valid ? (int)s_ord[q0 + sub] : nq;
   int h, k;
@@ -531,6 +594,10 @@ __device__ __forceinline__ void cluster_task(int q0, int nq, const RegTile& T, c
   // packed copies for the force-only form (atoms 0,1 and 2,3)
   float2 px[2], py[2], pz[2];
   float2 qx[2], qy[2], qz[2];
+  unsigned qi[4][3];   // EXACT: the cluster atoms' integer sums, with one offset per addition
+  unsigned chk = 0u;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) qi[u][0] = qi[u][1] = qi[u][2] = 0u;
 #pragma unroll
   for (int p = 0; p < 2; ++p) {
     px[p] = make_float2(pi[2 * p].x, pi[2 * p + 1].x);
@@ -600,8 +667,20 @@ __device__ __forceinline__ void cluster_task(int q0, int nq, const RegTile& T, c
             cB1[p] = make_float2(ta ? b3_1 : b2_1, tc ? b3_1 : b2_1);
           }
         }
-        entry_packed(px, py, pz, cA0, cB0, rc2, w0, E0 >> 16, qx, qy, qz, g0x, g0y, g0z);
-        entry_packed(px, py, pz, cA1, cB1, rc2, w1, E1 >> 16, qx, qy, qz, g1x, g1y, g1z);
+        if constexpr (EXACT) {
+          unsigned j0x, j0y, j0z, j1x, j1y, j1z;
+          entry_packed_exact(px, py, pz, cA0, cB0, rc2, w0, E0 >> 16, qi, j0x, j0y, j0z, chk);
+          entry_packed_exact(px, py, pz, cA1, cB1, rc2, w1, E1 >> 16, qi, j1x, j1y, j1z, chk);
+          if (e < n) {
+            atomicAdd(ax + 3 * t0, (int)j0x); atomicAdd(ay + 3 * t0, (int)j0y); atomicAdd(az + 3 * t0, (int)j0z);
+          }
+          if (e + LP < n) {
+            atomicAdd(ax + 3 * t1, (int)j1x); atomicAdd(ay + 3 * t1, (int)j1y); atomicAdd(az + 3 * t1, (int)j1z);
+          }
+        } else {
+          entry_packed(px, py, pz, cA0, cB0, rc2, w0, E0 >> 16, qx, qy, qz, g0x, g0y, g0z);
+          entry_packed(px, py, pz, cA1, cB1, rc2, w1, E1 >> 16, qx, qy, qz, g1x, g1y, g1z);
+        }
       } else {
         // C12, C6 and E(r_c) of j with a C_32 and with a C_33 atom, then per
         // atom of the cluster the one of its type (bit u of tb)
@@ -627,7 +706,7 @@ __device__ __forceinline__ void cluster_task(int q0, int nq, const RegTile& T, c
         entry_packed_energy(px, py, pz, c12a, c6a, sha, rc2, w0, E0 >> 16, ev2);
         entry_packed_energy(px, py, pz, c12b, c6b, shb, rc2, w1, E1 >> 16, ev2);
       }
-      if (!ENERGY) {
+      if (!ENERGY && !EXACT) {
         if (e < n) acc_add(ax, ay, az, t0, g0x, g0y, g0z, scale, lim, flags);
         if (e + LP < n) acc_add(ax, ay, az, t1, g1x, g1y, g1z, scale, lim, flags);
       }
@@ -651,7 +730,7 @@ __device__ __forceinline__ void cluster_task(int q0, int nq, const RegTile& T, c
     }
   }
   // forces on the cluster's atoms: fixed butterfly over the LP lanes
-  if (!ENERGY) {
+  if (!ENERGY && !EXACT) {
 #pragma unroll
     for (int u = 0; u < 4; ++u)
 #pragma unroll
@@ -666,6 +745,29 @@ __device__ __forceinline__ void cluster_task(int q0, int nq, const RegTile& T, c
         atomicAdd(ax + 3 * (i0 + u), acc_fix(sx));
         atomicAdd(ay + 3 * (i0 + u), acc_fix(sy));
         atomicAdd(az + 3 * (i0 + u), acc_fix(sz));
+      }
+  }
+  if constexpr (EXACT && !ENERGY) {
+    // each lane added one offset per entry slot it processed (two per
+    // iteration, the same count on every lane); the integer sums over the
+    // lanes are exact in any order
+    const unsigned n_add = 2u * (unsigned)((nmax + 2 * LP - 1) / (2 * LP));
+    if (chk >= 0x800000u) atomicOr(flags, kFlagFixOverflow);
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        unsigned v = qi[u][a] - n_add * kExactOff;
+#pragma unroll
+        for (int o = LP / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        qi[u][a] = v;
+      }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (sl == u && u < ni) {
+        atomicAdd(ax + 3 * (i0 + u), (int)qi[u][0]);
+        atomicAdd(ay + 3 * (i0 + u), (int)qi[u][1]);
+        atomicAdd(az + 3 * (i0 + u), (int)qi[u][2]);
       }
   }
   if (ENERGY) {
@@ -734,7 +836,7 @@ __device__ __forceinline__ void rank_clusters(const int* __restrict__ s_ncl, sho
 // the tile, its warps take tasks of 32/LP clusters from a shared counter
 // (longest lists first), and after a barrier the block flushes the tile's
 // accumulators.
-template <bool ENERGY, int NT, int LP>
+template <bool ENERGY, int NT, int LP, bool EXACT = false>
 __global__ void __launch_bounds__(NT, 768 / NT) k_cl_force(
     const float4* __restrict__ pos, const int* __restrict__ cell_start, const int* __restrict__ cl_start,
     const Region* __restrict__ regions, int n_regions, const RegionShape* __restrict__ shapes,
@@ -791,7 +893,7 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_cl_force(
         if (lane == 0) q0 = atomicAdd(&sh_q, CPW);
         q0 = __shfl_sync(0xffffffffu, q0, 0);
         if (q0 >= nq) break;
-        cluster_task<ENERGY, LP>(q0, nq, T, sp, ax, ay, az, s_ncl, s_ord, ecl, list, cap, R, fp, c, flags);
+        cluster_task<ENERGY, LP, EXACT>(q0, nq, T, sp, ax, ay, az, s_ncl, s_ord, ecl, list, cap, R, fp, c, flags);
       }
       __syncthreads();
       if (!ENERGY) flush_tile(T, ax, ay, az, flj, Npad, threadIdx.x >> 5, NT / 32);
@@ -827,16 +929,18 @@ void launch_cl_force(bool energy, const float4* pos, const int* cell_start, cons
                      const Region* regions, int n_regions, const RegionShape* shapes, const RepDev* reps,
                      const unsigned* list, const int* ncl, int cap, int tile_cap, const ForceParams& fp,
                      long long* flj, int Npad, double* epart, unsigned* flags, int block, int lanes,
-                     int persistent_grid, int* work, cudaStream_t st) {
+                     int persistent_grid, int* work, bool exact, cudaStream_t st) {
   if (n_regions <= 0) return;
   const int grid = persistent_grid > 0 ? persistent_grid : n_regions;
   const int pers = persistent_grid > 0;
   const size_t sm = cl_force_smem(tile_cap);
-#define MDG_CLF(E, NT, LP)                                                                                    \
-  k_cl_force<E, NT, LP><<<grid, NT, sm, st>>>(pos, cell_start, cl_start, regions, n_regions, shapes, reps, list, \
-                                              ncl, cap, tile_cap, fp, flj, Npad, epart, flags, pers, work)
-#define MDG_CLF2(NT, LP) \
-  if (energy) MDG_CLF(true, NT, LP); else MDG_CLF(false, NT, LP);
+#define MDG_CLF(E, NT, LP, X)                                                                                    \
+  k_cl_force<E, NT, LP, X><<<grid, NT, sm, st>>>(pos, cell_start, cl_start, regions, n_regions, shapes, reps, list, \
+                                                 ncl, cap, tile_cap, fp, flj, Npad, epart, flags, pers, work)
+#define MDG_CLF2(NT, LP)                  \
+  if (energy) MDG_CLF(true, NT, LP, false); \
+  else if (exact) MDG_CLF(false, NT, LP, true); \
+  else MDG_CLF(false, NT, LP, false);
   if (block == 128) {
     if (lanes == 8) { MDG_CLF2(128, 8) } else if (lanes == 32) { MDG_CLF2(128, 32) } else { MDG_CLF2(128, 16) }
   } else if (block == 384) {
@@ -870,8 +974,10 @@ cudaError_t tile_kernels_init() {
   const int mb = (int)cl_build_smem(kStageCapMax), mf = (int)cl_force_smem(kStageCapMax);
   cudaError_t e = cudaFuncSetAttribute(k_cl_build<256, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mb);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cl_build<256, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mb);
-#define MDG_ATTR(E, NT, LP) \
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cl_force<E, NT, LP>, cudaFuncAttributeMaxDynamicSharedMemorySize, mf);
+#define MDG_ATTR(E, NT, LP)                                                                                   \
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cl_force<E, NT, LP>, cudaFuncAttributeMaxDynamicSharedMemorySize, mf); \
+  if (e == cudaSuccess && !E)                                                                                 \
+    e = cudaFuncSetAttribute(k_cl_force<false, NT, LP, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mf);
 #define MDG_ATTR3(E, NT) MDG_ATTR(E, NT, 8) MDG_ATTR(E, NT, 16) MDG_ATTR(E, NT, 32)
   MDG_ATTR3(false, 128) MDG_ATTR3(true, 128) MDG_ATTR3(false, 256) MDG_ATTR3(true, 256)
   MDG_ATTR3(false, 384) MDG_ATTR3(true, 384)

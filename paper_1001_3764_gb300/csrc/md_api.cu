@@ -72,6 +72,7 @@ struct md_system {
   int lj_block = 256, persistent_grid = 0;   // persistent_grid > 0: fixed grid for the LJ kernel
   int lj_lanes = 8;                          // lanes per 4-atom cluster in the LJ kernel
   int lj_region = 3;                         // cells per side (x, y) of an LJ / list region
+  bool lj_pair_exact = false;                // each LJ pair force converted once, +q to i and -q to j
   int* work = nullptr;                       // LJ work counters (persistent schedule)
   int *count = nullptr, *cell_start = nullptr, *cell_of = nullptr;
   int *slot = nullptr, *tmp = nullptr;
@@ -328,6 +329,8 @@ static int configure(md_system* s, const md_desc* d) {
   if (d->lj_region != 0 && d->lj_region != 2 && d->lj_region != 3)
     return fail(s, MD_EINVAL, "lj_region must be 0, 2 or 3");
   s->lj_region = d->lj_region ? d->lj_region : 3;
+  if (d->lj_pair_exact != 0 && d->lj_pair_exact != 1) return fail(s, MD_EINVAL, "lj_pair_exact must be 0 or 1");
+  s->lj_pair_exact = d->lj_pair_exact == 1;
   // default block: two resident blocks of 12 warps for the 3 x 3 regions'
   // larger tiles, three of 8 warps for 2 x 2
   s->lj_block = d->lj_block ? d->lj_block : (s->lj_region == 3 ? 384 : 256);
@@ -504,7 +507,7 @@ static void enqueue_forces(md_system* s, bool energy, void* F_out = nullptr) {
   prof_mark(s);   // closes the integrate group (integrator, displacement check, clear)
   launch_cl_force(energy, s->pos, s->cell_start, s->cl_start, s->regions, (int)s->regions_h.size(), s->shapes,
                   s->reps, s->list, s->ncl, s->cap, s->tile_cap, s->fp, flj, s->Npad, s->lj_part, s->flags,
-                  s->lj_block, s->lj_lanes, s->persistent_grid, s->work, s->st);
+                  s->lj_block, s->lj_lanes, s->persistent_grid, s->work, s->lj_pair_exact, s->st);
   prof_mark(s);
   if (s->generic)
     launch_bonded_generic(energy, (const double*)s->x, s->inv_perm, flj, s->Npad, (int)s->N, s->tiles_int,

@@ -270,7 +270,7 @@ void launch_cl_force(bool energy, const float4* pos, const int* cell_start, cons
                      const Region* regions, int n_regions, const RegionShape* shapes, const RepDev* reps,
                      const unsigned* list, const int* ncl, int cap, int tile_cap, const ForceParams& fp,
                      long long* flj, int Npad, double* epart, unsigned* flags, int block, int lanes,
-                     int persistent_grid, int* work, cudaStream_t st);
+                     int persistent_grid, int* work, bool exact, cudaStream_t st);
 int lj_blocks_per_sm(int block, int lanes, int tile_cap);
 cudaError_t tile_kernels_init();
 int tile_capacity_max();

@@ -61,7 +61,9 @@ def test_workspace_size_without_gpu(lib):
 
 
 @pytest.mark.parametrize("field,value", [("dt", 0.0), ("rc", -1.0), ("rebin_every", 0), ("precision", 7),
-                                         ("thermostat", 3), ("sites_per_chain", 2), ("n_replicas", 0)])
+                                         ("thermostat", 3), ("sites_per_chain", 2), ("n_replicas", 0),
+                                         ("lj_block", 192), ("lj_lanes", 4), ("lj_region", 4), ("lj_pair_exact", 2),
+                                         ("displacement", 5)])
 def test_bad_descriptors_are_rejected(lib, field, value):
     m = chaingen.melt(10, seed=1)
     d, keep = _desc(m, **{field: value})

@@ -14,6 +14,8 @@ Tolerances (stated here, derived from the arithmetic):
   * energies: 1e-5 relative (FP32 terms summed in FP64)
   * short trajectories: 1e-5 nm after 50 steps
 """
+import math
+
 import numpy as np
 import pytest
 from scipy.spatial import cKDTree
@@ -246,6 +248,36 @@ def test_net_force_vanishes():
     q = 2.0 ** -13
     bound = 1e-6 * scale * np.sqrt(n) + 6.0 * q * np.sqrt(40.0 * n / 12.0)
     assert np.abs(f.sum(0)).max() < bound
+    s.close()
+
+
+def test_pairwise_exact_lj_forces_sum_to_zero_and_match_oracle():
+    """With lj_pair_exact every LJ pair force is converted once and added to
+    i and subtracted from j as the same integer, so the LJ forces sum to
+    exactly zero over the system (bonded terms switched off so that the
+    total force is the LJ force), and they still match the FP64 oracle.
+    A relaxed melt: its close 1-4 pairs push forces past 512 kJ/mol/nm, the
+    range of a single-FFMA rounding, so the two-part rounding is exercised."""
+    m, _ = _oracle_relaxed(12, seed=61)
+    p = dict(md.default_params())
+    p.update(kb=0.0, ka=0.0, kphi=0.0)
+    po = oracle.default_params()
+    po.update(kb=0.0, ka=0.0, kphi=0.0)
+    s = md.System(m, precision=md.MD_MIXED, params=p, lj_pair_exact=True)
+    f = s.forces()
+    for a in range(3):
+        assert math.fsum(f[:, a]) == 0.0
+    x, _ = _uploaded(m)
+    f_orc, _, _ = _oracle(m, params=po).forces(x)
+    assert np.max(np.abs(f_orc)) > 512.0   # beyond the range of a single FFMA rounding
+    check_forces(f, f_orc, x, m["L"])
+    # the same system without the option: same forces to FP32 rounding,
+    # and the trajectory runs
+    q = md.System(m, precision=md.MD_MIXED, params=p)
+    g = q.forces()
+    assert np.sqrt(np.sum((f - g) ** 2) / np.sum(g ** 2)) < FORCE_TOL
+    s.step(20)
+    q.close()
     s.close()
 
 
