@@ -111,29 +111,25 @@ __device__ __forceinline__ void region_setup(RegTile& T, const Region& g, const 
   __syncthreads();
 }
 
-// Copy the tile into shared memory in the region frame.  Tile atom t lies
-// in tile cell k with off[k] <= t < off[k + 1] (binary search over the
-// table); every thread starts asynchronous copies (cp.async, global to
-// shared without registers) for atoms t = threadIdx.x + i NT, so the whole
-// tile is in flight at once; after the wait and a barrier, a warp per tile
-// cell adds the cell's frame shift.  The w component keeps the LJ type
+// Copy the tile into shared memory in the region frame.  Warps take tile
+// cells in turn and their lanes start asynchronous copies (cp.async, global
+// to shared without registers) of the cell's atoms, so the whole tile is in
+// flight at once; after the wait and a barrier, a warp per tile cell adds
+// the cell's frame shift.  The w component keeps the LJ type
 // (0.0 / 1.0) that binning and integration store; WITH_TAG (list build)
 // replaces it by the bits of the atom's chain/site tag, which the build
 // needs instead.  tile_issue starts the copies, tile_finish waits for them,
 // shifts, and ends with a barrier.
 template <int NT>
 __device__ __forceinline__ void tile_issue(const RegTile& T, const float4* __restrict__ pos, float4* __restrict__ sp) {
-  const int total = T.off[T.n_tile], nt = T.n_tile;
-  for (int t = threadIdx.x; t < total; t += NT) {
-    int lo = 0, hi = nt - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (T.off[mid] <= t) lo = mid; else hi = mid - 1;
-    }
-    const int j = T.start[lo] + (t - T.off[lo]);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(sp + t)),
-                 "l"(pos + j)
-                 : "memory");
+  const int nt = T.n_tile, lane = threadIdx.x & 31;
+  for (int k = threadIdx.x >> 5; k < nt; k += NT / 32) {
+    const int t0 = T.off[k], n = T.off[k + 1] - t0;
+    const float4* src = pos + T.start[k];
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(sp + t0);
+    for (int q = lane; q < n; q += 32)
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst + 16u * (unsigned)q), "l"(src + q)
+                   : "memory");
   }
   asm volatile("cp.async.commit_group;" ::: "memory");
 }
@@ -565,6 +561,7 @@ template <bool ENERGY, int LP, bool EXACT = false>
 __device__ __forceinline__ void cluster_task(int q0, int nq, const RegTile& T, const float4* __restrict__ sp,
                                              int* __restrict__ ax, int* __restrict__ ay, int* __restrict__ az,
                                              const int* __restrict__ s_ncl, const short* __restrict__ s_ord,
+                                             const int* __restrict__ s_cl, const int* __restrict__ s_in,
                                              float (*__restrict__ ecl)[kEnergyVals], const unsigned* __restrict__ list,
                                              int cap, const RepDev& R, const ForceParams& fp, const LjConst& c,
                                              unsigned* __restrict__ flags) {
@@ -576,10 +573,9 @@ __device__ __forceinline__ void cluster_task(int q0, int nq, const RegTile& T, c
   const float A0 = c.A0 * cs, A1 = c.A1 * cs, A2 = c.A2 * cs, B0 = c.B0 * cs, B1 = c.B1 * cs, B2 = c.B2 * cs;
   const bool valid = q0 + sub < nq;
   const int q = valid ? (int)s_ord[q0 + sub] : nq;
-  int h, k;
-  cluster_of(T, valid ? q : nq - 1, h, k);
-  const int i0 = T.off[h] + 4 * k;
-  const int ni = valid ? min(4, T.off[h + 1] - i0) : 0;
+  const int in = s_in[valid ? q : nq - 1];   // first tile atom << 3 | atoms
+  const int i0 = in >> 3;
+  const int ni = valid ? (in & 7) : 0;
   const int n = valid ? s_ncl[q] : 0;
   int nmax = n;
 #pragma unroll
@@ -619,7 +615,7 @@ __device__ __forceinline__ void cluster_task(int q0, int nq, const RegTile& T, c
 #pragma unroll
     for (int a = 0; a < kEnergyVals; ++a) ev2[a] = make_float2(0.f, 0.f);
   }
-  const unsigned* L = list + (size_t)(valid ? T.cl0[h] + k : 0) * cap;
+  const unsigned* L = list + (size_t)(valid ? s_cl[q] : 0) * cap;
   // clusters without a chain end (the common case) share one pair
   // coefficient per j type: two scalar FMAs per entry instead of four
   // FFMA2 (same values: each coefficient is the same single-rounded FMA)
@@ -855,6 +851,8 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_cl_force(
   __shared__ int sh_r, sh_q;
   __shared__ int s_ncl[kRegionClusterCap];     // list length of each of the region's clusters
   __shared__ short s_ord[kRegionClusterCap];   // the clusters, longest list first (ties: lower index)
+  __shared__ int s_cl[kRegionClusterCap];      // global id of each of the region's clusters
+  __shared__ int s_in[kRegionClusterCap];      // its first tile atom << 3 | its atoms (1..4)
   // energy form: each cluster's 8 sums (FP32 lane tree), added over the
   // region's clusters in cluster order, so the result does not depend on
   // which warp took which cluster
@@ -881,7 +879,10 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_cl_force(
       for (int q = threadIdx.x; q < nq; q += NT) {
         int h, k;
         cluster_of(T, q, h, k);
-        s_ncl[q] = __ldg(ncl + T.cl0[h] + k);
+        const int cl = T.cl0[h] + k, i0 = T.off[h] + 4 * k;
+        s_ncl[q] = __ldg(ncl + cl);
+        s_cl[q] = cl;
+        s_in[q] = (i0 << 3) | min(4, T.off[h + 1] - i0);
       }
       if (threadIdx.x == 0) sh_q = 0;
       tile_finish<false, NT>(T, sp, nullptr);   // ends with a barrier
@@ -893,7 +894,8 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_cl_force(
         if (lane == 0) q0 = atomicAdd(&sh_q, CPW);
         q0 = __shfl_sync(0xffffffffu, q0, 0);
         if (q0 >= nq) break;
-        cluster_task<ENERGY, LP, EXACT>(q0, nq, T, sp, ax, ay, az, s_ncl, s_ord, ecl, list, cap, R, fp, c, flags);
+        cluster_task<ENERGY, LP, EXACT>(q0, nq, T, sp, ax, ay, az, s_ncl, s_ord, s_cl, s_in, ecl, list, cap, R, fp, c,
+                                        flags);
       }
       __syncthreads();
       if (!ENERGY) flush_tile(T, ax, ay, az, flj, Npad, threadIdx.x >> 5, NT / 32);
