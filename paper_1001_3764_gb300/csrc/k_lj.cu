@@ -560,7 +560,7 @@ __device__ __forceinline__ LjConst lj_const(const RepDev& R) {
 template <bool ENERGY, int LP, bool EXACT = false>
 __device__ __forceinline__ void cluster_task(int q0, int nq, const RegTile& T, const float4* __restrict__ sp,
                                              int* __restrict__ ax, int* __restrict__ ay, int* __restrict__ az,
-                                             const int* __restrict__ s_ncl, const short* __restrict__ s_ord,
+                                             const int* __restrict__ s_key, const short* __restrict__ s_ord,
                                              const int* __restrict__ s_cl, const int* __restrict__ s_in,
                                              float (*__restrict__ ecl)[kEnergyVals], const unsigned* __restrict__ list,
                                              int cap, const RepDev& R, const ForceParams& fp, const LjConst& c,
@@ -576,7 +576,7 @@ __device__ __forceinline__ void cluster_task(int q0, int nq, const RegTile& T, c
   const int in = s_in[valid ? q : nq - 1];   // first tile atom << 3 | atoms
   const int i0 = in >> 3;
   const int ni = valid ? (in & 7) : 0;
-  const int n = valid ? s_ncl[q] : 0;
+  const int n = valid ? s_key[q] >> 9 : 0;
   int nmax = n;
 #pragma unroll
   for (int o = LP; o < 32; o <<= 1) nmax = max(nmax, __shfl_xor_sync(0xffffffffu, nmax, o));
@@ -813,15 +813,20 @@ __device__ __forceinline__ void region_energy(const RegTile& T, int nq, bool fit
 }
 
 // longest list first: warps that take the last clusters finish soon, and
-// the clusters that share a warp have similar lengths (threads t0, t0 + nt, ...)
-__device__ __forceinline__ void rank_clusters(const int* __restrict__ s_ncl, short* __restrict__ s_ord, int nq,
+// the clusters that share a warp have similar lengths.  Cluster q's key is
+// (list length << 9) | (511 - q), unique (q < 512) so that ties go to the
+// lower index; its rank is the number of larger keys (threads t0, t0 + nt,
+// ...; four keys per shared load, the slots past nq hold -1).
+__device__ __forceinline__ void rank_clusters(const int* __restrict__ s_key, short* __restrict__ s_ord, int nq,
                                               int t0, int nt) {
+  const int4* k4 = reinterpret_cast<const int4*>(s_key);
+  const int n4 = (nq + 3) >> 2;
   for (int q = t0; q < nq; q += nt) {
-    const int nqv = s_ncl[q];
+    const int kq = s_key[q];
     int rank = 0;
-    for (int o = 0; o < nq; ++o) {
-      const int no = s_ncl[o];
-      rank += (no > nqv) || (no == nqv && o < q);
+    for (int o = 0; o < n4; ++o) {
+      const int4 k = k4[o];
+      rank += (k.x > kq) + (k.y > kq) + (k.z > kq) + (k.w > kq);
     }
     s_ord[rank] = (short)q;
   }
@@ -849,7 +854,7 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_cl_force(
   int* az = ax + 2;
   __shared__ RegTile T;
   __shared__ int sh_r, sh_q;
-  __shared__ int s_ncl[kRegionClusterCap];     // list length of each of the region's clusters
+  __shared__ __align__(16) int s_key[kRegionClusterCap];   // (list length << 9) | (511 - q) of cluster q
   __shared__ short s_ord[kRegionClusterCap];   // the clusters, longest list first (ties: lower index)
   __shared__ int s_cl[kRegionClusterCap];      // global id of each of the region's clusters
   __shared__ int s_in[kRegionClusterCap];      // its first tile atom << 3 | its atoms (1..4)
@@ -874,19 +879,20 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_cl_force(
     } else {
       // list lengths and zeroed accumulators while the tile copies fly
       tile_issue<NT>(T, pos, sp);
-      if (!ENERGY)
-        for (int t = threadIdx.x; t < 3 * total; t += NT) ax[t] = 0;
-      for (int q = threadIdx.x; q < nq; q += NT) {
+      if (!ENERGY)   // 3 tile_cap is a multiple of 4: the rounded-up span stays in the buffer
+        for (int t = threadIdx.x; t < (3 * total + 3) / 4; t += NT) reinterpret_cast<int4*>(ax)[t] = make_int4(0, 0, 0, 0);
+      for (int q = threadIdx.x; q < ((nq + 3) & ~3); q += NT) {
+        if (q >= nq) { s_key[q] = -1; continue; }
         int h, k;
         cluster_of(T, q, h, k);
         const int cl = T.cl0[h] + k, i0 = T.off[h] + 4 * k;
-        s_ncl[q] = __ldg(ncl + cl);
+        s_key[q] = (__ldg(ncl + cl) << 9) | (511 - q);
         s_cl[q] = cl;
         s_in[q] = (i0 << 3) | min(4, T.off[h + 1] - i0);
       }
       if (threadIdx.x == 0) sh_q = 0;
       tile_finish<false, NT>(T, sp, nullptr);   // ends with a barrier
-      rank_clusters(s_ncl, s_ord, nq, threadIdx.x, NT);
+      rank_clusters(s_key, s_ord, nq, threadIdx.x, NT);
       __syncthreads();
       const LjConst c = lj_const(R);
       for (;;) {
@@ -894,7 +900,7 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_cl_force(
         if (lane == 0) q0 = atomicAdd(&sh_q, CPW);
         q0 = __shfl_sync(0xffffffffu, q0, 0);
         if (q0 >= nq) break;
-        cluster_task<ENERGY, LP, EXACT>(q0, nq, T, sp, ax, ay, az, s_ncl, s_ord, s_cl, s_in, ecl, list, cap, R, fp, c,
+        cluster_task<ENERGY, LP, EXACT>(q0, nq, T, sp, ax, ay, az, s_key, s_ord, s_cl, s_in, ecl, list, cap, R, fp, c,
                                         flags);
       }
       __syncthreads();
