@@ -733,15 +733,19 @@ __device__ __forceinline__ void cluster_task(int q0, int nq, const RegTile& T, c
       for (int a = 0; a < 3; ++a)
 #pragma unroll
         for (int o = LP / 2; o > 0; o >>= 1) fi[u][a] += __shfl_xor_sync(0xffffffffu, fi[u][a], o);
+    // every lane holds the four atoms' sums: lane u < ni adds atom u's (one
+    // path for the lanes instead of four divergent ones)
+    float gx = fi[0][0], gy = fi[0][1], gz = fi[0][2];
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
-      if (sl == u && u < ni) {
-        const float sx = fi[u][0] * scale, sy = fi[u][1] * scale, sz = fi[u][2] * scale;
-        range_check(sx, sy, sz, flags);
-        atomicAdd(ax + 3 * (i0 + u), acc_fix(sx));
-        atomicAdd(ay + 3 * (i0 + u), acc_fix(sy));
-        atomicAdd(az + 3 * (i0 + u), acc_fix(sz));
-      }
+    for (int u = 1; u < 4; ++u)
+      if (sl == u) { gx = fi[u][0]; gy = fi[u][1]; gz = fi[u][2]; }
+    if (sl < ni) {
+      const float sx = gx * scale, sy = gy * scale, sz = gz * scale;
+      range_check(sx, sy, sz, flags);
+      atomicAdd(ax + 3 * (i0 + sl), acc_fix(sx));
+      atomicAdd(ay + 3 * (i0 + sl), acc_fix(sy));
+      atomicAdd(az + 3 * (i0 + sl), acc_fix(sz));
+    }
   }
   if constexpr (EXACT && !ENERGY) {
     // each lane added one offset per entry slot it processed (two per
@@ -758,13 +762,15 @@ __device__ __forceinline__ void cluster_task(int q0, int nq, const RegTile& T, c
         for (int o = LP / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         qi[u][a] = v;
       }
+    unsigned vx = qi[0][0], vy = qi[0][1], vz = qi[0][2];
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
-      if (sl == u && u < ni) {
-        atomicAdd(ax + 3 * (i0 + u), (int)qi[u][0]);
-        atomicAdd(ay + 3 * (i0 + u), (int)qi[u][1]);
-        atomicAdd(az + 3 * (i0 + u), (int)qi[u][2]);
-      }
+    for (int u = 1; u < 4; ++u)
+      if (sl == u) { vx = qi[u][0]; vy = qi[u][1]; vz = qi[u][2]; }
+    if (sl < ni) {
+      atomicAdd(ax + 3 * (i0 + sl), (int)vx);
+      atomicAdd(ay + 3 * (i0 + sl), (int)vy);
+      atomicAdd(az + 3 * (i0 + sl), (int)vz);
+    }
   }
   if (ENERGY) {
 #pragma unroll
