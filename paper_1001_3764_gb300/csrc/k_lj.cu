@@ -565,6 +565,7 @@ __device__ __forceinline__ void cluster_task(int q0, int nq, const RegTile& T, c
                                              float (*__restrict__ ecl)[kEnergyVals], const unsigned* __restrict__ list,
                                              int cap, const RepDev& R, const ForceParams& fp, const LjConst& c,
                                              unsigned* __restrict__ flags) {
+  static_assert(LP == 8 || LP == 16 || LP == 32, "lanes per cluster: 8, 16 or 32");
   const int lane = threadIdx.x & 31, sub = lane / LP, sl = lane % LP;
   const float rc2 = c.rc2, scale = c.scale, lim = c.lim;
   // EXACT: the coefficients carry the accumulator scale (pair forces in
@@ -725,26 +726,42 @@ __device__ __forceinline__ void cluster_task(int q0, int nq, const RegTile& T, c
       fi[2 * p][2] = qz[p].x; fi[2 * p + 1][2] = qz[p].y;
     }
   }
-  // forces on the cluster's atoms: fixed butterfly over the LP lanes
+  // forces on the cluster's atoms: a fixed xor tree over the LP lanes
+  // (offsets LP/2, ..., 2, 1).  The offsets above 4 add all twelve sums;
+  // at 4 and 2 each lane keeps half of the atoms it still holds and receives
+  // the partner's part of them, so that after offset 1 lanes 2u and 2u + 1
+  // hold atom u.  Every sum is formed by the same tree of additions as a
+  // full butterfly (the same bits), with half the shuffles.
   if (!ENERGY && !EXACT) {
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
+    for (int o = LP / 2; o > 4; o >>= 1)
 #pragma unroll
-      for (int a = 0; a < 3; ++a)
+      for (int u = 0; u < 4; ++u)
 #pragma unroll
-        for (int o = LP / 2; o > 0; o >>= 1) fi[u][a] += __shfl_xor_sync(0xffffffffu, fi[u][a], o);
-    // every lane holds the four atoms' sums: lane u < ni adds atom u's (one
-    // path for the lanes instead of four divergent ones)
-    float gx = fi[0][0], gy = fi[0][1], gz = fi[0][2];
+        for (int a = 0; a < 3; ++a) fi[u][a] += __shfl_xor_sync(0xffffffffu, fi[u][a], o);
+    const bool hi = (sl & 4) != 0, mid = (sl & 2) != 0;
+    float r1[2][3];   // atoms 2 hi + j
 #pragma unroll
-    for (int u = 1; u < 4; ++u)
-      if (sl == u) { gx = fi[u][0]; gy = fi[u][1]; gz = fi[u][2]; }
-    if (sl < ni) {
-      const float sx = gx * scale, sy = gy * scale, sz = gz * scale;
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const float keep = hi ? fi[2 + j][a] : fi[j][a], send = hi ? fi[j][a] : fi[2 + j][a];
+        r1[j][a] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+      }
+    float g[3];       // atom 2 hi + mid
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const float keep = mid ? r1[1][a] : r1[0][a], send = mid ? r1[0][a] : r1[1][a];
+      g[a] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+      g[a] += __shfl_xor_sync(0xffffffffu, g[a], 1);
+    }
+    const int u = sl >> 1;
+    if ((sl & 1) == 0 && u < ni) {
+      const float sx = g[0] * scale, sy = g[1] * scale, sz = g[2] * scale;
       range_check(sx, sy, sz, flags);
-      atomicAdd(ax + 3 * (i0 + sl), acc_fix(sx));
-      atomicAdd(ay + 3 * (i0 + sl), acc_fix(sy));
-      atomicAdd(az + 3 * (i0 + sl), acc_fix(sz));
+      atomicAdd(ax + 3 * (i0 + u), acc_fix(sx));
+      atomicAdd(ay + 3 * (i0 + u), acc_fix(sy));
+      atomicAdd(az + 3 * (i0 + u), acc_fix(sz));
     }
   }
   if constexpr (EXACT && !ENERGY) {
