@@ -26,7 +26,7 @@
 // evaluates list entries against its cluster's four atoms i (r2inv = 0
 // beyond r_c, as in the Sec. 3.2 listing).  The force on i is
 // summed in FP32 registers in list order and reduced over the lanes by a
-// fixed butterfly; the force on j of one entry (at most four pairs, summed in
+// fixed xor tree; the force on j of one entry (at most four pairs, summed in
 // FP32) is converted once to 2^-13 kJ/mol/nm fixed point and added to the
 // tile's int32 accumulators in shared memory; at the end each tile atom's
 // accumulator is added to the int64 force (2^-32 kJ/mol/nm) with one
@@ -383,6 +383,9 @@ __device__ __forceinline__ void range_check(float sx, float sy, float sz, unsign
   else if (!(a < 1073741824.0f)) atomicOr(flags, kFlagFixOverflow);
 }
 
+constexpr float kMagic = 12582912.0f;   // 1.5 2^23: FP32 spacing 1 in [2^23, 2^24)
+constexpr unsigned kMagicBits = 0x4B400000u;
+
 // Add the force g (cell units) on tile atom t to the 2^-13 accumulators.
 // While |g| scale < 2^22 (|g| < 512 kJ/mol/nm, the usual case) the
 // conversion is one FFMA: g scale + 1.5 2^23 lies in [2^23, 2^24), where
@@ -393,12 +396,10 @@ __device__ __forceinline__ void range_check(float sx, float sy, float sz, unsign
 __device__ __forceinline__ void acc_add(int* __restrict__ ax, int* __restrict__ ay, int* __restrict__ az, int t,
                                         float gx, float gy, float gz, float scale, float lim,
                                         unsigned* __restrict__ flags) {
-  constexpr float kMagicF = 12582912.0f;   // 1.5 2^23
-  constexpr int kMagicI = 0x4B400000;
   if (fabsf(gx) + fabsf(gy) + fabsf(gz) < lim) {
-    atomicAdd(ax + 3 * t, __float_as_int(fmaf(gx, scale, kMagicF)) - kMagicI);
-    atomicAdd(ay + 3 * t, __float_as_int(fmaf(gy, scale, kMagicF)) - kMagicI);
-    atomicAdd(az + 3 * t, __float_as_int(fmaf(gz, scale, kMagicF)) - kMagicI);
+    atomicAdd(ax + 3 * t, __float_as_int(fmaf(gx, scale, kMagic)) - (int)kMagicBits);
+    atomicAdd(ay + 3 * t, __float_as_int(fmaf(gy, scale, kMagic)) - (int)kMagicBits);
+    atomicAdd(az + 3 * t, __float_as_int(fmaf(gz, scale, kMagic)) - (int)kMagicBits);
   } else {
     gx *= scale; gy *= scale; gz *= scale;
     range_check(gx, gy, gz, flags);
@@ -458,8 +459,6 @@ __device__ __forceinline__ void entry_packed(const float2 (&px)[2], const float2
 // which the caller removes by counting.  |v| >= 2^30 (2^17 kJ/mol/nm, the
 // range checked by the default path) or a non-finite v leaves t outside
 // [2^23, 2^24) and sets bit 23 or above of `chk`.
-constexpr float kMagic = 12582912.0f;   // 1.5 2^23
-constexpr unsigned kMagicBits = 0x4B400000u;
 constexpr unsigned kExactOff = (kMagicBits << 8) + kMagicBits;
 __device__ __forceinline__ void exact_round(float2 v, unsigned& b0, unsigned& b1, unsigned& chk) {
   const float2 mg = make_float2(kMagic, kMagic), nmg = make_float2(-kMagic, -kMagic);
