@@ -573,13 +573,12 @@ __device__ __forceinline__ void cluster_task(int q0, int nq, const RegTile& T, c
   const float A0 = c.A0 * cs, A1 = c.A1 * cs, A2 = c.A2 * cs, B0 = c.B0 * cs, B1 = c.B1 * cs, B2 = c.B2 * cs;
   const bool valid = q0 + sub < nq;
   const int q = valid ? (int)s_ord[q0 + sub] : nq;
-  const int in = s_in[valid ? q : nq - 1];   // first tile atom << 3 | atoms
-  const int i0 = in >> 3;
+  const int in = s_in[valid ? q : nq - 1];   // first tile atom << 7 | chain-end bits << 3 | atoms
+  const int i0 = in >> 7;
   const int ni = valid ? (in & 7) : 0;
   const int n = valid ? s_key[q] >> 9 : 0;
-  int nmax = n;
-#pragma unroll
-  for (int o = LP; o < 32; o <<= 1) nmax = max(nmax, __shfl_xor_sync(0xffffffffu, nmax, o));
+  // the task's clusters are consecutive in longest-first order: the first is the longest
+  const int nmax = s_key[s_ord[q0]] >> 9;
   float4 pi[4];   // w: LJ type (1.0 for a C_33 chain end)
 #pragma unroll
   for (int u = 0; u < 4; ++u) pi[u] = sp[i0 + max(0, min(u, ni - 1))];
@@ -619,14 +618,8 @@ __device__ __forceinline__ void cluster_task(int q0, int nq, const RegTile& T, c
   // clusters without a chain end (the common case) share one pair
   // coefficient per j type: two scalar FMAs per entry instead of four
   // FFMA2 (same values: each coefficient is the same single-rounded FMA)
-  bool uni_c = true;
-  unsigned tb = 0u;   // bit u: atom u is a C_33 chain end
-#pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    uni_c &= pi[u].w == 0.f;
-    tb |= pi[u].w != 0.f ? (1u << u) : 0u;
-  }
-  const bool uni = __all_sync(0xffffffffu, uni_c);
+  const unsigned tb = ((unsigned)in >> 3) & 15u;   // bit u: atom u is a C_33 chain end
+  const bool uni = __all_sync(0xffffffffu, tb == 0u);
   // two entries per lane per iteration (independent work for the
   // scheduler), the next two in flight; an entry past the list is 0:
   // tile atom 0 with an empty mask, which adds nothing
@@ -838,9 +831,12 @@ __device__ __forceinline__ void region_energy(const RegTile& T, int nq, bool fit
 // the clusters that share a warp have similar lengths.  Cluster q's key is
 // (list length << 9) | (511 - q), unique (q < 512) so that ties go to the
 // lower index; its rank is the number of larger keys (threads t0, t0 + nt,
-// ...; four keys per shared load, the slots past nq hold -1).
-__device__ __forceinline__ void rank_clusters(const int* __restrict__ s_key, short* __restrict__ s_ord, int nq,
-                                              int t0, int nt) {
+// ...; four keys per shared load, the slots past nq hold -1).  The same
+// thread records in s_in which of the cluster's four slots hold a C_33
+// chain end (bit u; a slot past the cell's last atom repeats that atom).
+__device__ __forceinline__ void rank_clusters(const int* __restrict__ s_key, short* __restrict__ s_ord,
+                                              int* __restrict__ s_in, const float4* __restrict__ sp, int nq, int t0,
+                                              int nt) {
   const int4* k4 = reinterpret_cast<const int4*>(s_key);
   const int n4 = (nq + 3) >> 2;
   for (int q = t0; q < nq; q += nt) {
@@ -851,6 +847,11 @@ __device__ __forceinline__ void rank_clusters(const int* __restrict__ s_key, sho
       rank += (k.x > kq) + (k.y > kq) + (k.z > kq) + (k.w > kq);
     }
     s_ord[rank] = (short)q;
+    const int in = s_in[q], i0 = in >> 7, ni = in & 7;
+    unsigned tb = 0u;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) tb |= sp[i0 + min(u, ni - 1)].w != 0.f ? (1u << u) : 0u;
+    s_in[q] = in | (int)(tb << 3);
   }
 }
 
@@ -879,7 +880,7 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_cl_force(
   __shared__ __align__(16) int s_key[kRegionClusterCap];   // (list length << 9) | (511 - q) of cluster q
   __shared__ short s_ord[kRegionClusterCap];   // the clusters, longest list first (ties: lower index)
   __shared__ int s_cl[kRegionClusterCap];      // global id of each of the region's clusters
-  __shared__ int s_in[kRegionClusterCap];      // its first tile atom << 3 | its atoms (1..4)
+  __shared__ int s_in[kRegionClusterCap];      // first tile atom << 7 | chain-end bits << 3 | atoms (1..4)
   // energy form: each cluster's 8 sums (FP32 lane tree), added over the
   // region's clusters in cluster order, so the result does not depend on
   // which warp took which cluster
@@ -910,11 +911,11 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_cl_force(
         const int cl = T.cl0[h] + k, i0 = T.off[h] + 4 * k;
         s_key[q] = (__ldg(ncl + cl) << 9) | (511 - q);
         s_cl[q] = cl;
-        s_in[q] = (i0 << 3) | min(4, T.off[h + 1] - i0);
+        s_in[q] = (i0 << 7) | min(4, T.off[h + 1] - i0);
       }
       if (threadIdx.x == 0) sh_q = 0;
       tile_finish<false, NT>(T, sp, nullptr);   // ends with a barrier
-      rank_clusters(s_key, s_ord, nq, threadIdx.x, NT);
+      rank_clusters(s_key, s_ord, s_in, sp, nq, threadIdx.x, NT);
       __syncthreads();
       const LjConst c = lj_const(R);
       for (;;) {
