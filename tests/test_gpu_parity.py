@@ -685,6 +685,25 @@ def test_schedules_and_block_shapes_agree():
     assert np.abs(x3 - x2).max() < 1e-6
 
 
+@pytest.mark.parametrize("lanes", [16, 32])
+def test_lanes_per_cluster_give_the_oracle_forces(lanes):
+    """16 or 32 lanes per cluster split a cluster's list into other partial
+    sums (FP32 rounding apart from 8 lanes) and reduce them over more levels
+    of the lane tree: forces against the oracle, and a 12-step trajectory
+    within 1e-6 nm of the 8-lane one."""
+    m = chaingen.melt(30, seed=23)
+    x, _ = _uploaded(m)
+    f_orc = _oracle(m).forces(x)[0]
+    s = md.System(m, precision=md.MD_MIXED, rebin_every=4, lj_lanes=lanes)
+    r = md.System(m, precision=md.MD_MIXED, rebin_every=4, lj_lanes=8)
+    check_forces(s.forces(), f_orc, x, m["L"])
+    s.step(12)
+    r.step(12)
+    assert np.abs(s.state()[0] - r.state()[0]).max() < 1e-6
+    s.close()
+    r.close()
+
+
 def test_autotune_picks_a_working_setting_and_caches_it(tmp_path):
     m = chaingen.melt(20, seed=29)
     cache = str(tmp_path / "tune.txt")
