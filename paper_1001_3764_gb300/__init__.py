@@ -386,7 +386,11 @@ class System:
     `melts` is a dict or a list of dicts with keys pos (N,3), vel (N,3), L,
     n_chains, sites (the chaingen format).  Device memory is a torch uint8
     tensor handed to the library as its workspace; the library runs on a
-    torch stream (`self.stream`).
+    torch stream (`self.stream`).  The keyword arguments are the md_desc
+    fields of include/md.h (lj_region, lj_block, lj_lanes and schedule shape
+    the LJ kernel; lj_pair_exact=True rounds every LJ pair force once so that
+    the LJ forces sum to exactly zero; displacement picks the policy for an
+    atom that moved more than skin/2 between list builds).
     """
 
     def __init__(self, melts, precision: int = MD_MIXED, dt: float = 0.001, rc: float = 1.0,
